@@ -1,0 +1,172 @@
+/*
+ * vbarms.h -- C ABI of the GB300 (sm_103a) VBARMS library.
+ *
+ * VBARMS ("Using the VBARMS method in parallel computing", Carpentieri, Liao,
+ * Sosonkina, Bonfiglioli, arXiv 1508.02219) is a variable-block multilevel
+ * incomplete LU preconditioner.  This library implements its data-parallel
+ * path on one GPU:
+ *   Step 1   angle-based row-pattern compression and block permutation
+ *            (Section 2.1, Eq. 3)                        -> vbarms_compress
+ *   Steps 2-4 scaling, block independent-set ordering and the two-sweep block
+ *            partial factorization, repeated per level, with the last level
+ *            factored by block ILUT (Section 3, Eq. 4-8, Alg. 3, Section 3.1)
+ *                                                        -> vbarms_factor
+ *   Alg. 2   the multilevel forward/backward solve       -> vbarms_apply
+ *   FGMRES   flexible GMRES(m) with the preconditioner   -> fgmres_solve
+ *
+ * Conventions (every entry point):
+ *  - Return a vb_status; never abort, never trap the GPU.  On error the
+ *    output handles/arrays are left untouched and vbarms_last_error() returns
+ *    a message (thread-local).
+ *  - Indices are 0-based.  CSR columns must be ascending and unique.
+ *  - Handles are library-owned and freed by the matching *_destroy.
+ *  - Device work is enqueued on the stream given at creation (a cudaStream_t
+ *    passed as void*, NULL = the legacy default stream).  Calls that return
+ *    sizes or statuses synchronize that stream.
+ *  - Vectors given to vbarms_apply / fgmres_solve are caller-owned device
+ *    arrays of doubles in the ORIGINAL (unpermuted) numbering.
+ *
+ * Internal scratch and factors live in device memory obtained with
+ * cudaMallocAsync on the handle's stream.
+ */
+#ifndef VBARMS_H
+#define VBARMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VB_OK = 0,
+  VB_EINVAL = 1,     /* invalid argument or malformed CSR                     */
+  VB_ENOMEM = 2,     /* device allocation failed                              */
+  VB_ECUDA = 3,      /* a CUDA runtime call failed                            */
+  VB_ESINGULAR = 4,  /* an exactly singular pivot block (GEPP found a 0 pivot)*/
+  VB_ETIMEOUT = 5,   /* a bounded device wait ran out (wait_limit)            */
+  VB_ENOCONV = 6,    /* FGMRES reached maxit without meeting rtol             */
+  VB_EINTERNAL = 7   /* an internal consistency check failed                  */
+} vb_status;
+
+typedef struct vbarms_vbsr_st* vbarms_vbsr; /* VBCSR matrix P_B A P_B^T + P_B */
+typedef struct vbarms_prec_st* vbarms_prec; /* multilevel VBARMS factorization */
+
+enum { VB_FP64 = 0, VB_FP32_MIXED = 1 };
+
+typedef struct {
+  /* VB_FP64: every factor in FP64.  VB_FP32_MIXED: W, G, Schur complements and
+   * last-level factors stored and computed in FP32 (FP32 accumulation); pivot
+   * blocks whose 1-norm condition estimate exceeds fp64_pivot_cond keep FP64
+   * LU factors and are applied in FP64.                                      */
+  int precision;
+  double fp64_pivot_cond; /* default 1e4                                     */
+  double ddtol;           /* Step 3: supernodes with weight < ddtol go to C
+                             (default 0 = off)                               */
+  uint64_t wait_limit;    /* spin iterations of a bounded device wait before
+                             VB_ETIMEOUT (0 = default, about 1 s)            */
+} vbarms_opts;
+
+/* Fill *opt with the defaults above. */
+void vbarms_opts_default(vbarms_opts* opt);
+
+/* Step 1 (Section 2.1, Eq. 3).  Angle-based compression of an n x n CSR
+ * matrix: rows i < j with |P_i n P_j| / sqrt(|P_i| |P_j|) >= tau are grouped
+ * greedily in natural order (a still-unassigned row becomes a leader and
+ * claims every later unassigned row similar to it); groups are ordered by
+ * leader, members ascending.  The result holds P_B, the block sizes and
+ * P_B A P_B^T as a VBCSR matrix whose blocks are dense and zero padded.
+ *   n        number of rows/columns (n >= 0)
+ *   rowptr   int64[n+1], colind int32[nnz], val double[nnz]; host arrays when
+ *            on_device == 0, device arrays when on_device != 0.  Borrowed for
+ *            the duration of the call (copied).
+ *   tau      similarity threshold, 0 < tau <= 1 (1 = exact dense blocks)
+ *   stream   cudaStream_t for all work of the returned handle (NULL: default)
+ * Errors: VB_EINVAL for tau out of range or a malformed CSR (rowptr not
+ * monotone, column out of range, unsorted or duplicate columns).           */
+vb_status vbarms_compress(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                          const double* val, int on_device, double tau, void* stream,
+                          vbarms_vbsr* out);
+
+/* Build a VBCSR handle directly from host block arrays (square partition,
+ * P_B = identity).  bsz int32[nblk]; bptr int64[nblk+1]; bcol int32[nnzb]
+ * ascending per row; voff int64[nnzb+1] with voff[b+1]-voff[b] =
+ * bsz[row]*bsz[bcol[b]]; val double[voff[nnzb]] row-major blocks.          */
+vb_status vbarms_vbsr_from_blocks(int64_t nblk, const int32_t* bsz, const int64_t* bptr,
+                                  const int32_t* bcol, const int64_t* voff, const double* val,
+                                  void* stream, vbarms_vbsr* out);
+
+/* Sizes and the quality measures of Section 2: av_bd = nnz(A) / sum of the
+ * sizes of the stored blocks, av_bs = n / number of diagonal blocks.       */
+vb_status vbarms_vbsr_query(vbarms_vbsr A, int64_t* n, int64_t* nblk, int64_t* nnzb,
+                            int64_t* nval, double* av_bd, double* av_bs);
+
+/* Copy P_B and the block structure to host arrays (any pointer may be NULL):
+ * perm int32[n] (perm[k] = original row at permuted position k), bsz
+ * int32[nblk], bptr int64[nblk+1], bcol int32[nnzb], voff int64[nnzb+1],
+ * val double[nval].                                                        */
+vb_status vbarms_vbsr_export(vbarms_vbsr A, int32_t* perm, int32_t* bsz, int64_t* bptr,
+                             int32_t* bcol, int64_t* voff, double* val);
+
+/* Steps 2-4 of Section 3 repeated nlev times (Eq. 7-8), then block ILUT of
+ * the last Schur complement (Section 3 dropping rule, Alg. 3 in block form).
+ * Per level: two-sided max-abs scaling; weighted greedy block independent set
+ * on the quotient graph of A + A^T (weight ||A_YY||_F / sum_Z ||A_YZ||_F,
+ * visited by weight descending, index ascending; one supernode per group);
+ * GEPP of every pivot block; W = L^{-1} P F and G = E U^{-1} with dropping;
+ * S = C - G W (exact except at the last reduction).  A block B (m x n) is
+ * dropped iff ||B||_F < droptol * m * n; lfil >= 0 keeps at most lfil blocks
+ * (largest norm, lower column on ties) per block row of W, G, L_S, U_S;
+ * lfil < 0 keeps all.  Levels stop early when nothing is left to eliminate.
+ * opt may be NULL (defaults).  Errors: VB_EINVAL (nlev < 0, droptol < 0),
+ * VB_ESINGULAR (a pivot block is exactly singular), VB_ENOMEM.             */
+vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil,
+                        const vbarms_opts* opt, vbarms_prec* out);
+
+/* y = M^{-1} x (Alg. 2).  x, y: device double[n], original numbering, must
+ * not alias.  Runs on the stream of the matrix the handle was built from.   */
+vb_status vbarms_apply(vbarms_prec M, const double* x, double* y);
+
+/* Right-preconditioned flexible GMRES(restart) on A x = b (FP64 Arnoldi with
+ * modified Gram-Schmidt, Givens rotations, true residual at every restart).
+ * M may be NULL (no preconditioner).  b, x: device double[n] in the original
+ * numbering; x holds the initial guess on entry and the solution on exit.
+ * Stops when ||b - A x||_2 <= rtol ||b||_2.  *iters = total inner steps,
+ * *relres = final true relative residual.  VB_ENOCONV when maxit is reached
+ * (x, iters and relres are still set).                                      */
+vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x, double rtol,
+                       int restart, int maxit, int* iters, double* relres);
+
+/* Statistics of a factorization: levels performed, the memory ratio
+ * (stored factor scalars / nnz(A)) and wall seconds of the setup phases
+ * (phase_s[0..7]: scale, ordering, gather, pivot LU, W, G, Schur, last-level
+ * ILUT; any pointer may be NULL).                                           */
+vb_status vbarms_prec_stats(vbarms_prec M, int* levels_used, double* mem_ratio, double* phase_s);
+
+/* Export one factor of level lev (0 <= lev < levels: which = 0 scaled level
+ * matrix, 1 pivot LU blocks, 2 F, 3 E, 4 C, 5 W, 6 G, 7 S; lev == levels:
+ * which = 0 scaled last-level matrix, 1 pivot LU blocks, 8 L_S, 9 U_S) as
+ * host VBCSR arrays with values converted to double.  Call once with the
+ * array pointers NULL to get the sizes.                                     */
+vb_status vbarms_prec_export(vbarms_prec M, int lev, int which, int64_t* nbr, int64_t* nbc,
+                             int64_t* nnzb, int64_t* nval, int32_t* rsz, int32_t* csz,
+                             int64_t* bptr, int32_t* bcol, int64_t* voff, double* val);
+
+/* Export a per-level vector: which = 0 row scaling r, 1 column scaling c,
+ * 2 Step 3 weights w (doubles, into d); 3 the ordering P_I (D supernodes
+ * ascending then C supernodes ascending), 4 GEPP pivots, 5 pivot precision
+ * tags (1 = FP64 kept) (int32, into iv).  *len receives the length; pass
+ * NULL arrays to query it.                                                  */
+vb_status vbarms_prec_vector(vbarms_prec M, int lev, int which, double* d, int32_t* iv, int64_t* len);
+
+void vbarms_vbsr_destroy(vbarms_vbsr A);
+void vbarms_prec_destroy(vbarms_prec M);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* vbarms_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBARMS_H */

@@ -1,0 +1,457 @@
+// The C ABI of the library (include/vbarms.h): handles, the multilevel
+// factorization driver (Steps 2-4 per level, Eq. 7-8, last-level ILUT) and
+// the FGMRES outer loop.
+#include <chrono>
+#include <cmath>
+#include <memory>
+
+#include "prec.cuh"
+#include "vbsr_ops.cuh"
+
+using namespace vb;
+
+struct vbarms_vbsr_st {
+  cudaStream_t s = nullptr;
+  Compressed C;
+  DBuf<int> status;
+  DBuf<int64_t> rowblk;  // scalar row -> block row, for the SpMV
+};
+
+struct vbarms_prec_st {
+  std::unique_ptr<PrecBase> impl;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+vb_status set_err(vb_status st, const std::string& m) {
+  g_err = m;
+  return st;
+}
+
+template <typename F>
+vb_status guarded(F&& f) {
+  try {
+    f();
+    g_err.clear();
+    return VB_OK;
+  } catch (const Error& e) {
+    return set_err(e.st, e.msg);
+  } catch (const std::bad_alloc&) {
+    return set_err(VB_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return set_err(VB_EINTERNAL, e.what());
+  }
+}
+
+struct PhaseTimer {
+  cudaStream_t s;
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  explicit PhaseTimer(cudaStream_t st) : s(st) {}
+  void mark(int phase_ending) {
+    cudaEvent_t e;
+    VB_CUDA(cudaEventCreate(&e));
+    VB_CUDA(cudaEventRecord(e, s));
+    marks.push_back({phase_ending, e});
+  }
+  void accumulate(double* out) {
+    VB_CUDA(cudaStreamSynchronize(s));
+    for (size_t i = 1; i < marks.size(); ++i) {
+      float ms = 0;
+      VB_CUDA(cudaEventElapsedTime(&ms, marks[i - 1].second, marks[i].second));
+      if (marks[i].first >= 0) out[marks[i].first] += ms * 1e-3;
+    }
+  }
+  ~PhaseTimer() {
+    for (auto& m : marks) cudaEventDestroy(m.second);
+  }
+};
+
+template <typename T>
+std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts& o) {
+  auto P = std::make_unique<PrecDev<T>>();
+  cudaStream_t s = Ah.s;
+  P->s = s;
+  P->n = Ah.C.n;
+  P->precision = o.precision;
+  P->wait_limit = o.wait_limit;
+  P->status.alloc(1, s);
+  P->status.zero();
+  int* dst = P->status.p;
+  P->perm.alloc(Ah.C.n, s);
+  if (Ah.C.n)
+    VB_CUDA(cudaMemcpyAsync(P->perm.p, Ah.C.perm.p, Ah.C.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  const bool mixed = o.precision == VB_FP32_MIXED;
+  PhaseTimer tm(s);
+  tm.mark(-1);
+  // current level input: FP64 (the compressed matrix) or T (a Schur complement)
+  const VBDev<double>* cur64 = &Ah.C.A;
+  VBDev<T> curT;
+  bool cur_is64 = true;
+  double fill = 0;
+  for (int l = 0; l < o.nlev; ++l) {
+    const int64_t p = cur_is64 ? cur64->nbr : curT.nbr;
+    if (p == 0) break;
+    LevelDev<T> L;
+    DBuf<int32_t> newpos;
+    int64_t nD = 0;
+    if (cur_is64) {
+      copy_vb<double, double>(*cur64, L.A64, s);
+      scale_level_t<double>(L.A64, L.r, L.c, s);
+      tm.mark(PH_SCALE);
+      nD = is_order<double>(L.A64, o.ddtol, L.w, L.pI, newpos, s);
+      tm.mark(PH_ORDER);
+      if (nD == 0) break;
+      gather_parts<double, T>(L.A64, L.pI, newpos, nD, L, s, dst);
+    } else {
+      copy_vb<T, T>(curT, L.AT, s);
+      scale_level_t<T>(L.AT, L.r, L.c, s);
+      tm.mark(PH_SCALE);
+      nD = is_order<T>(L.AT, o.ddtol, L.w, L.pI, newpos, s);
+      tm.mark(PH_ORDER);
+      if (nD == 0) break;
+      gather_parts<T, T>(L.AT, L.pI, newpos, nD, L, s, dst);
+    }
+    tm.mark(PH_GATHER);
+    pivot_lu(L.D, L.piv, L.ptag, L.D32, mixed, o.fp64_pivot_cond, s, dst);
+    tm.mark(PH_PIVOT);
+    w_or_g<T>(L.F, 0, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.W, s);
+    tm.mark(PH_W);
+    w_or_g<T>(L.E, 1, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.G, s);
+    tm.mark(PH_G);
+    schur<T>(L.C, L.G, L.W, l == o.nlev - 1, o.droptol, L.S, s, dst);
+    tm.mark(PH_SCHUR);
+    fill += (double)(L.D.nval + L.W.nval + L.G.nval);
+    LevelMaps M;
+    if (cur_is64)
+      build_level_maps<T>(L, L.A64.rsz.p, L.A64.roff.p, L.A64.nbr, M, s);
+    else
+      build_level_maps<T>(L, L.AT.rsz.p, L.AT.roff.p, L.AT.nbr, M, s);
+    // the next level starts from S; F, E, C are no longer needed by the solve
+    copy_vb<T, T>(L.S, curT, s);
+    cur_is64 = false;
+    P->maps.push_back(std::move(M));
+    P->lev.push_back(std::move(L));
+    tm.mark(-1);
+  }
+  // last level: scale, then block ILUT
+  LastDev<T>& X = P->last;
+  if (cur_is64)
+    copy_vb<T, double>(*cur64, X.A, s);
+  else
+    X.A = std::move(curT);
+  scale_level_t<T>(X.A, X.r, X.c, s);
+  ilut_last<T>(X, o.droptol, o.lfil, mixed, o.fp64_pivot_cond, o.wait_limit, s, dst);
+  tm.mark(PH_ILUT);
+  fill += (double)(X.Dg.nval + X.L.nval + X.U.nval);
+  tm.accumulate(P->phase_s);
+  P->mem_ratio = Ah.C.nnz ? fill / (double)Ah.C.nnz : 0.0;
+  return P;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void vbarms_opts_default(vbarms_opts* opt) {
+  if (!opt) return;
+  opt->precision = VB_FP64;
+  opt->fp64_pivot_cond = 1e4;
+  opt->ddtol = 0.0;
+  opt->wait_limit = 0;
+}
+
+const char* vbarms_last_error(void) { return g_err.c_str(); }
+
+vb_status vbarms_compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, int on_device,
+                          double tau, void* stream, vbarms_vbsr* out) {
+  if (!out) return set_err(VB_EINVAL, "out is NULL");
+  if (n < 0 || !(tau > 0.0 && tau <= 1.0)) return set_err(VB_EINVAL, "n < 0 or tau outside (0, 1]");
+  if (n > 0 && !rowptr) return set_err(VB_EINVAL, "rowptr is NULL");
+  if (n > 0 && !on_device && rowptr[n] > 0 && (!colind || !val)) return set_err(VB_EINVAL, "colind/val NULL");
+  if (n > 0 && on_device && (!colind || !val)) return set_err(VB_EINVAL, "colind/val NULL");
+  if (n >= (int64_t)1 << 31) return set_err(VB_EINVAL, "n must fit in int32");
+  auto h = std::make_unique<vbarms_vbsr_st>();
+  vb_status st = guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    h->s = s;
+    h->status.alloc(1, s);
+    h->status.zero();
+    const int64_t* d_rowptr = rowptr;
+    const int32_t* d_colind = colind;
+    const double* d_val = val;
+    DBuf<int64_t> rp;
+    DBuf<int32_t> ci;
+    DBuf<double> vv;
+    int64_t nnz = 0;
+    if (!on_device) {
+      nnz = n ? rowptr[n] : 0;
+      if (n && rowptr[0] != 0) fail(VB_EINVAL, "rowptr[0] != 0");
+      if (nnz < 0) fail(VB_EINVAL, "negative nnz");
+      rp.alloc(n + 1, s);
+      ci.alloc(nnz, s);
+      vv.alloc(nnz, s);
+      h2d(rp.p, rowptr, n + 1, s);
+      h2d(ci.p, colind, nnz, s);
+      h2d(vv.p, val, nnz, s);
+      d_rowptr = rp.p;
+      d_colind = ci.p;
+      d_val = vv.p;
+    } else if (n == 0) {
+      rp.alloc(1, s);
+      rp.zero();
+      d_rowptr = rp.p;
+    }
+    compress_device(n, d_rowptr, d_colind, d_val, tau, s, h->status.p, h->C);
+    VB_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != VB_OK) return st;
+  *out = h.release();
+  return VB_OK;
+}
+
+vb_status vbarms_vbsr_from_blocks(int64_t nblk, const int32_t* bsz, const int64_t* bptr, const int32_t* bcol,
+                                  const int64_t* voff, const double* val, void* stream, vbarms_vbsr* out) {
+  if (!out || nblk < 0) return set_err(VB_EINVAL, "invalid arguments");
+  auto h = std::make_unique<vbarms_vbsr_st>();
+  vb_status st = guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    h->s = s;
+    h->status.alloc(1, s);
+    h->status.zero();
+    int64_t n = 0;
+    for (int64_t I = 0; I < nblk; ++I) {
+      if (bsz[I] <= 0) fail(VB_EINVAL, "block sizes must be positive");
+      n += bsz[I];
+    }
+    const int64_t nnzb = bptr[nblk];
+    for (int64_t I = 0; I < nblk; ++I) {
+      if (bptr[I + 1] < bptr[I]) fail(VB_EINVAL, "bptr not monotone");
+      for (int64_t b = bptr[I]; b < bptr[I + 1]; ++b) {
+        if (bcol[b] < 0 || bcol[b] >= nblk || (b > bptr[I] && bcol[b] <= bcol[b - 1]))
+          fail(VB_EINVAL, "block columns out of range or not ascending");
+        if (voff[b + 1] - voff[b] != (int64_t)bsz[I] * bsz[bcol[b]]) fail(VB_EINVAL, "voff inconsistent");
+      }
+    }
+    Compressed& C = h->C;
+    C.n = n;
+    C.perm.alloc(n, s);
+    std::vector<int32_t> id(n);
+    for (int64_t i = 0; i < n; ++i) id[i] = (int32_t)i;
+    h2d(C.perm.p, id.data(), n, s);
+    DBuf<int32_t> dsz(nblk, s);
+    h2d(dsz.p, bsz, nblk, s);
+    set_partitions(C.A, dsz.p, nblk, dsz.p, nblk, s);
+    C.A.nnzb = nnzb;
+    C.A.nval = voff[nnzb];
+    C.A.bptr.alloc(nblk + 1, s);
+    C.A.bcol.alloc(nnzb, s);
+    C.A.voff.alloc(nnzb + 1, s);
+    C.A.val.alloc(C.A.nval, s);
+    h2d(C.A.bptr.p, bptr, nblk + 1, s);
+    h2d(C.A.bcol.p, bcol, nnzb, s);
+    h2d(C.A.voff.p, voff, nnzb + 1, s);
+    h2d(C.A.val.p, val, C.A.nval, s);
+    int64_t nz = 0;
+    for (int64_t e = 0; e < C.A.nval; ++e) nz += val[e] != 0.0;
+    C.nnz = nz;
+    C.av_bd = C.A.nval ? (double)nz / (double)C.A.nval : 0;
+    C.av_bs = nblk ? (double)n / (double)nblk : 0;
+    VB_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != VB_OK) return st;
+  *out = h.release();
+  return VB_OK;
+}
+
+vb_status vbarms_vbsr_query(vbarms_vbsr A, int64_t* n, int64_t* nblk, int64_t* nnzb, int64_t* nval, double* av_bd,
+                            double* av_bs) {
+  if (!A) return set_err(VB_EINVAL, "NULL handle");
+  if (n) *n = A->C.n;
+  if (nblk) *nblk = A->C.A.nbr;
+  if (nnzb) *nnzb = A->C.A.nnzb;
+  if (nval) *nval = A->C.A.nval;
+  if (av_bd) *av_bd = A->C.av_bd;
+  if (av_bs) *av_bs = A->C.av_bs;
+  return VB_OK;
+}
+
+vb_status vbarms_vbsr_export(vbarms_vbsr A, int32_t* perm, int32_t* bsz, int64_t* bptr, int32_t* bcol,
+                             int64_t* voff, double* val) {
+  if (!A) return set_err(VB_EINVAL, "NULL handle");
+  return guarded([&] {
+    cudaStream_t s = A->s;
+    if (perm && A->C.n) VB_CUDA(cudaMemcpyAsync(perm, A->C.perm.p, A->C.n * 4, cudaMemcpyDeviceToHost, s));
+    export_vb(A->C.A, s, nullptr, nullptr, nullptr, nullptr, bsz, nullptr, bptr, bcol, voff, val);
+  });
+}
+
+vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil, const vbarms_opts* opt,
+                        vbarms_prec* out) {
+  if (!A || !out) return set_err(VB_EINVAL, "NULL handle");
+  if (nlev < 0 || !(droptol >= 0.0)) return set_err(VB_EINVAL, "nlev < 0 or droptol < 0");
+  vbarms_opts d;
+  vbarms_opts_default(&d);
+  if (!opt) opt = &d;
+  if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
+  FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
+               opt->wait_limit ? opt->wait_limit : (uint64_t)8000000};
+  auto h = std::make_unique<vbarms_prec_st>();
+  vb_status st = guarded([&] {
+    if (o.precision == VB_FP64)
+      h->impl = factor_impl<double>(*A, o);
+    else
+      h->impl = factor_impl<float>(*A, o);
+  });
+  if (st != VB_OK) {
+    cudaStreamSynchronize(A->s);
+    return st;
+  }
+  *out = h.release();
+  return VB_OK;
+}
+
+vb_status vbarms_apply(vbarms_prec M, const double* x, double* y) {
+  if (!M || !x || !y) return set_err(VB_EINVAL, "NULL argument");
+  if (x == y) return set_err(VB_EINVAL, "x and y must not alias");
+  return guarded([&] {
+    PrecBase& P = *M->impl;
+    DBuf<double> xp(P.n, P.s), yp(P.n, P.s);
+    gather_dev(xp.p, x, P.perm.p, P.n, P.s);
+    P.apply_perm(xp.p, yp.p);
+    scatter_dev(y, yp.p, P.perm.p, P.n, P.s);
+    VB_CUDA(cudaStreamSynchronize(P.s));
+  });
+}
+
+vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x, double rtol, int restart,
+                       int maxit, int* iters, double* relres) {
+  if (!A || !b || !x) return set_err(VB_EINVAL, "NULL argument");
+  if (restart < 1 || maxit < 0 || !(rtol >= 0.0)) return set_err(VB_EINVAL, "restart < 1, maxit < 0 or rtol < 0");
+  bool conv = false;
+  vb_status st = guarded([&] {
+    cudaStream_t s = A->s;
+    const int64_t n = A->C.n;
+    const int m = restart;
+    const int32_t* perm = A->C.perm.p;
+    DBuf<double> bp(n, s), xp(n, s), r(n, s), w(n, s), V((size_t)(m + 1) * n, s), Z((size_t)m * n, s);
+    DBuf<double> hcol(m + 2, s);
+    gather_dev(bp.p, b, perm, n, s);
+    gather_dev(xp.p, x, perm, n, s);
+    dot_dev(bp.p, bp.p, n, hcol.p, s);
+    const double bnorm = std::sqrt(d2h(hcol.p, s));
+    int it = 0;
+    double rnorm = 0;
+    if (bnorm == 0.0) {
+      VB_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+      VB_CUDA(cudaStreamSynchronize(s));
+      if (iters) *iters = 0;
+      if (relres) *relres = 0.0;
+      conv = true;
+      return;
+    }
+    const double target = rtol * bnorm;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m), hh(m + 2);
+    for (;;) {
+      spmv_vb(A->C.A, xp.p, w.p, s);
+      sub_dev(r.p, bp.p, w.p, n, s);
+      dot_dev(r.p, r.p, n, hcol.p, s);
+      rnorm = std::sqrt(d2h(hcol.p, s));
+      if (rnorm <= target || it >= maxit) break;
+      VB_CUDA(cudaMemcpyAsync(hcol.p + m + 1, &rnorm, sizeof(double), cudaMemcpyHostToDevice, s));
+      scale_dev(V.p, r.p, hcol.p + m + 1, n, s);
+      std::fill(gv.begin(), gv.end(), 0.0);
+      gv[0] = rnorm;
+      int j = 0;
+      for (; j < m && it < maxit; ++j) {
+        double* vj = V.p + (size_t)j * n;
+        double* zj = Z.p + (size_t)j * n;
+        if (M)
+          M->impl->apply_perm(vj, zj);
+        else
+          VB_CUDA(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        spmv_vb(A->C.A, zj, w.p, s);
+        for (int i = 0; i <= j; ++i) {
+          dot_dev(w.p, V.p + (size_t)i * n, n, hcol.p + i, s);
+          axpy_dev(w.p, V.p + (size_t)i * n, hcol.p + i, -1.0, n, s);
+        }
+        dot_dev(w.p, w.p, n, hcol.p + j + 1, s);
+        std::vector<double> hc = d2h_vec(hcol.p, j + 2, s);
+        const double hn = std::sqrt(hc[j + 1]);
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
+        H[(size_t)(j + 1) * m + j] = hn;
+        ++it;
+        for (int i = 0; i < j; ++i) {
+          const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+        }
+        const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+        const double d = std::sqrt(a * a + c * c);
+        cs[j] = d > 0.0 ? a / d : 1.0;
+        sn[j] = d > 0.0 ? c / d : 0.0;
+        H[(size_t)j * m + j] = d;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        gv[j + 1] = -sn[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        if (hn == 0.0 || std::fabs(gv[j + 1]) <= target) {
+          ++j;
+          break;
+        }
+        VB_CUDA(cudaMemcpyAsync(hcol.p + m + 1, &hn, sizeof(double), cudaMemcpyHostToDevice, s));
+        scale_dev(V.p + (size_t)(j + 1) * n, w.p, hcol.p + m + 1, n, s);
+        VB_CUDA(cudaStreamSynchronize(s));
+      }
+      for (int i = j - 1; i >= 0; --i) {
+        double sacc = gv[i];
+        for (int k = i + 1; k < j; ++k) sacc -= H[(size_t)i * m + k] * yv[k];
+        yv[i] = H[(size_t)i * m + i] != 0.0 ? sacc / H[(size_t)i * m + i] : 0.0;
+      }
+      for (int i = 0; i < j; ++i) axpy_host(xp.p, Z.p + (size_t)i * n, yv[i], n, s);
+    }
+    scatter_dev(x, xp.p, perm, n, s);
+    VB_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    if (relres) *relres = rnorm / bnorm;
+    conv = rnorm <= target;
+  });
+  if (st != VB_OK) return st;
+  return conv ? VB_OK : set_err(VB_ENOCONV, "FGMRES reached maxit");
+}
+
+vb_status vbarms_prec_stats(vbarms_prec M, int* levels_used, double* mem_ratio, double* phase_s) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  if (levels_used) *levels_used = M->impl->levels();
+  if (mem_ratio) *mem_ratio = M->impl->mem_ratio;
+  if (phase_s)
+    for (int i = 0; i < PH_COUNT; ++i) phase_s[i] = M->impl->phase_s[i];
+  return VB_OK;
+}
+
+vb_status vbarms_prec_export(vbarms_prec M, int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb,
+                             int64_t* nval, int32_t* rsz, int32_t* csz, int64_t* bptr, int32_t* bcol,
+                             int64_t* voff, double* val) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  return guarded([&] { M->impl->export_mat(lev, which, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val); });
+}
+
+vb_status vbarms_prec_vector(vbarms_prec M, int lev, int which, double* d, int32_t* iv, int64_t* len) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  return guarded([&] { M->impl->export_vec(lev, which, d, iv, len); });
+}
+
+void vbarms_vbsr_destroy(vbarms_vbsr A) {
+  if (!A) return;
+  cudaStreamSynchronize(A->s);
+  delete A;
+}
+
+void vbarms_prec_destroy(vbarms_prec M) {
+  if (!M) return;
+  if (M->impl) cudaStreamSynchronize(M->impl->s);
+  delete M;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Shared device/host plumbing of the VBARMS CUDA library: error handling,
+// stream-ordered device buffers, prefix sums, hashing and the device VBCSR
+// container.  No step of the method lives here.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "vbarms.h"
+
+namespace vb {
+
+struct Error {
+  vb_status st;
+  std::string msg;
+};
+
+[[noreturn]] inline void fail(vb_status st, const std::string& msg) { throw Error{st, msg}; }
+
+#define VB_CUDA(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      ::vb::fail(e_ == cudaErrorMemoryAllocation ? VB_ENOMEM : VB_ECUDA,                     \
+                 std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+#define VB_LAUNCH_CHECK() VB_CUDA(cudaGetLastError())
+
+// Device status word shared by the kernels of one call: first error wins.
+enum DevCode : int {
+  DEV_OK = 0,
+  DEV_EINVAL = 1,
+  DEV_ESINGULAR = 4,
+  DEV_ETIMEOUT = 5,
+  DEV_OVERFLOW = 100,  // a scratch capacity was too small: the host retries
+  DEV_INTERNAL = 7,
+};
+
+__device__ __forceinline__ void dev_fail(int* st, int code) { atomicCAS(st, 0, code); }
+
+// --------------------------------------------------------------------------
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+
+  DBuf() = default;
+  DBuf(size_t count, cudaStream_t st) { alloc(count, st); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr, o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p, n = o.n, s = o.s;
+      o.p = nullptr, o.n = 0;
+    }
+    return *this;
+  }
+  ~DBuf() { release(); }
+
+  void alloc(size_t count, cudaStream_t st) {
+    release();
+    s = st;
+    n = count;
+    if (count) {
+      cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), st);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        n = 0;
+        (void)cudaGetLastError();
+        fail(VB_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+      }
+    }
+  }
+  void zero() {
+    if (n) VB_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+  void fill_bytes(int b) {
+    if (n) VB_CUDA(cudaMemsetAsync(p, b, n * sizeof(T), s));
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+  }
+  T* get() const { return p; }
+};
+
+template <typename T>
+T d2h(const T* dptr, cudaStream_t s) {
+  T v;
+  VB_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
+  VB_CUDA(cudaStreamSynchronize(s));
+  return v;
+}
+
+template <typename T>
+std::vector<T> d2h_vec(const T* dptr, size_t n, cudaStream_t s) {
+  std::vector<T> v(n);
+  if (n) {
+    VB_CUDA(cudaMemcpyAsync(v.data(), dptr, n * sizeof(T), cudaMemcpyDeviceToHost, s));
+    VB_CUDA(cudaStreamSynchronize(s));
+  }
+  return v;
+}
+
+template <typename T>
+void h2d(T* dptr, const T* h, size_t n, cudaStream_t s) {
+  if (n) VB_CUDA(cudaMemcpyAsync(dptr, h, n * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+// Read the device status word, reset it, and turn a failure into an Error.
+void check_status(int* dst, cudaStream_t s, const char* where);
+
+inline unsigned grid_for(int64_t work, int per_block, int64_t cap = 152LL * 64) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+// --------------------------------------------------------------------------
+// Exclusive prefix sum: out[0] = 0, out[i+1] = out[i] + in[i] (out has n+1
+// entries).  in and out must not overlap.  Read the total from out[n].
+void scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+// --------------------------------------------------------------------------
+// Integer hash-set helpers (open addressing, linear probing, key -1 = empty).
+__device__ __forceinline__ uint32_t hmix(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// Insert key into keys[0..mask]; returns the slot, or -1 when the table is
+// full.  *fresh tells whether this call created the entry.
+__device__ __forceinline__ int hset_insert(int* keys, uint32_t mask, int key, bool* fresh) {
+  uint32_t h = hmix((uint32_t)key) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    int k = atomicCAS(&keys[h], -1, key);
+    if (k == -1) {
+      *fresh = true;
+      return (int)h;
+    }
+    if (k == key) {
+      *fresh = false;
+      return (int)h;
+    }
+    h = (h + 1) & mask;
+  }
+  *fresh = false;
+  return -1;
+}
+
+__device__ __forceinline__ int hset_find(const int* keys, uint32_t mask, int key) {
+  uint32_t h = hmix((uint32_t)key) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    int k = keys[h];
+    if (k == key) return (int)h;
+    if (k == -1) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_min_i(int v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_max_i(int v) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Binary search of key in the ascending array a[lo, hi); returns index or -1.
+__device__ __forceinline__ int64_t bsearch_i32(const int32_t* a, int64_t lo, int64_t hi, int32_t key) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    int32_t v = a[mid];
+    if (v == key) return mid;
+    if (v < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return -1;
+}
+
+// --------------------------------------------------------------------------
+// Device VBCSR matrix: block rows/cols of variable size, each stored block a
+// dense row-major rsz[I] x csz[J] array; blocks of a block row contiguous.
+template <typename T>
+struct VBView {
+  int64_t nbr, nbc;
+  const int32_t* rsz;
+  const int32_t* csz;
+  const int64_t* roff;
+  const int64_t* coff;
+  const int64_t* bptr;
+  const int32_t* bcol;
+  const int64_t* voff;
+  T* val;
+};
+
+template <typename T>
+struct VBDev {
+  int64_t nbr = 0, nbc = 0, nnzb = 0, nval = 0;
+  DBuf<int32_t> rsz, csz;
+  DBuf<int64_t> roff, coff;
+  DBuf<int64_t> bptr;
+  DBuf<int32_t> bcol;
+  DBuf<int64_t> voff;
+  DBuf<T> val;
+  bool same_partition = false;  // csz/coff alias rsz/roff
+
+  VBView<T> view() const {
+    VBView<T> v;
+    v.nbr = nbr;
+    v.nbc = nbc;
+    v.rsz = rsz.p;
+    v.roff = roff.p;
+    v.csz = same_partition ? rsz.p : csz.p;
+    v.coff = same_partition ? roff.p : coff.p;
+    v.bptr = bptr.p;
+    v.bcol = bcol.p;
+    v.voff = voff.p;
+    v.val = val.p;
+    return v;
+  }
+  const int32_t* csz_p() const { return same_partition ? rsz.p : csz.p; }
+  const int64_t* coff_p() const { return same_partition ? roff.p : coff.p; }
+  int64_t nrows_scalar(cudaStream_t s) const { return nbr ? d2h(roff.p + nbr, s) : 0; }
+};
+
+// Set partition arrays (sizes -> offsets) from device sizes.
+void set_partition(DBuf<int32_t>& sz, DBuf<int64_t>& off, const int32_t* src, int64_t nb, cudaStream_t s);
+
+}  // namespace vb

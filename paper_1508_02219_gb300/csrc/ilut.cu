@@ -1,0 +1,683 @@
+// Last-level block ILUT of VBARMS on the GPU (Section 3 dropping rule, the
+// block IKJ form of Alg. 3), on the scaled last Schur complement in natural
+// order.
+//
+// Row i is processed by one warp that took ticket i (tickets are handed out
+// in row order, so every row a warp waits for is already owned by a running
+// warp).  The warp keeps its working row in a private workspace (hash table
+// column -> slot, dense values), eliminates its L part in ascending column
+// order including fill -- waiting, with a bounded spin, until row k is
+// published -- then drops and trims, factors its diagonal block (GEPP) and
+// publishes its L and U rows to global pools.  Per element, the operation
+// order is the oracle's, so FP64 results match it bit for bit.
+//
+// A wait that runs out sets VB_ETIMEOUT and an abort flag that every other
+// warp checks; overflowing a pool or a workspace sets an overflow code and the
+// host repeats the kernel with larger buffers.
+#include <algorithm>
+
+#include "internal.h"
+#include "level.cuh"
+#include "vbsr_ops.cuh"
+
+namespace vb {
+namespace {
+
+constexpr int IW = 8;  // warps per block
+
+enum : int { SL_LIVE = 0, SL_LKEPT = 1, SL_DEAD = 2 };
+
+struct Pools {
+  // L and U rows: blocks in pool order; per row the first block and count
+  int32_t* lcol;
+  int64_t* lvo;  // value offset of each pool block
+  int32_t* ucol;
+  int64_t* uvo;
+  int64_t* lstart;
+  int32_t* lcnt;
+  int64_t* ustart;
+  int32_t* ucnt;
+  unsigned long long* ctr;  // [0] L blocks, [1] L values, [2] U blocks, [3] U values, [4] ticket, [5] max row need
+  int64_t lbcap, lvcap, ubcap, uvcap;
+  int32_t* done;
+  int* abort;
+};
+
+struct Workspace {
+  int* keys;      // [HT] per warp
+  int* hpos;      // [SMAX]
+  int* scol;      // [SMAX]
+  int64_t* soff;  // [SMAX]
+  int* sstate;    // [SMAX]
+  double* sf2;    // [SMAX]
+  int ht, smax;
+  int64_t vmax;
+};
+
+template <typename T>
+__device__ __forceinline__ T msub(T acc, T a, T b);
+template <>
+__device__ __forceinline__ double msub<double>(double acc, double a, double b) {
+  return __dsub_rn(acc, __dmul_rn(a, b));
+}
+template <>
+__device__ __forceinline__ float msub<float>(float acc, float a, float b) {
+  return __fmaf_rn(-a, b, acc);
+}
+
+__device__ __forceinline__ bool drop_rule(double f2, int m, int n, double t) {
+  const double thr = __dmul_rn(__dmul_rn(t, (double)m), (double)n);
+  return f2 < __dmul_rn(thr, thr);
+}
+
+template <typename T>
+__device__ __forceinline__ double fro2_seq(const T* v, int n) {
+  double s = 0.0;
+  for (int e = 0; e < n; ++e) {
+    const double x = (double)v[e];
+    s = __dadd_rn(s, __dmul_rn(x, x));
+  }
+  return s;
+}
+
+// x (one row of length m) <- x (P^T L U)^{-1} = x U^{-1} L^{-1} P, with the
+// factored pivot block read through L2 (written by another warp).
+template <typename T, typename TL>
+__device__ void ainv_right_row(const TL* lu, const int32_t* pv, int m, T* x) {
+  for (int j = 0; j < m; ++j) {
+    TL s = (TL)x[j];
+    for (int q = 0; q < j; ++q) s = msub<TL>(s, (TL)x[q], __ldcg(lu + q * m + j));
+    x[j] = (T)(s / __ldcg(lu + j * m + j));
+  }
+  for (int j = m - 1; j >= 0; --j) {
+    TL s = (TL)x[j];
+    for (int q = j + 1; q < m; ++q) s = msub<TL>(s, (TL)x[q], __ldcg(lu + q * m + j));
+    x[j] = (T)s;
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    const int p = __ldcg(pv + k);
+    if (p != k) {
+      const T t = x[k];
+      x[k] = x[p];
+      x[p] = t;
+    }
+  }
+}
+
+// Workspace hash: keys[h] = -2 - slot, -1 = empty; the column of a slot is
+// scol[slot].  Placement and lookup never run concurrently (separated by
+// __syncwarp), and the columns inserted in one phase are distinct.
+__device__ __forceinline__ int ws_place(int* keys, uint32_t mask, int slot, int col) {
+  uint32_t h = hmix((uint32_t)col) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    if (atomicCAS(&keys[h], -1, -2 - slot) == -1) return (int)h;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int ws_lookup(const int* keys, const int* scol, uint32_t mask, int col) {
+  uint32_t h = hmix((uint32_t)col) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int kv = keys[h];
+    if (kv == -1) return -1;
+    const int s = -2 - kv;
+    if (scol[s] == col) return s;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// Claim a new slot of sz values for column col; returns the slot or -1.
+template <typename T>
+__device__ __forceinline__ int ws_new_slot(const Workspace& ws, int* keys, int* hpos, int* scol, int64_t* soff,
+                                           int* sstate, int* nslots, unsigned long long* nvals, uint32_t hmask,
+                                           int col, int sz) {
+  const int slot = atomicAdd(nslots, 1);
+  const long long off = (long long)atomicAdd(nvals, (unsigned long long)sz);
+  if (slot >= ws.smax || off + sz > ws.vmax) return -1;
+  scol[slot] = col;
+  soff[slot] = off;
+  sstate[slot] = SL_LIVE;
+  hpos[slot] = ws_place(keys, hmask, slot, col);
+  return hpos[slot] < 0 ? -1 : slot;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(IW * 32)
+    k_ilut(VBView<T> A, Workspace ws, T* __restrict__ wvals_all, Pools P, T* __restrict__ lval,
+           T* __restrict__ uval, const int64_t* __restrict__ dgoff, double* __restrict__ dg,
+           float* __restrict__ dg32, int32_t* __restrict__ piv, int32_t* __restrict__ ptag, int mixed,
+           double cond_thr, double t, int lfil, unsigned long long wait_limit, int* st) {
+  __shared__ int s_nslots[IW];
+  __shared__ unsigned long long s_nvals[IW];
+  __shared__ int s_flag[IW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t wid = (int64_t)blockIdx.x * IW + warp;
+  int* keys = ws.keys + wid * ws.ht;
+  int* hpos = ws.hpos + wid * ws.smax;
+  int* scol = ws.scol + wid * ws.smax;
+  int64_t* soff = ws.soff + wid * ws.smax;
+  int* sstate = ws.sstate + wid * ws.smax;
+  double* sf2 = ws.sf2 + wid * ws.smax;
+  T* wv = wvals_all + wid * ws.vmax;
+  const uint32_t hmask = (uint32_t)ws.ht - 1;
+  volatile int* vflag = &s_flag[warp];
+  volatile int* vns = &s_nslots[warp];
+  for (int k = lane; k < ws.ht; k += 32) keys[k] = -1;
+  __syncwarp();
+
+  for (;;) {
+    long long row = 0;
+    if (lane == 0) row = (long long)atomicAdd(P.ctr + 4, 1ULL);
+    row = __shfl_sync(0xffffffffu, row, 0);
+    if (row >= A.nbr) break;
+    const int64_t i = row;
+    const int ni = A.rsz[i];
+    if (lane == 0) {
+      s_nslots[warp] = 0;
+      s_nvals[warp] = 0;
+      s_flag[warp] = 0;
+    }
+    __syncwarp();
+    // ---- load row i of A into the workspace (distinct columns)
+    for (int64_t b = A.bptr[i] + lane; b < A.bptr[i + 1]; b += 32) {
+      const int32_t J = A.bcol[b];
+      const int sz = ni * A.csz[J];
+      const int slot = ws_new_slot<T>(ws, keys, hpos, scol, soff, sstate, &s_nslots[warp], &s_nvals[warp], hmask,
+                                      J, sz);
+      if (slot < 0) {
+        *vflag = 1;
+        continue;
+      }
+      for (int e = 0; e < sz; ++e) wv[soff[slot] + e] = A.val[A.voff[b] + e];
+    }
+    __syncwarp();
+    int status_local = *vflag ? DEV_OVERFLOW : 0;
+    int64_t last = -1;
+    // ---- eliminate the L part in ascending column order (including fill)
+    while (status_local == 0) {
+      const int ns = min(*vns, ws.smax);
+      int best = 0x7fffffff, bslot = -1;
+      for (int s = lane; s < ns; s += 32) {
+        const int c = scol[s];
+        if (sstate[s] == SL_LIVE && c > last && c < i && c < best) {
+          best = c;
+          bslot = s;
+        }
+      }
+      const int kmin = warp_min_i(best);
+      if (kmin == 0x7fffffff) break;
+      const unsigned who = __ballot_sync(0xffffffffu, bslot >= 0 && best == kmin);
+      const int sk = __shfl_sync(0xffffffffu, bslot, __ffs(who) - 1);
+      const int64_t k = kmin;
+      last = k;
+      // bounded wait until row k is published
+      if (lane == 0) {
+        unsigned long long it = 0;
+        while (*((volatile int32_t*)&P.done[k]) == 0) {
+          if (*((volatile int*)P.abort) != 0) {
+            *vflag = 2;
+            break;
+          }
+          if (++it > wait_limit) {
+            dev_fail(st, DEV_ETIMEOUT);
+            atomicExch(P.abort, 1);
+            *vflag = 2;
+            break;
+          }
+          __nanosleep(128);
+        }
+        __threadfence();
+      }
+      __syncwarp();
+      if (*vflag == 2) {
+        status_local = DEV_ETIMEOUT;
+        break;
+      }
+      const int nk = A.rsz[k];
+      T* m = wv + soff[sk];
+      const bool use64 = sizeof(T) == sizeof(double) || (ptag && __ldcg(ptag + k));
+      for (int a = lane; a < ni; a += 32) {
+        if (use64)
+          ainv_right_row<T, double>(dg + dgoff[k], piv + A.roff[k], nk, m + a * nk);
+        else
+          ainv_right_row<T, float>(dg32 + dgoff[k], piv + A.roff[k], nk, m + a * nk);
+      }
+      __syncwarp();
+      double f2 = 0.0;
+      if (lane == 0) f2 = fro2_seq(m, ni * nk);
+      f2 = __shfl_sync(0xffffffffu, f2, 0);
+      if (drop_rule(f2, ni, nk, t)) {
+        if (lane == 0) sstate[sk] = SL_DEAD;
+        __syncwarp();
+        continue;
+      }
+      if (lane == 0) {
+        sstate[sk] = SL_LKEPT;
+        sf2[sk] = f2;
+      }
+      const int64_t u0 = __ldcg(P.ustart + k);
+      const int uc = __ldcg(P.ucnt + k);
+      // create the fill blocks of the U columns of row k that are missing:
+      // probe (read-only) then place, separated by __syncwarp
+      for (int q0 = 0; q0 < uc; q0 += 32) {
+        const int q = q0 + lane;
+        int32_t j = -1;
+        bool missing = false;
+        if (q < uc) {
+          j = __ldcg(P.ucol + u0 + q);
+          missing = ws_lookup(keys, scol, hmask, j) < 0;
+        }
+        __syncwarp();
+        if (missing) {
+          const int sz = ni * A.rsz[j];
+          const int slot = ws_new_slot<T>(ws, keys, hpos, scol, soff, sstate, &s_nslots[warp], &s_nvals[warp],
+                                          hmask, j, sz);
+          if (slot < 0)
+            *vflag = 1;
+          else
+            for (int e = 0; e < sz; ++e) wv[soff[slot] + e] = (T)0;
+        }
+        __syncwarp();
+      }
+      if (*vflag == 1) {
+        status_local = DEV_OVERFLOW;
+        break;
+      }
+      // a_ij -= m * u_kj, one U block at a time, lanes over its elements
+      for (int q = 0; q < uc; ++q) {
+        const int32_t j = __ldcg(P.ucol + u0 + q);
+        const int nj = A.rsz[j];
+        const int slot = ws_lookup(keys, scol, hmask, j);
+        if (slot < 0) {
+          status_local = DEV_INTERNAL;
+          break;
+        }
+        T* B = wv + soff[slot];
+        const T* U = uval + __ldcg(P.uvo + u0 + q);
+        for (int e = lane; e < ni * nj; e += 32) {
+          const int a = e / nj, jj = e - a * nj;
+          T acc = B[e];
+          for (int r = 0; r < nk; ++r) acc = msub<T>(acc, m[a * nk + r], __ldcg(U + r * nj + jj));
+          B[e] = acc;
+        }
+        __syncwarp();
+      }
+    }
+    const int ns = min(*vns, ws.smax);
+    if (status_local == 0) {
+      int dslot = -1;
+      for (int s = lane; s < ns; s += 32)
+        if (scol[s] == i && sstate[s] == SL_LIVE) dslot = s;
+      dslot = warp_max_i(dslot);
+      if (dslot < 0) status_local = DEV_ESINGULAR;
+    }
+    if (status_local == 0) {
+      // U part: threshold on the blocks right of the diagonal
+      for (int s = lane; s < ns; s += 32) {
+        const int c = scol[s];
+        if (sstate[s] == SL_LIVE && c > i) {
+          const int nc = A.rsz[c];
+          const double f2 = fro2_seq(wv + soff[s], ni * nc);
+          sf2[s] = f2;
+          if (drop_rule(f2, ni, nc, t)) sstate[s] = SL_DEAD;
+        }
+      }
+      __syncwarp();
+      // lfil: lane 0 trims the L part, lane 1 the U part (disjoint slots)
+      if (lfil >= 0 && lane < 2) {
+        const bool isL = lane == 0;
+        const int mark = isL ? 10 : 20;
+        int cnt = 0;
+        for (int s = 0; s < ns; ++s)
+          cnt += (isL ? sstate[s] == SL_LKEPT : (sstate[s] == SL_LIVE && scol[s] > i)) ? 1 : 0;
+        if (cnt > lfil) {
+          for (int sel = 0; sel < lfil; ++sel) {
+            int bs = -1;
+            for (int s = 0; s < ns; ++s) {
+              const bool in = isL ? sstate[s] == SL_LKEPT : (sstate[s] == SL_LIVE && scol[s] > i);
+              if (!in) continue;
+              if (bs < 0 || sf2[s] > sf2[bs] || (sf2[s] == sf2[bs] && scol[s] < scol[bs])) bs = s;
+            }
+            if (bs < 0) break;
+            sstate[bs] = mark;
+          }
+          for (int s = 0; s < ns; ++s) {
+            const bool in = isL ? sstate[s] == SL_LKEPT : (sstate[s] == SL_LIVE && scol[s] > i);
+            if (in) sstate[s] = SL_DEAD;
+          }
+          for (int s = 0; s < ns; ++s)
+            if (sstate[s] == mark) sstate[s] = isL ? SL_LKEPT : SL_LIVE;
+        }
+      }
+      __syncwarp();
+      int nl = 0, nu = 0;
+      long long vl = 0, vu = 0;
+      for (int s = lane; s < ns; s += 32) {
+        const int c = scol[s];
+        if (sstate[s] == SL_LKEPT) {
+          ++nl;
+          vl += (long long)ni * A.rsz[c];
+        } else if (sstate[s] == SL_LIVE && c > i) {
+          ++nu;
+          vu += (long long)ni * A.rsz[c];
+        }
+      }
+      nl = warp_sum_i(nl);
+      nu = warp_sum_i(nu);
+      vl = warp_sum_ll(vl);
+      vu = warp_sum_ll(vu);
+      unsigned long long lb = 0, lvv = 0, ub = 0, uvv = 0;
+      if (lane == 0) {
+        lb = atomicAdd(P.ctr + 0, (unsigned long long)nl);
+        lvv = atomicAdd(P.ctr + 1, (unsigned long long)vl);
+        ub = atomicAdd(P.ctr + 2, (unsigned long long)nu);
+        uvv = atomicAdd(P.ctr + 3, (unsigned long long)vu);
+      }
+      lb = __shfl_sync(0xffffffffu, lb, 0);
+      lvv = __shfl_sync(0xffffffffu, lvv, 0);
+      ub = __shfl_sync(0xffffffffu, ub, 0);
+      uvv = __shfl_sync(0xffffffffu, uvv, 0);
+      const bool fits = (int64_t)(lb + nl) <= P.lbcap && (int64_t)(lvv + vl) <= P.lvcap &&
+                        (int64_t)(ub + nu) <= P.ubcap && (int64_t)(uvv + vu) <= P.uvcap;
+      if (!fits) status_local = DEV_OVERFLOW;
+      if (status_local == 0) {
+        // both rows in ascending column order (rank by column)
+        for (int s = lane; s < ns; s += 32) {
+          const int c = scol[s];
+          const bool isL = sstate[s] == SL_LKEPT;
+          const bool isU = sstate[s] == SL_LIVE && c > i;
+          if (!isL && !isU) continue;
+          int rank = 0;
+          long long vo = 0;
+          for (int q = 0; q < ns; ++q) {
+            const int cq = scol[q];
+            const bool same = isL ? sstate[q] == SL_LKEPT : (sstate[q] == SL_LIVE && cq > i);
+            if (same && cq < c) {
+              ++rank;
+              vo += (long long)ni * A.rsz[cq];
+            }
+          }
+          const int nc = A.rsz[c];
+          if (isL) {
+            P.lcol[lb + rank] = c;
+            P.lvo[lb + rank] = (int64_t)(lvv + vo);
+            for (int e = 0; e < ni * nc; ++e) lval[lvv + vo + e] = wv[soff[s] + e];
+          } else {
+            P.ucol[ub + rank] = c;
+            P.uvo[ub + rank] = (int64_t)(uvv + vo);
+            for (int e = 0; e < ni * nc; ++e) uval[uvv + vo + e] = wv[soff[s] + e];
+          }
+        }
+        int dslot = -1;
+        for (int s = lane; s < ns; s += 32)
+          if (scol[s] == i && sstate[s] == SL_LIVE) dslot = s;
+        dslot = warp_max_i(dslot);
+        if (lane == 0) {
+          P.lstart[i] = (int64_t)lb;
+          P.lcnt[i] = nl;
+          P.ustart[i] = (int64_t)ub;
+          P.ucnt[i] = nu;
+          // GEPP of the diagonal block in FP64 (the oracle's order)
+          double* a = dg + dgoff[i];
+          const T* src = wv + soff[dslot];
+          for (int e = 0; e < ni * ni; ++e) a[e] = (double)src[e];
+          double norm1 = 0.0;
+          if (mixed)
+            for (int jj = 0; jj < ni; ++jj) {
+              double sum = 0.0;
+              for (int ii = 0; ii < ni; ++ii) sum += fabs(a[ii * ni + jj]);
+              norm1 = fmax(norm1, sum);
+            }
+          int32_t* pv = piv + A.roff[i];
+          bool singular = false;
+          for (int kk = 0; kk < ni; ++kk) {
+            int pr = kk;
+            double bestv = fabs(a[kk * ni + kk]);
+            for (int ii = kk + 1; ii < ni; ++ii) {
+              const double v = fabs(a[ii * ni + kk]);
+              if (v > bestv) {
+                bestv = v;
+                pr = ii;
+              }
+            }
+            if (bestv == 0.0) {
+              singular = true;
+              break;
+            }
+            pv[kk] = pr;
+            if (pr != kk)
+              for (int jj = 0; jj < ni; ++jj) {
+                const double tt = a[kk * ni + jj];
+                a[kk * ni + jj] = a[pr * ni + jj];
+                a[pr * ni + jj] = tt;
+              }
+            const double d = a[kk * ni + kk];
+            for (int ii = kk + 1; ii < ni; ++ii) {
+              const double l = __ddiv_rn(a[ii * ni + kk], d);
+              a[ii * ni + kk] = l;
+              for (int jj = kk + 1; jj < ni; ++jj)
+                a[ii * ni + jj] = __dsub_rn(a[ii * ni + jj], __dmul_rn(l, a[kk * ni + jj]));
+            }
+          }
+          if (singular) {
+            *vflag = 3;
+          } else if (mixed) {
+            int tag = 1;
+            if (ni <= 64) {
+              double x[64];
+              double inv1 = 0.0;
+              for (int jj = 0; jj < ni; ++jj) {
+                for (int ii = 0; ii < ni; ++ii) x[ii] = ii == jj ? 1.0 : 0.0;
+                for (int kk = 0; kk < ni; ++kk)
+                  if (pv[kk] != kk) {
+                    const double tt = x[kk];
+                    x[kk] = x[pv[kk]];
+                    x[pv[kk]] = tt;
+                  }
+                for (int ii = 1; ii < ni; ++ii)
+                  for (int kk = 0; kk < ii; ++kk) x[ii] -= a[ii * ni + kk] * x[kk];
+                for (int ii = ni - 1; ii >= 0; --ii) {
+                  double sum = x[ii];
+                  for (int kk = ii + 1; kk < ni; ++kk) sum -= a[ii * ni + kk] * x[kk];
+                  x[ii] = sum / a[ii * ni + ii];
+                }
+                double cs = 0.0;
+                for (int ii = 0; ii < ni; ++ii) cs += fabs(x[ii]);
+                inv1 = fmax(inv1, cs);
+              }
+              tag = norm1 * inv1 > cond_thr ? 1 : 0;
+            }
+            ptag[i] = tag;
+            for (int e = 0; e < ni * ni; ++e) dg32[dgoff[i] + e] = (float)a[e];
+          }
+        }
+        __syncwarp();
+        if (*vflag == 3) status_local = DEV_ESINGULAR;
+      }
+    }
+    if (status_local != 0 && lane == 0) {
+      dev_fail(st, status_local);
+      atomicExch(P.abort, 1);
+      P.lcnt[i] = 0;
+      P.ucnt[i] = 0;
+      P.lstart[i] = 0;
+      P.ustart[i] = 0;
+    }
+    if (lane == 0) atomicMax(P.ctr + 5, s_nvals[warp]);
+    // publish the row
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicExch(&P.done[i], 1);
+    }
+    // clear the hash positions this row used
+    for (int s = lane; s < ns; s += 32)
+      if (hpos[s] >= 0) keys[hpos[s]] = -1;
+    __syncwarp();
+  }
+}
+
+// Gather the pooled rows into VBCSR (warp per row).
+template <typename T>
+__global__ void k_pool_to_vb(int64_t nbr, const int64_t* __restrict__ start, const int32_t* __restrict__ pcol,
+                             const int64_t* __restrict__ pvo, const T* __restrict__ pval,
+                             const int64_t* __restrict__ bptr, const int64_t* __restrict__ voff,
+                             int32_t* __restrict__ bcol, T* __restrict__ val) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nbr; i += (int64_t)gridDim.x * wpb) {
+    const int64_t n = bptr[i + 1] - bptr[i];
+    for (int64_t q = lane; q < n; q += 32) bcol[bptr[i] + q] = pcol[start[i] + q];
+    __syncwarp();
+    for (int64_t q = 0; q < n; ++q) {
+      const int64_t d = bptr[i] + q;
+      const int64_t sz = voff[d + 1] - voff[d];
+      const int64_t src = pvo[start[i] + q];
+      for (int64_t e = lane; e < sz; e += 32) val[voff[d] + e] = pval[src + e];
+    }
+  }
+}
+
+__global__ void k_sq_sizes(int64_t n, const int32_t* __restrict__ sz, int64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int64_t)sz[i] * sz[i];
+}
+
+__global__ void k_count_to_i64(int64_t n, const int32_t* __restrict__ c, int64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = c[i];
+}
+
+__global__ void k_iota(int64_t n, int64_t* __restrict__ bptr, int32_t* __restrict__ bcol) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+    bptr[i] = i;
+    if (i < n) bcol[i] = (int32_t)i;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, uint64_t wait_limit, cudaStream_t s,
+               int* dst) {
+  const VBDev<T>& A = X.A;
+  const int64_t p = A.nbr;
+  const int64_t n = p ? d2h(A.roff.p + p, s) : 0;
+  // pivot blocks: block diagonal structure
+  set_partitions(X.Dg, A.rsz.p, p, A.rsz.p, p, s);
+  X.Dg.bptr.alloc(p + 1, s);
+  X.Dg.bcol.alloc(p, s);
+  k_iota<<<grid_for(p + 1, 256), 256, 0, s>>>(p, X.Dg.bptr.p, X.Dg.bcol.p);
+  VB_LAUNCH_CHECK();
+  X.Dg.nnzb = p;
+  X.Dg.voff.alloc(p + 1, s);
+  {
+    DBuf<int64_t> sq(p, s);
+    if (p) {
+      k_sq_sizes<<<grid_for(p, 256), 256, 0, s>>>(p, A.rsz.p, sq.p);
+      VB_LAUNCH_CHECK();
+    }
+    scan_i64(sq.p, X.Dg.voff.p, p, s);
+  }
+  X.Dg.nval = p ? d2h(X.Dg.voff.p + p, s) : 0;
+  X.Dg.val.alloc(X.Dg.nval, s);
+  X.piv.alloc(n, s);
+  X.ptag.alloc(p, s);
+  X.ptag.zero();
+  if (mixed) copy_vb<float, double>(X.Dg, X.Dg32, s);
+  set_partitions(X.L, A.rsz.p, p, A.rsz.p, p, s);
+  set_partitions(X.U, A.rsz.p, p, A.rsz.p, p, s);
+  if (p == 0) {
+    X.L.bptr.alloc(1, s);
+    X.L.bptr.zero();
+    X.U.bptr.alloc(1, s);
+    X.U.bptr.zero();
+    X.L.voff.alloc(1, s);
+    X.L.voff.zero();
+    X.U.voff.alloc(1, s);
+    X.U.voff.zero();
+    return;
+  }
+
+  int dev = 0;
+  VB_CUDA(cudaGetDevice(&dev));
+  int nsm = 0;
+  VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int64_t lbcap = std::max<int64_t>(4 * A.nnzb, 1024), lvcap = std::max<int64_t>(4 * A.nval, 1 << 16);
+  int64_t ubcap = lbcap, uvcap = lvcap;
+  int smax = 1024;
+  int64_t vmax = 32768;
+  int blocks_per_sm = 2;
+  for (int attempt = 0; attempt < 6; ++attempt) {
+    const int64_t nblocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * blocks_per_sm, (p + IW - 1) / IW));
+    const int64_t nwarps = nblocks * IW;
+    int ht = 1;
+    while (ht < 2 * smax) ht <<= 1;
+    DBuf<int> keys(nwarps * ht, s), hpos(nwarps * smax, s), scol(nwarps * smax, s), sstate(nwarps * smax, s);
+    DBuf<int64_t> soff(nwarps * smax, s);
+    DBuf<double> sf2(nwarps * smax, s);
+    DBuf<T> wvals(nwarps * vmax, s);
+    Workspace ws{keys.p, hpos.p, scol.p, soff.p, sstate.p, sf2.p, ht, smax, vmax};
+    DBuf<int32_t> lcol(lbcap, s), ucol(ubcap, s), lcnt(p, s), ucnt(p, s), done(p, s);
+    DBuf<int64_t> lvo(lbcap, s), uvo(ubcap, s), lstart(p, s), ustart(p, s);
+    DBuf<T> lval(lvcap, s), uval(uvcap, s);
+    DBuf<unsigned long long> ctr(8, s);
+    DBuf<int> abort(1, s);
+    ctr.zero();
+    done.zero();
+    abort.zero();
+    Pools P{lcol.p, lvo.p, ucol.p, uvo.p, lstart.p, lcnt.p, ustart.p, ucnt.p, ctr.p,
+            lbcap,  lvcap, ubcap,  uvcap, done.p,  abort.p};
+    k_ilut<T><<<(unsigned)nblocks, IW * 32, 0, s>>>(A.view(), ws, wvals.p, P, lval.p, uval.p, X.Dg.voff.p,
+                                                     X.Dg.val.p, mixed ? X.Dg32.val.p : nullptr, X.piv.p,
+                                                     mixed ? X.ptag.p : nullptr, mixed ? 1 : 0, cond_thr, t, lfil,
+                                                     (unsigned long long)wait_limit, dst);
+    VB_LAUNCH_CHECK();
+    const int st = d2h(dst, s);
+    if (st == DEV_OVERFLOW) {
+      VB_CUDA(cudaMemsetAsync(dst, 0, sizeof(int), s));
+      std::vector<unsigned long long> c = d2h_vec(ctr.p, 8, s);
+      lbcap = std::max<int64_t>(2 * lbcap, (int64_t)c[0] + 1024);
+      lvcap = std::max<int64_t>(2 * lvcap, (int64_t)c[1] + 4096);
+      ubcap = std::max<int64_t>(2 * ubcap, (int64_t)c[2] + 1024);
+      uvcap = std::max<int64_t>(2 * uvcap, (int64_t)c[3] + 4096);
+      if ((int64_t)c[5] >= vmax / 2) vmax *= 4;
+      smax *= 2;
+      continue;
+    }
+    check_status(dst, s, "vbarms_factor: last-level block ILUT");
+    // assemble L and U
+    for (int which = 0; which < 2; ++which) {
+      VBDev<T>& M = which == 0 ? X.L : X.U;
+      DBuf<int32_t>& cnt = which == 0 ? lcnt : ucnt;
+      DBuf<int64_t>& start = which == 0 ? lstart : ustart;
+      DBuf<int32_t>& pcol = which == 0 ? lcol : ucol;
+      DBuf<int64_t>& pvo = which == 0 ? lvo : uvo;
+      DBuf<T>& pval = which == 0 ? lval : uval;
+      M.bptr.alloc(p + 1, s);
+      DBuf<int64_t> c64(p, s);
+      k_count_to_i64<<<grid_for(p, 256), 256, 0, s>>>(p, cnt.p, c64.p);
+      VB_LAUNCH_CHECK();
+      scan_i64(c64.p, M.bptr.p, p, s);
+      M.nnzb = d2h(M.bptr.p + p, s);
+      M.bcol.alloc(M.nnzb, s);
+      // bcol first (needed by the offsets), then offsets, then values
+      k_pool_to_vb<T><<<grid_for(p, 8), 256, 0, s>>>(p, start.p, pcol.p, pvo.p, pval.p, M.bptr.p, nullptr,
+                                                       M.bcol.p, nullptr);
+      VB_LAUNCH_CHECK();
+      finish_offsets(M, s);
+      k_pool_to_vb<T><<<grid_for(p, 8), 256, 0, s>>>(p, start.p, pcol.p, pvo.p, pval.p, M.bptr.p, M.voff.p,
+                                                       M.bcol.p, M.val.p);
+      VB_LAUNCH_CHECK();
+    }
+    return;
+  }
+  fail(VB_ENOMEM, "vbarms_factor: last-level ILUT workspace could not be sized");
+}
+
+template void ilut_last<double>(LastDev<double>&, double, int, bool, double, uint64_t, cudaStream_t, int*);
+template void ilut_last<float>(LastDev<float>&, double, int, bool, double, uint64_t, cudaStream_t, int*);
+
+}  // namespace vb

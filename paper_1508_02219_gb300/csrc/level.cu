@@ -1,0 +1,949 @@
+// Steps 2-4 of VBARMS for one level on the GPU (Section 3, Eq. 4-8, and the
+// two-sweep implementation of Section 3.1).
+//
+//   A5  Step 2: row max-abs scaling, then column max-abs scaling of the row
+//       scaled matrix (column maxima by atomicMax on the IEEE bit patterns of
+//       non-negative doubles, which order like the values)
+//   A6  Step 3: weights w(Y) = ||A_YY||_F / sum_Z ||A_YZ||_F in a fixed order
+//       (one thread per supernode, no contraction), then the greedy independent
+//       set in (w desc, index asc) order as the lexicographically first MIS,
+//       decided in deterministic rounds; P_I puts D ascending, then C ascending
+//   A7  gather of D (pivot blocks), F, E, C and batched GEPP of the pivot
+//       blocks (one thread per block, the oracle's operation order)
+//   A8  W = L^{-1} P F, A9 G = E U^{-1}, each block tested against the drop
+//       rule and trimmed to lfil per block row
+//   A10 S = C - G W as a row-wise block SpGEMM: hashed symbolic union of the
+//       patterns of C and of the W rows reached from G, then the numeric
+//       accumulation in the order C, then G blocks ascending, then k
+//
+// FP64 kernels evaluate every product and sum as separate IEEE operations in
+// the oracle's order (the library is built without FMA contraction), so FP64
+// results match the CPU oracle bit for bit.  FP32 kernels use fused
+// multiply-adds.
+#include <algorithm>
+
+#include "internal.h"
+#include "level.cuh"
+#include "vbsr_ops.cuh"
+
+namespace vb {
+namespace {
+
+constexpr int LW = 8;           // warps per block
+constexpr int PAT_CAP = 1024;   // per-warp shared hash capacity
+constexpr int PAT_LIMIT = 640;
+
+template <typename T>
+__device__ __forceinline__ T msub(T acc, T a, T b);
+template <>
+__device__ __forceinline__ double msub<double>(double acc, double a, double b) {
+  return __dsub_rn(acc, __dmul_rn(a, b));
+}
+template <>
+__device__ __forceinline__ float msub<float>(float acc, float a, float b) {
+  return __fmaf_rn(-a, b, acc);
+}
+
+// ---- A5: Step 2 scaling ----------------------------------------------------
+template <typename TA>
+__global__ void k_rowmax(VBView<TA> A, double* __restrict__ r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < A.nbr; I += (int64_t)gridDim.x * wpb) {
+    const int m = A.rsz[I];
+    for (int a = lane; a < m; a += 32) {
+      double mx = 0.0;
+      for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
+        const int nc = A.csz[A.bcol[b]];
+        const TA* v = A.val + A.voff[b] + (int64_t)a * nc;
+        for (int j = 0; j < nc; ++j) mx = fmax(mx, fabs((double)v[j]));
+      }
+      r[A.roff[I] + a] = mx > 0.0 ? __ddiv_rn(1.0, mx) : 1.0;
+    }
+  }
+}
+
+template <typename TA>
+__global__ void k_colmax(VBView<TA> A, const double* __restrict__ r, unsigned long long* __restrict__ cmax) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < A.nbr; I += (int64_t)gridDim.x * wpb) {
+    const int m = A.rsz[I];
+    const int64_t r0 = A.roff[I];
+    for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
+      const int J = A.bcol[b];
+      const int nc = A.csz[J];
+      const int64_t c0 = A.coff[J];
+      const TA* v = A.val + A.voff[b];
+      for (int e = lane; e < m * nc; e += 32) {
+        const int a = e / nc, j = e - a * nc;
+        const double x = fabs(__dmul_rn(r[r0 + a], (double)v[e]));
+        atomicMax(&cmax[c0 + j], (unsigned long long)__double_as_longlong(x));
+      }
+    }
+  }
+}
+
+__global__ void k_colinv(int64_t n, const unsigned long long* __restrict__ cmax, double* __restrict__ c) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double x = __longlong_as_double((long long)cmax[j]);
+    c[j] = x > 0.0 ? __ddiv_rn(1.0, x) : 1.0;
+  }
+}
+
+template <typename TA>
+__global__ void k_apply_scale(VBView<TA> A, const double* __restrict__ r, const double* __restrict__ c) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < A.nbr; I += (int64_t)gridDim.x * wpb) {
+    const int m = A.rsz[I];
+    const int64_t r0 = A.roff[I];
+    for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
+      const int J = A.bcol[b];
+      const int nc = A.csz[J];
+      const int64_t c0 = A.coff[J];
+      TA* v = A.val + A.voff[b];
+      for (int e = lane; e < m * nc; e += 32) {
+        const int a = e / nc, j = e - a * nc;
+        v[e] = (TA)__dmul_rn(__dmul_rn(r[r0 + a], (double)v[e]), c[c0 + j]);
+      }
+    }
+  }
+}
+
+// ---- A6: Step 3 ----------------------------------------------------------
+template <typename TA>
+__global__ void k_weights(VBView<TA> A, double* __restrict__ w) {
+  for (int64_t Y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; Y < A.nbr; Y += (int64_t)gridDim.x * blockDim.x) {
+    double dsum = 0.0, diag = 0.0;
+    const int m = A.rsz[Y];
+    for (int64_t b = A.bptr[Y]; b < A.bptr[Y + 1]; ++b) {
+      const int nc = A.csz[A.bcol[b]];
+      const TA* v = A.val + A.voff[b];
+      double s = 0.0;
+      for (int e = 0; e < m * nc; ++e) {
+        const double x = (double)v[e];
+        s = __dadd_rn(s, __dmul_rn(x, x));
+      }
+      const double f = __dsqrt_rn(s);
+      dsum = __dadd_rn(dsum, f);
+      if (A.bcol[b] == Y) diag = f;
+    }
+    w[Y] = dsum > 0.0 ? __ddiv_rn(diag, dsum) : 0.0;
+  }
+}
+
+__global__ void k_tcount(int64_t nbr, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
+                         int32_t* __restrict__ tcnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < nbr; I += (int64_t)gridDim.x * wpb)
+    for (int64_t b = bptr[I] + lane; b < bptr[I + 1]; b += 32) atomicAdd(&tcnt[bcol[b]], 1);
+}
+
+__global__ void k_tfill(int64_t nbr, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
+                        const int64_t* __restrict__ tptr, int32_t* __restrict__ tfill, int32_t* __restrict__ trow) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < nbr; I += (int64_t)gridDim.x * wpb)
+    for (int64_t b = bptr[I] + lane; b < bptr[I + 1]; b += 32) {
+      const int32_t J = bcol[b];
+      trow[tptr[J] + atomicAdd(&tfill[J], 1)] = (int32_t)I;
+    }
+}
+
+__device__ __forceinline__ bool better(const double* w, int64_t u, int64_t v) {
+  return w[u] > w[v] || (w[u] == w[v] && u < v);
+}
+
+// state: 0 undecided, 1 in D, 2 out (this round), 3 out.
+__global__ void k_is_init(int64_t p, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
+                          const int64_t* __restrict__ tptr, const int32_t* __restrict__ trow,
+                          const double* __restrict__ w, double ddtol, int32_t* __restrict__ pending,
+                          int32_t* __restrict__ state, unsigned long long* remaining) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p; v += (int64_t)gridDim.x * blockDim.x) {
+    int cnt = 0;
+    for (int64_t b = bptr[v]; b < bptr[v + 1]; ++b) {
+      const int64_t u = bcol[b];
+      if (u != v && better(w, u, v)) ++cnt;
+    }
+    for (int64_t t = tptr[v]; t < tptr[v + 1]; ++t) {
+      const int64_t u = trow[t];
+      if (u != v && better(w, u, v)) ++cnt;
+    }
+    pending[v] = cnt;
+    if (w[v] < ddtol) {  // too weakly dominant: never a pivot (forced into C)
+      state[v] = 2;
+      atomicAdd(remaining, (unsigned long long)-1LL);
+    } else {
+      state[v] = 0;
+    }
+  }
+}
+
+__global__ void k_is_round_a(int64_t p, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
+                             const int64_t* __restrict__ tptr, const int32_t* __restrict__ trow,
+                             const int32_t* __restrict__ pending, int32_t* __restrict__ state,
+                             unsigned long long* remaining) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p; v += (int64_t)gridDim.x * blockDim.x) {
+    if (state[v] != 0 || pending[v] != 0) continue;
+    state[v] = 1;
+    long long dec = 1;
+    for (int64_t b = bptr[v]; b < bptr[v + 1]; ++b) {
+      const int32_t u = bcol[b];
+      if (u != v && atomicCAS(&state[u], 0, 2) == 0) ++dec;
+    }
+    for (int64_t t = tptr[v]; t < tptr[v + 1]; ++t) {
+      const int32_t u = trow[t];
+      if (u != v && atomicCAS(&state[u], 0, 2) == 0) ++dec;
+    }
+    atomicAdd(remaining, (unsigned long long)(-dec));
+  }
+}
+
+__global__ void k_is_round_b(int64_t p, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
+                             const int64_t* __restrict__ tptr, const int32_t* __restrict__ trow,
+                             const double* __restrict__ w, int32_t* __restrict__ pending,
+                             int32_t* __restrict__ state) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < p; u += (int64_t)gridDim.x * blockDim.x) {
+    if (state[u] != 2) continue;
+    state[u] = 3;
+    for (int64_t b = bptr[u]; b < bptr[u + 1]; ++b) {
+      const int64_t x = bcol[b];
+      if (x != u && better(w, u, x)) atomicSub(&pending[x], 1);
+    }
+    for (int64_t t = tptr[u]; t < tptr[u + 1]; ++t) {
+      const int64_t x = trow[t];
+      if (x != u && better(w, u, x)) atomicSub(&pending[x], 1);
+    }
+  }
+}
+
+__global__ void k_is_flags(int64_t p, const int32_t* __restrict__ state, int32_t* __restrict__ isD,
+                           int32_t* __restrict__ isC) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p; v += (int64_t)gridDim.x * blockDim.x) {
+    const bool d = state[v] == 1;
+    isD[v] = d ? 1 : 0;
+    isC[v] = d ? 0 : 1;
+  }
+}
+
+__global__ void k_is_positions(int64_t p, const int32_t* __restrict__ isD, const int64_t* __restrict__ scanD,
+                               const int64_t* __restrict__ scanC, int64_t nD, int32_t* __restrict__ newpos,
+                               int32_t* __restrict__ pI) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = isD[v] ? scanD[v] : nD + scanC[v];
+    newpos[v] = (int32_t)k;
+    pI[k] = (int32_t)v;
+  }
+}
+
+__global__ void k_perm_sizes(int64_t p, const int32_t* __restrict__ pI, const int32_t* __restrict__ rsz,
+                             int32_t* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = rsz[pI[k]];
+}
+
+// ---- A7: gather of D, F, E, C -----------------------------------------------
+// PASS 0: counts per part row; PASS 1: bcol of every part and the source block
+// of every destination block.
+template <int PASS>
+__global__ void k_gather(int64_t p, int64_t nD, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
+                         const int32_t* __restrict__ newpos, int64_t* __restrict__ cntF, int64_t* __restrict__ cntE,
+                         int64_t* __restrict__ cntC, const int64_t* __restrict__ pF, const int64_t* __restrict__ pE,
+                         const int64_t* __restrict__ pC, int32_t* __restrict__ colF, int32_t* __restrict__ colE,
+                         int32_t* __restrict__ colC, int64_t* __restrict__ srcD, int64_t* __restrict__ srcF,
+                         int64_t* __restrict__ srcE, int64_t* __restrict__ srcC, int* st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t Y = blockIdx.x * wpb + (threadIdx.x >> 5); Y < p; Y += (int64_t)gridDim.x * wpb) {
+    const int64_t k = newpos[Y];
+    const bool rowD = k < nD;
+    int64_t baseX = 0, baseY = 0;  // running destinations: rowD: F ; else: E (X) and C (Y)
+    if (PASS == 1) {
+      if (rowD)
+        baseX = pF[k];
+      else {
+        baseX = pE[k - nD];
+        baseY = pC[k - nD];
+      }
+    }
+    int cX = 0, cY = 0, diag = 0;
+    for (int64_t b0 = bptr[Y]; b0 < bptr[Y + 1]; b0 += 32) {
+      const int64_t b = b0 + lane;
+      const bool valid = b < bptr[Y + 1];
+      int32_t Z = valid ? bcol[b] : -1;
+      const int64_t nz = valid ? newpos[Z] : -1;
+      const bool colD = valid && nz < nD;
+      const bool isdiag = valid && Z == Y;
+      bool toX, toY;
+      if (rowD) {
+        toX = valid && !colD;  // F
+        toY = false;
+        if (valid && colD && !isdiag) dev_fail(st, DEV_INTERNAL);  // D supernodes are uncoupled
+        if (isdiag && PASS == 1) srcD[k] = b;
+        diag += isdiag ? 1 : 0;
+      } else {
+        toX = colD;             // E
+        toY = valid && !colD;   // C
+      }
+      const unsigned mX = __ballot_sync(0xffffffffu, toX), mY = __ballot_sync(0xffffffffu, toY);
+      if (PASS == 1) {
+        const unsigned lt = (1u << lane) - 1u;
+        if (toX) {
+          const int64_t d = baseX + __popc(mX & lt);
+          if (rowD) {
+            colF[d] = (int32_t)(nz - nD);
+            srcF[d] = b;
+          } else {
+            colE[d] = (int32_t)nz;
+            srcE[d] = b;
+          }
+        }
+        if (toY) {
+          const int64_t d = baseY + __popc(mY & lt);
+          colC[d] = (int32_t)(nz - nD);
+          srcC[d] = b;
+        }
+        baseX += __popc(mX);
+        baseY += __popc(mY);
+      }
+      cX += __popc(mX);
+      cY += __popc(mY);
+    }
+    diag = warp_sum_i(diag);
+    if (PASS == 0 && lane == 0) {
+      if (rowD) {
+        cntF[k] = cX;
+        if (diag != 1) dev_fail(st, DEV_ESINGULAR);  // a missing pivot block is zero
+      } else {
+        cntE[k - nD] = cX;
+        cntC[k - nD] = cY;
+      }
+    }
+  }
+}
+
+template <typename TS, typename TD>
+__global__ void k_copy_blocks(int64_t nblocks, const int64_t* __restrict__ src, const int64_t* __restrict__ svoff,
+                              const TS* __restrict__ sval, const int64_t* __restrict__ dvoff, TD* __restrict__ dval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t d = blockIdx.x * wpb + (threadIdx.x >> 5); d < nblocks; d += (int64_t)gridDim.x * wpb) {
+    const int64_t b = src[d];
+    const int64_t n = svoff[b + 1] - svoff[b];
+    for (int64_t e = lane; e < n; e += 32) dval[dvoff[d] + e] = (TD)sval[svoff[b] + e];
+  }
+}
+
+// ---- A7: batched GEPP ------------------------------------------------------
+constexpr int KAPPA_MAX = 64;  // largest block given a condition estimate
+
+__global__ void k_gepp(int64_t nD, const int32_t* __restrict__ sz, const int64_t* __restrict__ roff,
+                       const int64_t* __restrict__ voff, double* __restrict__ val, int32_t* __restrict__ piv,
+                       int mixed, double cond_thr, int32_t* __restrict__ ptag, float* __restrict__ val32, int* st) {
+  for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < nD; y += (int64_t)gridDim.x * blockDim.x) {
+    const int m = sz[y];
+    double* a = val + voff[y];
+    int32_t* pv = piv + roff[y];
+    double norm1 = 0.0;
+    if (mixed) {
+      for (int j = 0; j < m; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += fabs(a[i * m + j]);
+        norm1 = fmax(norm1, s);
+      }
+    }
+    bool singular = false;
+    for (int k = 0; k < m; ++k) {
+      int p = k;
+      double best = fabs(a[k * m + k]);
+      for (int i = k + 1; i < m; ++i) {
+        const double v = fabs(a[i * m + k]);
+        if (v > best) {
+          best = v;
+          p = i;
+        }
+      }
+      if (best == 0.0) {
+        singular = true;
+        break;
+      }
+      pv[k] = p;
+      if (p != k)
+        for (int j = 0; j < m; ++j) {
+          const double t = a[k * m + j];
+          a[k * m + j] = a[p * m + j];
+          a[p * m + j] = t;
+        }
+      const double d = a[k * m + k];
+      for (int i = k + 1; i < m; ++i) {
+        const double l = __ddiv_rn(a[i * m + k], d);
+        a[i * m + k] = l;
+        for (int j = k + 1; j < m; ++j) a[i * m + j] = __dsub_rn(a[i * m + j], __dmul_rn(l, a[k * m + j]));
+      }
+    }
+    if (singular) {
+      dev_fail(st, DEV_ESINGULAR);
+      continue;
+    }
+    if (mixed) {
+      int tag = 1;
+      if (m <= KAPPA_MAX) {
+        // ||D^{-1}||_1 from the explicit inverse columns
+        double inv1 = 0.0;
+        double x[KAPPA_MAX];
+        for (int j = 0; j < m; ++j) {
+          for (int i = 0; i < m; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+          for (int k = 0; k < m; ++k)
+            if (pv[k] != k) {
+              const double t = x[k];
+              x[k] = x[pv[k]];
+              x[pv[k]] = t;
+            }
+          for (int i = 1; i < m; ++i)
+            for (int k = 0; k < i; ++k) x[i] -= a[i * m + k] * x[k];
+          for (int i = m - 1; i >= 0; --i) {
+            double s = x[i];
+            for (int k = i + 1; k < m; ++k) s -= a[i * m + k] * x[k];
+            x[i] = s / a[i * m + i];
+          }
+          double cs = 0.0;
+          for (int i = 0; i < m; ++i) cs += fabs(x[i]);
+          inv1 = fmax(inv1, cs);
+        }
+        tag = (norm1 * inv1 > cond_thr) ? 1 : 0;
+      }
+      ptag[y] = tag;
+      for (int e = 0; e < m * m; ++e) val32[voff[y] + e] = (float)a[e];
+    }
+  }
+}
+
+// ---- A8 / A9: W = L^{-1} P F and G = E U^{-1} -----------------------------
+// Each lane owns one block of its warp's block row.  X is computed in place
+// in a copy of F (resp. E).  The FP32 path uses the FP32 LU unless the pivot
+// block is tagged FP64, then it promotes the block to FP64.
+template <typename T, typename TL>
+__device__ void linvp_block(const TL* lu, const int32_t* pv, int m, T* x, int n) {
+  for (int k = 0; k < m; ++k)
+    if (pv[k] != k)
+      for (int j = 0; j < n; ++j) {
+        const T t = x[k * n + j];
+        x[k * n + j] = x[pv[k] * n + j];
+        x[pv[k] * n + j] = t;
+      }
+  for (int i = 1; i < m; ++i)
+    for (int k = 0; k < i; ++k) {
+      const TL l = lu[i * m + k];
+      for (int j = 0; j < n; ++j) x[i * n + j] = (T)msub<TL>((TL)x[i * n + j], l, (TL)x[k * n + j]);
+    }
+}
+
+template <typename T, typename TL>
+__device__ void uinv_right_block(const TL* lu, int m, T* x, int r) {
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < m; ++j) {
+      TL s = (TL)x[i * m + j];
+      for (int k = 0; k < j; ++k) s = msub<TL>(s, (TL)x[i * m + k], lu[k * m + j]);
+      x[i * m + j] = (T)(s / lu[j * m + j]);
+    }
+}
+
+__device__ __forceinline__ double fro2_d(const double* v, int n) {
+  double s = 0.0;
+  for (int e = 0; e < n; ++e) s = __dadd_rn(s, __dmul_rn(v[e], v[e]));
+  return s;
+}
+__device__ __forceinline__ double fro2_d(const float* v, int n) {
+  double s = 0.0;
+  for (int e = 0; e < n; ++e) {
+    const double x = (double)v[e];
+    s = __dadd_rn(s, __dmul_rn(x, x));
+  }
+  return s;
+}
+
+__device__ __forceinline__ bool drop_rule(double f2, int m, int n, double t) {
+  const double thr = __dmul_rn(__dmul_rn(t, (double)m), (double)n);
+  return f2 < __dmul_rn(thr, thr);
+}
+
+// WHICH = 0: W rows (D nodes) from F; WHICH = 1: G rows (C nodes) from E.
+template <typename T, int WHICH>
+__global__ void k_wg_cand(VBView<T> X, const int32_t* __restrict__ dsz, const int64_t* __restrict__ droff,
+                          const int64_t* __restrict__ dvoff, const double* __restrict__ dval,
+                          const float* __restrict__ dval32, const int32_t* __restrict__ piv,
+                          const int32_t* __restrict__ ptag, double t, double* __restrict__ f2,
+                          int8_t* __restrict__ keep) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t R = blockIdx.x * wpb + (threadIdx.x >> 5); R < X.nbr; R += (int64_t)gridDim.x * wpb) {
+    const int mr = X.rsz[R];
+    for (int64_t b = X.bptr[R] + lane; b < X.bptr[R + 1]; b += 32) {
+      const int32_t Cc = X.bcol[b];
+      const int nc = X.csz[Cc];
+      T* x = X.val + X.voff[b];
+      const int64_t y = WHICH == 0 ? R : Cc;  // pivot block used
+      const int m = dsz[y];
+      const bool use64 = (sizeof(T) == sizeof(double)) || (ptag && ptag[y]);
+      if (WHICH == 0) {
+        if (use64)
+          linvp_block<T, double>(dval + dvoff[y], piv + droff[y], m, x, nc);
+        else
+          linvp_block<T, float>(dval32 + dvoff[y], piv + droff[y], m, x, nc);
+      } else {
+        if (use64)
+          uinv_right_block<T, double>(dval + dvoff[y], m, x, mr);
+        else
+          uinv_right_block<T, float>(dval32 + dvoff[y], m, x, mr);
+      }
+      const double f = fro2_d(x, mr * nc);
+      f2[b] = f;
+      keep[b] = drop_rule(f, mr, nc, t) ? 0 : 1;
+    }
+  }
+}
+
+// Keep at most lfil blocks per row among the kept ones: largest f2, lower
+// column on ties (one thread per block row, repeated selection).
+__global__ void k_lfil(int64_t nbr, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
+                       const double* __restrict__ f2, int8_t* __restrict__ keep, int lfil, int32_t skip_col_is_row) {
+  for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < nbr; R += (int64_t)gridDim.x * blockDim.x) {
+    int cnt = 0;
+    for (int64_t b = bptr[R]; b < bptr[R + 1]; ++b) cnt += keep[b] && !(skip_col_is_row && bcol[b] == R);
+    if (cnt <= lfil) continue;
+    // mark the lfil largest with keep = 2, then clear the remaining 1s
+    for (int sel = 0; sel < lfil; ++sel) {
+      int64_t best = -1;
+      for (int64_t b = bptr[R]; b < bptr[R + 1]; ++b) {
+        if (keep[b] != 1 || (skip_col_is_row && bcol[b] == R)) continue;
+        if (best < 0 || f2[b] > f2[best] || (f2[b] == f2[best] && bcol[b] < bcol[best])) best = b;
+      }
+      if (best < 0) break;
+      keep[best] = 2;
+    }
+    for (int64_t b = bptr[R]; b < bptr[R + 1]; ++b) {
+      if (skip_col_is_row && bcol[b] == R) continue;
+      keep[b] = keep[b] == 2 ? 1 : 0;
+    }
+  }
+}
+
+// ---- A10: Schur complement S = C - G W ---------------------------------------
+// Pattern: per C row r, the union of C's columns and of the columns of the W
+// rows Y with G_rY stored.  PASS 0 counts, PASS 1 writes them ascending.
+template <bool GLOBAL, int PASS>
+__global__ void __launch_bounds__(LW * 32)
+    k_schur_pattern(int64_t nrows, const int32_t* __restrict__ list, const int64_t* __restrict__ Cbptr,
+                    const int32_t* __restrict__ Cbcol, const int64_t* __restrict__ Gbptr,
+                    const int32_t* __restrict__ Gbcol, const int64_t* __restrict__ Wbptr,
+                    const int32_t* __restrict__ Wbcol, int* gtab, uint32_t gcap, int64_t* __restrict__ cnt,
+                    const int64_t* __restrict__ Sbptr, int32_t* __restrict__ Sbcol, int32_t* __restrict__ heavy,
+                    int* nheavy, int* st) {
+  extern __shared__ int smem[];
+  __shared__ int nfresh[LW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* keys;
+  uint32_t cap;
+  int limit;
+  if (GLOBAL) {
+    keys = gtab + ((size_t)blockIdx.x * LW + warp) * gcap;
+    cap = gcap;
+    limit = (int)gcap;
+  } else {
+    keys = smem + warp * PAT_CAP;
+    cap = PAT_CAP;
+    limit = PAT_LIMIT;
+  }
+  for (int64_t t = (int64_t)blockIdx.x * LW + warp; t < nrows; t += (int64_t)gridDim.x * LW) {
+    const int64_t r = list ? list[t] : t;
+    for (uint32_t k = lane; k < cap; k += 32) keys[k] = -1;
+    if (lane == 0) nfresh[warp] = 0;
+    __syncwarp();
+    bool full = false;
+    for (int64_t b = Cbptr[r] + lane; b < Cbptr[r + 1]; b += 32) {
+      bool fresh;
+      if (hset_insert(keys, cap - 1, Cbcol[b], &fresh) < 0) {
+        full = true;
+        break;
+      }
+      if (fresh) atomicAdd(&nfresh[warp], 1);
+    }
+    __syncwarp();
+    bool over = __any_sync(0xffffffffu, full) || *((volatile int*)&nfresh[warp]) > limit;
+    for (int64_t g = Gbptr[r]; g < Gbptr[r + 1] && !over; ++g) {
+      const int32_t Y = Gbcol[g];
+      for (int64_t b = Wbptr[Y] + lane; b < Wbptr[Y + 1]; b += 32) {
+        bool fresh;
+        if (hset_insert(keys, cap - 1, Wbcol[b], &fresh) < 0) {
+          full = true;
+          break;
+        }
+        if (fresh) atomicAdd(&nfresh[warp], 1);
+      }
+      __syncwarp();
+      over = __any_sync(0xffffffffu, full) || *((volatile int*)&nfresh[warp]) > limit;
+    }
+    if (over) {
+      if (lane == 0) {
+        if (GLOBAL)
+          dev_fail(st, DEV_INTERNAL);
+        else if (PASS == 0)
+          heavy[atomicAdd(nheavy, 1)] = (int32_t)r;
+      }
+      __syncwarp();
+      continue;
+    }
+    const int nf = *((volatile int*)&nfresh[warp]);
+    if (PASS == 0) {
+      if (lane == 0) cnt[r] = nf;
+    } else {
+      int base = 0;
+      for (uint32_t k0 = 0; k0 < cap; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        const int key = k < cap ? keys[k] : -1;
+        const unsigned bm = __ballot_sync(0xffffffffu, key >= 0);
+        __syncwarp();
+        if (key >= 0) keys[base + __popc(bm & ((1u << lane) - 1u))] = key;
+        base += __popc(bm);
+        __syncwarp();
+      }
+      const int64_t out = Sbptr[r];
+      for (int a = lane; a < nf; a += 32) {
+        const int key = keys[a];
+        int rank = 0;
+        for (int q = 0; q < nf; ++q) rank += keys[q] < key ? 1 : 0;
+        Sbcol[out + rank] = key;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Numeric phase, one warp per block row r of S.  Every element receives its
+// updates in the oracle's order: C value, then the G blocks ascending, each
+// contributing its k terms in order.
+template <typename T>
+__global__ void __launch_bounds__(LW * 32)
+    k_schur_numeric(VBView<T> C, VBView<T> G, VBView<T> W, VBView<T> S) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < S.nbr; r += (int64_t)gridDim.x * wpb) {
+    const int nr = S.rsz[r];
+    const int64_t s0 = S.bptr[r], s1 = S.bptr[r + 1];
+    for (int64_t q = s0; q < s1; ++q) {
+      const int32_t J = S.bcol[q];
+      const int64_t cb = bsearch_i32(C.bcol, C.bptr[r], C.bptr[r + 1], J);
+      const int n = nr * S.csz[J];
+      T* dst = S.val + S.voff[q];
+      for (int e = lane; e < n; e += 32) dst[e] = cb >= 0 ? C.val[C.voff[cb] + e] : (T)0;
+    }
+    __syncwarp();
+    for (int64_t g = G.bptr[r]; g < G.bptr[r + 1]; ++g) {
+      const int32_t Y = G.bcol[g];
+      const int m = G.csz[Y];
+      const T* gb = G.val + G.voff[g];
+      for (int64_t wb = W.bptr[Y]; wb < W.bptr[Y + 1]; ++wb) {
+        const int32_t sc = W.bcol[wb];
+        const int ns = W.csz[sc];
+        const int64_t q = bsearch_i32(S.bcol, s0, s1, sc);
+        if (q < 0) continue;  // cannot happen: the symbolic phase put every W column in the row
+        const T* wv = W.val + W.voff[wb];
+        T* dst = S.val + S.voff[q];
+        for (int e = lane; e < nr * ns; e += 32) {
+          const int i = e / ns, j = e - i * ns;
+          T acc = dst[e];
+          for (int k = 0; k < m; ++k) acc = msub<T>(acc, gb[i * m + k], wv[k * ns + j]);
+          dst[e] = acc;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Last reduction: drop off-diagonal blocks of S below the threshold.
+template <typename T>
+__global__ void k_schur_drop(VBView<T> S, double t, int8_t* __restrict__ keep) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < S.nbr; r += (int64_t)gridDim.x * wpb) {
+    const int nr = S.rsz[r];
+    for (int64_t b = S.bptr[r] + lane; b < S.bptr[r + 1]; b += 32) {
+      const int32_t J = S.bcol[b];
+      const int nc = S.csz[J];
+      keep[b] = (J == r || !drop_rule(fro2_d(S.val + S.voff[b], nr * nc), nr, nc, t)) ? 1 : 0;
+    }
+  }
+}
+
+}  // namespace
+
+// ============================================================================
+template <typename TA>
+void scale_level_t(VBDev<TA>& A, DBuf<double>& r, DBuf<double>& c, cudaStream_t s) {
+  const int64_t n = A.nbr ? d2h(A.roff.p + A.nbr, s) : 0;
+  r.alloc(n, s);
+  c.alloc(n, s);
+  if (!A.nbr) return;
+  DBuf<unsigned long long> cmax(n, s);
+  cmax.zero();
+  const unsigned g = grid_for(A.nbr, LW);
+  k_rowmax<TA><<<g, LW * 32, 0, s>>>(A.view(), r.p);
+  VB_LAUNCH_CHECK();
+  k_colmax<TA><<<g, LW * 32, 0, s>>>(A.view(), r.p, cmax.p);
+  VB_LAUNCH_CHECK();
+  k_colinv<<<grid_for(n, 256), 256, 0, s>>>(n, cmax.p, c.p);
+  VB_LAUNCH_CHECK();
+  k_apply_scale<TA><<<g, LW * 32, 0, s>>>(A.view(), r.p, c.p);
+  VB_LAUNCH_CHECK();
+}
+template void scale_level_t<double>(VBDev<double>&, DBuf<double>&, DBuf<double>&, cudaStream_t);
+template void scale_level_t<float>(VBDev<float>&, DBuf<double>&, DBuf<double>&, cudaStream_t);
+
+void scale_level(VBDev<double>& A, DBuf<double>& r, DBuf<double>& c, cudaStream_t s) { scale_level_t(A, r, c, s); }
+
+template <typename TA>
+int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t>& pI, DBuf<int32_t>& newpos,
+                 cudaStream_t s) {
+  const int64_t p = A.nbr;
+  w.alloc(p, s);
+  pI.alloc(p, s);
+  newpos.alloc(p, s);
+  if (!p) return 0;
+  const unsigned g = grid_for(p, 256);
+  k_weights<TA><<<g, 256, 0, s>>>(A.view(), w.p);
+  VB_LAUNCH_CHECK();
+  DBuf<int32_t> tcnt(p, s), trow(A.nnzb, s), pending(p, s), state(p, s);
+  DBuf<int64_t> tptr(p + 1, s);
+  tcnt.zero();
+  const unsigned gw = grid_for(p, LW);
+  k_tcount<<<gw, LW * 32, 0, s>>>(p, A.bptr.p, A.bcol.p, tcnt.p);
+  VB_LAUNCH_CHECK();
+  scan_i32_to_i64(tcnt.p, tptr.p, p, s);
+  tcnt.zero();
+  k_tfill<<<gw, LW * 32, 0, s>>>(p, A.bptr.p, A.bcol.p, tptr.p, tcnt.p, trow.p);
+  VB_LAUNCH_CHECK();
+  DBuf<unsigned long long> remaining(1, s);
+  {
+    unsigned long long pp = (unsigned long long)p;
+    h2d(remaining.p, &pp, 1, s);
+  }
+  k_is_init<<<g, 256, 0, s>>>(p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, ddtol, pending.p, state.p, remaining.p);
+  VB_LAUNCH_CHECK();
+  for (int64_t round = 0;; ++round) {
+    k_is_round_b<<<g, 256, 0, s>>>(p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, pending.p, state.p);
+    VB_LAUNCH_CHECK();
+    k_is_round_a<<<g, 256, 0, s>>>(p, A.bptr.p, A.bcol.p, tptr.p, trow.p, pending.p, state.p, remaining.p);
+    VB_LAUNCH_CHECK();
+    if (round < 4 || (round & 3) == 3)
+      if (d2h(remaining.p, s) == 0) break;
+    if (round > p + 8) fail(VB_EINTERNAL, "independent-set rounds did not terminate");
+  }
+  DBuf<int32_t> isD(p, s), isC(p, s);
+  k_is_flags<<<g, 256, 0, s>>>(p, state.p, isD.p, isC.p);
+  VB_LAUNCH_CHECK();
+  DBuf<int64_t> scanD(p + 1, s), scanC(p + 1, s);
+  scan_i32_to_i64(isD.p, scanD.p, p, s);
+  scan_i32_to_i64(isC.p, scanC.p, p, s);
+  const int64_t nD = d2h(scanD.p + p, s);
+  k_is_positions<<<g, 256, 0, s>>>(p, isD.p, scanD.p, scanC.p, nD, newpos.p, pI.p);
+  VB_LAUNCH_CHECK();
+  return nD;
+}
+template int64_t is_order<double>(const VBDev<double>&, double, DBuf<double>&, DBuf<int32_t>&, DBuf<int32_t>&,
+                                  cudaStream_t);
+template int64_t is_order<float>(const VBDev<float>&, double, DBuf<double>&, DBuf<int32_t>&, DBuf<int32_t>&,
+                                 cudaStream_t);
+
+template <typename TA, typename T>
+void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_t>& newpos, int64_t nD,
+                  LevelDev<T>& L, cudaStream_t s, int* dst) {
+  const int64_t p = A.nbr, nC = p - nD;
+  L.nD = nD;
+  L.nC = nC;
+  DBuf<int32_t> psz(p, s);
+  k_perm_sizes<<<grid_for(p, 256), 256, 0, s>>>(p, pI.p, A.rsz.p, psz.p);
+  VB_LAUNCH_CHECK();
+  const int32_t* szD = psz.p;
+  const int32_t* szC = psz.p + nD;
+  set_partitions(L.D, szD, nD, szD, nD, s);
+  set_partitions(L.F, szD, nD, szC, nC, s);
+  set_partitions(L.E, szC, nC, szD, nD, s);
+  set_partitions(L.C, szC, nC, szC, nC, s);
+  DBuf<int64_t> cF(nD, s), cE(nC, s), cC(nC, s);
+  const unsigned gw = grid_for(p, LW);
+  k_gather<0><<<gw, LW * 32, 0, s>>>(p, nD, A.bptr.p, A.bcol.p, newpos.p, cF.p, cE.p, cC.p, nullptr, nullptr,
+                                     nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, dst);
+  VB_LAUNCH_CHECK();
+  check_status(dst, s, "vbarms_factor: gather");
+  L.F.bptr.alloc(nD + 1, s);
+  L.E.bptr.alloc(nC + 1, s);
+  L.C.bptr.alloc(nC + 1, s);
+  scan_i64(cF.p, L.F.bptr.p, nD, s);
+  scan_i64(cE.p, L.E.bptr.p, nC, s);
+  scan_i64(cC.p, L.C.bptr.p, nC, s);
+  const int64_t nF = d2h(L.F.bptr.p + nD, s), nE = d2h(L.E.bptr.p + nC, s), nCC = d2h(L.C.bptr.p + nC, s);
+  L.F.bcol.alloc(nF, s);
+  L.E.bcol.alloc(nE, s);
+  L.C.bcol.alloc(nCC, s);
+  // D: one block per row, column = row
+  {
+    std::vector<int64_t> hb(nD + 1);
+    std::vector<int32_t> hc(nD);
+    for (int64_t k = 0; k <= nD; ++k) hb[k] = k;
+    for (int64_t k = 0; k < nD; ++k) hc[k] = (int32_t)k;
+    L.D.bptr.alloc(nD + 1, s);
+    L.D.bcol.alloc(nD, s);
+    h2d(L.D.bptr.p, hb.data(), nD + 1, s);
+    h2d(L.D.bcol.p, hc.data(), nD, s);
+    VB_CUDA(cudaStreamSynchronize(s));
+  }
+  DBuf<int64_t> sD(nD, s), sF(nF, s), sE(nE, s), sC(nCC, s);
+  k_gather<1><<<gw, LW * 32, 0, s>>>(p, nD, A.bptr.p, A.bcol.p, newpos.p, nullptr, nullptr, nullptr, L.F.bptr.p,
+                                     L.E.bptr.p, L.C.bptr.p, L.F.bcol.p, L.E.bcol.p, L.C.bcol.p, sD.p, sF.p, sE.p,
+                                     sC.p, dst);
+  VB_LAUNCH_CHECK();
+  finish_offsets(L.D, s);
+  finish_offsets(L.F, s);
+  finish_offsets(L.E, s);
+  finish_offsets(L.C, s);
+  if (nD) k_copy_blocks<TA, double><<<grid_for(nD, LW), LW * 32, 0, s>>>(nD, sD.p, A.voff.p, A.val.p, L.D.voff.p, L.D.val.p);
+  if (nF) k_copy_blocks<TA, T><<<grid_for(nF, LW), LW * 32, 0, s>>>(nF, sF.p, A.voff.p, A.val.p, L.F.voff.p, L.F.val.p);
+  if (nE) k_copy_blocks<TA, T><<<grid_for(nE, LW), LW * 32, 0, s>>>(nE, sE.p, A.voff.p, A.val.p, L.E.voff.p, L.E.val.p);
+  if (nCC) k_copy_blocks<TA, T><<<grid_for(nCC, LW), LW * 32, 0, s>>>(nCC, sC.p, A.voff.p, A.val.p, L.C.voff.p, L.C.val.p);
+  VB_LAUNCH_CHECK();
+  check_status(dst, s, "vbarms_factor: gather");
+}
+
+void pivot_lu(VBDev<double>& D, DBuf<int32_t>& piv, DBuf<int32_t>& ptag, VBDev<float>& D32, bool mixed,
+              double cond_thr, cudaStream_t s, int* dst) {
+  const int64_t nD = D.nbr;
+  const int64_t nsc = nD ? d2h(D.roff.p + nD, s) : 0;
+  piv.alloc(nsc, s);
+  ptag.alloc(nD, s);
+  if (mixed) {
+    copy_vb<float, double>(D, D32, s);
+  }
+  if (nD) {
+    k_gepp<<<grid_for(nD, 128), 128, 0, s>>>(nD, D.rsz.p, D.roff.p, D.voff.p, D.val.p, piv.p, mixed ? 1 : 0,
+                                             cond_thr, ptag.p, mixed ? D32.val.p : nullptr, dst);
+    VB_LAUNCH_CHECK();
+  }
+  check_status(dst, s, "vbarms_factor: pivot LU");
+}
+
+template <typename T>
+void w_or_g(const VBDev<T>& X, int which, const VBDev<double>& D, const VBDev<float>& D32, const DBuf<int32_t>& piv,
+            const DBuf<int32_t>& ptag, bool mixed, double t, int lfil, VBDev<T>& out, cudaStream_t s) {
+  VBDev<T> cand;
+  copy_vb<T, T>(X, cand, s);
+  DBuf<double> f2(cand.nnzb, s);
+  DBuf<int8_t> keep(cand.nnzb, s);
+  if (cand.nbr && cand.nnzb) {
+    const unsigned g = grid_for(cand.nbr, LW);
+    if (which == 0)
+      k_wg_cand<T, 0><<<g, LW * 32, 0, s>>>(cand.view(), D.rsz.p, D.roff.p, D.voff.p, D.val.p,
+                                            mixed ? D32.val.p : nullptr, piv.p, mixed ? ptag.p : nullptr, t, f2.p,
+                                            keep.p);
+    else
+      k_wg_cand<T, 1><<<g, LW * 32, 0, s>>>(cand.view(), D.rsz.p, D.roff.p, D.voff.p, D.val.p,
+                                            mixed ? D32.val.p : nullptr, piv.p, mixed ? ptag.p : nullptr, t, f2.p,
+                                            keep.p);
+    VB_LAUNCH_CHECK();
+    if (lfil >= 0) {
+      k_lfil<<<grid_for(cand.nbr, 128), 128, 0, s>>>(cand.nbr, cand.bptr.p, cand.bcol.p, f2.p, keep.p, lfil, 0);
+      VB_LAUNCH_CHECK();
+    }
+  }
+  compact_blocks(cand, keep.p, out, s);
+}
+
+template <typename T>
+void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_reduction, double t, VBDev<T>& S,
+           cudaStream_t s, int* dst) {
+  const int64_t nC = C.nbr;
+  VBDev<T> Sf;
+  set_partitions(Sf, C.rsz.p, nC, C.rsz.p, nC, s);
+  Sf.bptr.alloc(nC + 1, s);
+  DBuf<int64_t> cnt(nC, s);
+  DBuf<int32_t> heavy(std::max<int64_t>(nC, 1), s);
+  DBuf<int> nheavy(1, s);
+  nheavy.zero();
+  const size_t smem = (size_t)LW * PAT_CAP * sizeof(int);
+  VB_CUDA(cudaFuncSetAttribute(k_schur_pattern<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VB_CUDA(cudaFuncSetAttribute(k_schur_pattern<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned gl = grid_for(nC, LW, 152LL * 24);
+  if (nC) {
+    k_schur_pattern<false, 0><<<gl, LW * 32, smem, s>>>(nC, nullptr, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
+                                                        W.bptr.p, W.bcol.p, nullptr, 0, cnt.p, nullptr, nullptr,
+                                                        heavy.p, nheavy.p, dst);
+    VB_LAUNCH_CHECK();
+  }
+  const int nh = d2h(nheavy.p, s);
+  uint32_t gcap = 0;
+  int64_t hb = 0;
+  DBuf<int> gtab;
+  if (nh > 0) {
+    gcap = 1024;
+    while ((int64_t)gcap < 2 * nC + 64) gcap <<= 1;
+    int64_t warps = std::max<int64_t>(1, (256LL << 20) / ((int64_t)gcap * 4));
+    warps = std::min<int64_t>(warps, nh);
+    hb = (warps + LW - 1) / LW;
+    gtab.alloc((size_t)hb * LW * gcap, s);
+    k_schur_pattern<true, 0><<<(unsigned)hb, LW * 32, 0, s>>>(nh, heavy.p, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
+                                                             W.bptr.p, W.bcol.p, gtab.p, gcap, cnt.p, nullptr,
+                                                             nullptr, nullptr, nullptr, dst);
+    VB_LAUNCH_CHECK();
+  }
+  check_status(dst, s, "vbarms_factor: Schur pattern");
+  scan_i64(cnt.p, Sf.bptr.p, nC, s);
+  Sf.nnzb = nC ? d2h(Sf.bptr.p + nC, s) : 0;
+  Sf.bcol.alloc(Sf.nnzb, s);
+  if (nC) {
+    k_schur_pattern<false, 1><<<gl, LW * 32, smem, s>>>(nC, nullptr, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
+                                                        W.bptr.p, W.bcol.p, nullptr, 0, nullptr, Sf.bptr.p,
+                                                        Sf.bcol.p, nullptr, nullptr, dst);
+    VB_LAUNCH_CHECK();
+  }
+  if (nh > 0) {
+    k_schur_pattern<true, 1><<<(unsigned)hb, LW * 32, 0, s>>>(nh, heavy.p, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
+                                                             W.bptr.p, W.bcol.p, gtab.p, gcap, nullptr, Sf.bptr.p,
+                                                             Sf.bcol.p, nullptr, nullptr, dst);
+    VB_LAUNCH_CHECK();
+  }
+  check_status(dst, s, "vbarms_factor: Schur pattern");
+  finish_offsets(Sf, s);
+  if (nC) {
+    k_schur_numeric<T><<<grid_for(nC, LW, 152LL * 32), LW * 32, 0, s>>>(C.view(), G.view(), W.view(), Sf.view());
+    VB_LAUNCH_CHECK();
+  }
+  if (last_reduction && nC) {
+    DBuf<int8_t> keep(Sf.nnzb, s);
+    k_schur_drop<T><<<grid_for(nC, LW), LW * 32, 0, s>>>(Sf.view(), t, keep.p);
+    VB_LAUNCH_CHECK();
+    compact_blocks(Sf, keep.p, S, s);
+  } else {
+    S = std::move(Sf);
+  }
+}
+
+#define VB_LEVEL_INST(TA, T)                                                                                     \
+  template void gather_parts<TA, T>(const VBDev<TA>&, const DBuf<int32_t>&, const DBuf<int32_t>&, int64_t,     \
+                                    LevelDev<T>&, cudaStream_t, int*);
+VB_LEVEL_INST(double, double)
+VB_LEVEL_INST(double, float)
+VB_LEVEL_INST(float, float)
+template void w_or_g<double>(const VBDev<double>&, int, const VBDev<double>&, const VBDev<float>&,
+                             const DBuf<int32_t>&, const DBuf<int32_t>&, bool, double, int, VBDev<double>&,
+                             cudaStream_t);
+template void w_or_g<float>(const VBDev<float>&, int, const VBDev<double>&, const VBDev<float>&,
+                            const DBuf<int32_t>&, const DBuf<int32_t>&, bool, double, int, VBDev<float>&,
+                            cudaStream_t);
+template void schur<double>(const VBDev<double>&, const VBDev<double>&, const VBDev<double>&, bool, double,
+                            VBDev<double>&, cudaStream_t, int*);
+template void schur<float>(const VBDev<float>&, const VBDev<float>&, const VBDev<float>&, bool, double,
+                           VBDev<float>&, cudaStream_t, int*);
+
+}  // namespace vb

@@ -1,0 +1,42 @@
+// Host entry points of the per-level kernels (Steps 2-4) and of the
+// last-level block ILUT and the solve phase.
+#pragma once
+
+#include "internal.h"
+
+namespace vb {
+
+// Step 3: weights, independent set, P_I.  Returns nD.
+template <typename TA>
+int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t>& pI, DBuf<int32_t>& newpos,
+                 cudaStream_t s);
+
+// Eq. 4: the D (FP64 pivot blocks), F, E, C parts of P_I A P_I^T.
+template <typename TA, typename T>
+void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_t>& newpos, int64_t nD,
+                  LevelDev<T>& L, cudaStream_t s, int* dst);
+
+// Batched GEPP of the pivot blocks (in place), with the mixed-precision tag.
+void pivot_lu(VBDev<double>& D, DBuf<int32_t>& piv, DBuf<int32_t>& ptag, VBDev<float>& D32, bool mixed,
+              double cond_thr, cudaStream_t s, int* dst);
+
+// which = 0: W = L^{-1} P F from F;  which = 1: G = E U^{-1} from E.
+template <typename T>
+void w_or_g(const VBDev<T>& X, int which, const VBDev<double>& D, const VBDev<float>& D32, const DBuf<int32_t>& piv,
+            const DBuf<int32_t>& ptag, bool mixed, double t, int lfil, VBDev<T>& out, cudaStream_t s);
+
+// Eq. 6: S = C - G W (drop at the last reduction).
+template <typename T>
+void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_reduction, double t, VBDev<T>& S,
+           cudaStream_t s, int* dst);
+
+// Last level: block ILUT in natural order (Alg. 3 in block form).
+template <typename T>
+void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, uint64_t wait_limit, cudaStream_t s,
+               int* dst);
+
+// Solve phase (Alg. 2) helpers.
+template <typename T>
+struct PrecDev;
+
+}  // namespace vb

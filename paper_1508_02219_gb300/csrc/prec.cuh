@@ -1,0 +1,68 @@
+// The multilevel factorization object and the solve-phase entry points.
+#pragma once
+
+#include <memory>
+
+#include "internal.h"
+#include "level.cuh"
+
+namespace vb {
+
+enum Phase { PH_SCALE = 0, PH_ORDER, PH_GATHER, PH_PIVOT, PH_W, PH_G, PH_SCHUR, PH_ILUT, PH_COUNT };
+
+// Per level: the scalar permutation of P_I (new scalar position -> old).
+struct LevelMaps {
+  DBuf<int32_t> sperm;
+  int64_t n = 0, nf = 0;
+};
+
+struct PrecBase {
+  cudaStream_t s = nullptr;
+  int64_t n = 0;
+  int precision = VB_FP64;
+  uint64_t wait_limit = 0;
+  double phase_s[PH_COUNT] = {0};
+  double mem_ratio = 0;
+  DBuf<int32_t> perm;  // P_B of the matrix the factorization was built from
+  DBuf<int> status;
+  virtual ~PrecBase() = default;
+  virtual int levels() const = 0;
+  // y = M^{-1} x, both in the block-permuted (P_B) numbering, device FP64
+  virtual void apply_perm(const double* x, double* y) = 0;
+  virtual void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval,
+                          int32_t* rsz, int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff,
+                          double* val) = 0;
+  virtual void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) = 0;
+};
+
+template <typename T>
+struct PrecDev : PrecBase {
+  std::vector<LevelDev<T>> lev;
+  std::vector<LevelMaps> maps;
+  LastDev<T> last;
+  DBuf<double> work;  // apply scratch: 2 * n per level depth, allocated once
+  int levels() const override { return (int)lev.size(); }
+  void apply_perm(const double* x, double* y) override;
+  void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval, int32_t* rsz,
+                  int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) override;
+  void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) override;
+};
+
+// Build the scalar permutation of level L.
+template <typename T>
+void build_level_maps(const LevelDev<T>& L, const int32_t* rsz, const int64_t* roff, int64_t p, LevelMaps& M,
+                      cudaStream_t s);
+
+// y = A x on a VBCSR matrix (FP64), scalar rows in order.
+void spmv_vb(const VBDev<double>& A, const double* x, double* y, cudaStream_t s);
+
+// Vector kernels used by FGMRES (deterministic two-stage reductions).
+void dot_dev(const double* x, const double* y, int64_t n, double* out, cudaStream_t s);
+void axpy_dev(double* y, const double* x, const double* alpha_dev, double sign, int64_t n, cudaStream_t s);
+void axpy_host(double* y, const double* x, double alpha, int64_t n, cudaStream_t s);
+void scale_dev(double* y, const double* x, const double* div_dev, int64_t n, cudaStream_t s);
+void sub_dev(double* r, const double* b, const double* ax, int64_t n, cudaStream_t s);
+void gather_dev(double* y, const double* x, const int32_t* idx, int64_t n, cudaStream_t s);
+void scatter_dev(double* y, const double* x, const int32_t* idx, int64_t n, cudaStream_t s);
+
+}  // namespace vb

@@ -1,0 +1,580 @@
+// Solve phase of VBARMS on the GPU: Alg. 2 (VBARMS_Solve) over the levels,
+// the sync-free block triangular solves of the last level, the VBCSR SpMV and
+// the vector kernels of FGMRES.
+//
+// Vectors are FP64.  FP64 factors are applied in the oracle's operation
+// order; FP32 factors are promoted to FP64 as they are read.
+#include "prec.cuh"
+#include "vbsr_ops.cuh"
+
+namespace vb {
+namespace {
+
+constexpr int SW = 8;
+constexpr int TRI_R = 4;  // scalar rows per lane in the triangular solves (blocks up to 128)
+
+template <typename T>
+__device__ __forceinline__ double ld(const T* p) {
+  return (double)*p;
+}
+
+// bh[q] = r[sp[q]] * b[sp[q]]
+__global__ void k_gather_scale(int64_t n, const int32_t* __restrict__ sp, const double* __restrict__ r,
+                               const double* __restrict__ b, double* __restrict__ bh) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t o = sp[q];
+    bh[q] = __dmul_rn(r[o], b[o]);
+  }
+}
+
+// x[sp[q]] = c[sp[q]] * xh[q]
+__global__ void k_scatter_scale(int64_t n, const int32_t* __restrict__ sp, const double* __restrict__ c,
+                                const double* __restrict__ xh, double* __restrict__ x) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t o = sp[q];
+    x[o] = __dmul_rn(c[o], xh[q]);
+  }
+}
+
+__global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ y) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = __dmul_rn(a[q], b[q]);
+}
+
+// u <- L^{-1} P u per pivot block (one thread per block).
+template <typename TL>
+__device__ void pivot_forward(const TL* lu, const int32_t* pv, int m, double* u) {
+  for (int k = 0; k < m; ++k)
+    if (pv[k] != k) {
+      const double t = u[k];
+      u[k] = u[pv[k]];
+      u[pv[k]] = t;
+    }
+  for (int i = 1; i < m; ++i)
+    for (int k = 0; k < i; ++k) u[i] = __dsub_rn(u[i], __dmul_rn(ld(lu + i * m + k), u[k]));
+}
+
+template <typename TL>
+__device__ void pivot_backward(const TL* lu, int m, double* u) {
+  for (int i = m - 1; i >= 0; --i) {
+    double s = u[i];
+    for (int k = i + 1; k < m; ++k) s = __dsub_rn(s, __dmul_rn(ld(lu + i * m + k), u[k]));
+    u[i] = __ddiv_rn(s, ld(lu + i * m + i));
+  }
+}
+
+__global__ void k_pivot_fwd(int64_t nD, const int32_t* __restrict__ sz, const int64_t* __restrict__ roff,
+                            const int64_t* __restrict__ voff, const double* __restrict__ lu64,
+                            const float* __restrict__ lu32, const int32_t* __restrict__ ptag,
+                            const int32_t* __restrict__ piv, double* __restrict__ u) {
+  for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < nD; y += (int64_t)gridDim.x * blockDim.x) {
+    if (lu32 && !ptag[y])
+      pivot_forward<float>(lu32 + voff[y], piv + roff[y], sz[y], u + roff[y]);
+    else
+      pivot_forward<double>(lu64 + voff[y], piv + roff[y], sz[y], u + roff[y]);
+  }
+}
+
+__global__ void k_pivot_bwd(int64_t nD, const int32_t* __restrict__ sz, const int64_t* __restrict__ roff,
+                            const int64_t* __restrict__ voff, const double* __restrict__ lu64,
+                            const float* __restrict__ lu32, const int32_t* __restrict__ ptag,
+                            const double* __restrict__ u, double* __restrict__ x) {
+  for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < nD; y += (int64_t)gridDim.x * blockDim.x) {
+    const int m = sz[y];
+    for (int a = 0; a < m; ++a) x[roff[y] + a] = u[roff[y] + a];
+    if (lu32 && !ptag[y])
+      pivot_backward<float>(lu32 + voff[y], m, x + roff[y]);
+    else
+      pivot_backward<double>(lu64 + voff[y], m, x + roff[y]);
+  }
+}
+
+// y_row -= M x  for every scalar row of a VBCSR M (one thread per scalar row,
+// blocks in order, then the entries of the row).
+template <typename T>
+__global__ void k_bsr_sub(VBView<T> M, const int64_t* __restrict__ rowblk, int64_t nrows,
+                          const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nrows; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = rowblk[q];
+    const int a = (int)(q - M.roff[I]);
+    double s = y[q];
+    for (int64_t b = M.bptr[I]; b < M.bptr[I + 1]; ++b) {
+      const int32_t J = M.bcol[b];
+      const int nc = M.csz[J];
+      const T* v = M.val + M.voff[b] + (int64_t)a * nc;
+      const double* xj = x + M.coff[J];
+      for (int k = 0; k < nc; ++k) s = __dsub_rn(s, __dmul_rn(ld(v + k), xj[k]));
+    }
+    y[q] = s;
+  }
+}
+
+// y = A x (FP64), one thread per scalar row.
+__global__ void k_spmv(VBView<double> A, const int64_t* __restrict__ rowblk, int64_t nrows,
+                       const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nrows; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = rowblk[q];
+    const int a = (int)(q - A.roff[I]);
+    double s = 0.0;
+    for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
+      const int32_t J = A.bcol[b];
+      const int nc = A.csz[J];
+      const double* v = A.val + A.voff[b] + (int64_t)a * nc;
+      const double* xj = x + A.coff[J];
+      for (int k = 0; k < nc; ++k) s = __dadd_rn(s, __dmul_rn(v[k], xj[k]));
+    }
+    y[q] = s;
+  }
+}
+
+__global__ void k_rowblk(int64_t nbr, const int64_t* __restrict__ roff, int64_t* __restrict__ rowblk) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < nbr; I += (int64_t)gridDim.x * wpb)
+    for (int64_t q = roff[I] + lane; q < roff[I + 1]; q += 32) rowblk[q] = I;
+}
+
+// Sync-free block forward substitution y_i -= sum_{k<i} L_ik y_k, rows in
+// ticket order, one warp per block row, bounded waits.
+template <typename T>
+__global__ void k_tri_fwd(VBView<T> L, double* __restrict__ y, int32_t* __restrict__ done,
+                          unsigned long long* ticket, int* abort, unsigned long long wait_limit, int* st) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    long long row = 0;
+    if (lane == 0) row = (long long)atomicAdd(ticket, 1ULL);
+    row = __shfl_sync(0xffffffffu, row, 0);
+    if (row >= L.nbr) break;
+    const int64_t i = row;
+    const int ni = L.rsz[i];
+    const int64_t r0 = L.roff[i];
+    double s[TRI_R];
+#pragma unroll
+    for (int t = 0; t < TRI_R; ++t) s[t] = lane + 32 * t < ni ? y[r0 + lane + 32 * t] : 0.0;
+    bool failed = ni > 32 * TRI_R;
+    if (failed && lane == 0) dev_fail(st, DEV_INTERNAL);
+    for (int64_t b = L.bptr[i]; b < L.bptr[i + 1] && !failed; ++b) {
+      const int32_t k = L.bcol[b];
+      if (lane == 0) {
+        unsigned long long it = 0;
+        while (*((volatile int32_t*)&done[k]) == 0) {
+          if (*((volatile int*)abort)) {
+            failed = true;
+            break;
+          }
+          if (++it > wait_limit) {
+            dev_fail(st, DEV_ETIMEOUT);
+            atomicExch(abort, 1);
+            failed = true;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+      }
+      failed = __shfl_sync(0xffffffffu, failed, 0);
+      if (failed) break;
+      const int nk = L.csz[k];
+      const double* yk = y + L.coff[k];
+#pragma unroll
+      for (int t = 0; t < TRI_R; ++t) {
+        const int a = lane + 32 * t;
+        if (a < ni) {
+          const T* v = L.val + L.voff[b] + (int64_t)a * nk;
+          for (int q = 0; q < nk; ++q) s[t] = __dsub_rn(s[t], __dmul_rn(ld(v + q), __ldcg(yk + q)));
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < TRI_R; ++t)
+      if (lane + 32 * t < ni) y[r0 + lane + 32 * t] = s[t];
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicExch(&done[i], 1);
+    }
+  }
+}
+
+// Sync-free block backward substitution x_i = D_i^{-1}(y_i - sum_{j>i} U_ij x_j),
+// rows in descending ticket order.
+template <typename T>
+__global__ void k_tri_bwd(VBView<T> U, const int64_t* __restrict__ dgoff, const double* __restrict__ lu64,
+                          const float* __restrict__ lu32, const int32_t* __restrict__ ptag,
+                          const int32_t* __restrict__ piv, const double* __restrict__ y, double* __restrict__ x,
+                          int32_t* __restrict__ done, unsigned long long* ticket, int* abort,
+                          unsigned long long wait_limit, int* st) {
+  __shared__ double sv[SW][32 * TRI_R];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    long long t0 = 0;
+    if (lane == 0) t0 = (long long)atomicAdd(ticket, 1ULL);
+    t0 = __shfl_sync(0xffffffffu, t0, 0);
+    if (t0 >= U.nbr) break;
+    const int64_t i = U.nbr - 1 - t0;
+    const int ni = U.rsz[i];
+    const int64_t r0 = U.roff[i];
+    double s[TRI_R];
+#pragma unroll
+    for (int t = 0; t < TRI_R; ++t) s[t] = lane + 32 * t < ni ? y[r0 + lane + 32 * t] : 0.0;
+    bool failed = ni > 32 * TRI_R;
+    if (failed && lane == 0) dev_fail(st, DEV_INTERNAL);
+    for (int64_t b = U.bptr[i]; b < U.bptr[i + 1] && !failed; ++b) {
+      const int32_t j = U.bcol[b];
+      if (lane == 0) {
+        unsigned long long it = 0;
+        while (*((volatile int32_t*)&done[j]) == 0) {
+          if (*((volatile int*)abort)) {
+            failed = true;
+            break;
+          }
+          if (++it > wait_limit) {
+            dev_fail(st, DEV_ETIMEOUT);
+            atomicExch(abort, 1);
+            failed = true;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+      }
+      failed = __shfl_sync(0xffffffffu, failed, 0);
+      if (failed) break;
+      const int nj = U.csz[j];
+      const double* xj = x + U.coff[j];
+#pragma unroll
+      for (int t = 0; t < TRI_R; ++t) {
+        const int a = lane + 32 * t;
+        if (a < ni) {
+          const T* v = U.val + U.voff[b] + (int64_t)a * nj;
+          for (int q = 0; q < nj; ++q) s[t] = __dsub_rn(s[t], __dmul_rn(ld(v + q), __ldcg(xj + q)));
+        }
+      }
+    }
+    if (!failed) {
+#pragma unroll
+      for (int t = 0; t < TRI_R; ++t)
+        if (lane + 32 * t < ni) sv[warp][lane + 32 * t] = s[t];
+      __syncwarp();
+      if (lane == 0) {
+        double* u = sv[warp];
+        if (lu32 && !ptag[i]) {
+          pivot_forward<float>(lu32 + dgoff[i], piv + r0, ni, u);
+          pivot_backward<float>(lu32 + dgoff[i], ni, u);
+        } else {
+          pivot_forward<double>(lu64 + dgoff[i], piv + r0, ni, u);
+          pivot_backward<double>(lu64 + dgoff[i], ni, u);
+        }
+      }
+      __syncwarp();
+      for (int a = lane; a < ni; a += 32) x[r0 + a] = sv[warp][a];
+    }
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      atomicExch(&done[i], 1);
+    }
+  }
+}
+
+// Deterministic two-stage dot product.
+constexpr int RT = 256;
+constexpr int RB = 512;
+
+__global__ void __launch_bounds__(RT) k_dot_partial(const double* __restrict__ x, const double* __restrict__ y,
+                                                    int64_t n, double* __restrict__ part) {
+  __shared__ double red[RT / 32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < n; i += (int64_t)gridDim.x * RT) s += x[i] * y[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < RT / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_dot_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double red[RB];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_axpy_dev(double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ a,
+                           double sign, int64_t n) {
+  const double al = sign * *a;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += al * x[i];
+}
+__global__ void k_axpy_host(double* __restrict__ y, const double* __restrict__ x, double a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+__global__ void k_scale_dev(double* __restrict__ y, const double* __restrict__ x, const double* __restrict__ d,
+                            int64_t n) {
+  const double dv = *d;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] / dv;
+}
+__global__ void k_sub(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ ax, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - ax[i];
+}
+__global__ void k_gather(double* __restrict__ y, const double* __restrict__ x, const int32_t* __restrict__ idx,
+                         int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[idx[i]];
+}
+__global__ void k_scatter(double* __restrict__ y, const double* __restrict__ x, const int32_t* __restrict__ idx,
+                          int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[idx[i]] = x[i];
+}
+
+__global__ void k_sperm(int64_t p, const int32_t* __restrict__ pI, const int32_t* __restrict__ rsz,
+                        const int64_t* __restrict__ roff, const int64_t* __restrict__ newoff,
+                        int32_t* __restrict__ sperm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t k = blockIdx.x * wpb + (threadIdx.x >> 5); k < p; k += (int64_t)gridDim.x * wpb) {
+    const int32_t Y = pI[k];
+    for (int a = lane; a < rsz[Y]; a += 32) sperm[newoff[k] + a] = (int32_t)(roff[Y] + a);
+  }
+}
+
+__global__ void k_perm_sizes2(int64_t p, const int32_t* __restrict__ pI, const int32_t* __restrict__ rsz,
+                              int32_t* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = rsz[pI[k]];
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+void dot_dev(const double* x, const double* y, int64_t n, double* out, cudaStream_t s) {
+  const int nb = (int)std::min<int64_t>(RB, std::max<int64_t>(1, (n + RT - 1) / RT));
+  DBuf<double> p(nb, s);
+  k_dot_partial<<<nb, RT, 0, s>>>(x, y, n, p.p);
+  k_dot_final<<<1, RB, 0, s>>>(p.p, nb, out);
+  VB_LAUNCH_CHECK();
+}
+void axpy_dev(double* y, const double* x, const double* a, double sign, int64_t n, cudaStream_t s) {
+  if (n) k_axpy_dev<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, a, sign, n);
+  VB_LAUNCH_CHECK();
+}
+void axpy_host(double* y, const double* x, double a, int64_t n, cudaStream_t s) {
+  if (n) k_axpy_host<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, a, n);
+  VB_LAUNCH_CHECK();
+}
+void scale_dev(double* y, const double* x, const double* d, int64_t n, cudaStream_t s) {
+  if (n) k_scale_dev<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, d, n);
+  VB_LAUNCH_CHECK();
+}
+void sub_dev(double* r, const double* b, const double* ax, int64_t n, cudaStream_t s) {
+  if (n) k_sub<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(r, b, ax, n);
+  VB_LAUNCH_CHECK();
+}
+void gather_dev(double* y, const double* x, const int32_t* idx, int64_t n, cudaStream_t s) {
+  if (n) k_gather<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, idx, n);
+  VB_LAUNCH_CHECK();
+}
+void scatter_dev(double* y, const double* x, const int32_t* idx, int64_t n, cudaStream_t s) {
+  if (n) k_scatter<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, idx, n);
+  VB_LAUNCH_CHECK();
+}
+
+// Row-block map of a VBCSR (scalar row -> block row), cached per matrix.
+static void make_rowblk(int64_t nbr, const int64_t* roff, int64_t n, DBuf<int64_t>& rb, cudaStream_t s) {
+  rb.alloc(n, s);
+  if (nbr) k_rowblk<<<grid_for(nbr, 8), 256, 0, s>>>(nbr, roff, rb.p);
+  VB_LAUNCH_CHECK();
+}
+
+void spmv_vb(const VBDev<double>& A, const double* x, double* y, cudaStream_t s) {
+  const int64_t n = A.nrows_scalar(s);
+  DBuf<int64_t> rb;
+  make_rowblk(A.nbr, A.roff.p, n, rb, s);
+  if (n) k_spmv<<<grid_for(n, 128, 152LL * 32), 128, 0, s>>>(A.view(), rb.p, n, x, y);
+  VB_LAUNCH_CHECK();
+}
+
+template <typename T>
+void build_level_maps(const LevelDev<T>& L, const int32_t* rsz, const int64_t* roff, int64_t p, LevelMaps& M,
+                      cudaStream_t s) {
+  M.n = p ? d2h(roff + p, s) : 0;
+  M.sperm.alloc(M.n, s);
+  DBuf<int32_t> psz(p, s);
+  DBuf<int64_t> newoff(p + 1, s);
+  if (p) {
+    k_perm_sizes2<<<grid_for(p, 256), 256, 0, s>>>(p, L.pI.p, rsz, psz.p);
+    VB_LAUNCH_CHECK();
+  }
+  scan_i32_to_i64(psz.p, newoff.p, p, s);
+  M.nf = p ? d2h(newoff.p + L.nD, s) : 0;
+  if (p) {
+    k_sperm<<<grid_for(p, 8), 256, 0, s>>>(p, L.pI.p, rsz, roff, newoff.p, M.sperm.p);
+    VB_LAUNCH_CHECK();
+  }
+}
+template void build_level_maps<double>(const LevelDev<double>&, const int32_t*, const int64_t*, int64_t,
+                                       LevelMaps&, cudaStream_t);
+template void build_level_maps<float>(const LevelDev<float>&, const int32_t*, const int64_t*, int64_t, LevelMaps&,
+                                      cudaStream_t);
+
+// --------------------------------------------------------------------------
+template <typename T>
+void PrecDev<T>::apply_perm(const double* x, double* y) {
+  // scratch: per level bh, xh (n_l each) and per-matrix row maps; last: 2 n
+  const int nl = (int)lev.size();
+  int64_t total = 0;
+  for (int l = 0; l < nl; ++l) total += 2 * maps[l].n;
+  const int64_t nlast = last.A.nbr ? last.A.nrows_scalar(s) : 0;
+  total += 2 * nlast;
+  if ((int64_t)work.n < total) work.alloc(total, s);
+  const bool mixed = sizeof(T) != sizeof(double);
+  double* wp = work.p;
+  const double* in = x;
+  double* out = y;
+  std::vector<double*> bh(nl), xh(nl);
+  for (int l = 0; l < nl; ++l) {
+    bh[l] = wp;
+    wp += maps[l].n;
+    xh[l] = wp;
+    wp += maps[l].n;
+  }
+  // forward sweep down the levels
+  for (int l = 0; l < nl; ++l) {
+    const LevelDev<T>& L = lev[l];
+    const LevelMaps& M = maps[l];
+    const double* b = l == 0 ? in : bh[l - 1] + maps[l - 1].nf;
+    if (M.n) k_gather_scale<<<grid_for(M.n, 256), 256, 0, s>>>(M.n, M.sperm.p, L.r.p, b, bh[l]);
+    if (L.nD)
+      k_pivot_fwd<<<grid_for(L.nD, 128), 128, 0, s>>>(L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
+                                                      mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, bh[l]);
+    const int64_t ng = M.n - M.nf;
+    if (ng && L.G.nnzb) {
+      DBuf<int64_t> rb;
+      make_rowblk(L.G.nbr, L.G.roff.p, ng, rb, s);
+      k_bsr_sub<T><<<grid_for(ng, 128), 128, 0, s>>>(L.G.view(), rb.p, ng, bh[l], bh[l] + M.nf);
+    }
+    VB_LAUNCH_CHECK();
+  }
+  // last level: z = S2 (L U)^{-1} S1 g
+  {
+    const double* g = nl == 0 ? in : bh[nl - 1] + maps[nl - 1].nf;
+    double* z = nl == 0 ? out : xh[nl - 1] + maps[nl - 1].nf;
+    if (nlast) {
+      double* yy = wp;
+      double* xx = wp + nlast;
+      k_mul<<<grid_for(nlast, 256), 256, 0, s>>>(nlast, last.r.p, g, yy);
+      const int64_t p = last.A.nbr;
+      DBuf<int32_t> flags(2 * p, s);
+      DBuf<unsigned long long> tick(2, s);
+      DBuf<int> abort(1, s);
+      flags.zero();
+      tick.zero();
+      abort.zero();
+      int dev = 0, nsm = 0;
+      VB_CUDA(cudaGetDevice(&dev));
+      VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 4, (p + SW - 1) / SW));
+      k_tri_fwd<T><<<nb, SW * 32, 0, s>>>(last.L.view(), yy, flags.p, tick.p, abort.p,
+                                          (unsigned long long)wait_limit, status.p);
+      k_tri_bwd<T><<<nb, SW * 32, 0, s>>>(last.U.view(), last.Dg.voff.p, last.Dg.val.p,
+                                          mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx,
+                                          flags.p + p, tick.p + 1, abort.p, (unsigned long long)wait_limit,
+                                          status.p);
+      k_mul<<<grid_for(nlast, 256), 256, 0, s>>>(nlast, last.c.p, xx, z);
+      VB_LAUNCH_CHECK();
+      check_status(status.p, s, "vbarms_apply: last-level triangular solves");
+    }
+  }
+  // backward sweep up the levels
+  for (int l = nl - 1; l >= 0; --l) {
+    const LevelDev<T>& L = lev[l];
+    const LevelMaps& M = maps[l];
+    double* xo = l == 0 ? out : xh[l - 1] + maps[l - 1].nf;
+    if (M.nf && L.W.nnzb) {
+      DBuf<int64_t> rb;
+      make_rowblk(L.W.nbr, L.W.roff.p, M.nf, rb, s);
+      k_bsr_sub<T><<<grid_for(M.nf, 128), 128, 0, s>>>(L.W.view(), rb.p, M.nf, xh[l] + M.nf, bh[l]);
+    }
+    if (L.nD)
+      k_pivot_bwd<<<grid_for(L.nD, 128), 128, 0, s>>>(L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
+                                                      mixed ? L.D32.val.p : nullptr, L.ptag.p, bh[l], xh[l]);
+    if (M.n) k_scatter_scale<<<grid_for(M.n, 256), 256, 0, s>>>(M.n, M.sperm.p, L.c.p, xh[l], xo);
+    VB_LAUNCH_CHECK();
+  }
+}
+
+template <typename T>
+void PrecDev<T>::export_mat(int l, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval,
+                            int32_t* rsz, int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) {
+  const int nl = (int)lev.size();
+  if (l < 0 || l > nl) fail(VB_EINVAL, "level out of range");
+  if (l == nl) {
+    switch (which) {
+      case 0: return export_vb(last.A, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+      case 1: return export_vb(last.Dg, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+      case 8: return export_vb(last.L, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+      case 9: return export_vb(last.U, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    }
+    fail(VB_EINVAL, "matrix selector out of range");
+  }
+  const LevelDev<T>& L = lev[l];
+  switch (which) {
+    case 0:
+      if (L.A64.nbr || !L.AT.nbr) return export_vb(L.A64, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+      return export_vb(L.AT, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 1: return export_vb(L.D, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 2: return export_vb(L.F, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 3: return export_vb(L.E, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 4: return export_vb(L.C, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 5: return export_vb(L.W, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 6: return export_vb(L.G, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 7: return export_vb(L.S, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+  }
+  fail(VB_EINVAL, "matrix selector out of range");
+}
+
+template <typename T>
+void PrecDev<T>::export_vec(int l, int which, double* d, int32_t* iv, int64_t* len) {
+  const int nl = (int)lev.size();
+  if (l < 0 || l > nl) fail(VB_EINVAL, "level out of range");
+  const DBuf<double>* dv = nullptr;
+  const DBuf<int32_t>* ivb = nullptr;
+  if (l == nl) {
+    if (which == 0) dv = &last.r;
+    if (which == 1) dv = &last.c;
+    if (which == 4) ivb = &last.piv;
+    if (which == 5) ivb = &last.ptag;
+  } else {
+    const LevelDev<T>& L = lev[l];
+    if (which == 0) dv = &L.r;
+    if (which == 1) dv = &L.c;
+    if (which == 2) dv = &L.w;
+    if (which == 3) ivb = &L.pI;
+    if (which == 4) ivb = &L.piv;
+    if (which == 5) ivb = &L.ptag;
+  }
+  if (!dv && !ivb) fail(VB_EINVAL, "vector selector out of range");
+  const int64_t n = dv ? (int64_t)dv->n : (int64_t)ivb->n;
+  if (len) *len = n;
+  if (dv && d && n) VB_CUDA(cudaMemcpyAsync(d, dv->p, n * 8, cudaMemcpyDeviceToHost, s));
+  if (ivb && iv && n) VB_CUDA(cudaMemcpyAsync(iv, ivb->p, n * 4, cudaMemcpyDeviceToHost, s));
+  VB_CUDA(cudaStreamSynchronize(s));
+}
+
+template struct PrecDev<double>;
+template struct PrecDev<float>;
+
+}  // namespace vb

@@ -1,0 +1,153 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 CPU oracle
+on the same seeded inputs (compression, ordering and FP64 factors bit-exact;
+solve and FGMRES within the stated tolerances)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import (FP64_REL, as_dict, compare_factor, compare_vb, cuda_ok, gpu_compress, rel_fro, torch, vb)
+from paper_1508_02219_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
+
+
+def compress_both(m, tau, on_device=False):
+    A = gpu_compress(m, tau, on_device=on_device)
+    c = oracle.compress(m.n, m.rowptr, m.colind, m.val, tau)
+    g = A.export()
+    assert np.array_equal(g["perm"], c.perm), "P_B differs"
+    assert np.array_equal(g["bsz"], c.bsz), "block sizes differ"
+    compare_vb(dict(rsz=g["bsz"], csz=g["bsz"], bptr=g["bptr"], bcol=g["bcol"], voff=g["voff"], val=g["val"]),
+               as_dict(c.A), "VBSR")
+    q = A.query()
+    assert q["av_bd"] == c.av_bd and q["av_bs"] == c.av_bs
+    return A, c
+
+
+@pytest.mark.parametrize("case", ["grid_tau1", "geo_tau08", "geo_tau075_l4", "geo_tau05", "random_empty",
+                                  "geo_scrambled"])
+def test_compress_bit_exact(case):
+    if case == "grid_tau1":
+        m, tau = synth.grid_7pt(10, 10, 10, 5, seed=0, scramble=True), 1.0
+    elif case == "geo_tau08":
+        m, tau = synth.geometric(3000, 6, seed=1), 0.8
+    elif case == "geo_tau075_l4":
+        m, tau = synth.geometric(2000, 4, seed=2), 0.75
+    elif case == "geo_tau05":
+        m, tau = synth.geometric(1500, 5, seed=3), 0.5
+    elif case == "random_empty":
+        m, tau = synth.random_sparse(3000, 0.003, seed=4, empty_rows=40), 0.5
+    else:
+        m, tau = synth.geometric(1000, 6, seed=5, scramble=True), 0.8
+    compress_both(m, tau, on_device=(case == "geo_tau08"))
+
+
+def test_compress_heavy_rows_and_dense():
+    # dense rows/columns exceed the shared-memory tables: global-table path
+    rng = np.random.default_rng(0)
+    a = (rng.random((1500, 1500)) < 0.002).astype(float) * rng.standard_normal((1500, 1500))
+    a[:, 7] = 1.0
+    a[11, :] = 2.0
+    a[np.arange(1500), np.arange(1500)] += 5.0
+    m = synth.from_dense(a)
+    compress_both(m, 0.5)
+    d = synth.from_dense(rng.standard_normal((300, 300)), keep_zeros=True)
+    A, c = compress_both(d, 1.0)
+    assert len(c.bsz) == 1
+
+
+def test_compress_edge_cases():
+    V = vb()
+    compress_both(synth.from_dense(np.array([[3.0]])), 1.0)
+    A = V.vbarms_compress(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), 1.0)
+    assert A.query()["nblk"] == 0
+    m = synth.from_dense(np.eye(5) + np.diag(np.ones(4), 1))
+    bad = m.colind.copy()
+    bad[1], bad[2] = bad[2], bad[1]
+    with pytest.raises(V.VbarmsError) as e:
+        V.vbarms_compress(m.n, m.rowptr, bad, m.val, 1.0)
+    assert e.value.status == V.VB_EINVAL
+    with pytest.raises(V.VbarmsError) as e:
+        V.vbarms_compress(m.n, m.rowptr, m.colind, m.val, 0.0)
+    assert e.value.status == V.VB_EINVAL
+    oob = m.colind.copy()
+    oob[-1] = 99
+    with pytest.raises(V.VbarmsError):
+        V.vbarms_compress(m.n, m.rowptr, oob, m.val, 1.0)
+
+
+FACTOR_CASES = {
+    "grid10_l5": (lambda: synth.grid_7pt(10, 10, 10, 5, seed=0, scramble=True), 1.0, 2, 1e-3, 20),
+    "geo_nodrop": (lambda: synth.geometric(1200, 4, seed=6), 0.75, 1, 0.0, -1),
+    "geo_3lev": (lambda: synth.geometric(2500, 6, seed=7), 0.8, 3, 1e-4, -1),
+    "geo_lfil": (lambda: synth.geometric(2000, 5, seed=8), 0.8, 2, 1e-3, 6),
+    "geo_pivoting": (lambda: synth.geometric(1500, 6, seed=9, dominance=1.5, ill_frac=0.01), 0.8, 3, 1e-4, 30),
+    "geo_ilut_only": (lambda: synth.geometric(800, 3, seed=10), 0.75, 0, 1e-3, 10),
+}
+
+
+@pytest.mark.parametrize("case", list(FACTOR_CASES))
+def test_fp64_factor_bit_exact(case):
+    gen, tau, nlev, t, lfil = FACTOR_CASES[case]
+    m = gen()
+    V = vb()
+    A, c = compress_both(m, tau)
+    P = V.vbarms_factor(A, nlev, t, lfil, precision="fp64")
+    Po = oracle.Prec(c.A, nlev, t, lfil)
+    compare_factor(P, Po)
+
+
+@pytest.mark.parametrize("case", ["grid10_l5", "geo_3lev", "geo_pivoting"])
+def test_apply_and_fgmres_fp64(case):
+    gen, tau, nlev, t, lfil = FACTOR_CASES[case]
+    m = gen()
+    V = vb()
+    A, c = compress_both(m, tau)
+    P = V.vbarms_factor(A, nlev, t, lfil, precision="fp64")
+    Po = oracle.Prec(c.A, nlev, t, lfil)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(m.n)
+    # oracle works in the P_B numbering
+    yo_p = Po.apply(x[c.perm])
+    yo = np.empty(m.n)
+    yo[c.perm] = yo_p
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    V.vbarms_apply(P, xd, yd)
+    y = yd.cpu().numpy()
+    assert rel_fro(y, yo) <= 1e-12
+    b = synth.ones_rhs(m)
+    bd = torch.from_numpy(b).cuda()
+    xs = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    its, rr, st = V.fgmres_solve(A, P, bd, xs, rtol=1e-8, restart=50, maxit=1000)
+    xo, its_o, rr_o, st_o = oracle.fgmres(c.A, Po, b[c.perm], rtol=1e-8, restart=50, maxit=1000)
+    assert st == V.VB_OK and st_o == oracle.OK
+    assert abs(its - its_o) <= 1, f"FGMRES iterations {its} vs oracle {its_o}"
+    assert rr <= 1e-8
+    xg = xs.cpu().numpy()
+    assert np.allclose(xg, 1.0, atol=1e-5)
+
+
+def test_no_drop_factor_is_exact_inverse():
+    """t = 0, no lfil: M = A, so FGMRES converges in one iteration."""
+    V = vb()
+    m = synth.geometric(1500, 4, seed=11)
+    A = gpu_compress(m, 0.75)
+    P = V.vbarms_factor(A, 2, 0.0, -1)
+    b = torch.from_numpy(synth.ones_rhs(m)).cuda()
+    x = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    its, rr, st = V.fgmres_solve(A, P, b, x, rtol=1e-8)
+    assert st == V.VB_OK and its == 1
+    assert torch.allclose(x, torch.ones_like(x), atol=1e-8)
+
+
+def test_singular_pivot_reported():
+    V = vb()
+    a = np.eye(4)
+    a[2:, 2:] = [[1.0, 2.0], [2.0, 4.0]]
+    m = synth.from_dense(a, keep_zeros=False)
+    # blocks of sizes 2 and 2 from tau = 1 compression (rows 2,3 share a pattern)
+    A = gpu_compress(m, 1.0)
+    with pytest.raises(V.VbarmsError) as e:
+        V.vbarms_factor(A, 1, 0.0, -1)
+    assert e.value.status == V.VB_ESINGULAR
