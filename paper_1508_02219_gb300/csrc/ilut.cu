@@ -96,7 +96,7 @@ __device__ void ainv_right_row(const TL* lu, const int32_t* pv, int m, T* x) {
   }
   for (int k = m - 1; k >= 0; --k) {
     const int p = __ldcg(pv + k);
-    if (p != k) {
+    if (p > k && p < m) {  // GEPP interchanges satisfy k <= p < m
       const T t = x[k];
       x[k] = x[p];
       x[p] = t;
@@ -135,7 +135,9 @@ __device__ __forceinline__ int ws_new_slot(const Workspace& ws, int* keys, int* 
                                            int col, int sz) {
   const int slot = atomicAdd(nslots, 1);
   const long long off = (long long)atomicAdd(nvals, (unsigned long long)sz);
-  if (slot >= ws.smax || off + sz > ws.vmax) return -1;
+  if (slot >= ws.smax) return -1;
+  hpos[slot] = -1;  // the end-of-row reset skips slots that were never placed
+  if (off + sz > ws.vmax) return -1;
   scol[slot] = col;
   soff[slot] = off;
   sstate[slot] = SL_LIVE;
@@ -228,6 +230,9 @@ __global__ void __launch_bounds__(IW * 32)
           }
           __nanosleep(128);
         }
+        // a row that failed still publishes (so no one waits forever) but
+        // raises abort first: its factors must not be used
+        if (*((volatile int*)P.abort) != 0) *vflag = 2;
         __threadfence();
       }
       __syncwarp();
@@ -258,7 +263,11 @@ __global__ void __launch_bounds__(IW * 32)
         sf2[sk] = f2;
       }
       const int64_t u0 = __ldcg(P.ustart + k);
-      const int uc = __ldcg(P.ucnt + k);
+      int uc = __ldcg(P.ucnt + k);
+      if (u0 < 0 || uc < 0 || u0 + uc > P.ubcap) {  // never true for a published row: record and skip
+        status_local = DEV_INTERNAL;
+        break;
+      }
       // create the fill blocks of the U columns of row k that are missing:
       // probe (read-only) then place, separated by __syncwarp
       for (int q0 = 0; q0 < uc; q0 += 32) {
@@ -267,7 +276,12 @@ __global__ void __launch_bounds__(IW * 32)
         bool missing = false;
         if (q < uc) {
           j = __ldcg(P.ucol + u0 + q);
-          missing = ws_lookup(keys, scol, hmask, j) < 0;
+          if (j <= k || j >= A.nbr) {  // a published U column is always right of k: record and skip
+            *vflag = 4;
+            j = -1;
+          } else {
+            missing = ws_lookup(keys, scol, hmask, j) < 0;
+          }
         }
         __syncwarp();
         if (missing) {
@@ -285,6 +299,10 @@ __global__ void __launch_bounds__(IW * 32)
         status_local = DEV_OVERFLOW;
         break;
       }
+      if (*vflag == 4) {
+        status_local = DEV_INTERNAL;
+        break;
+      }
       // a_ij -= m * u_kj, one U block at a time, lanes over its elements
       for (int q = 0; q < uc; ++q) {
         const int32_t j = __ldcg(P.ucol + u0 + q);
@@ -295,7 +313,12 @@ __global__ void __launch_bounds__(IW * 32)
           break;
         }
         T* B = wv + soff[slot];
-        const T* U = uval + __ldcg(P.uvo + u0 + q);
+        const int64_t uo = __ldcg(P.uvo + u0 + q);
+        if (uo < 0 || uo + (int64_t)nk * nj > P.uvcap) {
+          status_local = DEV_INTERNAL;
+          break;
+        }
+        const T* U = uval + uo;
         for (int e = lane; e < ni * nj; e += 32) {
           const int a = e / nj, jj = e - a * nj;
           T acc = B[e];
@@ -506,12 +529,11 @@ __global__ void __launch_bounds__(IW * 32)
       P.ustart[i] = 0;
     }
     if (lane == 0) atomicMax(P.ctr + 5, s_nvals[warp]);
-    // publish the row
+    // publish the row: every lane's writes are made visible device-wide
+    // before lane 0 raises the flag
+    __threadfence();
     __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      atomicExch(&P.done[i], 1);
-    }
+    if (lane == 0) atomicExch(&P.done[i], 1);
     // clear the hash positions this row used
     for (int s = lane; s < ns; s += 32)
       if (hpos[s] >= 0) keys[hpos[s]] = -1;
@@ -529,8 +551,10 @@ __global__ void k_pool_to_vb(int64_t nbr, const int64_t* __restrict__ start, con
   const int64_t wpb = blockDim.x >> 5;
   for (int64_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nbr; i += (int64_t)gridDim.x * wpb) {
     const int64_t n = bptr[i + 1] - bptr[i];
-    for (int64_t q = lane; q < n; q += 32) bcol[bptr[i] + q] = pcol[start[i] + q];
-    __syncwarp();
+    if (!voff) {  // first pass: columns only (the value offsets do not exist yet)
+      for (int64_t q = lane; q < n; q += 32) bcol[bptr[i] + q] = pcol[start[i] + q];
+      continue;
+    }
     for (int64_t q = 0; q < n; ++q) {
       const int64_t d = bptr[i] + q;
       const int64_t sz = voff[d + 1] - voff[d];
@@ -628,6 +652,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
     ctr.zero();
     done.zero();
     abort.zero();
+    X.piv.zero();
     Pools P{lcol.p, lvo.p, ucol.p, uvo.p, lstart.p, lcnt.p, ustart.p, ucnt.p, ctr.p,
             lbcap,  lvcap, ubcap,  uvcap, done.p,  abort.p};
     k_ilut<T><<<(unsigned)nblocks, IW * 32, 0, s>>>(A.view(), ws, wvals.p, P, lval.p, uval.p, X.Dg.voff.p,

@@ -170,6 +170,7 @@ __global__ void k_tri_fwd(VBView<T> L, double* __restrict__ y, int32_t* __restri
           }
           __nanosleep(64);
         }
+        if (*((volatile int*)abort)) failed = true;  // a failed row publishes after raising abort
         __threadfence();
       }
       failed = __shfl_sync(0xffffffffu, failed, 0);
@@ -188,11 +189,9 @@ __global__ void k_tri_fwd(VBView<T> L, double* __restrict__ y, int32_t* __restri
 #pragma unroll
     for (int t = 0; t < TRI_R; ++t)
       if (lane + 32 * t < ni) y[r0 + lane + 32 * t] = s[t];
+    __threadfence();  // every lane's writes before the flag
     __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      atomicExch(&done[i], 1);
-    }
+    if (lane == 0) atomicExch(&done[i], 1);
   }
 }
 
@@ -236,6 +235,7 @@ __global__ void k_tri_bwd(VBView<T> U, const int64_t* __restrict__ dgoff, const 
           }
           __nanosleep(64);
         }
+        if (*((volatile int*)abort)) failed = true;  // a failed row publishes after raising abort
         __threadfence();
       }
       failed = __shfl_sync(0xffffffffu, failed, 0);
@@ -269,11 +269,9 @@ __global__ void k_tri_bwd(VBView<T> U, const int64_t* __restrict__ dgoff, const 
       __syncwarp();
       for (int a = lane; a < ni; a += 32) x[r0 + a] = sv[warp][a];
     }
+    __threadfence();  // every lane's writes before the flag
     __syncwarp();
-    if (lane == 0) {
-      __threadfence();
-      atomicExch(&done[i], 1);
-    }
+    if (lane == 0) atomicExch(&done[i], 1);
   }
 }
 

@@ -204,28 +204,29 @@ def geometric(n_nodes: int, ell: int = 6, seed: int = 0, approx: bool = True,
         blocks += rng.standard_normal((nblk, ell, ell)) * np.sqrt(noise_var)
     ill_nodes = np.zeros(0, dtype=np.int64)
     if dominance is not None:
-        z = rng.standard_normal((n_nodes, ell, ell))
+        # Dense pivot blocks D_a = s_a U diag(sig) V^T (U, V random orthogonal,
+        # sig ~ U[1, 2]) with s_a = dominance * sum_b ||A_ab||_F / min(sig):
+        # block diagonally dominant by at least `dominance` in the 2-norm.
+        # Planted nodes get sig = (1, ..., 1, 1/ill_cond) and s_a =
+        # dominance * sum_b ||A_ab||_F, i.e. kappa_2(D_a) = ill_cond exactly.
+        u, _ = np.linalg.qr(rng.standard_normal((n_nodes, ell, ell)))
+        v, _ = np.linalg.qr(rng.standard_normal((n_nodes, ell, ell)))
+        sig = rng.uniform(1.0, 2.0, (n_nodes, ell))
         n_ill = int(round(ill_frac * n_nodes))
         ill_nodes = np.sort(rng.choice(n_nodes, size=n_ill, replace=False)) if n_ill else ill_nodes
-        for a in ill_nodes:
-            u, _ = np.linalg.qr(rng.standard_normal((ell, ell)))
-            v, _ = np.linalg.qr(rng.standard_normal((ell, ell)))
-            s = np.ones(ell)
-            s[-1] = 1.0 / ill_cond
-            z[a] = (u * s) @ v.T
-        zk = z.copy()
+        sig[ill_nodes] = 1.0
+        sig[ill_nodes, -1] = 1.0 / ill_cond
+        z = np.einsum("nij,nj,nkj->nik", u, sig, v)
         if keep is not None:
-            zk = np.where(keep[diag], z, 0.0)
-            keep[diag[ill_nodes]] = True
-            zk[ill_nodes] = z[ill_nodes]
+            keep[diag] = True
         offn = blocks if keep is None else np.where(keep, blocks, 0.0)
         fro = np.sqrt((offn ** 2).sum(axis=(1, 2)))
         fro[diag] = 0.0
         off_sum = np.bincount(row_node, weights=fro, minlength=n_nodes)
-        zf = np.sqrt((zk ** 2).sum(axis=(1, 2)))
-        s_a = dominance * off_sum / np.where(zf > 0, zf, 1.0)
-        s_a = np.where(off_sum > 0, s_a, 1.0)
-        blocks[diag] = zk * s_a[:, None, None]
+        denom = sig.min(axis=1)
+        denom[ill_nodes] = 1.0
+        s_a = np.where(off_sum > 0, dominance * off_sum / denom, 1.0)
+        blocks[diag] = z * s_a[:, None, None]
     m = _expand_blocks(n_nodes, ell, nptr, nidx, blocks, keep)
     m.meta.update(kind="geometric", nodes=n_nodes, ell=ell, seed=seed, radius=r,
                   node_of_row=np.repeat(np.arange(n_nodes), ell), ill_nodes=ill_nodes,

@@ -63,7 +63,7 @@ def test_compress_edge_cases():
     assert A.query()["nblk"] == 0
     m = synth.from_dense(np.eye(5) + np.diag(np.ones(4), 1))
     bad = m.colind.copy()
-    bad[1], bad[2] = bad[2], bad[1]
+    bad[0], bad[1] = bad[1], bad[0]  # row 0 becomes [1, 0]
     with pytest.raises(V.VbarmsError) as e:
         V.vbarms_compress(m.n, m.rowptr, bad, m.val, 1.0)
     assert e.value.status == V.VB_EINVAL
