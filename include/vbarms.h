@@ -159,6 +159,20 @@ vb_status vbarms_prec_export(vbarms_prec M, int lev, int which, int64_t* nbr, in
  * NULL arrays to query it.                                                  */
 vb_status vbarms_prec_vector(vbarms_prec M, int lev, int which, double* d, int32_t* iv, int64_t* len);
 
+/* Measured launches of one kernel of a factorization, timed with CUDA events
+ * on the factorization's stream: kernel 0 = the numeric phase of the Schur
+ * complement S = C - G W (Eq. 6), one launch per level.  *launches = count,
+ * *ms = summed device time, *bytes = summed algorithmic bytes (C, G, W read
+ * and S written once, values plus index arrays), *flops = summed
+ * 2 n_r n_Y n_s over the block triples.  Any pointer may be NULL.           */
+vb_status vbarms_prec_kernel_stats(vbarms_prec M, int kernel, int* launches, double* ms, double* bytes,
+                                   double* flops);
+
+/* Number of kernels this library has launched since it was loaded (all
+ * threads, all handles); read it before and after a call to count the
+ * launches of that call.                                                   */
+uint64_t vbarms_launch_count(void);
+
 void vbarms_vbsr_destroy(vbarms_vbsr A);
 void vbarms_prec_destroy(vbarms_prec M);
 

@@ -120,7 +120,11 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
     tm.mark(PH_W);
     w_or_g<T>(L.E, 1, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.G, s);
     tm.mark(PH_G);
-    schur<T>(L.C, L.G, L.W, l == o.nlev - 1, o.droptol, L.S, s, dst);
+    KernelRec rec;
+    rec.kernel = 0;
+    rec.level = l;
+    schur<T>(L.C, L.G, L.W, l == o.nlev - 1, o.droptol, L.S, s, dst, &rec);
+    P->krec.push_back(rec);
     tm.mark(PH_SCHUR);
     fill += (double)(L.D.nval + L.W.nval + L.G.nval);
     LevelMaps M;
@@ -146,6 +150,13 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
   tm.mark(PH_ILUT);
   fill += (double)(X.Dg.nval + X.L.nval + X.U.nval);
   tm.accumulate(P->phase_s);
+  for (auto& r : P->krec) {
+    float ms = 0;
+    if (r.e0 && r.e1) {
+      VB_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
+      r.ms = ms;
+    }
+  }
   P->mem_ratio = Ah.C.nnz ? fill / (double)Ah.C.nnz : 0.0;
   return P;
 }
@@ -427,6 +438,27 @@ vb_status vbarms_prec_stats(vbarms_prec M, int* levels_used, double* mem_ratio, 
   if (mem_ratio) *mem_ratio = M->impl->mem_ratio;
   if (phase_s)
     for (int i = 0; i < PH_COUNT; ++i) phase_s[i] = M->impl->phase_s[i];
+  return VB_OK;
+}
+
+uint64_t vbarms_launch_count(void) { return g_launch_count.load(); }
+
+vb_status vbarms_prec_kernel_stats(vbarms_prec M, int kernel, int* launches, double* ms, double* bytes,
+                                   double* flops) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  int n = 0;
+  double t = 0, b = 0, f = 0;
+  for (const auto& r : M->impl->krec) {
+    if (r.kernel != kernel || r.ms < 0) continue;
+    ++n;
+    t += r.ms;
+    b += r.bytes;
+    f += r.flops;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (bytes) *bytes = b;
+  if (flops) *flops = f;
   return VB_OK;
 }
 

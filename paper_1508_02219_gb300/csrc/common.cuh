@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -31,6 +32,15 @@ struct Error {
   } while (0)
 
 #define VB_LAUNCH_CHECK() VB_CUDA(cudaGetLastError())
+
+// Every kernel of the library is launched through launch(), which counts it.
+extern std::atomic<unsigned long long> g_launch_count;
+
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
+}
 
 // Device status word shared by the kernels of one call: first error wins.
 enum DevCode : int {

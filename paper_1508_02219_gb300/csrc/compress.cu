@@ -402,7 +402,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   const int64_t nnz = out.nnz;
   DBuf<int32_t> len(n, s);
   if (n) {
-    k_validate<<<grid_for(n, 256), 256, 0, s>>>(n, rowptr, colind, len.p, dst);
+    launch(k_validate, grid_for(n, 256), 256, 0, s, n, rowptr, colind, len.p, dst);
     VB_LAUNCH_CHECK();
   }
   check_status(dst, s, "vbarms_compress: CSR validation");
@@ -412,13 +412,13 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   DBuf<int64_t> cptr(n + 1, s);
   ccnt.zero();
   if (nnz) {
-    k_col_count<<<grid_for(nnz, 256, 152LL * 64), 256, 0, s>>>(nnz, colind, ccnt.p);
+    launch(k_col_count, grid_for(nnz, 256, 152LL * 64), 256, 0, s, nnz, colind, ccnt.p);
     VB_LAUNCH_CHECK();
   }
   scan_i32_to_i64(ccnt.p, cptr.p, n, s);
   ccnt.zero();
   if (n) {
-    k_col_fill<<<grid_for(n, 8), 256, 0, s>>>(n, rowptr, colind, cptr.p, ccnt.p, crow.p);
+    launch(k_col_fill, grid_for(n, 8), 256, 0, s, n, rowptr, colind, cptr.p, ccnt.p, crow.p);
     VB_LAUNCH_CHECK();
   }
   ccnt.release();
@@ -438,14 +438,14 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
     counters.zero();
     nheavy.zero();
     if (n) {
-      k_similar<false><<<grid_for(n, CW, 152LL * 24), CW * 32, smem_sim, s>>>(
+      launch(k_similar<false>, grid_for(n, CW, 152LL * 24), CW * 32, smem_sim, s, 
           n, nullptr, rowptr, colind, cptr.p, crow.p, len.p, tau2, nullptr, 0, simstart.p, simcnt.p, simbuf.p,
           simcap, counters.p, heavy.p, nheavy.p, dst);
       VB_LAUNCH_CHECK();
     }
     const int nh = d2h(nheavy.p, s);
     if (nh > 0) {
-      k_heavy_bound<<<grid_for(nh, 8), 256, 0, s>>>(nh, heavy.p, rowptr, colind, cptr.p, n, counters.p + 1);
+      launch(k_heavy_bound, grid_for(nh, 8), 256, 0, s, nh, heavy.p, rowptr, colind, cptr.p, n, counters.p + 1);
       VB_LAUNCH_CHECK();
       const uint64_t bound = d2h(counters.p + 1, s);
       uint32_t gcap = 1024;
@@ -455,7 +455,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
       warps = std::min<int64_t>(warps, nh);
       const int64_t blocks = (warps + CW - 1) / CW;
       DBuf<int> gtab((size_t)blocks * CW * 2 * gcap, s);
-      k_similar<true><<<(unsigned)blocks, CW * 32, 0, s>>>(nh, heavy.p, rowptr, colind, cptr.p, crow.p, len.p,
+      launch(k_similar<true>, (unsigned)blocks, CW * 32, 0, s, nh, heavy.p, rowptr, colind, cptr.p, crow.p, len.p,
                                                           tau2, gtab.p, gcap, simstart.p, simcnt.p, simbuf.p,
                                                           simcap, counters.p, nullptr, nullptr, dst);
       VB_LAUNCH_CHECK();
@@ -475,7 +475,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   state.zero();
   group.fill_bytes(0x7f);
   if (n) {
-    k_pending<<<grid_for(n, 8), 256, 0, s>>>(n, simstart.p, simcnt.p, simbuf.p, pending.p);
+    launch(k_pending, grid_for(n, 8), 256, 0, s, n, simstart.p, simcnt.p, simbuf.p, pending.p);
     VB_LAUNCH_CHECK();
   }
   DBuf<unsigned long long> remaining(1, s);
@@ -484,9 +484,9 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
     h2d(remaining.p, &nn, 1, s);
   }
   for (int64_t round = 0; n > 0; ++round) {
-    k_round_a<<<grid_for(n, 256), 256, 0, s>>>(n, simstart.p, simcnt.p, simbuf.p, pending.p, state.p, remaining.p);
+    launch(k_round_a, grid_for(n, 256), 256, 0, s, n, simstart.p, simcnt.p, simbuf.p, pending.p, state.p, remaining.p);
     VB_LAUNCH_CHECK();
-    k_round_b<<<grid_for(n, 256), 256, 0, s>>>(n, simstart.p, simcnt.p, simbuf.p, pending.p, state.p);
+    launch(k_round_b, grid_for(n, 256), 256, 0, s, n, simstart.p, simcnt.p, simbuf.p, pending.p, state.p);
     VB_LAUNCH_CHECK();
     if ((round & 3) == 3 || round < 4) {
       if (d2h(remaining.p, s) == 0) break;
@@ -494,7 +494,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
     if (round > n + 8) fail(VB_EINTERNAL, "vbarms_compress: leader rounds did not terminate");
   }
   if (n) {
-    k_groups<<<grid_for(n, 256), 256, 0, s>>>(n, simstart.p, simcnt.p, simbuf.p, state.p, group.p, isleader.p);
+    launch(k_groups, grid_for(n, 256), 256, 0, s, n, simstart.p, simcnt.p, simbuf.p, state.p, group.p, isleader.p);
     VB_LAUNCH_CHECK();
   }
   DBuf<int64_t> lead_scan(n + 1, s);
@@ -503,7 +503,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   DBuf<int32_t> blk(n, s), offin(n, s), bsz(p, s);
   bsz.zero();
   if (n) {
-    k_block_of<<<grid_for(n, 256), 256, 0, s>>>(n, group.p, lead_scan.p, blk.p, bsz.p, dst);
+    launch(k_block_of, grid_for(n, 256), 256, 0, s, n, group.p, lead_scan.p, blk.p, bsz.p, dst);
     VB_LAUNCH_CHECK();
   }
   check_status(dst, s, "vbarms_compress: grouping");
@@ -511,7 +511,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   scan_i32_to_i64(bsz.p, boff.p, p, s);
   out.perm.alloc(n, s);
   if (n) {
-    k_member_rank<<<grid_for(n, 256), 256, 0, s>>>(n, simstart.p, simcnt.p, simbuf.p, group.p, blk.p, boff.p,
+    launch(k_member_rank, grid_for(n, 256), 256, 0, s, n, simstart.p, simcnt.p, simbuf.p, group.p, blk.p, boff.p,
                                                    offin.p, out.perm.p);
     VB_LAUNCH_CHECK();
   }
@@ -534,7 +534,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   VB_CUDA(cudaFuncSetAttribute(k_block_pattern<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pat));
   nheavy.zero();
   if (p) {
-    k_block_pattern<false, 0><<<grid_for(p, CW, 152LL * 24), CW * 32, smem_pat, s>>>(
+    launch(k_block_pattern<false, 0>, grid_for(p, CW, 152LL * 24), CW * 32, smem_pat, s, 
         p, nullptr, A.roff.p, out.perm.p, rowptr, colind, blk.p, nullptr, 0, bcnt.p, nullptr, nullptr, heavy.p,
         nheavy.p, dst);
     VB_LAUNCH_CHECK();
@@ -552,7 +552,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
     warps = std::min<int64_t>(warps, nhb);
     hblocks = (warps + CW - 1) / CW;
     gtabb.alloc((size_t)hblocks * CW * gcapb, s);
-    k_block_pattern<true, 0><<<(unsigned)hblocks, CW * 32, 0, s>>>(nhb, heavy.p, A.roff.p, out.perm.p, rowptr,
+    launch(k_block_pattern<true, 0>, (unsigned)hblocks, CW * 32, 0, s, nhb, heavy.p, A.roff.p, out.perm.p, rowptr,
                                                                   colind, blk.p, gtabb.p, gcapb, bcnt.p, nullptr,
                                                                   nullptr, nullptr, nullptr, dst);
     VB_LAUNCH_CHECK();
@@ -566,13 +566,13 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
     DBuf<int> dummy(1, s);
     dummy.zero();
     DBuf<int32_t> hv2(std::max<int>(nhb, 1), s);
-    k_block_pattern<false, 1><<<grid_for(p, CW, 152LL * 24), CW * 32, smem_pat, s>>>(
+    launch(k_block_pattern<false, 1>, grid_for(p, CW, 152LL * 24), CW * 32, smem_pat, s, 
         p, nullptr, A.roff.p, out.perm.p, rowptr, colind, blk.p, nullptr, 0, nullptr, A.bptr.p, A.bcol.p, hv2.p,
         dummy.p, dst);
     VB_LAUNCH_CHECK();
   }
   if (nhb > 0) {
-    k_block_pattern<true, 1><<<(unsigned)hblocks, CW * 32, 0, s>>>(nhb, heavy.p, A.roff.p, out.perm.p, rowptr,
+    launch(k_block_pattern<true, 1>, (unsigned)hblocks, CW * 32, 0, s, nhb, heavy.p, A.roff.p, out.perm.p, rowptr,
                                                                   colind, blk.p, gtabb.p, gcapb, nullptr, A.bptr.p,
                                                                   A.bcol.p, nullptr, nullptr, dst);
     VB_LAUNCH_CHECK();
@@ -581,7 +581,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   finish_offsets(A, s);
   A.val.zero();
   if (n) {
-    k_scatter_values<<<grid_for(n, 8), 256, 0, s>>>(n, rowptr, colind, val, blk.p, offin.p, A.rsz.p, A.bptr.p,
+    launch(k_scatter_values, grid_for(n, 8), 256, 0, s, n, rowptr, colind, val, blk.p, offin.p, A.rsz.p, A.bptr.p,
                                                      A.bcol.p, A.voff.p, A.val.p, dst);
     VB_LAUNCH_CHECK();
   }

@@ -593,14 +593,14 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   set_partitions(X.Dg, A.rsz.p, p, A.rsz.p, p, s);
   X.Dg.bptr.alloc(p + 1, s);
   X.Dg.bcol.alloc(p, s);
-  k_iota<<<grid_for(p + 1, 256), 256, 0, s>>>(p, X.Dg.bptr.p, X.Dg.bcol.p);
+  launch(k_iota, grid_for(p + 1, 256), 256, 0, s, p, X.Dg.bptr.p, X.Dg.bcol.p);
   VB_LAUNCH_CHECK();
   X.Dg.nnzb = p;
   X.Dg.voff.alloc(p + 1, s);
   {
     DBuf<int64_t> sq(p, s);
     if (p) {
-      k_sq_sizes<<<grid_for(p, 256), 256, 0, s>>>(p, A.rsz.p, sq.p);
+      launch(k_sq_sizes, grid_for(p, 256), 256, 0, s, p, A.rsz.p, sq.p);
       VB_LAUNCH_CHECK();
     }
     scan_i64(sq.p, X.Dg.voff.p, p, s);
@@ -655,7 +655,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
     X.piv.zero();
     Pools P{lcol.p, lvo.p, ucol.p, uvo.p, lstart.p, lcnt.p, ustart.p, ucnt.p, ctr.p,
             lbcap,  lvcap, ubcap,  uvcap, done.p,  abort.p};
-    k_ilut<T><<<(unsigned)nblocks, IW * 32, 0, s>>>(A.view(), ws, wvals.p, P, lval.p, uval.p, X.Dg.voff.p,
+    launch(k_ilut<T>, (unsigned)nblocks, IW * 32, 0, s, A.view(), ws, wvals.p, P, lval.p, uval.p, X.Dg.voff.p,
                                                      X.Dg.val.p, mixed ? X.Dg32.val.p : nullptr, X.piv.p,
                                                      mixed ? X.ptag.p : nullptr, mixed ? 1 : 0, cond_thr, t, lfil,
                                                      (unsigned long long)wait_limit, dst);
@@ -683,17 +683,17 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
       DBuf<T>& pval = which == 0 ? lval : uval;
       M.bptr.alloc(p + 1, s);
       DBuf<int64_t> c64(p, s);
-      k_count_to_i64<<<grid_for(p, 256), 256, 0, s>>>(p, cnt.p, c64.p);
+      launch(k_count_to_i64, grid_for(p, 256), 256, 0, s, p, cnt.p, c64.p);
       VB_LAUNCH_CHECK();
       scan_i64(c64.p, M.bptr.p, p, s);
       M.nnzb = d2h(M.bptr.p + p, s);
       M.bcol.alloc(M.nnzb, s);
       // bcol first (needed by the offsets), then offsets, then values
-      k_pool_to_vb<T><<<grid_for(p, 8), 256, 0, s>>>(p, start.p, pcol.p, pvo.p, pval.p, M.bptr.p, nullptr,
+      launch(k_pool_to_vb<T>, grid_for(p, 8), 256, 0, s, p, start.p, pcol.p, pvo.p, pval.p, M.bptr.p, nullptr,
                                                        M.bcol.p, nullptr);
       VB_LAUNCH_CHECK();
       finish_offsets(M, s);
-      k_pool_to_vb<T><<<grid_for(p, 8), 256, 0, s>>>(p, start.p, pcol.p, pvo.p, pval.p, M.bptr.p, M.voff.p,
+      launch(k_pool_to_vb<T>, grid_for(p, 8), 256, 0, s, p, start.p, pcol.p, pvo.p, pval.p, M.bptr.p, M.voff.p,
                                                        M.bcol.p, M.val.p);
       VB_LAUNCH_CHECK();
     }

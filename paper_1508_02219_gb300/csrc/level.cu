@@ -663,6 +663,26 @@ __global__ void __launch_bounds__(LW * 32)
   }
 }
 
+// Flop count of the numeric phase: 2 n_r n_Y (sum of n_s over W row Y) per
+// G block (r, Y).
+template <typename T>
+__global__ void k_schur_flops(VBView<T> G, const int64_t* __restrict__ Wbptr, const int32_t* __restrict__ Wbcol,
+                              const int32_t* __restrict__ Wcsz, unsigned long long* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  unsigned long long acc = 0;
+  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < G.nbr; r += (int64_t)gridDim.x * wpb) {
+    const unsigned long long nr = G.rsz[r];
+    for (int64_t g = G.bptr[r] + lane; g < G.bptr[r + 1]; g += 32) {
+      const int32_t Y = G.bcol[g];
+      unsigned long long ws = 0;
+      for (int64_t b = Wbptr[Y]; b < Wbptr[Y + 1]; ++b) ws += Wcsz[Wbcol[b]];
+      acc += 2ULL * nr * (unsigned long long)G.csz[Y] * ws;
+    }
+  }
+  atomicAdd(out, acc);
+}
+
 // Last reduction: drop off-diagonal blocks of S below the threshold.
 template <typename T>
 __global__ void k_schur_drop(VBView<T> S, double t, int8_t* __restrict__ keep) {
@@ -690,13 +710,13 @@ void scale_level_t(VBDev<TA>& A, DBuf<double>& r, DBuf<double>& c, cudaStream_t 
   DBuf<unsigned long long> cmax(n, s);
   cmax.zero();
   const unsigned g = grid_for(A.nbr, LW);
-  k_rowmax<TA><<<g, LW * 32, 0, s>>>(A.view(), r.p);
+  launch(k_rowmax<TA>, g, LW * 32, 0, s, A.view(), r.p);
   VB_LAUNCH_CHECK();
-  k_colmax<TA><<<g, LW * 32, 0, s>>>(A.view(), r.p, cmax.p);
+  launch(k_colmax<TA>, g, LW * 32, 0, s, A.view(), r.p, cmax.p);
   VB_LAUNCH_CHECK();
-  k_colinv<<<grid_for(n, 256), 256, 0, s>>>(n, cmax.p, c.p);
+  launch(k_colinv, grid_for(n, 256), 256, 0, s, n, cmax.p, c.p);
   VB_LAUNCH_CHECK();
-  k_apply_scale<TA><<<g, LW * 32, 0, s>>>(A.view(), r.p, c.p);
+  launch(k_apply_scale<TA>, g, LW * 32, 0, s, A.view(), r.p, c.p);
   VB_LAUNCH_CHECK();
 }
 template void scale_level_t<double>(VBDev<double>&, DBuf<double>&, DBuf<double>&, cudaStream_t);
@@ -713,42 +733,42 @@ int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t
   newpos.alloc(p, s);
   if (!p) return 0;
   const unsigned g = grid_for(p, 256);
-  k_weights<TA><<<g, 256, 0, s>>>(A.view(), w.p);
+  launch(k_weights<TA>, g, 256, 0, s, A.view(), w.p);
   VB_LAUNCH_CHECK();
   DBuf<int32_t> tcnt(p, s), trow(A.nnzb, s), pending(p, s), state(p, s);
   DBuf<int64_t> tptr(p + 1, s);
   tcnt.zero();
   const unsigned gw = grid_for(p, LW);
-  k_tcount<<<gw, LW * 32, 0, s>>>(p, A.bptr.p, A.bcol.p, tcnt.p);
+  launch(k_tcount, gw, LW * 32, 0, s, p, A.bptr.p, A.bcol.p, tcnt.p);
   VB_LAUNCH_CHECK();
   scan_i32_to_i64(tcnt.p, tptr.p, p, s);
   tcnt.zero();
-  k_tfill<<<gw, LW * 32, 0, s>>>(p, A.bptr.p, A.bcol.p, tptr.p, tcnt.p, trow.p);
+  launch(k_tfill, gw, LW * 32, 0, s, p, A.bptr.p, A.bcol.p, tptr.p, tcnt.p, trow.p);
   VB_LAUNCH_CHECK();
   DBuf<unsigned long long> remaining(1, s);
   {
     unsigned long long pp = (unsigned long long)p;
     h2d(remaining.p, &pp, 1, s);
   }
-  k_is_init<<<g, 256, 0, s>>>(p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, ddtol, pending.p, state.p, remaining.p);
+  launch(k_is_init, g, 256, 0, s, p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, ddtol, pending.p, state.p, remaining.p);
   VB_LAUNCH_CHECK();
   for (int64_t round = 0;; ++round) {
-    k_is_round_b<<<g, 256, 0, s>>>(p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, pending.p, state.p);
+    launch(k_is_round_b, g, 256, 0, s, p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, pending.p, state.p);
     VB_LAUNCH_CHECK();
-    k_is_round_a<<<g, 256, 0, s>>>(p, A.bptr.p, A.bcol.p, tptr.p, trow.p, pending.p, state.p, remaining.p);
+    launch(k_is_round_a, g, 256, 0, s, p, A.bptr.p, A.bcol.p, tptr.p, trow.p, pending.p, state.p, remaining.p);
     VB_LAUNCH_CHECK();
     if (round < 4 || (round & 3) == 3)
       if (d2h(remaining.p, s) == 0) break;
     if (round > p + 8) fail(VB_EINTERNAL, "independent-set rounds did not terminate");
   }
   DBuf<int32_t> isD(p, s), isC(p, s);
-  k_is_flags<<<g, 256, 0, s>>>(p, state.p, isD.p, isC.p);
+  launch(k_is_flags, g, 256, 0, s, p, state.p, isD.p, isC.p);
   VB_LAUNCH_CHECK();
   DBuf<int64_t> scanD(p + 1, s), scanC(p + 1, s);
   scan_i32_to_i64(isD.p, scanD.p, p, s);
   scan_i32_to_i64(isC.p, scanC.p, p, s);
   const int64_t nD = d2h(scanD.p + p, s);
-  k_is_positions<<<g, 256, 0, s>>>(p, isD.p, scanD.p, scanC.p, nD, newpos.p, pI.p);
+  launch(k_is_positions, g, 256, 0, s, p, isD.p, scanD.p, scanC.p, nD, newpos.p, pI.p);
   VB_LAUNCH_CHECK();
   return nD;
 }
@@ -764,7 +784,7 @@ void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_
   L.nD = nD;
   L.nC = nC;
   DBuf<int32_t> psz(p, s);
-  k_perm_sizes<<<grid_for(p, 256), 256, 0, s>>>(p, pI.p, A.rsz.p, psz.p);
+  launch(k_perm_sizes, grid_for(p, 256), 256, 0, s, p, pI.p, A.rsz.p, psz.p);
   VB_LAUNCH_CHECK();
   const int32_t* szD = psz.p;
   const int32_t* szC = psz.p + nD;
@@ -774,7 +794,7 @@ void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_
   set_partitions(L.C, szC, nC, szC, nC, s);
   DBuf<int64_t> cF(nD, s), cE(nC, s), cC(nC, s);
   const unsigned gw = grid_for(p, LW);
-  k_gather<0><<<gw, LW * 32, 0, s>>>(p, nD, A.bptr.p, A.bcol.p, newpos.p, cF.p, cE.p, cC.p, nullptr, nullptr,
+  launch(k_gather<0>, gw, LW * 32, 0, s, p, nD, A.bptr.p, A.bcol.p, newpos.p, cF.p, cE.p, cC.p, nullptr, nullptr,
                                      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, dst);
   VB_LAUNCH_CHECK();
   check_status(dst, s, "vbarms_factor: gather");
@@ -801,7 +821,7 @@ void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_
     VB_CUDA(cudaStreamSynchronize(s));
   }
   DBuf<int64_t> sD(nD, s), sF(nF, s), sE(nE, s), sC(nCC, s);
-  k_gather<1><<<gw, LW * 32, 0, s>>>(p, nD, A.bptr.p, A.bcol.p, newpos.p, nullptr, nullptr, nullptr, L.F.bptr.p,
+  launch(k_gather<1>, gw, LW * 32, 0, s, p, nD, A.bptr.p, A.bcol.p, newpos.p, nullptr, nullptr, nullptr, L.F.bptr.p,
                                      L.E.bptr.p, L.C.bptr.p, L.F.bcol.p, L.E.bcol.p, L.C.bcol.p, sD.p, sF.p, sE.p,
                                      sC.p, dst);
   VB_LAUNCH_CHECK();
@@ -809,10 +829,10 @@ void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_
   finish_offsets(L.F, s);
   finish_offsets(L.E, s);
   finish_offsets(L.C, s);
-  if (nD) k_copy_blocks<TA, double><<<grid_for(nD, LW), LW * 32, 0, s>>>(nD, sD.p, A.voff.p, A.val.p, L.D.voff.p, L.D.val.p);
-  if (nF) k_copy_blocks<TA, T><<<grid_for(nF, LW), LW * 32, 0, s>>>(nF, sF.p, A.voff.p, A.val.p, L.F.voff.p, L.F.val.p);
-  if (nE) k_copy_blocks<TA, T><<<grid_for(nE, LW), LW * 32, 0, s>>>(nE, sE.p, A.voff.p, A.val.p, L.E.voff.p, L.E.val.p);
-  if (nCC) k_copy_blocks<TA, T><<<grid_for(nCC, LW), LW * 32, 0, s>>>(nCC, sC.p, A.voff.p, A.val.p, L.C.voff.p, L.C.val.p);
+  if (nD) launch(k_copy_blocks<TA, double>, grid_for(nD, LW), LW * 32, 0, s, nD, sD.p, A.voff.p, A.val.p, L.D.voff.p, L.D.val.p);
+  if (nF) launch(k_copy_blocks<TA, T>, grid_for(nF, LW), LW * 32, 0, s, nF, sF.p, A.voff.p, A.val.p, L.F.voff.p, L.F.val.p);
+  if (nE) launch(k_copy_blocks<TA, T>, grid_for(nE, LW), LW * 32, 0, s, nE, sE.p, A.voff.p, A.val.p, L.E.voff.p, L.E.val.p);
+  if (nCC) launch(k_copy_blocks<TA, T>, grid_for(nCC, LW), LW * 32, 0, s, nCC, sC.p, A.voff.p, A.val.p, L.C.voff.p, L.C.val.p);
   VB_LAUNCH_CHECK();
   check_status(dst, s, "vbarms_factor: gather");
 }
@@ -827,7 +847,7 @@ void pivot_lu(VBDev<double>& D, DBuf<int32_t>& piv, DBuf<int32_t>& ptag, VBDev<f
     copy_vb<float, double>(D, D32, s);
   }
   if (nD) {
-    k_gepp<<<grid_for(nD, 128), 128, 0, s>>>(nD, D.rsz.p, D.roff.p, D.voff.p, D.val.p, piv.p, mixed ? 1 : 0,
+    launch(k_gepp, grid_for(nD, 128), 128, 0, s, nD, D.rsz.p, D.roff.p, D.voff.p, D.val.p, piv.p, mixed ? 1 : 0,
                                              cond_thr, ptag.p, mixed ? D32.val.p : nullptr, dst);
     VB_LAUNCH_CHECK();
   }
@@ -844,16 +864,16 @@ void w_or_g(const VBDev<T>& X, int which, const VBDev<double>& D, const VBDev<fl
   if (cand.nbr && cand.nnzb) {
     const unsigned g = grid_for(cand.nbr, LW);
     if (which == 0)
-      k_wg_cand<T, 0><<<g, LW * 32, 0, s>>>(cand.view(), D.rsz.p, D.roff.p, D.voff.p, D.val.p,
+      launch(k_wg_cand<T, 0>, g, LW * 32, 0, s, cand.view(), D.rsz.p, D.roff.p, D.voff.p, D.val.p,
                                             mixed ? D32.val.p : nullptr, piv.p, mixed ? ptag.p : nullptr, t, f2.p,
                                             keep.p);
     else
-      k_wg_cand<T, 1><<<g, LW * 32, 0, s>>>(cand.view(), D.rsz.p, D.roff.p, D.voff.p, D.val.p,
+      launch(k_wg_cand<T, 1>, g, LW * 32, 0, s, cand.view(), D.rsz.p, D.roff.p, D.voff.p, D.val.p,
                                             mixed ? D32.val.p : nullptr, piv.p, mixed ? ptag.p : nullptr, t, f2.p,
                                             keep.p);
     VB_LAUNCH_CHECK();
     if (lfil >= 0) {
-      k_lfil<<<grid_for(cand.nbr, 128), 128, 0, s>>>(cand.nbr, cand.bptr.p, cand.bcol.p, f2.p, keep.p, lfil, 0);
+      launch(k_lfil, grid_for(cand.nbr, 128), 128, 0, s, cand.nbr, cand.bptr.p, cand.bcol.p, f2.p, keep.p, lfil, 0);
       VB_LAUNCH_CHECK();
     }
   }
@@ -862,7 +882,7 @@ void w_or_g(const VBDev<T>& X, int which, const VBDev<double>& D, const VBDev<fl
 
 template <typename T>
 void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_reduction, double t, VBDev<T>& S,
-           cudaStream_t s, int* dst) {
+           cudaStream_t s, int* dst, KernelRec* rec) {
   const int64_t nC = C.nbr;
   VBDev<T> Sf;
   set_partitions(Sf, C.rsz.p, nC, C.rsz.p, nC, s);
@@ -876,7 +896,7 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
   VB_CUDA(cudaFuncSetAttribute(k_schur_pattern<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned gl = grid_for(nC, LW, 152LL * 24);
   if (nC) {
-    k_schur_pattern<false, 0><<<gl, LW * 32, smem, s>>>(nC, nullptr, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
+    launch(k_schur_pattern<false, 0>, gl, LW * 32, smem, s, nC, nullptr, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
                                                         W.bptr.p, W.bcol.p, nullptr, 0, cnt.p, nullptr, nullptr,
                                                         heavy.p, nheavy.p, dst);
     VB_LAUNCH_CHECK();
@@ -892,7 +912,7 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
     warps = std::min<int64_t>(warps, nh);
     hb = (warps + LW - 1) / LW;
     gtab.alloc((size_t)hb * LW * gcap, s);
-    k_schur_pattern<true, 0><<<(unsigned)hb, LW * 32, 0, s>>>(nh, heavy.p, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
+    launch(k_schur_pattern<true, 0>, (unsigned)hb, LW * 32, 0, s, nh, heavy.p, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
                                                              W.bptr.p, W.bcol.p, gtab.p, gcap, cnt.p, nullptr,
                                                              nullptr, nullptr, nullptr, dst);
     VB_LAUNCH_CHECK();
@@ -902,13 +922,13 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
   Sf.nnzb = nC ? d2h(Sf.bptr.p + nC, s) : 0;
   Sf.bcol.alloc(Sf.nnzb, s);
   if (nC) {
-    k_schur_pattern<false, 1><<<gl, LW * 32, smem, s>>>(nC, nullptr, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
+    launch(k_schur_pattern<false, 1>, gl, LW * 32, smem, s, nC, nullptr, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
                                                         W.bptr.p, W.bcol.p, nullptr, 0, nullptr, Sf.bptr.p,
                                                         Sf.bcol.p, nullptr, nullptr, dst);
     VB_LAUNCH_CHECK();
   }
   if (nh > 0) {
-    k_schur_pattern<true, 1><<<(unsigned)hb, LW * 32, 0, s>>>(nh, heavy.p, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
+    launch(k_schur_pattern<true, 1>, (unsigned)hb, LW * 32, 0, s, nh, heavy.p, C.bptr.p, C.bcol.p, G.bptr.p, G.bcol.p,
                                                              W.bptr.p, W.bcol.p, gtab.p, gcap, nullptr, Sf.bptr.p,
                                                              Sf.bcol.p, nullptr, nullptr, dst);
     VB_LAUNCH_CHECK();
@@ -916,12 +936,32 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
   check_status(dst, s, "vbarms_factor: Schur pattern");
   finish_offsets(Sf, s);
   if (nC) {
-    k_schur_numeric<T><<<grid_for(nC, LW, 152LL * 32), LW * 32, 0, s>>>(C.view(), G.view(), W.view(), Sf.view());
+    if (rec) {
+      // algorithmic work of the numeric phase: read C, G, W and write S once
+      // (values and their index arrays); flops = sum over (r, Y, s) of
+      // 2 n_r n_Y n_s
+      auto idx = [](const VBDev<T>& M) {
+        return 8.0 * (M.nbr + 1) + 4.0 * M.nnzb + 8.0 * (M.nnzb + 1);
+      };
+      rec->bytes = (double)sizeof(T) * (double)(C.nval + G.nval + W.nval + Sf.nval) + idx(C) + idx(G) + idx(W) +
+                   idx(Sf);
+      DBuf<unsigned long long> fl(1, s);
+      fl.zero();
+      if (G.nnzb) launch(k_schur_flops<T>, grid_for(G.nbr, LW), LW * 32, 0, s, G.view(), W.bptr.p, W.bcol.p,
+                         W.csz_p(), fl.p);
+      VB_LAUNCH_CHECK();
+      rec->flops = (double)d2h(fl.p, s);
+      VB_CUDA(cudaEventCreate(&rec->e0));
+      VB_CUDA(cudaEventCreate(&rec->e1));
+      VB_CUDA(cudaEventRecord(rec->e0, s));
+    }
+    launch(k_schur_numeric<T>, grid_for(nC, LW, 152LL * 32), LW * 32, 0, s, C.view(), G.view(), W.view(), Sf.view());
     VB_LAUNCH_CHECK();
+    if (rec) VB_CUDA(cudaEventRecord(rec->e1, s));
   }
   if (last_reduction && nC) {
     DBuf<int8_t> keep(Sf.nnzb, s);
-    k_schur_drop<T><<<grid_for(nC, LW), LW * 32, 0, s>>>(Sf.view(), t, keep.p);
+    launch(k_schur_drop<T>, grid_for(nC, LW), LW * 32, 0, s, Sf.view(), t, keep.p);
     VB_LAUNCH_CHECK();
     compact_blocks(Sf, keep.p, S, s);
   } else {
@@ -942,8 +982,8 @@ template void w_or_g<float>(const VBDev<float>&, int, const VBDev<double>&, cons
                             const DBuf<int32_t>&, const DBuf<int32_t>&, bool, double, int, VBDev<float>&,
                             cudaStream_t);
 template void schur<double>(const VBDev<double>&, const VBDev<double>&, const VBDev<double>&, bool, double,
-                            VBDev<double>&, cudaStream_t, int*);
+                            VBDev<double>&, cudaStream_t, int*, KernelRec*);
 template void schur<float>(const VBDev<float>&, const VBDev<float>&, const VBDev<float>&, bool, double,
-                           VBDev<float>&, cudaStream_t, int*);
+                           VBDev<float>&, cudaStream_t, int*, KernelRec*);
 
 }  // namespace vb

@@ -25,10 +25,20 @@ template <typename T>
 void w_or_g(const VBDev<T>& X, int which, const VBDev<double>& D, const VBDev<float>& D32, const DBuf<int32_t>& piv,
             const DBuf<int32_t>& ptag, bool mixed, double t, int lfil, VBDev<T>& out, cudaStream_t s);
 
-// Eq. 6: S = C - G W (drop at the last reduction).
+// Timing record of one launch of a measured kernel (CUDA events on the
+// launching stream) with its algorithmic bytes and flops.
+struct KernelRec {
+  int kernel = 0;  // 0 = Schur numeric
+  int level = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double bytes = 0, flops = 0, ms = -1;
+};
+
+// Eq. 6: S = C - G W (drop at the last reduction).  rec (may be NULL)
+// receives the timing of the numeric launch.
 template <typename T>
 void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_reduction, double t, VBDev<T>& S,
-           cudaStream_t s, int* dst);
+           cudaStream_t s, int* dst, KernelRec* rec);
 
 // Last level: block ILUT in natural order (Alg. 3 in block form).
 template <typename T>

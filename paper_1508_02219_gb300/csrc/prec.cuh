@@ -25,7 +25,13 @@ struct PrecBase {
   double mem_ratio = 0;
   DBuf<int32_t> perm;  // P_B of the matrix the factorization was built from
   DBuf<int> status;
-  virtual ~PrecBase() = default;
+  std::vector<KernelRec> krec;  // timed launches (Schur numeric per level)
+  virtual ~PrecBase() {
+    for (auto& r : krec) {
+      if (r.e0) cudaEventDestroy(r.e0);
+      if (r.e1) cudaEventDestroy(r.e1);
+    }
+  }
   virtual int levels() const = 0;
   // y = M^{-1} x, both in the block-permuted (P_B) numbering, device FP64
   virtual void apply_perm(const double* x, double* y) = 0;

@@ -361,39 +361,39 @@ __global__ void k_perm_sizes2(int64_t p, const int32_t* __restrict__ pI, const i
 void dot_dev(const double* x, const double* y, int64_t n, double* out, cudaStream_t s) {
   const int nb = (int)std::min<int64_t>(RB, std::max<int64_t>(1, (n + RT - 1) / RT));
   DBuf<double> p(nb, s);
-  k_dot_partial<<<nb, RT, 0, s>>>(x, y, n, p.p);
-  k_dot_final<<<1, RB, 0, s>>>(p.p, nb, out);
+  launch(k_dot_partial, nb, RT, 0, s, x, y, n, p.p);
+  launch(k_dot_final, 1, RB, 0, s, p.p, nb, out);
   VB_LAUNCH_CHECK();
 }
 void axpy_dev(double* y, const double* x, const double* a, double sign, int64_t n, cudaStream_t s) {
-  if (n) k_axpy_dev<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, a, sign, n);
+  if (n) launch(k_axpy_dev, grid_for(n, 256, 152LL * 16), 256, 0, s, y, x, a, sign, n);
   VB_LAUNCH_CHECK();
 }
 void axpy_host(double* y, const double* x, double a, int64_t n, cudaStream_t s) {
-  if (n) k_axpy_host<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, a, n);
+  if (n) launch(k_axpy_host, grid_for(n, 256, 152LL * 16), 256, 0, s, y, x, a, n);
   VB_LAUNCH_CHECK();
 }
 void scale_dev(double* y, const double* x, const double* d, int64_t n, cudaStream_t s) {
-  if (n) k_scale_dev<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, d, n);
+  if (n) launch(k_scale_dev, grid_for(n, 256, 152LL * 16), 256, 0, s, y, x, d, n);
   VB_LAUNCH_CHECK();
 }
 void sub_dev(double* r, const double* b, const double* ax, int64_t n, cudaStream_t s) {
-  if (n) k_sub<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(r, b, ax, n);
+  if (n) launch(k_sub, grid_for(n, 256, 152LL * 16), 256, 0, s, r, b, ax, n);
   VB_LAUNCH_CHECK();
 }
 void gather_dev(double* y, const double* x, const int32_t* idx, int64_t n, cudaStream_t s) {
-  if (n) k_gather<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, idx, n);
+  if (n) launch(k_gather, grid_for(n, 256, 152LL * 16), 256, 0, s, y, x, idx, n);
   VB_LAUNCH_CHECK();
 }
 void scatter_dev(double* y, const double* x, const int32_t* idx, int64_t n, cudaStream_t s) {
-  if (n) k_scatter<<<grid_for(n, 256, 152LL * 16), 256, 0, s>>>(y, x, idx, n);
+  if (n) launch(k_scatter, grid_for(n, 256, 152LL * 16), 256, 0, s, y, x, idx, n);
   VB_LAUNCH_CHECK();
 }
 
 // Row-block map of a VBCSR (scalar row -> block row), cached per matrix.
 static void make_rowblk(int64_t nbr, const int64_t* roff, int64_t n, DBuf<int64_t>& rb, cudaStream_t s) {
   rb.alloc(n, s);
-  if (nbr) k_rowblk<<<grid_for(nbr, 8), 256, 0, s>>>(nbr, roff, rb.p);
+  if (nbr) launch(k_rowblk, grid_for(nbr, 8), 256, 0, s, nbr, roff, rb.p);
   VB_LAUNCH_CHECK();
 }
 
@@ -401,7 +401,7 @@ void spmv_vb(const VBDev<double>& A, const double* x, double* y, cudaStream_t s)
   const int64_t n = A.nrows_scalar(s);
   DBuf<int64_t> rb;
   make_rowblk(A.nbr, A.roff.p, n, rb, s);
-  if (n) k_spmv<<<grid_for(n, 128, 152LL * 32), 128, 0, s>>>(A.view(), rb.p, n, x, y);
+  if (n) launch(k_spmv, grid_for(n, 128, 152LL * 32), 128, 0, s, A.view(), rb.p, n, x, y);
   VB_LAUNCH_CHECK();
 }
 
@@ -413,13 +413,13 @@ void build_level_maps(const LevelDev<T>& L, const int32_t* rsz, const int64_t* r
   DBuf<int32_t> psz(p, s);
   DBuf<int64_t> newoff(p + 1, s);
   if (p) {
-    k_perm_sizes2<<<grid_for(p, 256), 256, 0, s>>>(p, L.pI.p, rsz, psz.p);
+    launch(k_perm_sizes2, grid_for(p, 256), 256, 0, s, p, L.pI.p, rsz, psz.p);
     VB_LAUNCH_CHECK();
   }
   scan_i32_to_i64(psz.p, newoff.p, p, s);
   M.nf = p ? d2h(newoff.p + L.nD, s) : 0;
   if (p) {
-    k_sperm<<<grid_for(p, 8), 256, 0, s>>>(p, L.pI.p, rsz, roff, newoff.p, M.sperm.p);
+    launch(k_sperm, grid_for(p, 8), 256, 0, s, p, L.pI.p, rsz, roff, newoff.p, M.sperm.p);
     VB_LAUNCH_CHECK();
   }
 }
@@ -454,15 +454,15 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
     const LevelDev<T>& L = lev[l];
     const LevelMaps& M = maps[l];
     const double* b = l == 0 ? in : bh[l - 1] + maps[l - 1].nf;
-    if (M.n) k_gather_scale<<<grid_for(M.n, 256), 256, 0, s>>>(M.n, M.sperm.p, L.r.p, b, bh[l]);
+    if (M.n) launch(k_gather_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.r.p, b, bh[l]);
     if (L.nD)
-      k_pivot_fwd<<<grid_for(L.nD, 128), 128, 0, s>>>(L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
+      launch(k_pivot_fwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
                                                       mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, bh[l]);
     const int64_t ng = M.n - M.nf;
     if (ng && L.G.nnzb) {
       DBuf<int64_t> rb;
       make_rowblk(L.G.nbr, L.G.roff.p, ng, rb, s);
-      k_bsr_sub<T><<<grid_for(ng, 128), 128, 0, s>>>(L.G.view(), rb.p, ng, bh[l], bh[l] + M.nf);
+      launch(k_bsr_sub<T>, grid_for(ng, 128), 128, 0, s, L.G.view(), rb.p, ng, bh[l], bh[l] + M.nf);
     }
     VB_LAUNCH_CHECK();
   }
@@ -473,7 +473,7 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
     if (nlast) {
       double* yy = wp;
       double* xx = wp + nlast;
-      k_mul<<<grid_for(nlast, 256), 256, 0, s>>>(nlast, last.r.p, g, yy);
+      launch(k_mul, grid_for(nlast, 256), 256, 0, s, nlast, last.r.p, g, yy);
       const int64_t p = last.A.nbr;
       DBuf<int32_t> flags(2 * p, s);
       DBuf<unsigned long long> tick(2, s);
@@ -485,13 +485,13 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
       VB_CUDA(cudaGetDevice(&dev));
       VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 4, (p + SW - 1) / SW));
-      k_tri_fwd<T><<<nb, SW * 32, 0, s>>>(last.L.view(), yy, flags.p, tick.p, abort.p,
+      launch(k_tri_fwd<T>, nb, SW * 32, 0, s, last.L.view(), yy, flags.p, tick.p, abort.p,
                                           (unsigned long long)wait_limit, status.p);
-      k_tri_bwd<T><<<nb, SW * 32, 0, s>>>(last.U.view(), last.Dg.voff.p, last.Dg.val.p,
+      launch(k_tri_bwd<T>, nb, SW * 32, 0, s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
                                           mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx,
                                           flags.p + p, tick.p + 1, abort.p, (unsigned long long)wait_limit,
                                           status.p);
-      k_mul<<<grid_for(nlast, 256), 256, 0, s>>>(nlast, last.c.p, xx, z);
+      launch(k_mul, grid_for(nlast, 256), 256, 0, s, nlast, last.c.p, xx, z);
       VB_LAUNCH_CHECK();
       check_status(status.p, s, "vbarms_apply: last-level triangular solves");
     }
@@ -504,12 +504,12 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
     if (M.nf && L.W.nnzb) {
       DBuf<int64_t> rb;
       make_rowblk(L.W.nbr, L.W.roff.p, M.nf, rb, s);
-      k_bsr_sub<T><<<grid_for(M.nf, 128), 128, 0, s>>>(L.W.view(), rb.p, M.nf, xh[l] + M.nf, bh[l]);
+      launch(k_bsr_sub<T>, grid_for(M.nf, 128), 128, 0, s, L.W.view(), rb.p, M.nf, xh[l] + M.nf, bh[l]);
     }
     if (L.nD)
-      k_pivot_bwd<<<grid_for(L.nD, 128), 128, 0, s>>>(L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
+      launch(k_pivot_bwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
                                                       mixed ? L.D32.val.p : nullptr, L.ptag.p, bh[l], xh[l]);
-    if (M.n) k_scatter_scale<<<grid_for(M.n, 256), 256, 0, s>>>(M.n, M.sperm.p, L.c.p, xh[l], xo);
+    if (M.n) launch(k_scatter_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.c.p, xh[l], xo);
     VB_LAUNCH_CHECK();
   }
 }

@@ -3,6 +3,8 @@
 
 namespace vb {
 
+std::atomic<unsigned long long> g_launch_count{0};
+
 void check_status(int* dst, cudaStream_t s, const char* where) {
   int st = d2h(dst, s);
   if (st == DEV_OK) return;
@@ -91,15 +93,15 @@ void scan_impl(const TIn* in, int64_t* out, int64_t n, cudaStream_t s) {
   }
   const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (tiles == 1) {
-    k_tile_scan<TIn><<<1, SCAN_T, 0, s>>>(in, n, out, nullptr);
+    launch(k_tile_scan<TIn>, 1, SCAN_T, 0, s, in, n, out, nullptr);
     VB_LAUNCH_CHECK();
     return;
   }
   DBuf<int64_t> sums(tiles, s), offs(tiles + 1, s);
-  k_tile_sums<TIn><<<(unsigned)tiles, SCAN_T, 0, s>>>(in, n, sums.p);
+  launch(k_tile_sums<TIn>, (unsigned)tiles, SCAN_T, 0, s, in, n, sums.p);
   VB_LAUNCH_CHECK();
   scan_impl<int64_t>(sums.p, offs.p, tiles, s);
-  k_tile_scan<TIn><<<(unsigned)tiles, SCAN_T, 0, s>>>(in, n, out, offs.p);
+  launch(k_tile_scan<TIn>, (unsigned)tiles, SCAN_T, 0, s, in, n, out, offs.p);
   VB_LAUNCH_CHECK();
 }
 

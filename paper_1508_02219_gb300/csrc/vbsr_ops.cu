@@ -20,7 +20,7 @@ void finish_offsets(VBDev<T>& M, cudaStream_t s) {
   M.voff.alloc(M.nnzb + 1, s);
   if (M.nnzb) {
     DBuf<int64_t> vsz(M.nnzb, s);
-    k_block_sizes<<<grid_for(M.nbr, 8), 256, 0, s>>>(M.nbr, M.bptr.p, M.bcol.p, M.rsz.p, M.csz_p(), vsz.p);
+    launch(k_block_sizes, grid_for(M.nbr, 8), 256, 0, s, M.nbr, M.bptr.p, M.bcol.p, M.rsz.p, M.csz_p(), vsz.p);
     VB_LAUNCH_CHECK();
     scan_i64(vsz.p, M.voff.p, M.nnzb, s);
     M.nval = d2h(M.voff.p + M.nnzb, s);
@@ -114,7 +114,7 @@ void compact_blocks(const VBDev<T>& src, const int8_t* keep, VBDev<T>& dst, cuda
   DBuf<int64_t> cnt(src.nbr, s);
   const unsigned g = grid_for(src.nbr, 8);
   if (src.nbr) {
-    k_count_keep<<<g, 256, 0, s>>>(src.nbr, src.bptr.p, keep, cnt.p);
+    launch(k_count_keep, g, 256, 0, s, src.nbr, src.bptr.p, keep, cnt.p);
     VB_LAUNCH_CHECK();
   }
   scan_i64(cnt.p, dst.bptr.p, src.nbr, s);
@@ -122,12 +122,12 @@ void compact_blocks(const VBDev<T>& src, const int8_t* keep, VBDev<T>& dst, cuda
   dst.bcol.alloc(dst.nnzb, s);
   DBuf<int64_t> map(src.nnzb, s);
   if (src.nbr) {
-    k_keep_map<<<g, 256, 0, s>>>(src.nbr, src.bptr.p, keep, dst.bptr.p, src.bcol.p, dst.bcol.p, map.p);
+    launch(k_keep_map, g, 256, 0, s, src.nbr, src.bptr.p, keep, dst.bptr.p, src.bcol.p, dst.bcol.p, map.p);
     VB_LAUNCH_CHECK();
   }
   finish_offsets(dst, s);
   if (src.nbr && dst.nval) {
-    k_copy_kept<T><<<g, 256, 0, s>>>(src.nbr, src.bptr.p, map.p, src.voff.p, dst.voff.p, src.val.p, dst.val.p);
+    launch(k_copy_kept<T>, g, 256, 0, s, src.nbr, src.bptr.p, map.p, src.voff.p, dst.voff.p, src.val.p, dst.val.p);
     VB_LAUNCH_CHECK();
   }
 }
@@ -135,7 +135,7 @@ void compact_blocks(const VBDev<T>& src, const int8_t* keep, VBDev<T>& dst, cuda
 template <typename TD, typename TS>
 void convert_values(const VBDev<TS>& src, VBDev<TD>& dst, cudaStream_t s) {
   if (src.nval)
-    k_convert<TD, TS><<<grid_for(src.nval, 256, 152LL * 32), 256, 0, s>>>(src.nval, src.val.p, dst.val.p);
+    launch(k_convert<TD, TS>, grid_for(src.nval, 256, 152LL * 32), 256, 0, s, src.nval, src.val.p, dst.val.p);
   VB_LAUNCH_CHECK();
 }
 
@@ -171,7 +171,7 @@ void export_vb(const VBDev<T>& M, cudaStream_t s, int64_t* nbr, int64_t* nbc, in
       VB_CUDA(cudaMemcpyAsync(val, M.val.p, M.nval * 8, cudaMemcpyDeviceToHost, s));
     } else {
       DBuf<double> tmp(M.nval, s);
-      k_convert<double, T><<<grid_for(M.nval, 256, 152LL * 32), 256, 0, s>>>(M.nval, M.val.p, tmp.p);
+      launch(k_convert<double, T>, grid_for(M.nval, 256, 152LL * 32), 256, 0, s, M.nval, M.val.p, tmp.p);
       VB_LAUNCH_CHECK();
       VB_CUDA(cudaMemcpyAsync(val, tmp.p, M.nval * 8, cudaMemcpyDeviceToHost, s));
       VB_CUDA(cudaStreamSynchronize(s));

@@ -71,6 +71,8 @@ def lib():
                 "vbarms_prec_export": (i32, [vp, i32, i32, P(i64), P(i64), P(i64), P(i64), vp, vp, vp, vp, vp,
                                              vp]),
                 "vbarms_prec_vector": (i32, [vp, i32, i32, vp, vp, P(i64)]),
+                "vbarms_prec_kernel_stats": (i32, [vp, i32, P(i32), P(d), P(d), P(d)]),
+                "vbarms_launch_count": (C.c_uint64, []),
                 "vbarms_vbsr_destroy": (None, [vp]),
                 "vbarms_prec_destroy": (None, [vp]),
             }
@@ -183,6 +185,12 @@ class Prec:
         _check(lib().vbarms_prec_stats(self.h, C.byref(lv), C.byref(mr), C.cast(ph, C.c_void_p)))
         return dict(levels=lv.value, mem_ratio=mr.value, phase_s=dict(zip(PHASES, list(ph))))
 
+    def kernel_stats(self, kernel: int = 0) -> dict:
+        n = C.c_int()
+        ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+        _check(lib().vbarms_prec_kernel_stats(self.h, kernel, C.byref(n), C.byref(ms), C.byref(by), C.byref(fl)))
+        return dict(launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
+
     @property
     def levels(self) -> int:
         return self.stats()["levels"]
@@ -255,3 +263,8 @@ def exported_symbols() -> list[str]:
     txt = open(hdr).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(vbarms_\w+|fgmres_solve)\s*\(", txt)))
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(lib().vbarms_launch_count())
