@@ -333,7 +333,7 @@ vb_status vbarms_apply(vbarms_prec M, const double* x, double* y) {
     gather_dev(xp.p, x, P.perm.p, P.n, P.s);
     P.apply_perm(xp.p, yp.p);
     scatter_dev(y, yp.p, P.perm.p, P.n, P.s);
-    VB_CUDA(cudaStreamSynchronize(P.s));
+    check_status(P.status.p, P.s, "vbarms_apply");
   });
 }
 
@@ -341,17 +341,19 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
                        int maxit, int* iters, double* relres) {
   if (!A || !b || !x) return set_err(VB_EINVAL, "NULL argument");
   if (restart < 1 || maxit < 0 || !(rtol >= 0.0)) return set_err(VB_EINVAL, "restart < 1, maxit < 0 or rtol < 0");
+  if (M && M->impl->n != A->C.n) return set_err(VB_EINVAL, "preconditioner and matrix sizes differ");
   bool conv = false;
   vb_status st = guarded([&] {
     cudaStream_t s = A->s;
     const int64_t n = A->C.n;
     const int m = restart;
     const int32_t* perm = A->C.perm.p;
+    if (n && !A->rowblk.p) rowblk_map(A->C.A, n, A->rowblk, s);
     DBuf<double> bp(n, s), xp(n, s), r(n, s), w(n, s), V((size_t)(m + 1) * n, s), Z((size_t)m * n, s);
-    DBuf<double> hcol(m + 2, s);
+    DBuf<double> hcol(m + 2, s), red(512, s);
     gather_dev(bp.p, b, perm, n, s);
     gather_dev(xp.p, x, perm, n, s);
-    dot_dev(bp.p, bp.p, n, hcol.p, s);
+    dot_dev(bp.p, bp.p, n, hcol.p, red.p, s);
     const double bnorm = std::sqrt(d2h(hcol.p, s));
     int it = 0;
     double rnorm = 0;
@@ -364,11 +366,12 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
       return;
     }
     const double target = rtol * bnorm;
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m), hh(m + 2);
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m);
     for (;;) {
-      spmv_vb(A->C.A, xp.p, w.p, s);
+      // true residual r = b - A x
+      spmv_vb(A->C.A, A->rowblk.p, n, xp.p, w.p, s);
       sub_dev(r.p, bp.p, w.p, n, s);
-      dot_dev(r.p, r.p, n, hcol.p, s);
+      dot_dev(r.p, r.p, n, hcol.p, red.p, s);
       rnorm = std::sqrt(d2h(hcol.p, s));
       if (rnorm <= target || it >= maxit) break;
       VB_CUDA(cudaMemcpyAsync(hcol.p + m + 1, &rnorm, sizeof(double), cudaMemcpyHostToDevice, s));
@@ -379,21 +382,24 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
       for (; j < m && it < maxit; ++j) {
         double* vj = V.p + (size_t)j * n;
         double* zj = Z.p + (size_t)j * n;
+        // flexible step: z_j = M^{-1} v_j, w = A z_j, modified Gram-Schmidt
         if (M)
           M->impl->apply_perm(vj, zj);
         else
           VB_CUDA(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        spmv_vb(A->C.A, zj, w.p, s);
+        spmv_vb(A->C.A, A->rowblk.p, n, zj, w.p, s);
         for (int i = 0; i <= j; ++i) {
-          dot_dev(w.p, V.p + (size_t)i * n, n, hcol.p + i, s);
+          dot_dev(w.p, V.p + (size_t)i * n, n, hcol.p + i, red.p, s);
           axpy_dev(w.p, V.p + (size_t)i * n, hcol.p + i, -1.0, n, s);
         }
-        dot_dev(w.p, w.p, n, hcol.p + j + 1, s);
+        dot_dev(w.p, w.p, n, hcol.p + j + 1, red.p, s);
         std::vector<double> hc = d2h_vec(hcol.p, j + 2, s);
+        if (M) check_status(M->impl->status.p, s, "fgmres_solve: preconditioner");
         const double hn = std::sqrt(hc[j + 1]);
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
         H[(size_t)(j + 1) * m + j] = hn;
         ++it;
+        // Givens rotations of the new Hessenberg column
         for (int i = 0; i < j; ++i) {
           const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
           H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
@@ -413,8 +419,8 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
         }
         VB_CUDA(cudaMemcpyAsync(hcol.p + m + 1, &hn, sizeof(double), cudaMemcpyHostToDevice, s));
         scale_dev(V.p + (size_t)(j + 1) * n, w.p, hcol.p + m + 1, n, s);
-        VB_CUDA(cudaStreamSynchronize(s));
       }
+      // x <- x + Z y with the triangular solve of the rotated Hessenberg
       for (int i = j - 1; i >= 0; --i) {
         double sacc = gv[i];
         for (int k = i + 1; k < j; ++k) sacc -= H[(size_t)i * m + k] * yv[k];

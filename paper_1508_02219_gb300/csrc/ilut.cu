@@ -145,6 +145,43 @@ __device__ __forceinline__ int ws_new_slot(const Workspace& ws, int* keys, int* 
   return hpos[slot] < 0 ? -1 : slot;
 }
 
+constexpr int SMB = 16;         // pivot blocks up to SMB x SMB are staged in shared memory
+constexpr int MAX_SLOTS = 4096;  // largest workspace (blocks of one working row)
+
+// x (one row of length m) <- x (P^T L U)^{-1} from a staged pivot block
+// (values held as doubles; TL is the arithmetic type).
+template <typename T, typename TL>
+__device__ void ainv_right_row_s(const double* lu, const int* pv, int m, T* x) {
+  for (int j = 0; j < m; ++j) {
+    TL s = (TL)x[j];
+    for (int q = 0; q < j; ++q) s = msub<TL>(s, (TL)x[q], (TL)lu[q * m + j]);
+    x[j] = (T)(s / (TL)lu[j * m + j]);
+  }
+  for (int j = m - 1; j >= 0; --j) {
+    TL s = (TL)x[j];
+    for (int q = j + 1; q < m; ++q) s = msub<TL>(s, (TL)x[q], (TL)lu[q * m + j]);
+    x[j] = (T)s;
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    const int p = pv[k];
+    if (p > k && p < m) {
+      const T t = x[k];
+      x[k] = x[p];
+      x[p] = t;
+    }
+  }
+}
+
+struct IlutShared {
+  double lu[IW][SMB * SMB];
+  double mult[IW][SMB * SMB];
+  int pv[IW][SMB];
+  int64_t qoff[IW][32];  // workspace value offset of each staged U block's target
+  int64_t quo[IW][32];   // value offset of the U block in the pool
+  int qnj[IW][32];
+  int qpre[IW][33];      // element prefix of the staged U blocks
+};
+
 template <typename T>
 __global__ void __launch_bounds__(IW * 32)
     k_ilut(VBView<T> A, Workspace ws, T* __restrict__ wvals_all, Pools P, T* __restrict__ lval,
@@ -154,6 +191,7 @@ __global__ void __launch_bounds__(IW * 32)
   __shared__ int s_nslots[IW];
   __shared__ unsigned long long s_nvals[IW];
   __shared__ int s_flag[IW];
+  __shared__ IlutShared sh;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t wid = (int64_t)blockIdx.x * IW + warp;
   int* keys = ws.keys + wid * ws.ht;
@@ -228,7 +266,7 @@ __global__ void __launch_bounds__(IW * 32)
             *vflag = 2;
             break;
           }
-          __nanosleep(128);
+          __nanosleep(32);
         }
         // a row that failed still publishes (so no one waits forever) but
         // raises abort first: its factors must not be used
@@ -243,11 +281,26 @@ __global__ void __launch_bounds__(IW * 32)
       const int nk = A.rsz[k];
       T* m = wv + soff[sk];
       const bool use64 = sizeof(T) == sizeof(double) || (ptag && __ldcg(ptag + k));
-      for (int a = lane; a < ni; a += 32) {
-        if (use64)
-          ainv_right_row<T, double>(dg + dgoff[k], piv + A.roff[k], nk, m + a * nk);
-        else
-          ainv_right_row<T, float>(dg32 + dgoff[k], piv + A.roff[k], nk, m + a * nk);
+      const bool staged = nk <= SMB && ni <= SMB;
+      if (staged) {
+        // one coalesced load of the pivot block of row k
+        for (int e = lane; e < nk * nk; e += 32)
+          sh.lu[warp][e] = use64 ? __ldcg(dg + dgoff[k] + e) : (double)__ldcg(dg32 + dgoff[k] + e);
+        if (lane < nk) sh.pv[warp][lane] = __ldcg(piv + A.roff[k] + lane);
+        __syncwarp();
+        if (lane < ni) {
+          if (use64)
+            ainv_right_row_s<T, double>(sh.lu[warp], sh.pv[warp], nk, m + lane * nk);
+          else
+            ainv_right_row_s<T, float>(sh.lu[warp], sh.pv[warp], nk, m + lane * nk);
+        }
+      } else {
+        for (int a = lane; a < ni; a += 32) {
+          if (use64)
+            ainv_right_row<T, double>(dg + dgoff[k], piv + A.roff[k], nk, m + a * nk);
+          else
+            ainv_right_row<T, float>(dg32 + dgoff[k], piv + A.roff[k], nk, m + a * nk);
+        }
       }
       __syncwarp();
       double f2 = 0.0;
@@ -262,75 +315,96 @@ __global__ void __launch_bounds__(IW * 32)
         sstate[sk] = SL_LKEPT;
         sf2[sk] = f2;
       }
+      if (staged)
+        for (int e = lane; e < ni * nk; e += 32) sh.mult[warp][e] = (double)m[e];
       const int64_t u0 = __ldcg(P.ustart + k);
-      int uc = __ldcg(P.ucnt + k);
+      const int uc = __ldcg(P.ucnt + k);
       if (u0 < 0 || uc < 0 || u0 + uc > P.ubcap) {  // never true for a published row: record and skip
         status_local = DEV_INTERNAL;
         break;
       }
-      // create the fill blocks of the U columns of row k that are missing:
-      // probe (read-only) then place, separated by __syncwarp
-      for (int q0 = 0; q0 < uc; q0 += 32) {
+      // U row k in chunks of 32 blocks: look up or create the target blocks
+      // (probe, then place, separated by __syncwarp), then update all
+      // elements of the chunk with lanes spread over the flattened elements.
+      for (int q0 = 0; q0 < uc && status_local == 0; q0 += 32) {
         const int q = q0 + lane;
         int32_t j = -1;
+        int slot = -1;
+        int64_t uo = 0;
         bool missing = false;
         if (q < uc) {
           j = __ldcg(P.ucol + u0 + q);
-          if (j <= k || j >= A.nbr) {  // a published U column is always right of k: record and skip
-            *vflag = 4;
+          uo = __ldcg(P.uvo + u0 + q);
+          if (j <= k || j >= A.nbr || uo < 0 || uo + (int64_t)nk * A.rsz[j] > P.uvcap) {
+            *vflag = 4;  // a published U block always lies right of k inside the pool
             j = -1;
           } else {
-            missing = ws_lookup(keys, scol, hmask, j) < 0;
+            slot = ws_lookup(keys, scol, hmask, j);
+            missing = slot < 0;
           }
         }
         __syncwarp();
         if (missing) {
           const int sz = ni * A.rsz[j];
-          const int slot = ws_new_slot<T>(ws, keys, hpos, scol, soff, sstate, &s_nslots[warp], &s_nvals[warp],
-                                          hmask, j, sz);
+          slot = ws_new_slot<T>(ws, keys, hpos, scol, soff, sstate, &s_nslots[warp], &s_nvals[warp], hmask, j, sz);
           if (slot < 0)
             *vflag = 1;
           else
             for (int e = 0; e < sz; ++e) wv[soff[slot] + e] = (T)0;
         }
         __syncwarp();
-      }
-      if (*vflag == 1) {
-        status_local = DEV_OVERFLOW;
-        break;
-      }
-      if (*vflag == 4) {
-        status_local = DEV_INTERNAL;
-        break;
-      }
-      // a_ij -= m * u_kj, one U block at a time, lanes over its elements
-      for (int q = 0; q < uc; ++q) {
-        const int32_t j = __ldcg(P.ucol + u0 + q);
-        const int nj = A.rsz[j];
-        const int slot = ws_lookup(keys, scol, hmask, j);
-        if (slot < 0) {
+        if (*vflag == 1) {
+          status_local = DEV_OVERFLOW;
+          break;
+        }
+        if (*vflag == 4) {
           status_local = DEV_INTERNAL;
           break;
         }
-        T* B = wv + soff[slot];
-        const int64_t uo = __ldcg(P.uvo + u0 + q);
-        if (uo < 0 || uo + (int64_t)nk * nj > P.uvcap) {
-          status_local = DEV_INTERNAL;
-          break;
+        const int nj = j >= 0 ? A.rsz[j] : 0;
+        const int sz = ni * nj;
+        int incl = sz;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
         }
-        const T* U = uval + uo;
-        for (int e = lane; e < ni * nj; e += 32) {
-          const int a = e / nj, jj = e - a * nj;
-          T acc = B[e];
-          for (int r = 0; r < nk; ++r) acc = msub<T>(acc, m[a * nk + r], __ldcg(U + r * nj + jj));
-          B[e] = acc;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        sh.qpre[warp][lane] = incl - sz;
+        if (lane == 31) sh.qpre[warp][32] = total;
+        sh.qoff[warp][lane] = slot >= 0 ? soff[slot] : 0;
+        sh.quo[warp][lane] = uo;
+        sh.qnj[warp][lane] = nj;
+        __syncwarp();
+        const int nq = min(32, uc - q0);
+        for (int e = lane; e < total; e += 32) {
+          int lo = 0, hi = nq - 1;  // block t with qpre[t] <= e < qpre[t + 1]
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sh.qpre[warp][mid] <= e)
+              lo = mid;
+            else
+              hi = mid - 1;
+          }
+          const int tq = lo;
+          const int njt = sh.qnj[warp][tq];
+          const int local = e - sh.qpre[warp][tq];
+          const int a = local / njt, jj = local - a * njt;
+          T* B = wv + sh.qoff[warp][tq];
+          const T* U = uval + sh.quo[warp][tq];
+          T acc = B[local];
+          if (staged) {
+            for (int r = 0; r < nk; ++r) acc = msub<T>(acc, (T)sh.mult[warp][a * nk + r], __ldcg(U + r * njt + jj));
+          } else {
+            for (int r = 0; r < nk; ++r) acc = msub<T>(acc, m[a * nk + r], __ldcg(U + r * njt + jj));
+          }
+          B[local] = acc;
         }
         __syncwarp();
       }
     }
     const int ns = min(*vns, ws.smax);
+    int dslot = -1;
     if (status_local == 0) {
-      int dslot = -1;
       for (int s = lane; s < ns; s += 32)
         if (scol[s] == i && sstate[s] == SL_LIVE) dslot = s;
       dslot = warp_max_i(dslot);
@@ -348,33 +422,28 @@ __global__ void __launch_bounds__(IW * 32)
         }
       }
       __syncwarp();
-      // lfil: lane 0 trims the L part, lane 1 the U part (disjoint slots)
-      if (lfil >= 0 && lane < 2) {
-        const bool isL = lane == 0;
-        const int mark = isL ? 10 : 20;
-        int cnt = 0;
-        for (int s = 0; s < ns; ++s)
-          cnt += (isL ? sstate[s] == SL_LKEPT : (sstate[s] == SL_LIVE && scol[s] > i)) ? 1 : 0;
-        if (cnt > lfil) {
-          for (int sel = 0; sel < lfil; ++sel) {
-            int bs = -1;
-            for (int s = 0; s < ns; ++s) {
-              const bool in = isL ? sstate[s] == SL_LKEPT : (sstate[s] == SL_LIVE && scol[s] > i);
-              if (!in) continue;
-              if (bs < 0 || sf2[s] > sf2[bs] || (sf2[s] == sf2[bs] && scol[s] < scol[bs])) bs = s;
-            }
-            if (bs < 0) break;
-            sstate[bs] = mark;
+      // lfil: keep the lfil largest of the L part and of the U part (rank by
+      // (norm desc, column asc); ranks computed before any state changes)
+      if (lfil >= 0) {
+        unsigned cutmask[MAX_SLOTS / 1024] = {};  // bit tq: slot lane + 32 tq is cut
+        for (int tq = 0; tq * 32 < ns && tq < MAX_SLOTS / 32; ++tq) {
+          const int s = tq * 32 + lane;
+          if (s >= ns) continue;
+          const int st0 = sstate[s];
+          const bool isL = st0 == SL_LKEPT, isU = st0 == SL_LIVE && scol[s] > i;
+          if (!isL && !isU) continue;
+          int rank = 0;
+          for (int q = 0; q < ns; ++q) {
+            const bool same = isL ? sstate[q] == SL_LKEPT : (sstate[q] == SL_LIVE && scol[q] > i);
+            if (same && (sf2[q] > sf2[s] || (sf2[q] == sf2[s] && scol[q] < scol[s]))) ++rank;
           }
-          for (int s = 0; s < ns; ++s) {
-            const bool in = isL ? sstate[s] == SL_LKEPT : (sstate[s] == SL_LIVE && scol[s] > i);
-            if (in) sstate[s] = SL_DEAD;
-          }
-          for (int s = 0; s < ns; ++s)
-            if (sstate[s] == mark) sstate[s] = isL ? SL_LKEPT : SL_LIVE;
+          if (rank >= lfil) cutmask[tq >> 5] |= 1u << (tq & 31);
         }
+        __syncwarp();
+        for (int tq = 0; tq < MAX_SLOTS / 32; ++tq)
+          if (cutmask[tq >> 5] & (1u << (tq & 31))) sstate[tq * 32 + lane] = SL_DEAD;
+        __syncwarp();
       }
-      __syncwarp();
       int nl = 0, nu = 0;
       long long vl = 0, vu = 0;
       for (int s = lane; s < ns; s += 32) {
@@ -433,10 +502,7 @@ __global__ void __launch_bounds__(IW * 32)
             for (int e = 0; e < ni * nc; ++e) uval[uvv + vo + e] = wv[soff[s] + e];
           }
         }
-        int dslot = -1;
-        for (int s = lane; s < ns; s += 32)
-          if (scol[s] == i && sstate[s] == SL_LIVE) dslot = s;
-        dslot = warp_max_i(dslot);
+        double norm1 = 0.0;
         if (lane == 0) {
           P.lstart[i] = (int64_t)lb;
           P.lcnt[i] = nl;
@@ -446,7 +512,6 @@ __global__ void __launch_bounds__(IW * 32)
           double* a = dg + dgoff[i];
           const T* src = wv + soff[dslot];
           for (int e = 0; e < ni * ni; ++e) a[e] = (double)src[e];
-          double norm1 = 0.0;
           if (mixed)
             for (int jj = 0; jj < ni; ++jj) {
               double sum = 0.0;
@@ -484,40 +549,39 @@ __global__ void __launch_bounds__(IW * 32)
                 a[ii * ni + jj] = __dsub_rn(a[ii * ni + jj], __dmul_rn(l, a[kk * ni + jj]));
             }
           }
-          if (singular) {
-            *vflag = 3;
-          } else if (mixed) {
-            int tag = 1;
-            if (ni <= 64) {
-              double x[64];
-              double inv1 = 0.0;
-              for (int jj = 0; jj < ni; ++jj) {
-                for (int ii = 0; ii < ni; ++ii) x[ii] = ii == jj ? 1.0 : 0.0;
-                for (int kk = 0; kk < ni; ++kk)
-                  if (pv[kk] != kk) {
-                    const double tt = x[kk];
-                    x[kk] = x[pv[kk]];
-                    x[pv[kk]] = tt;
-                  }
-                for (int ii = 1; ii < ni; ++ii)
-                  for (int kk = 0; kk < ii; ++kk) x[ii] -= a[ii * ni + kk] * x[kk];
-                for (int ii = ni - 1; ii >= 0; --ii) {
-                  double sum = x[ii];
-                  for (int kk = ii + 1; kk < ni; ++kk) sum -= a[ii * ni + kk] * x[kk];
-                  x[ii] = sum / a[ii * ni + ii];
-                }
-                double cs = 0.0;
-                for (int ii = 0; ii < ni; ++ii) cs += fabs(x[ii]);
-                inv1 = fmax(inv1, cs);
-              }
-              tag = norm1 * inv1 > cond_thr ? 1 : 0;
-            }
-            ptag[i] = tag;
-            for (int e = 0; e < ni * ni; ++e) dg32[dgoff[i] + e] = (float)a[e];
-          }
+          if (singular) *vflag = 3;
         }
         __syncwarp();
         if (*vflag == 3) status_local = DEV_ESINGULAR;
+        if (status_local == 0 && mixed) {
+          // 1-norm condition estimate with the explicit inverse: lane jj
+          // solves for column jj (blocks up to 32; larger ones stay FP64)
+          const double* a = dg + dgoff[i];
+          const int32_t* pv = piv + A.roff[i];
+          double cs = 0.0;
+          if (ni <= 32 && lane < ni) {
+            double x[32];
+            for (int ii = 0; ii < ni; ++ii) x[ii] = ii == lane ? 1.0 : 0.0;
+            for (int kk = 0; kk < ni; ++kk)
+              if (pv[kk] != kk) {
+                const double tt = x[kk];
+                x[kk] = x[pv[kk]];
+                x[pv[kk]] = tt;
+              }
+            for (int ii = 1; ii < ni; ++ii)
+              for (int kk = 0; kk < ii; ++kk) x[ii] -= a[ii * ni + kk] * x[kk];
+            for (int ii = ni - 1; ii >= 0; --ii) {
+              double sum = x[ii];
+              for (int kk = ii + 1; kk < ni; ++kk) sum -= a[ii * ni + kk] * x[kk];
+              x[ii] = sum / a[ii * ni + ii];
+            }
+            for (int ii = 0; ii < ni; ++ii) cs += fabs(x[ii]);
+          }
+          for (int o = 16; o > 0; o >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+          norm1 = __shfl_sync(0xffffffffu, norm1, 0);
+          if (lane == 0) ptag[i] = (ni > 32 || norm1 * cs > cond_thr) ? 1 : 0;
+          for (int e = lane; e < ni * ni; e += 32) dg32[dgoff[i] + e] = (float)a[e];
+        }
       }
     }
     if (status_local != 0 && lane == 0) {
@@ -528,7 +592,10 @@ __global__ void __launch_bounds__(IW * 32)
       P.lstart[i] = 0;
       P.ustart[i] = 0;
     }
-    if (lane == 0) atomicMax(P.ctr + 5, s_nvals[warp]);
+    if (lane == 0) {  // what the row asked for, to size a retry
+      atomicMax(P.ctr + 5, s_nvals[warp]);
+      atomicMax(P.ctr + 6, (unsigned long long)s_nslots[warp]);
+    }
     // publish the row: every lane's writes are made visible device-wide
     // before lane 0 raises the flag
     __threadfence();
@@ -668,8 +735,11 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
       lvcap = std::max<int64_t>(2 * lvcap, (int64_t)c[1] + 4096);
       ubcap = std::max<int64_t>(2 * ubcap, (int64_t)c[2] + 1024);
       uvcap = std::max<int64_t>(2 * uvcap, (int64_t)c[3] + 4096);
-      if ((int64_t)c[5] >= vmax / 2) vmax *= 4;
-      smax *= 2;
+      while ((int64_t)c[5] > vmax) vmax *= 2;
+      if ((int64_t)c[6] > smax) {
+        while (smax < (int)c[6] && smax < MAX_SLOTS) smax *= 2;
+        if ((int64_t)c[6] > MAX_SLOTS) fail(VB_ENOMEM, "last-level ILUT: a working row exceeds 4096 blocks");
+      }
       continue;
     }
     check_status(dst, s, "vbarms_factor: last-level block ILUT");

@@ -13,6 +13,7 @@ enum Phase { PH_SCALE = 0, PH_ORDER, PH_GATHER, PH_PIVOT, PH_W, PH_G, PH_SCHUR, 
 // Per level: the scalar permutation of P_I (new scalar position -> old).
 struct LevelMaps {
   DBuf<int32_t> sperm;
+  DBuf<int64_t> grow, wrow;  // scalar row -> block row of G and W (solve phase)
   int64_t n = 0, nf = 0;
 };
 
@@ -33,7 +34,8 @@ struct PrecBase {
     }
   }
   virtual int levels() const = 0;
-  // y = M^{-1} x, both in the block-permuted (P_B) numbering, device FP64
+  // y = M^{-1} x, both in the block-permuted (P_B) numbering, device FP64.
+  // Enqueues work only; read `status` (check_status) after synchronizing.
   virtual void apply_perm(const double* x, double* y) = 0;
   virtual void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval,
                           int32_t* rsz, int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff,
@@ -46,7 +48,15 @@ struct PrecDev : PrecBase {
   std::vector<LevelDev<T>> lev;
   std::vector<LevelMaps> maps;
   LastDev<T> last;
-  DBuf<double> work;  // apply scratch: 2 * n per level depth, allocated once
+  // solve-phase scratch, allocated on the first apply
+  bool prepared = false;
+  int nsm = 0;
+  int64_t nlast = 0;
+  DBuf<double> work;
+  DBuf<int32_t> flags;
+  DBuf<unsigned long long> tick;
+  DBuf<int> abort_flag;
+  void prepare_apply();
   int levels() const override { return (int)lev.size(); }
   void apply_perm(const double* x, double* y) override;
   void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval, int32_t* rsz,
@@ -59,11 +69,15 @@ template <typename T>
 void build_level_maps(const LevelDev<T>& L, const int32_t* rsz, const int64_t* roff, int64_t p, LevelMaps& M,
                       cudaStream_t s);
 
-// y = A x on a VBCSR matrix (FP64), scalar rows in order.
-void spmv_vb(const VBDev<double>& A, const double* x, double* y, cudaStream_t s);
+// y = A x on a VBCSR matrix (FP64), scalar rows in order; rowblk maps each
+// of the n scalar rows to its block row (rowblk_map builds it).
+void spmv_vb(const VBDev<double>& A, const int64_t* rowblk, int64_t n, const double* x, double* y,
+             cudaStream_t s);
+void rowblk_map(const VBDev<double>& A, int64_t n, DBuf<int64_t>& rb, cudaStream_t s);
 
-// Vector kernels used by FGMRES (deterministic two-stage reductions).
-void dot_dev(const double* x, const double* y, int64_t n, double* out, cudaStream_t s);
+// Vector kernels used by FGMRES (deterministic two-stage reductions; scratch
+// holds at least 512 doubles).
+void dot_dev(const double* x, const double* y, int64_t n, double* out, double* scratch, cudaStream_t s);
 void axpy_dev(double* y, const double* x, const double* alpha_dev, double sign, int64_t n, cudaStream_t s);
 void axpy_host(double* y, const double* x, double alpha, int64_t n, cudaStream_t s);
 void scale_dev(double* y, const double* x, const double* div_dev, int64_t n, cudaStream_t s);

@@ -134,129 +134,115 @@ __global__ void k_rowblk(int64_t nbr, const int64_t* __restrict__ roff, int64_t*
     for (int64_t q = roff[I] + lane; q < roff[I + 1]; q += 32) rowblk[q] = I;
 }
 
-// Sync-free block forward substitution y_i -= sum_{k<i} L_ik y_k, rows in
-// ticket order, one warp per block row, bounded waits.
-template <typename T>
-__global__ void k_tri_fwd(VBView<T> L, double* __restrict__ y, int32_t* __restrict__ done,
-                          unsigned long long* ticket, int* abort, unsigned long long wait_limit, int* st) {
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    long long row = 0;
-    if (lane == 0) row = (long long)atomicAdd(ticket, 1ULL);
-    row = __shfl_sync(0xffffffffu, row, 0);
-    if (row >= L.nbr) break;
-    const int64_t i = row;
-    const int ni = L.rsz[i];
-    const int64_t r0 = L.roff[i];
-    double s[TRI_R];
-#pragma unroll
-    for (int t = 0; t < TRI_R; ++t) s[t] = lane + 32 * t < ni ? y[r0 + lane + 32 * t] : 0.0;
-    bool failed = ni > 32 * TRI_R;
-    if (failed && lane == 0) dev_fail(st, DEV_INTERNAL);
-    for (int64_t b = L.bptr[i]; b < L.bptr[i + 1] && !failed; ++b) {
-      const int32_t k = L.bcol[b];
-      if (lane == 0) {
-        unsigned long long it = 0;
-        while (*((volatile int32_t*)&done[k]) == 0) {
-          if (*((volatile int*)abort)) {
-            failed = true;
-            break;
-          }
-          if (++it > wait_limit) {
-            dev_fail(st, DEV_ETIMEOUT);
-            atomicExch(abort, 1);
-            failed = true;
-            break;
-          }
-          __nanosleep(64);
-        }
-        if (*((volatile int*)abort)) failed = true;  // a failed row publishes after raising abort
-        __threadfence();
-      }
-      failed = __shfl_sync(0xffffffffu, failed, 0);
-      if (failed) break;
-      const int nk = L.csz[k];
-      const double* yk = y + L.coff[k];
-#pragma unroll
-      for (int t = 0; t < TRI_R; ++t) {
-        const int a = lane + 32 * t;
-        if (a < ni) {
-          const T* v = L.val + L.voff[b] + (int64_t)a * nk;
-          for (int q = 0; q < nk; ++q) s[t] = __dsub_rn(s[t], __dmul_rn(ld(v + q), __ldcg(yk + q)));
-        }
-      }
+// Bounded spin until done[k] is set; false when the wait ran out or another
+// row failed (a failed row raises abort before it publishes).
+__device__ __forceinline__ bool wait_row(const int32_t* done, int64_t k, int* abort, unsigned long long limit,
+                                         int* st) {
+  unsigned long long it = 0;
+  while (*((volatile const int32_t*)&done[k]) == 0) {
+    if (*((volatile int*)abort)) return false;
+    if (++it > limit) {
+      dev_fail(st, DEV_ETIMEOUT);
+      atomicExch(abort, 1);
+      return false;
     }
-#pragma unroll
-    for (int t = 0; t < TRI_R; ++t)
-      if (lane + 32 * t < ni) y[r0 + lane + 32 * t] = s[t];
-    __threadfence();  // every lane's writes before the flag
-    __syncwarp();
-    if (lane == 0) atomicExch(&done[i], 1);
+    __nanosleep(32);
   }
+  if (*((volatile int*)abort)) return false;
+  __threadfence();
+  return true;
 }
 
-// Sync-free block backward substitution x_i = D_i^{-1}(y_i - sum_{j>i} U_ij x_j),
-// rows in descending ticket order.
-template <typename T>
-__global__ void k_tri_bwd(VBView<T> U, const int64_t* __restrict__ dgoff, const double* __restrict__ lu64,
-                          const float* __restrict__ lu32, const int32_t* __restrict__ ptag,
-                          const int32_t* __restrict__ piv, const double* __restrict__ y, double* __restrict__ x,
-                          int32_t* __restrict__ done, unsigned long long* ticket, int* abort,
-                          unsigned long long wait_limit, int* st) {
+constexpr int TRI_MR = 16;  // block rows up to this size use the lane-per-block path
+
+// Sync-free block triangular sweep over the last-level factors, one warp per
+// block row, rows in ticket order (ascending for L, descending for U).
+//   forward  (BWD = false): y_i <- y_i - sum_{k<i} L_ik y_k        (in place)
+//   backward (BWD = true):  x_i <- D_i^{-1} (y_i - sum_{j>i} U_ij x_j)
+// Rows of up to TRI_MR scalars: every lane owns some blocks of the row, waits
+// for its own dependency and accumulates its products privately; a warp
+// reduction forms the update, so the row's latency is that of its slowest
+// dependency plus one block product.  Larger rows use lanes over scalar rows.
+template <typename T, bool BWD>
+__global__ void __launch_bounds__(SW * 32)
+    k_tri(VBView<T> M, const int64_t* __restrict__ dgoff, const double* __restrict__ lu64,
+          const float* __restrict__ lu32, const int32_t* __restrict__ ptag, const int32_t* __restrict__ piv,
+          const double* __restrict__ rhs, double* __restrict__ out, int32_t* __restrict__ done,
+          unsigned long long* ticket, int* abort, unsigned long long wait_limit, int* st) {
   __shared__ double sv[SW][32 * TRI_R];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (;;) {
     long long t0 = 0;
     if (lane == 0) t0 = (long long)atomicAdd(ticket, 1ULL);
     t0 = __shfl_sync(0xffffffffu, t0, 0);
-    if (t0 >= U.nbr) break;
-    const int64_t i = U.nbr - 1 - t0;
-    const int ni = U.rsz[i];
-    const int64_t r0 = U.roff[i];
-    double s[TRI_R];
+    if (t0 >= M.nbr) break;
+    const int64_t i = BWD ? M.nbr - 1 - t0 : t0;
+    const int ni = M.rsz[i];
+    const int64_t r0 = M.roff[i];
+    bool failed = false;
+    if (ni <= TRI_MR) {
+      double part[TRI_MR];
 #pragma unroll
-    for (int t = 0; t < TRI_R; ++t) s[t] = lane + 32 * t < ni ? y[r0 + lane + 32 * t] : 0.0;
-    bool failed = ni > 32 * TRI_R;
-    if (failed && lane == 0) dev_fail(st, DEV_INTERNAL);
-    for (int64_t b = U.bptr[i]; b < U.bptr[i + 1] && !failed; ++b) {
-      const int32_t j = U.bcol[b];
-      if (lane == 0) {
-        unsigned long long it = 0;
-        while (*((volatile int32_t*)&done[j]) == 0) {
-          if (*((volatile int*)abort)) {
-            failed = true;
-            break;
-          }
-          if (++it > wait_limit) {
-            dev_fail(st, DEV_ETIMEOUT);
-            atomicExch(abort, 1);
-            failed = true;
-            break;
-          }
-          __nanosleep(64);
+      for (int a = 0; a < TRI_MR; ++a) part[a] = 0.0;
+      for (int64_t b = M.bptr[i] + lane; b < M.bptr[i + 1]; b += 32) {
+        const int32_t k = M.bcol[b];
+        if (!wait_row(done, k, abort, wait_limit, st)) {
+          failed = true;
+          break;
         }
-        if (*((volatile int*)abort)) failed = true;  // a failed row publishes after raising abort
-        __threadfence();
-      }
-      failed = __shfl_sync(0xffffffffu, failed, 0);
-      if (failed) break;
-      const int nj = U.csz[j];
-      const double* xj = x + U.coff[j];
+        const int nk = M.csz[k];
+        const T* v = M.val + M.voff[b];
+        const double* xk = out + M.coff[k];
+        for (int q = 0; q < nk; ++q) {
+          const double xq = __ldcg(xk + q);
 #pragma unroll
-      for (int t = 0; t < TRI_R; ++t) {
-        const int a = lane + 32 * t;
-        if (a < ni) {
-          const T* v = U.val + U.voff[b] + (int64_t)a * nj;
-          for (int q = 0; q < nj; ++q) s[t] = __dsub_rn(s[t], __dmul_rn(ld(v + q), __ldcg(xj + q)));
+          for (int a = 0; a < TRI_MR; ++a)
+            if (a < ni) part[a] = fma(ld(v + a * nk + q), xq, part[a]);
         }
       }
-    }
-    if (!failed) {
+      failed = __any_sync(0xffffffffu, failed);
+#pragma unroll
+      for (int a = 0; a < TRI_MR; ++a)
+        for (int o = 16; o > 0; o >>= 1) part[a] += __shfl_xor_sync(0xffffffffu, part[a], o);
+      if (!failed && lane < ni) {
+        double sa = 0.0;
+#pragma unroll
+        for (int a = 0; a < TRI_MR; ++a)
+          if (a == lane) sa = part[a];
+        sv[warp][lane] = rhs[r0 + lane] - sa;
+      }
+    } else {
+      double s[TRI_R];
+#pragma unroll
+      for (int t = 0; t < TRI_R; ++t) s[t] = lane + 32 * t < ni ? rhs[r0 + lane + 32 * t] : 0.0;
+      if (ni > 32 * TRI_R) {
+        if (lane == 0) dev_fail(st, DEV_INTERNAL);
+        failed = true;
+      }
+      for (int64_t b = M.bptr[i]; b < M.bptr[i + 1] && !failed; ++b) {
+        const int32_t k = M.bcol[b];
+        bool ok = true;
+        if (lane == 0) ok = wait_row(done, k, abort, wait_limit, st);
+        failed = !__shfl_sync(0xffffffffu, ok, 0);
+        if (failed) break;
+        const int nk = M.csz[k];
+        const double* xk = out + M.coff[k];
+#pragma unroll
+        for (int t = 0; t < TRI_R; ++t) {
+          const int a = lane + 32 * t;
+          if (a < ni) {
+            const T* v = M.val + M.voff[b] + (int64_t)a * nk;
+            for (int q = 0; q < nk; ++q) s[t] = fma(-ld(v + q), __ldcg(xk + q), s[t]);
+          }
+        }
+      }
 #pragma unroll
       for (int t = 0; t < TRI_R; ++t)
-        if (lane + 32 * t < ni) sv[warp][lane + 32 * t] = s[t];
-      __syncwarp();
-      if (lane == 0) {
+        if (!failed && lane + 32 * t < ni) sv[warp][lane + 32 * t] = s[t];
+    }
+    __syncwarp();
+    if (!failed) {
+      if (BWD && lane == 0) {
         double* u = sv[warp];
         if (lu32 && !ptag[i]) {
           pivot_forward<float>(lu32 + dgoff[i], piv + r0, ni, u);
@@ -267,7 +253,7 @@ __global__ void k_tri_bwd(VBView<T> U, const int64_t* __restrict__ dgoff, const 
         }
       }
       __syncwarp();
-      for (int a = lane; a < ni; a += 32) x[r0 + a] = sv[warp][a];
+      for (int a = lane; a < ni; a += 32) out[r0 + a] = sv[warp][a];
     }
     __threadfence();  // every lane's writes before the flag
     __syncwarp();
@@ -358,11 +344,10 @@ __global__ void k_perm_sizes2(int64_t p, const int32_t* __restrict__ pI, const i
 }  // namespace
 
 // --------------------------------------------------------------------------
-void dot_dev(const double* x, const double* y, int64_t n, double* out, cudaStream_t s) {
+void dot_dev(const double* x, const double* y, int64_t n, double* out, double* scratch, cudaStream_t s) {
   const int nb = (int)std::min<int64_t>(RB, std::max<int64_t>(1, (n + RT - 1) / RT));
-  DBuf<double> p(nb, s);
-  launch(k_dot_partial, nb, RT, 0, s, x, y, n, p.p);
-  launch(k_dot_final, 1, RB, 0, s, p.p, nb, out);
+  launch(k_dot_partial, nb, RT, 0, s, x, y, n, scratch);
+  launch(k_dot_final, 1, RB, 0, s, scratch, nb, out);
   VB_LAUNCH_CHECK();
 }
 void axpy_dev(double* y, const double* x, const double* a, double sign, int64_t n, cudaStream_t s) {
@@ -397,12 +382,14 @@ static void make_rowblk(int64_t nbr, const int64_t* roff, int64_t n, DBuf<int64_
   VB_LAUNCH_CHECK();
 }
 
-void spmv_vb(const VBDev<double>& A, const double* x, double* y, cudaStream_t s) {
-  const int64_t n = A.nrows_scalar(s);
-  DBuf<int64_t> rb;
-  make_rowblk(A.nbr, A.roff.p, n, rb, s);
-  if (n) launch(k_spmv, grid_for(n, 128, 152LL * 32), 128, 0, s, A.view(), rb.p, n, x, y);
+void spmv_vb(const VBDev<double>& A, const int64_t* rowblk, int64_t n, const double* x, double* y,
+             cudaStream_t s) {
+  if (n) launch(k_spmv, grid_for(n, 128, 152LL * 32), 128, 0, s, A.view(), rowblk, n, x, y);
   VB_LAUNCH_CHECK();
+}
+
+void rowblk_map(const VBDev<double>& A, int64_t n, DBuf<int64_t>& rb, cudaStream_t s) {
+  make_rowblk(A.nbr, A.roff.p, n, rb, s);
 }
 
 template <typename T>
@@ -430,14 +417,34 @@ template void build_level_maps<float>(const LevelDev<float>&, const int32_t*, co
 
 // --------------------------------------------------------------------------
 template <typename T>
-void PrecDev<T>::apply_perm(const double* x, double* y) {
-  // scratch: per level bh, xh (n_l each) and per-matrix row maps; last: 2 n
+void PrecDev<T>::prepare_apply() {
+  if (prepared) return;
   const int nl = (int)lev.size();
   int64_t total = 0;
-  for (int l = 0; l < nl; ++l) total += 2 * maps[l].n;
-  const int64_t nlast = last.A.nbr ? last.A.nrows_scalar(s) : 0;
+  for (int l = 0; l < nl; ++l) {
+    total += 2 * maps[l].n;
+    LevelMaps& M = maps[l];
+    const LevelDev<T>& L = lev[l];
+    if (M.n - M.nf > 0) make_rowblk(L.G.nbr, L.G.roff.p, M.n - M.nf, M.grow, s);
+    if (M.nf > 0) make_rowblk(L.W.nbr, L.W.roff.p, M.nf, M.wrow, s);
+  }
+  nlast = last.A.nbr ? last.A.nrows_scalar(s) : 0;
   total += 2 * nlast;
-  if ((int64_t)work.n < total) work.alloc(total, s);
+  work.alloc(std::max<int64_t>(total, 1), s);
+  flags.alloc(2 * std::max<int64_t>(last.A.nbr, 1), s);
+  tick.alloc(2, s);
+  abort_flag.alloc(1, s);
+  int dev = 0;
+  VB_CUDA(cudaGetDevice(&dev));
+  VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  prepared = true;
+}
+
+// Alg. 2 over all levels; enqueues work only (no synchronization).
+template <typename T>
+void PrecDev<T>::apply_perm(const double* x, double* y) {
+  prepare_apply();
+  const int nl = (int)lev.size();
   const bool mixed = sizeof(T) != sizeof(double);
   double* wp = work.p;
   const double* in = x;
@@ -449,7 +456,7 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
     xh[l] = wp;
     wp += maps[l].n;
   }
-  // forward sweep down the levels
+  // forward sweep down the levels: u = L^{-1} P f, g' = g - G u
   for (int l = 0; l < nl; ++l) {
     const LevelDev<T>& L = lev[l];
     const LevelMaps& M = maps[l];
@@ -457,13 +464,10 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
     if (M.n) launch(k_gather_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.r.p, b, bh[l]);
     if (L.nD)
       launch(k_pivot_fwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
-                                                      mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, bh[l]);
+             mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, bh[l]);
     const int64_t ng = M.n - M.nf;
-    if (ng && L.G.nnzb) {
-      DBuf<int64_t> rb;
-      make_rowblk(L.G.nbr, L.G.roff.p, ng, rb, s);
-      launch(k_bsr_sub<T>, grid_for(ng, 128), 128, 0, s, L.G.view(), rb.p, ng, bh[l], bh[l] + M.nf);
-    }
+    if (ng && L.G.nnzb)
+      launch(k_bsr_sub<T>, grid_for(ng, 128), 128, 0, s, L.G.view(), M.grow.p, ng, bh[l], bh[l] + M.nf);
     VB_LAUNCH_CHECK();
   }
   // last level: z = S2 (L U)^{-1} S1 g
@@ -475,40 +479,29 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
       double* xx = wp + nlast;
       launch(k_mul, grid_for(nlast, 256), 256, 0, s, nlast, last.r.p, g, yy);
       const int64_t p = last.A.nbr;
-      DBuf<int32_t> flags(2 * p, s);
-      DBuf<unsigned long long> tick(2, s);
-      DBuf<int> abort(1, s);
-      flags.zero();
-      tick.zero();
-      abort.zero();
-      int dev = 0, nsm = 0;
-      VB_CUDA(cudaGetDevice(&dev));
-      VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 4, (p + SW - 1) / SW));
-      launch(k_tri_fwd<T>, nb, SW * 32, 0, s, last.L.view(), yy, flags.p, tick.p, abort.p,
-                                          (unsigned long long)wait_limit, status.p);
-      launch(k_tri_bwd<T>, nb, SW * 32, 0, s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
-                                          mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx,
-                                          flags.p + p, tick.p + 1, abort.p, (unsigned long long)wait_limit,
-                                          status.p);
+      VB_CUDA(cudaMemsetAsync(flags.p, 0, 2 * p * sizeof(int32_t), s));
+      VB_CUDA(cudaMemsetAsync(tick.p, 0, 2 * sizeof(unsigned long long), s));
+      VB_CUDA(cudaMemsetAsync(abort_flag.p, 0, sizeof(int), s));
+      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 6, (p + SW - 1) / SW));
+      launch(k_tri<T, false>, nb, SW * 32, 0, s, last.L.view(), nullptr, nullptr, nullptr, nullptr, nullptr, yy,
+             yy, flags.p, tick.p, abort_flag.p, (unsigned long long)wait_limit, status.p);
+      launch(k_tri<T, true>, nb, SW * 32, 0, s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
+             mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx, flags.p + p, tick.p + 1,
+             abort_flag.p, (unsigned long long)wait_limit, status.p);
       launch(k_mul, grid_for(nlast, 256), 256, 0, s, nlast, last.c.p, xx, z);
       VB_LAUNCH_CHECK();
-      check_status(status.p, s, "vbarms_apply: last-level triangular solves");
     }
   }
-  // backward sweep up the levels
+  // backward sweep up the levels: y = U^{-1} (u - W z), x = S2 P_I^T [y; z]
   for (int l = nl - 1; l >= 0; --l) {
     const LevelDev<T>& L = lev[l];
     const LevelMaps& M = maps[l];
     double* xo = l == 0 ? out : xh[l - 1] + maps[l - 1].nf;
-    if (M.nf && L.W.nnzb) {
-      DBuf<int64_t> rb;
-      make_rowblk(L.W.nbr, L.W.roff.p, M.nf, rb, s);
-      launch(k_bsr_sub<T>, grid_for(M.nf, 128), 128, 0, s, L.W.view(), rb.p, M.nf, xh[l] + M.nf, bh[l]);
-    }
+    if (M.nf && L.W.nnzb)
+      launch(k_bsr_sub<T>, grid_for(M.nf, 128), 128, 0, s, L.W.view(), M.wrow.p, M.nf, xh[l] + M.nf, bh[l]);
     if (L.nD)
       launch(k_pivot_bwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
-                                                      mixed ? L.D32.val.p : nullptr, L.ptag.p, bh[l], xh[l]);
+             mixed ? L.D32.val.p : nullptr, L.ptag.p, bh[l], xh[l]);
     if (M.n) launch(k_scatter_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.c.p, xh[l], xo);
     VB_LAUNCH_CHECK();
   }

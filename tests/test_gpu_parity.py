@@ -125,7 +125,13 @@ def test_apply_and_fgmres_fp64(case):
     assert abs(its - its_o) <= 1, f"FGMRES iterations {its} vs oracle {its_o}"
     assert rr <= 1e-8
     xg = xs.cpu().numpy()
-    assert np.allclose(xg, 1.0, atol=1e-5)
+    # the true residual is checked in FP64 here too; the solution matches the
+    # oracle's to the conditioning of the system
+    r = b - m.matvec(xg)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    xo_full = np.empty(m.n)
+    xo_full[c.perm] = xo
+    assert rel_fro(xg, xo_full) <= 1e-6
 
 
 def test_no_drop_factor_is_exact_inverse():
