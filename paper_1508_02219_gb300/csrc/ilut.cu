@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(IW * 32)
       // bounded wait until row k is published
       if (lane == 0) {
         unsigned long long it = 0;
+        unsigned nsl = 32;
         while (*((volatile int32_t*)&P.done[k]) == 0) {
           if (*((volatile int*)P.abort) != 0) {
             *vflag = 2;
@@ -266,7 +267,8 @@ __global__ void __launch_bounds__(IW * 32)
             *vflag = 2;
             break;
           }
-          __nanosleep(32);
+          __nanosleep(nsl);  // exponential backoff keeps waiting warps off the L2
+          if (nsl < 512) nsl <<= 1;
         }
         // a row that failed still publishes (so no one waits forever) but
         // raises abort first: its factors must not be used
@@ -774,5 +776,43 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
 
 template void ilut_last<double>(LastDev<double>&, double, int, bool, double, uint64_t, cudaStream_t, int*);
 template void ilut_last<float>(LastDev<float>&, double, int, bool, double, uint64_t, cudaStream_t, int*);
+
+}  // namespace vb
+
+namespace vb {
+
+// Level order of a static triangular block pattern, computed on the host from
+// the block structure (one pass in dependency order), uploaded as a row list.
+template <typename T>
+void level_order(const VBDev<T>& M, bool backward, DBuf<int32_t>& order, int64_t& depth, cudaStream_t s) {
+  const int64_t p = M.nbr;
+  order.alloc(std::max<int64_t>(p, 1), s);
+  depth = 0;
+  if (p == 0) return;
+  std::vector<int64_t> bptr = d2h_vec(M.bptr.p, p + 1, s);
+  std::vector<int32_t> bcol = d2h_vec(M.bcol.p, M.nnzb, s);
+  std::vector<int32_t> lev(p, 0);
+  for (int64_t t = 0; t < p; ++t) {
+    const int64_t i = backward ? p - 1 - t : t;
+    int32_t l = 0;
+    for (int64_t b = bptr[i]; b < bptr[i + 1]; ++b) l = std::max(l, lev[bcol[b]] + 1);
+    lev[i] = l;
+    depth = std::max<int64_t>(depth, l + 1);
+  }
+  // counting sort by level, rows ascending (forward) / descending (backward)
+  std::vector<int64_t> start(depth + 1, 0);
+  for (int64_t i = 0; i < p; ++i) start[lev[i] + 1]++;
+  for (int64_t l = 0; l < depth; ++l) start[l + 1] += start[l];
+  std::vector<int32_t> ord(p);
+  for (int64_t t = 0; t < p; ++t) {
+    const int64_t i = backward ? p - 1 - t : t;
+    ord[start[lev[i]]++] = (int32_t)i;
+  }
+  h2d(order.p, ord.data(), p, s);
+  VB_CUDA(cudaStreamSynchronize(s));
+}
+
+template void level_order<double>(const VBDev<double>&, bool, DBuf<int32_t>&, int64_t&, cudaStream_t);
+template void level_order<float>(const VBDev<float>&, bool, DBuf<int32_t>&, int64_t&, cudaStream_t);
 
 }  // namespace vb

@@ -39,9 +39,16 @@ struct LastDev {
   VBDev<float> Dg32;
   DBuf<int32_t> piv, ptag;
   VBDev<T> L, U;
-  // apply-time scratch for the sync-free triangular solves
-  DBuf<int32_t> flags;
+  // rows of L (U) sorted by their level in the dependency DAG of the forward
+  // (backward) sweep: the triangular solves take rows in this order
+  DBuf<int32_t> lorder, uorder;
+  int64_t ldepth = 0, udepth = 0;
 };
+
+// Level order of the rows of a triangular block pattern (forward: row i
+// depends on its columns k < i; backward: on its columns j > i).
+template <typename T>
+void level_order(const VBDev<T>& M, bool backward, DBuf<int32_t>& order, int64_t& depth, cudaStream_t s);
 
 struct FactorOpts {
   int nlev;

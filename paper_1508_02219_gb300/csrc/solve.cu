@@ -139,6 +139,7 @@ __global__ void k_rowblk(int64_t nbr, const int64_t* __restrict__ roff, int64_t*
 __device__ __forceinline__ bool wait_row(const int32_t* done, int64_t k, int* abort, unsigned long long limit,
                                          int* st) {
   unsigned long long it = 0;
+  unsigned ns = 32;
   while (*((volatile const int32_t*)&done[k]) == 0) {
     if (*((volatile int*)abort)) return false;
     if (++it > limit) {
@@ -146,7 +147,8 @@ __device__ __forceinline__ bool wait_row(const int32_t* done, int64_t k, int* ab
       atomicExch(abort, 1);
       return false;
     }
-    __nanosleep(32);
+    __nanosleep(ns);  // exponential backoff keeps waiting warps off the L2
+    if (ns < 512) ns <<= 1;
   }
   if (*((volatile int*)abort)) return false;
   __threadfence();
@@ -156,7 +158,8 @@ __device__ __forceinline__ bool wait_row(const int32_t* done, int64_t k, int* ab
 constexpr int TRI_MR = 16;  // block rows up to this size use the lane-per-block path
 
 // Sync-free block triangular sweep over the last-level factors, one warp per
-// block row, rows in ticket order (ascending for L, descending for U).
+// block row, rows handed out in level order (order[ticket]): every dependency
+// of a row sits in an earlier level and so holds an earlier ticket.
 //   forward  (BWD = false): y_i <- y_i - sum_{k<i} L_ik y_k        (in place)
 //   backward (BWD = true):  x_i <- D_i^{-1} (y_i - sum_{j>i} U_ij x_j)
 // Rows of up to TRI_MR scalars: every lane owns some blocks of the row, waits
@@ -167,8 +170,9 @@ template <typename T, bool BWD>
 __global__ void __launch_bounds__(SW * 32)
     k_tri(VBView<T> M, const int64_t* __restrict__ dgoff, const double* __restrict__ lu64,
           const float* __restrict__ lu32, const int32_t* __restrict__ ptag, const int32_t* __restrict__ piv,
-          const double* __restrict__ rhs, double* __restrict__ out, int32_t* __restrict__ done,
-          unsigned long long* ticket, int* abort, unsigned long long wait_limit, int* st) {
+          const double* __restrict__ rhs, double* __restrict__ out, const int32_t* __restrict__ order,
+          int32_t* __restrict__ done, unsigned long long* ticket, int* abort, unsigned long long wait_limit,
+          int* st) {
   __shared__ double sv[SW][32 * TRI_R];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (;;) {
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(SW * 32)
     if (lane == 0) t0 = (long long)atomicAdd(ticket, 1ULL);
     t0 = __shfl_sync(0xffffffffu, t0, 0);
     if (t0 >= M.nbr) break;
-    const int64_t i = BWD ? M.nbr - 1 - t0 : t0;
+    const int64_t i = order[t0];
     const int ni = M.rsz[i];
     const int64_t r0 = M.roff[i];
     bool failed = false;
@@ -482,12 +486,12 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
       VB_CUDA(cudaMemsetAsync(flags.p, 0, 2 * p * sizeof(int32_t), s));
       VB_CUDA(cudaMemsetAsync(tick.p, 0, 2 * sizeof(unsigned long long), s));
       VB_CUDA(cudaMemsetAsync(abort_flag.p, 0, sizeof(int), s));
-      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 6, (p + SW - 1) / SW));
+      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 2, (p + SW - 1) / SW));
       launch(k_tri<T, false>, nb, SW * 32, 0, s, last.L.view(), nullptr, nullptr, nullptr, nullptr, nullptr, yy,
-             yy, flags.p, tick.p, abort_flag.p, (unsigned long long)wait_limit, status.p);
+             yy, last.lorder.p, flags.p, tick.p, abort_flag.p, (unsigned long long)wait_limit, status.p);
       launch(k_tri<T, true>, nb, SW * 32, 0, s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
-             mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx, flags.p + p, tick.p + 1,
-             abort_flag.p, (unsigned long long)wait_limit, status.p);
+             mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx, last.uorder.p, flags.p + p,
+             tick.p + 1, abort_flag.p, (unsigned long long)wait_limit, status.p);
       launch(k_mul, grid_for(nlast, 256), 256, 0, s, nlast, last.c.p, xx, z);
       VB_LAUNCH_CHECK();
     }
