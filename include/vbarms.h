@@ -127,6 +127,29 @@ vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil,
  * not alias.  Runs on the stream of the matrix the handle was built from.   */
 vb_status vbarms_apply(vbarms_prec M, const double* x, double* y);
 
+/* y = M^{-1} x like vbarms_apply, but allocating nothing: for callers that
+ * cannot allocate device memory when they apply the preconditioner (while a
+ * stream is being recorded into a CUDA graph, in solver loops that forbid
+ * allocator calls after set-up, or when device memory belongs to another
+ * runtime's pool).  The paper has no counterpart; this is an interface
+ * convenience.
+ * All scratch comes from one file-scope device array of
+ * vbarms_apply_static_max_bytes() bytes (64 MiB) that every GPU loading the
+ * library holds until the process exits.  A factorization that needs more
+ * (roughly n above 500k unknowns) is rejected with VB_EINVAL; use
+ * vbarms_apply then.  x, y: device double[n], original numbering, no
+ * aliasing; the call synchronizes the handle's stream before returning.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  Every call shares the same array and it keeps
+ * the previous call's contents (the call clears what must start at zero):
+ * calls that overlap on the GPU -- from several host threads, or on several
+ * streams -- race and must be serialized by the caller.                   */
+vb_status vbarms_apply_static(vbarms_prec M, const double* x, double* y);
+
+/* Size in bytes of the fixed scratch array of vbarms_apply_static. */
+uint64_t vbarms_apply_static_max_bytes(void);
+
 /* Right-preconditioned flexible GMRES(restart) on A x = b (FP64 Arnoldi with
  * modified Gram-Schmidt, Givens rotations, true residual at every restart).
  * M may be NULL (no preconditioner).  b, x: device double[n] in the original

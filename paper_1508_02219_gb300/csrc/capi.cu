@@ -17,10 +17,6 @@ struct vbarms_vbsr_st {
   DBuf<int64_t> rowblk;  // scalar row -> block row, for the SpMV
 };
 
-struct vbarms_prec_st {
-  std::unique_ptr<PrecBase> impl;
-};
-
 namespace {
 
 thread_local std::string g_err;
@@ -164,6 +160,8 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
 }
 
 }  // namespace
+
+void vb::set_last_error(const std::string& msg) { g_err = msg; }
 
 // ============================================================================
 extern "C" {

@@ -40,6 +40,11 @@ struct PrecBase {
   virtual void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval,
                           int32_t* rsz, int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff,
                           double* val) = 0;
+  // Bytes of caller-provided scratch that apply_with_scratch needs.
+  virtual size_t scratch_bytes() const = 0;
+  // y = M^{-1} x (original numbering) using only the given device scratch
+  // (256-byte aligned, scratch_bytes() long): allocates nothing.
+  virtual void apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm) = 0;
   virtual void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) = 0;
 };
 
@@ -59,10 +64,15 @@ struct PrecDev : PrecBase {
   void prepare_apply();
   int levels() const override { return (int)lev.size(); }
   void apply_perm(const double* x, double* y) override;
+  size_t scratch_bytes() const override;
+  void apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm) override;
   void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval, int32_t* rsz,
                   int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) override;
   void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) override;
 };
+
+// Record the message vbarms_last_error() returns on this thread.
+void set_last_error(const std::string& msg);
 
 // Build the scalar permutation of level L.
 template <typename T>
@@ -86,3 +96,8 @@ void gather_dev(double* y, const double* x, const int32_t* idx, int64_t n, cudaS
 void scatter_dev(double* y, const double* x, const int32_t* idx, int64_t n, cudaStream_t s);
 
 }  // namespace vb
+
+// Opaque handle of the C ABI: the factorization of one precision.
+struct vbarms_prec_st {
+  std::unique_ptr<vb::PrecBase> impl;
+};

@@ -511,6 +511,140 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
   }
 }
 
+// ---- the same solve with caller-provided scratch (no allocation) ----------
+// Layout of the scratch, each piece 256-byte aligned: the permuted x and y
+// (n doubles each), the per-level work vectors (2 n_l doubles each), the
+// last-level vectors (2 n_last doubles), the row->block maps of G and W
+// (n_l int64 per level), the last-level flags (2 p_last int32), two tickets
+// and the abort word.
+namespace {
+struct ScratchPlan {
+  size_t xp, yp, work, maps, flags, tick, abort, total;
+};
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+template <typename T>
+ScratchPlan plan_scratch(const PrecDev<T>& P) {
+  ScratchPlan sp{};
+  size_t o = 0;
+  int64_t nwork = 0, nmap = 0;
+  for (const auto& M : P.maps) {
+    nwork += 2 * M.n;
+    nmap += M.n;
+  }
+  const int64_t nlast = P.maps.empty() ? P.n : P.maps.back().n - P.maps.back().nf;
+  nwork += 2 * nlast;
+  sp.xp = o;
+  o = align256(o + (size_t)P.n * 8);
+  sp.yp = o;
+  o = align256(o + (size_t)P.n * 8);
+  sp.work = o;
+  o = align256(o + (size_t)nwork * 8);
+  sp.maps = o;
+  o = align256(o + (size_t)nmap * 8);
+  sp.flags = o;
+  o = align256(o + (size_t)(2 * P.last.A.nbr) * 4);
+  sp.tick = o;
+  o = align256(o + 2 * 8);
+  sp.abort = o;
+  o = align256(o + 4);
+  sp.total = o;
+  return sp;
+}
+}  // namespace
+
+template <typename T>
+size_t PrecDev<T>::scratch_bytes() const {
+  return plan_scratch(*this).total;
+}
+
+template <typename T>
+void PrecDev<T>::apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm_dev) {
+  const ScratchPlan sp = plan_scratch(*this);
+  double* xp = (double*)(scratch + sp.xp);
+  double* yp = (double*)(scratch + sp.yp);
+  double* wp = (double*)(scratch + sp.work);
+  int64_t* mp = (int64_t*)(scratch + sp.maps);
+  int32_t* fl = (int32_t*)(scratch + sp.flags);
+  unsigned long long* tk = (unsigned long long*)(scratch + sp.tick);
+  int* ab = (int*)(scratch + sp.abort);
+  const int nl = (int)lev.size();
+  const bool mixed = sizeof(T) != sizeof(double);
+  constexpr int kMaxLev = 64;  // fixed host arrays: this path allocates nothing
+  if (nl > kMaxLev) fail(VB_EINVAL, "more than 64 levels");
+  gather_dev(xp, x, perm.p, n, s);
+  double* bh[kMaxLev];
+  double* xh[kMaxLev];
+  int64_t* gmap[kMaxLev];
+  int64_t* wmap[kMaxLev];
+  for (int l = 0; l < nl; ++l) {
+    bh[l] = wp;
+    wp += maps[l].n;
+    xh[l] = wp;
+    wp += maps[l].n;
+    gmap[l] = mp;
+    wmap[l] = mp + (maps[l].n - maps[l].nf);
+    mp += maps[l].n;
+    const LevelDev<T>& L = lev[l];
+    if (maps[l].n - maps[l].nf > 0 && L.G.nbr)
+      launch(k_rowblk, grid_for(L.G.nbr, 8), 256, 0, s, L.G.nbr, L.G.roff.p, gmap[l]);
+    if (maps[l].nf > 0 && L.W.nbr) launch(k_rowblk, grid_for(L.W.nbr, 8), 256, 0, s, L.W.nbr, L.W.roff.p, wmap[l]);
+    VB_LAUNCH_CHECK();
+  }
+  const double* in = xp;
+  double* out = yp;
+  for (int l = 0; l < nl; ++l) {
+    const LevelDev<T>& L = lev[l];
+    const LevelMaps& M = maps[l];
+    const double* b = l == 0 ? in : bh[l - 1] + maps[l - 1].nf;
+    if (M.n) launch(k_gather_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.r.p, b, bh[l]);
+    if (L.nD)
+      launch(k_pivot_fwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
+             mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, bh[l]);
+    const int64_t ng = M.n - M.nf;
+    if (ng && L.G.nnzb)
+      launch(k_bsr_sub<T>, grid_for(ng, 128), 128, 0, s, L.G.view(), gmap[l], ng, bh[l], bh[l] + M.nf);
+    VB_LAUNCH_CHECK();
+  }
+  {
+    const int64_t nl_last = maps.empty() ? n : maps.back().n - maps.back().nf;
+    const double* g = nl == 0 ? in : bh[nl - 1] + maps[nl - 1].nf;
+    double* z = nl == 0 ? out : xh[nl - 1] + maps[nl - 1].nf;
+    if (nl_last) {
+      double* yy = wp;
+      double* xx = wp + nl_last;
+      launch(k_mul, grid_for(nl_last, 256), 256, 0, s, nl_last, last.r.p, g, yy);
+      const int64_t p = last.A.nbr;
+      // the scratch keeps the previous call's contents: clear what starts at 0
+      VB_CUDA(cudaMemsetAsync(fl, 0, 2 * p * sizeof(int32_t), s));
+      VB_CUDA(cudaMemsetAsync(tk, 0, 2 * sizeof(unsigned long long), s));
+      VB_CUDA(cudaMemsetAsync(ab, 0, sizeof(int), s));
+      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm_dev * 2, (p + SW - 1) / SW));
+      launch(k_tri<T, false>, nb, SW * 32, 0, s, last.L.view(), nullptr, nullptr, nullptr, nullptr, nullptr, yy,
+             yy, last.lorder.p, fl, tk, ab, (unsigned long long)wait_limit, status.p);
+      launch(k_tri<T, true>, nb, SW * 32, 0, s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
+             mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx, last.uorder.p, fl + p, tk + 1,
+             ab, (unsigned long long)wait_limit, status.p);
+      launch(k_mul, grid_for(nl_last, 256), 256, 0, s, nl_last, last.c.p, xx, z);
+      VB_LAUNCH_CHECK();
+    }
+  }
+  for (int l = nl - 1; l >= 0; --l) {
+    const LevelDev<T>& L = lev[l];
+    const LevelMaps& M = maps[l];
+    double* xo = l == 0 ? out : xh[l - 1] + maps[l - 1].nf;
+    if (M.nf && L.W.nnzb)
+      launch(k_bsr_sub<T>, grid_for(M.nf, 128), 128, 0, s, L.W.view(), wmap[l], M.nf, xh[l] + M.nf, bh[l]);
+    if (L.nD)
+      launch(k_pivot_bwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
+             mixed ? L.D32.val.p : nullptr, L.ptag.p, bh[l], xh[l]);
+    if (M.n) launch(k_scatter_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.c.p, xh[l], xo);
+    VB_LAUNCH_CHECK();
+  }
+  scatter_dev(y, yp, perm.p, n, s);
+}
+
 template <typename T>
 void PrecDev<T>::export_mat(int l, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval,
                             int32_t* rsz, int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) {

@@ -73,6 +73,8 @@ def lib():
                 "vbarms_prec_vector": (i32, [vp, i32, i32, vp, vp, P(i64)]),
                 "vbarms_prec_kernel_stats": (i32, [vp, i32, P(i32), P(d), P(d), P(d)]),
                 "vbarms_launch_count": (C.c_uint64, []),
+                "vbarms_apply_static": (i32, [vp, vp, vp]),
+                "vbarms_apply_static_max_bytes": (C.c_uint64, []),
                 "vbarms_vbsr_destroy": (None, [vp]),
                 "vbarms_prec_destroy": (None, [vp]),
             }
@@ -244,6 +246,16 @@ def vbarms_factor(A: VBSR, nlev: int, droptol: float, lfil: int, precision="fp64
 def vbarms_apply(M: Prec, x, y):
     """y = M^{-1} x (Alg. 2); x, y CUDA float64 tensors in original numbering."""
     _check(lib().vbarms_apply(M.h, _dp(x), _dp(y)))
+
+
+def vbarms_apply_static(M: Prec, x, y):
+    """y = M^{-1} x without any device allocation (fixed library scratch);
+    for callers that cannot allocate device memory when they apply."""
+    _check(lib().vbarms_apply_static(M.h, _dp(x), _dp(y)))
+
+
+def apply_static_max_bytes() -> int:
+    return int(lib().vbarms_apply_static_max_bytes())
 
 
 def fgmres_solve(A: VBSR, M: Prec | None, b, x, rtol=1e-8, restart=50, maxit=1000, raise_noconv=False):
