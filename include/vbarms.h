@@ -63,8 +63,8 @@ typedef struct {
   double fp64_pivot_cond; /* default 1e4                                     */
   double ddtol;           /* Step 3: supernodes with weight < ddtol go to C
                              (default 0 = off)                               */
-  uint64_t wait_limit;    /* spin iterations of a bounded device wait before
-                             VB_ETIMEOUT (0 = default, about 1 s)            */
+  uint64_t wait_limit;    /* nanoseconds one bounded device wait may last
+                             before VB_ETIMEOUT (0 = default, 30 s)          */
 } vbarms_opts;
 
 /* Fill *opt with the defaults above. */

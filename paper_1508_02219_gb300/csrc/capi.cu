@@ -308,7 +308,7 @@ vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil, const
   if (!opt) opt = &d;
   if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
   FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
-               opt->wait_limit ? opt->wait_limit : (uint64_t)8000000};
+               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
     if (o.precision == VB_FP64)

@@ -54,6 +54,16 @@ enum DevCode : int {
 
 __device__ __forceinline__ void dev_fail(int* st, int code) { atomicCAS(st, 0, code); }
 
+// Device-wide nanosecond timer (bounds the spin waits by time).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Default time budget of a bounded device wait: 30 s.
+constexpr unsigned long long kDefaultWaitNs = 30ull * 1000 * 1000 * 1000;
+
 // --------------------------------------------------------------------------
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
 template <typename T>

@@ -41,6 +41,8 @@ struct Pools {
   int64_t lbcap, lvcap, ubcap, uvcap;
   int32_t* done;
   int* abort;
+  int64_t* uvstart;  // value offset of the first U block of each row
+  int64_t* uvlen;    // values of the U row (its blocks are contiguous)
 };
 
 struct Workspace {
@@ -172,15 +174,93 @@ __device__ void ainv_right_row_s(const double* lu, const int* pv, int m, T* x) {
   }
 }
 
+// Warp-cooperative copy with eight independent loads in flight per lane.
+template <typename T>
+__device__ __forceinline__ void warp_copy(T* __restrict__ dst, const T* __restrict__ src, int64_t n, int lane) {
+  for (int64_t e0 = lane; e0 < n; e0 += 32 * 8) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t e = e0 + 32 * u;
+      if (e < n) v[u] = src[e];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t e = e0 + 32 * u;
+      if (e < n) dst[e] = v[u];
+    }
+  }
+}
+
+// Squared Frobenius norm in row-major order (the oracle's summation order),
+// with the loads issued eight at a time.
+template <typename T>
+__device__ __forceinline__ double fro2_batched(const T* __restrict__ v, int n) {
+  double s = 0.0;
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    T x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = e0 + u < n ? v[e0 + u] : (T)0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e0 + u < n) {
+        const double d = (double)x[u];
+        s = __dadd_rn(s, __dmul_rn(d, d));
+      }
+  }
+  return s;
+}
+
+constexpr int LCAP = 128;          // pending L columns tracked in shared memory per warp
+constexpr int USTAGE_BYTES = 6144;  // U row of a dependency staged in shared memory per warp
+
 struct IlutShared {
-  double lu[IW][SMB * SMB];
-  double mult[IW][SMB * SMB];
+  double lu[IW][SMB * SMB];     // pivot block of the dependency (FP64 values)
+  double mult[IW][SMB * SMB];   // multiplier block (T values, in place)
   int pv[IW][SMB];
   int64_t qoff[IW][32];  // workspace value offset of each staged U block's target
-  int64_t quo[IW][32];   // value offset of the U block in the pool
+  int64_t quo[IW][32];   // value offset of the U block within the staged row
   int qnj[IW][32];
   int qpre[IW][33];      // element prefix of the staged U blocks
+  int lc[IW][LCAP];      // pending L columns (INT_MAX when processed)
+  int ls[IW][LCAP];      // their slots
+  int nl[IW];
+  int64_t hdr[IW][4];    // ustart, ucnt, uvstart, uvlen of the dependency
+  int tag[IW];
+  __align__(16) unsigned char ustage[IW][USTAGE_BYTES];
 };
+
+constexpr size_t ilut_smem() { return sizeof(IlutShared); }
+
+// x (one row of length m) <- x (P^T L U)^{-1} from a staged pivot block; x
+// lives in shared memory.
+template <typename T, typename TL>
+__device__ void ainv_right_row_sh(const double* lu, const int* pv, int m, T* x) {
+  for (int j = 0; j < m; ++j) {
+    TL s = (TL)x[j];
+    for (int q = 0; q < j; ++q) s = msub<TL>(s, (TL)x[q], (TL)lu[q * m + j]);
+    x[j] = (T)(s / (TL)lu[j * m + j]);
+  }
+  for (int j = m - 1; j >= 0; --j) {
+    TL s = (TL)x[j];
+    for (int q = j + 1; q < m; ++q) s = msub<TL>(s, (TL)x[q], (TL)lu[q * m + j]);
+    x[j] = (T)s;
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    const int p = pv[k];
+    if (p > k && p < m) {
+      const T t = x[k];
+      x[k] = x[p];
+      x[p] = t;
+    }
+  }
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(IW * 32)
@@ -191,7 +271,8 @@ __global__ void __launch_bounds__(IW * 32)
   __shared__ int s_nslots[IW];
   __shared__ unsigned long long s_nvals[IW];
   __shared__ int s_flag[IW];
-  __shared__ IlutShared sh;
+  extern __shared__ __align__(16) unsigned char ilut_sm[];
+  IlutShared& sh = *reinterpret_cast<IlutShared*>(ilut_sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t wid = (int64_t)blockIdx.x * IW + warp;
   int* keys = ws.keys + wid * ws.ht;
@@ -201,9 +282,14 @@ __global__ void __launch_bounds__(IW * 32)
   int* sstate = ws.sstate + wid * ws.smax;
   double* sf2 = ws.sf2 + wid * ws.smax;
   T* wv = wvals_all + wid * ws.vmax;
+  T* mult = reinterpret_cast<T*>(sh.mult[warp]);
+  const T* ustage = reinterpret_cast<const T*>(sh.ustage[warp]);
+  T* ustage_w = reinterpret_cast<T*>(sh.ustage[warp]);
+  constexpr int USTAGE = USTAGE_BYTES / (int)sizeof(T);
   const uint32_t hmask = (uint32_t)ws.ht - 1;
   volatile int* vflag = &s_flag[warp];
   volatile int* vns = &s_nslots[warp];
+  volatile int* vnl = &sh.nl[warp];
   for (int k = lane; k < ws.ht; k += 32) keys[k] = -1;
   __syncwarp();
 
@@ -218,83 +304,133 @@ __global__ void __launch_bounds__(IW * 32)
       s_nslots[warp] = 0;
       s_nvals[warp] = 0;
       s_flag[warp] = 0;
+      sh.nl[warp] = 0;
     }
     __syncwarp();
-    // ---- load row i of A into the workspace (distinct columns)
-    for (int64_t b = A.bptr[i] + lane; b < A.bptr[i + 1]; b += 32) {
-      const int32_t J = A.bcol[b];
-      const int sz = ni * A.csz[J];
-      const int slot = ws_new_slot<T>(ws, keys, hpos, scol, soff, sstate, &s_nslots[warp], &s_nvals[warp], hmask,
-                                      J, sz);
-      if (slot < 0) {
-        *vflag = 1;
-        continue;
+    // ---- load row i of A into the workspace: slot q is the row's block q and
+    // the values arrive as one contiguous copy; columns left of the diagonal
+    // enter the shared list of pending L columns
+    {
+      const int64_t b0 = A.bptr[i], b1 = A.bptr[i + 1];
+      const int64_t v0 = A.voff[b0], nv = A.voff[b1] - v0;
+      const int nb = (int)(b1 - b0);
+      if (nb > ws.smax || nv > ws.vmax) {
+        if (lane == 0) {
+          *vflag = 1;
+          atomicMax(P.ctr + 5, (unsigned long long)nv);
+          atomicMax(P.ctr + 6, (unsigned long long)nb);
+        }
+      } else {
+        for (int64_t b = b0 + lane; b < b1; b += 32) {
+          const int slot = (int)(b - b0);
+          const int32_t J = A.bcol[b];
+          scol[slot] = J;
+          soff[slot] = A.voff[b] - v0;
+          sstate[slot] = SL_LIVE;
+          hpos[slot] = ws_place(keys, hmask, slot, J);  // the table holds 2 smax positions
+          if (J < i) {
+            const int q = atomicAdd(&sh.nl[warp], 1);
+            if (q < LCAP) {
+              sh.lc[warp][q] = J;
+              sh.ls[warp][q] = slot;
+            }
+          }
+        }
+        warp_copy(wv, A.val + v0, nv, lane);
+        if (lane == 0) {
+          s_nslots[warp] = nb;
+          s_nvals[warp] = (unsigned long long)nv;
+        }
       }
-      for (int e = 0; e < sz; ++e) wv[soff[slot] + e] = A.val[A.voff[b] + e];
     }
     __syncwarp();
     int status_local = *vflag ? DEV_OVERFLOW : 0;
     int64_t last = -1;
     // ---- eliminate the L part in ascending column order (including fill)
     while (status_local == 0) {
-      const int ns = min(*vns, ws.smax);
-      int best = 0x7fffffff, bslot = -1;
-      for (int s = lane; s < ns; s += 32) {
-        const int c = scol[s];
-        if (sstate[s] == SL_LIVE && c > last && c < i && c < best) {
-          best = c;
-          bslot = s;
+      // next pending L column: from the shared list while it has not
+      // overflowed, else by a scan of the workspace slots
+      int best = 0x7fffffff, bslot = -1, bpos = -1;
+      const int nlist = *vnl;
+      if (nlist <= LCAP) {
+        for (int q = lane; q < nlist; q += 32) {
+          const int c = sh.lc[warp][q];
+          if (c < best) {
+            best = c;
+            bslot = sh.ls[warp][q];
+            bpos = q;
+          }
+        }
+      } else {
+        const int ns = min(*vns, ws.smax);
+        for (int sidx = lane; sidx < ns; sidx += 32) {
+          const int c = scol[sidx];
+          if (sstate[sidx] == SL_LIVE && c > last && c < i && c < best) {
+            best = c;
+            bslot = sidx;
+          }
         }
       }
       const int kmin = warp_min_i(best);
       if (kmin == 0x7fffffff) break;
       const unsigned who = __ballot_sync(0xffffffffu, bslot >= 0 && best == kmin);
-      const int sk = __shfl_sync(0xffffffffu, bslot, __ffs(who) - 1);
+      const int owner = __ffs(who) - 1;
+      const int sk = __shfl_sync(0xffffffffu, bslot, owner);
+      if (lane == owner && bpos >= 0) sh.lc[warp][bpos] = 0x7fffffff;
       const int64_t k = kmin;
       last = k;
-      // bounded wait until row k is published
+      const int nk = A.rsz[k];
+      // bounded wait (acquire) until row k is published
       if (lane == 0) {
-        unsigned long long it = 0;
+        const unsigned long long t_start = global_ns();
         unsigned nsl = 32;
-        while (*((volatile int32_t*)&P.done[k]) == 0) {
+        while (ld_acquire_gpu(P.done + k) == 0) {
           if (*((volatile int*)P.abort) != 0) {
             *vflag = 2;
             break;
           }
-          if (++it > wait_limit) {
+          if (global_ns() - t_start > wait_limit) {  // wait_limit is a time budget in ns
             dev_fail(st, DEV_ETIMEOUT);
             atomicExch(P.abort, 1);
             *vflag = 2;
             break;
           }
           __nanosleep(nsl);  // exponential backoff keeps waiting warps off the L2
-          if (nsl < 512) nsl <<= 1;
+          if (nsl < 256) nsl <<= 1;
         }
         // a row that failed still publishes (so no one waits forever) but
         // raises abort first: its factors must not be used
         if (*((volatile int*)P.abort) != 0) *vflag = 2;
-        __threadfence();
       }
       __syncwarp();
       if (*vflag == 2) {
         status_local = DEV_ETIMEOUT;
         break;
       }
-      const int nk = A.rsz[k];
       T* m = wv + soff[sk];
-      const bool use64 = sizeof(T) == sizeof(double) || (ptag && __ldcg(ptag + k));
       const bool staged = nk <= SMB && ni <= SMB;
+      // one batch of independent loads: the pivot block of k (FP64; its FP32
+      // copy is the rounding of these values), the pivots, the precision tag,
+      // the extent of U row k and the multiplier block
       if (staged) {
-        // one coalesced load of the pivot block of row k
-        for (int e = lane; e < nk * nk; e += 32)
-          sh.lu[warp][e] = use64 ? __ldcg(dg + dgoff[k] + e) : (double)__ldcg(dg32 + dgoff[k] + e);
+        for (int e = lane; e < nk * nk; e += 32) sh.lu[warp][e] = __ldcg(dg + dgoff[k] + e);
         if (lane < nk) sh.pv[warp][lane] = __ldcg(piv + A.roff[k] + lane);
-        __syncwarp();
+        for (int e = lane; e < ni * nk; e += 32) mult[e] = m[e];
+      }
+      if (lane == 0) sh.tag[warp] = ptag ? __ldcg(ptag + k) : 1;
+      if (lane == 1) sh.hdr[warp][0] = __ldcg(P.ustart + k);
+      if (lane == 2) sh.hdr[warp][1] = __ldcg(P.ucnt + k);
+      if (lane == 3) sh.hdr[warp][2] = __ldcg(P.uvstart + k);
+      if (lane == 4) sh.hdr[warp][3] = __ldcg(P.uvlen + k);
+      __syncwarp();
+      const bool use64 = sizeof(T) == sizeof(double) || sh.tag[warp] != 0;
+      T* mm = staged ? mult : m;
+      if (staged) {
         if (lane < ni) {
           if (use64)
-            ainv_right_row_s<T, double>(sh.lu[warp], sh.pv[warp], nk, m + lane * nk);
+            ainv_right_row_sh<T, double>(sh.lu[warp], sh.pv[warp], nk, mm + lane * nk);
           else
-            ainv_right_row_s<T, float>(sh.lu[warp], sh.pv[warp], nk, m + lane * nk);
+            ainv_right_row_sh<T, float>(sh.lu[warp], sh.pv[warp], nk, mm + lane * nk);
         }
       } else {
         for (int a = lane; a < ni; a += 32) {
@@ -306,7 +442,7 @@ __global__ void __launch_bounds__(IW * 32)
       }
       __syncwarp();
       double f2 = 0.0;
-      if (lane == 0) f2 = fro2_seq(m, ni * nk);
+      if (lane == 0) f2 = fro2_seq(mm, ni * nk);
       f2 = __shfl_sync(0xffffffffu, f2, 0);
       if (drop_rule(f2, ni, nk, t)) {
         if (lane == 0) sstate[sk] = SL_DEAD;
@@ -318,12 +454,20 @@ __global__ void __launch_bounds__(IW * 32)
         sf2[sk] = f2;
       }
       if (staged)
-        for (int e = lane; e < ni * nk; e += 32) sh.mult[warp][e] = (double)m[e];
-      const int64_t u0 = __ldcg(P.ustart + k);
-      const int uc = __ldcg(P.ucnt + k);
-      if (u0 < 0 || uc < 0 || u0 + uc > P.ubcap) {  // never true for a published row: record and skip
-        status_local = DEV_INTERNAL;
+        for (int e = lane; e < ni * nk; e += 32) m[e] = mm[e];  // the kept multiplier is an L block
+      const int64_t u0 = sh.hdr[warp][0];
+      const int uc = (int)sh.hdr[warp][1];
+      const int64_t uvs = sh.hdr[warp][2];
+      const int64_t uvl = sh.hdr[warp][3];
+      if (u0 < 0 || uc < 0 || u0 + uc > P.ubcap || uvs < 0 || uvl < 0 || uvs + uvl > P.uvcap) {
+        status_local = DEV_INTERNAL;  // never true for a published row: record and skip
         break;
+      }
+      // stage U row k (contiguous in the pool) when it fits
+      const bool ust = uvl <= USTAGE;
+      if (ust) {
+#pragma unroll 4
+        for (int64_t e = lane; e < uvl; e += 32) ustage_w[e] = __ldcg(uval + uvs + e);
       }
       // U row k in chunks of 32 blocks: look up or create the target blocks
       // (probe, then place, separated by __syncwarp), then update all
@@ -337,8 +481,8 @@ __global__ void __launch_bounds__(IW * 32)
         if (q < uc) {
           j = __ldcg(P.ucol + u0 + q);
           uo = __ldcg(P.uvo + u0 + q);
-          if (j <= k || j >= A.nbr || uo < 0 || uo + (int64_t)nk * A.rsz[j] > P.uvcap) {
-            *vflag = 4;  // a published U block always lies right of k inside the pool
+          if (j <= k || j >= A.nbr || uo < uvs || uo + (int64_t)nk * A.rsz[j] > uvs + uvl) {
+            *vflag = 4;  // a published U block lies right of k inside its row's extent
             j = -1;
           } else {
             slot = ws_lookup(keys, scol, hmask, j);
@@ -349,10 +493,20 @@ __global__ void __launch_bounds__(IW * 32)
         if (missing) {
           const int sz = ni * A.rsz[j];
           slot = ws_new_slot<T>(ws, keys, hpos, scol, soff, sstate, &s_nslots[warp], &s_nvals[warp], hmask, j, sz);
-          if (slot < 0)
+          if (slot < 0) {
             *vflag = 1;
-          else
-            for (int e = 0; e < sz; ++e) wv[soff[slot] + e] = (T)0;
+          } else {
+            T* z = wv + soff[slot];
+#pragma unroll 4
+            for (int e = 0; e < sz; ++e) z[e] = (T)0;
+            if (j < i) {  // fill in the L part: pending for a later step
+              const int pq = atomicAdd(&sh.nl[warp], 1);
+              if (pq < LCAP) {
+                sh.lc[warp][pq] = j;
+                sh.ls[warp][pq] = slot;
+              }
+            }
+          }
         }
         __syncwarp();
         if (*vflag == 1) {
@@ -374,53 +528,98 @@ __global__ void __launch_bounds__(IW * 32)
         sh.qpre[warp][lane] = incl - sz;
         if (lane == 31) sh.qpre[warp][32] = total;
         sh.qoff[warp][lane] = slot >= 0 ? soff[slot] : 0;
-        sh.quo[warp][lane] = uo;
+        sh.quo[warp][lane] = uo - uvs;
         sh.qnj[warp][lane] = nj;
         __syncwarp();
         const int nq = min(32, uc - q0);
-        for (int e = lane; e < total; e += 32) {
-          int lo = 0, hi = nq - 1;  // block t with qpre[t] <= e < qpre[t + 1]
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sh.qpre[warp][mid] <= e)
-              lo = mid;
-            else
-              hi = mid - 1;
+        const T* Ubase = ust ? ustage : uval + uvs;
+        // four elements per lane in flight: their workspace loads overlap
+        for (int e0 = lane; e0 < total; e0 += 128) {
+          T acc[4];
+          T* dst[4];
+          int a4[4], jj4[4], nj4[4];
+          int64_t uo4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = e0 + 32 * u;
+            dst[u] = nullptr;
+            if (e < total) {
+              int lo = 0, hi = nq - 1;  // block tq with qpre[tq] <= e < qpre[tq + 1]
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sh.qpre[warp][mid] <= e)
+                  lo = mid;
+                else
+                  hi = mid - 1;
+              }
+              const int njt = sh.qnj[warp][lo];
+              const int local = e - sh.qpre[warp][lo];
+              a4[u] = local / njt;
+              jj4[u] = local - a4[u] * njt;
+              nj4[u] = njt;
+              uo4[u] = sh.quo[warp][lo];
+              dst[u] = wv + sh.qoff[warp][lo] + local;
+              acc[u] = *dst[u];
+            }
           }
-          const int tq = lo;
-          const int njt = sh.qnj[warp][tq];
-          const int local = e - sh.qpre[warp][tq];
-          const int a = local / njt, jj = local - a * njt;
-          T* B = wv + sh.qoff[warp][tq];
-          const T* U = uval + sh.quo[warp][tq];
-          T acc = B[local];
-          if (staged) {
-            for (int r = 0; r < nk; ++r) acc = msub<T>(acc, (T)sh.mult[warp][a * nk + r], __ldcg(U + r * njt + jj));
-          } else {
-            for (int r = 0; r < nk; ++r) acc = msub<T>(acc, m[a * nk + r], __ldcg(U + r * njt + jj));
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (!dst[u]) continue;
+            const T* U = Ubase + uo4[u];
+            T av = acc[u];
+            for (int r = 0; r < nk; ++r) av = msub<T>(av, mm[a4[u] * nk + r], U[r * nj4[u] + jj4[u]]);
+            *dst[u] = av;
           }
-          B[local] = acc;
         }
         __syncwarp();
       }
     }
     const int ns = min(*vns, ws.smax);
+    // ---- finish the row.  The slot metadata is staged in shared memory (the
+    // U-row stage buffer is free now) so that the scans below read on-chip
+    // data; rows with more than MSH slots read the workspace directly.
+    constexpr int MSH = USTAGE_BYTES / 24;
+    int* mcol = reinterpret_cast<int*>(sh.ustage[warp]);
+    int* mst = mcol + MSH;
+    int64_t* moff = reinterpret_cast<int64_t*>(mst + MSH);
+    double* mf2 = reinterpret_cast<double*>(moff + MSH);
+    const bool msh = ns <= MSH;
+    if (msh)
+      for (int q = lane; q < ns; q += 32) {
+        mcol[q] = scol[q];
+        mst[q] = sstate[q];
+        moff[q] = soff[q];
+        mf2[q] = sf2[q];
+      }
+    __syncwarp();
+    auto COL = [&](int q) { return msh ? mcol[q] : scol[q]; };
+    auto ST = [&](int q) { return msh ? mst[q] : sstate[q]; };
+    auto OFF = [&](int q) { return msh ? moff[q] : soff[q]; };
+    auto F2 = [&](int q) { return msh ? mf2[q] : sf2[q]; };
+    auto IS_L = [&](int q) { return ST(q) == SL_LKEPT; };
+    auto IS_U = [&](int q) { return ST(q) == SL_LIVE && COL(q) > i; };
     int dslot = -1;
     if (status_local == 0) {
-      for (int s = lane; s < ns; s += 32)
-        if (scol[s] == i && sstate[s] == SL_LIVE) dslot = s;
+      for (int q = lane; q < ns; q += 32)
+        if (COL(q) == i && ST(q) == SL_LIVE) dslot = q;
       dslot = warp_max_i(dslot);
       if (dslot < 0) status_local = DEV_ESINGULAR;
     }
+    bool fits = false;
+    unsigned long long lb = 0, lvv = 0, ub = 0, uvv = 0;
+    int nl = 0, nu = 0;
+    long long vl = 0, vu = 0;
     if (status_local == 0) {
       // U part: threshold on the blocks right of the diagonal
-      for (int s = lane; s < ns; s += 32) {
-        const int c = scol[s];
-        if (sstate[s] == SL_LIVE && c > i) {
+      for (int q = lane; q < ns; q += 32) {
+        const int c = COL(q);
+        if (ST(q) == SL_LIVE && c > i) {
           const int nc = A.rsz[c];
-          const double f2 = fro2_seq(wv + soff[s], ni * nc);
-          sf2[s] = f2;
-          if (drop_rule(f2, ni, nc, t)) sstate[s] = SL_DEAD;
+          const double f2 = fro2_batched(wv + OFF(q), ni * nc);
+          if (msh) mf2[q] = f2; else sf2[q] = f2;
+          if (drop_rule(f2, ni, nc, t)) {
+            if (msh) mst[q] = SL_DEAD; else sstate[q] = SL_DEAD;
+          }
         }
       }
       __syncwarp();
@@ -429,31 +628,36 @@ __global__ void __launch_bounds__(IW * 32)
       if (lfil >= 0) {
         unsigned cutmask[MAX_SLOTS / 1024] = {};  // bit tq: slot lane + 32 tq is cut
         for (int tq = 0; tq * 32 < ns && tq < MAX_SLOTS / 32; ++tq) {
-          const int s = tq * 32 + lane;
-          if (s >= ns) continue;
-          const int st0 = sstate[s];
-          const bool isL = st0 == SL_LKEPT, isU = st0 == SL_LIVE && scol[s] > i;
+          const int q = tq * 32 + lane;
+          if (q >= ns) continue;
+          const bool isL = IS_L(q), isU = IS_U(q);
           if (!isL && !isU) continue;
+          const double fq = F2(q);
+          const int cq = COL(q);
           int rank = 0;
-          for (int q = 0; q < ns; ++q) {
-            const bool same = isL ? sstate[q] == SL_LKEPT : (sstate[q] == SL_LIVE && scol[q] > i);
-            if (same && (sf2[q] > sf2[s] || (sf2[q] == sf2[s] && scol[q] < scol[s]))) ++rank;
+          for (int r2 = 0; r2 < ns; ++r2) {
+            const bool same = isL ? IS_L(r2) : IS_U(r2);
+            if (same) {
+              const double fr = F2(r2);
+              if (fr > fq || (fr == fq && COL(r2) < cq)) ++rank;
+            }
           }
           if (rank >= lfil) cutmask[tq >> 5] |= 1u << (tq & 31);
         }
         __syncwarp();
         for (int tq = 0; tq < MAX_SLOTS / 32; ++tq)
-          if (cutmask[tq >> 5] & (1u << (tq & 31))) sstate[tq * 32 + lane] = SL_DEAD;
+          if (cutmask[tq >> 5] & (1u << (tq & 31))) {
+            const int q = tq * 32 + lane;
+            if (msh) mst[q] = SL_DEAD; else sstate[q] = SL_DEAD;
+          }
         __syncwarp();
       }
-      int nl = 0, nu = 0;
-      long long vl = 0, vu = 0;
-      for (int s = lane; s < ns; s += 32) {
-        const int c = scol[s];
-        if (sstate[s] == SL_LKEPT) {
+      for (int q = lane; q < ns; q += 32) {
+        const int c = COL(q);
+        if (IS_L(q)) {
           ++nl;
           vl += (long long)ni * A.rsz[c];
-        } else if (sstate[s] == SL_LIVE && c > i) {
+        } else if (IS_U(q)) {
           ++nu;
           vu += (long long)ni * A.rsz[c];
         }
@@ -462,7 +666,6 @@ __global__ void __launch_bounds__(IW * 32)
       nu = warp_sum_i(nu);
       vl = warp_sum_ll(vl);
       vu = warp_sum_ll(vu);
-      unsigned long long lb = 0, lvv = 0, ub = 0, uvv = 0;
       if (lane == 0) {
         lb = atomicAdd(P.ctr + 0, (unsigned long long)nl);
         lvv = atomicAdd(P.ctr + 1, (unsigned long long)vl);
@@ -473,54 +676,26 @@ __global__ void __launch_bounds__(IW * 32)
       lvv = __shfl_sync(0xffffffffu, lvv, 0);
       ub = __shfl_sync(0xffffffffu, ub, 0);
       uvv = __shfl_sync(0xffffffffu, uvv, 0);
-      const bool fits = (int64_t)(lb + nl) <= P.lbcap && (int64_t)(lvv + vl) <= P.lvcap &&
-                        (int64_t)(ub + nu) <= P.ubcap && (int64_t)(uvv + vu) <= P.uvcap;
+      fits = (int64_t)(lb + nl) <= P.lbcap && (int64_t)(lvv + vl) <= P.lvcap && (int64_t)(ub + nu) <= P.ubcap &&
+             (int64_t)(uvv + vu) <= P.uvcap;
       if (!fits) status_local = DEV_OVERFLOW;
       if (status_local == 0) {
-        // both rows in ascending column order (rank by column)
-        for (int s = lane; s < ns; s += 32) {
-          const int c = scol[s];
-          const bool isL = sstate[s] == SL_LKEPT;
-          const bool isU = sstate[s] == SL_LIVE && c > i;
-          if (!isL && !isU) continue;
-          int rank = 0;
-          long long vo = 0;
-          for (int q = 0; q < ns; ++q) {
-            const int cq = scol[q];
-            const bool same = isL ? sstate[q] == SL_LKEPT : (sstate[q] == SL_LIVE && cq > i);
-            if (same && cq < c) {
-              ++rank;
-              vo += (long long)ni * A.rsz[cq];
-            }
-          }
-          const int nc = A.rsz[c];
-          if (isL) {
-            P.lcol[lb + rank] = c;
-            P.lvo[lb + rank] = (int64_t)(lvv + vo);
-            for (int e = 0; e < ni * nc; ++e) lval[lvv + vo + e] = wv[soff[s] + e];
-          } else {
-            P.ucol[ub + rank] = c;
-            P.uvo[ub + rank] = (int64_t)(uvv + vo);
-            for (int e = 0; e < ni * nc; ++e) uval[uvv + vo + e] = wv[soff[s] + e];
-          }
-        }
+        // GEPP of the diagonal block (FP64, the oracle's order), in shared
+        // memory when it fits
+        const bool gsh = ni <= SMB;
+        double* a = gsh ? sh.lu[warp] : dg + dgoff[i];
+        const T* srcd = wv + OFF(dslot);
+        for (int e = lane; e < ni * ni; e += 32) a[e] = (double)srcd[e];
+        __syncwarp();
         double norm1 = 0.0;
         if (lane == 0) {
-          P.lstart[i] = (int64_t)lb;
-          P.lcnt[i] = nl;
-          P.ustart[i] = (int64_t)ub;
-          P.ucnt[i] = nu;
-          // GEPP of the diagonal block in FP64 (the oracle's order)
-          double* a = dg + dgoff[i];
-          const T* src = wv + soff[dslot];
-          for (int e = 0; e < ni * ni; ++e) a[e] = (double)src[e];
           if (mixed)
             for (int jj = 0; jj < ni; ++jj) {
               double sum = 0.0;
               for (int ii = 0; ii < ni; ++ii) sum += fabs(a[ii * ni + jj]);
               norm1 = fmax(norm1, sum);
             }
-          int32_t* pv = piv + A.roff[i];
+          int* pv = sh.pv[warp];
           bool singular = false;
           for (int kk = 0; kk < ni; ++kk) {
             int pr = kk;
@@ -536,7 +711,8 @@ __global__ void __launch_bounds__(IW * 32)
               singular = true;
               break;
             }
-            pv[kk] = pr;
+            if (kk < SMB) pv[kk] = pr;
+            piv[A.roff[i] + kk] = pr;
             if (pr != kk)
               for (int jj = 0; jj < ni; ++jj) {
                 const double tt = a[kk * ni + jj];
@@ -555,35 +731,116 @@ __global__ void __launch_bounds__(IW * 32)
         }
         __syncwarp();
         if (*vflag == 3) status_local = DEV_ESINGULAR;
-        if (status_local == 0 && mixed) {
-          // 1-norm condition estimate with the explicit inverse: lane jj
-          // solves for column jj (blocks up to 32; larger ones stay FP64)
-          const double* a = dg + dgoff[i];
-          const int32_t* pv = piv + A.roff[i];
-          double cs = 0.0;
-          if (ni <= 32 && lane < ni) {
-            double x[32];
-            for (int ii = 0; ii < ni; ++ii) x[ii] = ii == lane ? 1.0 : 0.0;
-            for (int kk = 0; kk < ni; ++kk)
-              if (pv[kk] != kk) {
-                const double tt = x[kk];
-                x[kk] = x[pv[kk]];
-                x[pv[kk]] = tt;
+        if (status_local == 0) {
+          if (gsh)
+            for (int e = lane; e < ni * ni; e += 32) dg[dgoff[i] + e] = a[e];
+          if (mixed) {
+            // 1-norm condition estimate with the explicit inverse: lane jj
+            // solves for column jj (blocks up to 32; larger ones stay FP64)
+            double cs = 0.0;
+            if (ni <= 32 && lane < ni) {
+              const int* pvs = gsh ? sh.pv[warp] : nullptr;
+              double x[32];
+              for (int ii = 0; ii < ni; ++ii) x[ii] = ii == lane ? 1.0 : 0.0;
+              for (int kk = 0; kk < ni; ++kk) {
+                const int pk = pvs ? pvs[kk] : piv[A.roff[i] + kk];
+                if (pk != kk) {
+                  const double tt = x[kk];
+                  x[kk] = x[pk];
+                  x[pk] = tt;
+                }
               }
-            for (int ii = 1; ii < ni; ++ii)
-              for (int kk = 0; kk < ii; ++kk) x[ii] -= a[ii * ni + kk] * x[kk];
-            for (int ii = ni - 1; ii >= 0; --ii) {
-              double sum = x[ii];
-              for (int kk = ii + 1; kk < ni; ++kk) sum -= a[ii * ni + kk] * x[kk];
-              x[ii] = sum / a[ii * ni + ii];
+              for (int ii = 1; ii < ni; ++ii)
+                for (int kk = 0; kk < ii; ++kk) x[ii] -= a[ii * ni + kk] * x[kk];
+              for (int ii = ni - 1; ii >= 0; --ii) {
+                double sum = x[ii];
+                for (int kk = ii + 1; kk < ni; ++kk) sum -= a[ii * ni + kk] * x[kk];
+                x[ii] = sum / a[ii * ni + ii];
+              }
+              for (int ii = 0; ii < ni; ++ii) cs += fabs(x[ii]);
             }
-            for (int ii = 0; ii < ni; ++ii) cs += fabs(x[ii]);
+            for (int o = 16; o > 0; o >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+            norm1 = __shfl_sync(0xffffffffu, norm1, 0);
+            if (lane == 0) ptag[i] = (ni > 32 || norm1 * cs > cond_thr) ? 1 : 0;
+            for (int e = lane; e < ni * ni; e += 32) dg32[dgoff[i] + e] = (float)a[e];
           }
-          for (int o = 16; o > 0; o >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
-          norm1 = __shfl_sync(0xffffffffu, norm1, 0);
-          if (lane == 0) ptag[i] = (ni > 32 || norm1 * cs > cond_thr) ? 1 : 0;
-          for (int e = lane; e < ni * ni; e += 32) dg32[dgoff[i] + e] = (float)a[e];
         }
+      }
+    }
+    // Write the kept blocks of one part in column order: per chunk of 32
+    // slots the ranks come from the staged metadata, then the chunk's values
+    // are copied with lanes over the flattened elements, eight loads in
+    // flight per lane.
+    auto write_part = [&](bool isL, unsigned long long bstart, unsigned long long vstart, int32_t* pcol,
+                          int64_t* pvo, T* pval) {
+      for (int s0 = 0; s0 < ns; s0 += 32) {
+        const int q = s0 + lane;
+        int sz = 0;
+        int64_t src = 0, dstv = 0;
+        if (q < ns && (isL ? IS_L(q) : IS_U(q))) {
+          const int c = COL(q);
+          int rank = 0;
+          long long vo = 0;
+          for (int r2 = 0; r2 < ns; ++r2) {
+            const int cr = COL(r2);
+            if (cr < c && (isL ? IS_L(r2) : IS_U(r2))) {
+              ++rank;
+              vo += (long long)ni * A.rsz[cr];
+            }
+          }
+          sz = ni * A.rsz[c];
+          src = OFF(q);
+          dstv = (int64_t)vstart + vo;
+          pcol[bstart + rank] = c;
+          pvo[bstart + rank] = dstv;
+        }
+        int incl = sz;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        sh.qpre[warp][lane] = incl - sz;
+        sh.qoff[warp][lane] = src;
+        sh.quo[warp][lane] = dstv;
+        __syncwarp();
+        for (int e0 = lane; e0 < total; e0 += 32 * 8) {
+          T v[8];
+          int64_t d8[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = e0 + 32 * u;
+            d8[u] = -1;
+            if (e < total) {
+              int lo = 0, hi = 31;
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sh.qpre[warp][mid] <= e)
+                  lo = mid;
+                else
+                  hi = mid - 1;
+              }
+              // skip empty entries that share the same prefix
+              while (lo < 31 && sh.qpre[warp][lo + 1] <= e) ++lo;
+              const int local = e - sh.qpre[warp][lo];
+              v[u] = wv[sh.qoff[warp][lo] + local];
+              d8[u] = sh.quo[warp][lo] + local;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (d8[u] >= 0) pval[d8[u]] = v[u];
+        }
+        __syncwarp();
+      }
+    };
+    if (status_local == 0) {
+      write_part(false, ub, uvv, P.ucol, P.uvo, uval);
+      if (lane == 0) {
+        P.ustart[i] = (int64_t)ub;
+        P.ucnt[i] = nu;
+        P.uvstart[i] = (int64_t)uvv;
+        P.uvlen[i] = (int64_t)vu;
       }
     }
     if (status_local != 0 && lane == 0) {
@@ -593,19 +850,29 @@ __global__ void __launch_bounds__(IW * 32)
       P.ucnt[i] = 0;
       P.lstart[i] = 0;
       P.ustart[i] = 0;
+      P.uvstart[i] = 0;
+      P.uvlen[i] = 0;
     }
     if (lane == 0) {  // what the row asked for, to size a retry
       atomicMax(P.ctr + 5, s_nvals[warp]);
       atomicMax(P.ctr + 6, (unsigned long long)s_nslots[warp]);
     }
-    // publish the row: every lane's writes are made visible device-wide
-    // before lane 0 raises the flag
+    // publish the row (its U part and pivot block): every lane's writes are
+    // made visible device-wide before lane 0 raises the flag
     __threadfence();
     __syncwarp();
     if (lane == 0) atomicExch(&P.done[i], 1);
+    // the L part is read by no other row: written after publishing
+    if (status_local == 0) {
+      write_part(true, lb, lvv, P.lcol, P.lvo, lval);
+      if (lane == 0) {
+        P.lstart[i] = (int64_t)lb;
+        P.lcnt[i] = nl;
+      }
+    }
     // clear the hash positions this row used
-    for (int s = lane; s < ns; s += 32)
-      if (hpos[s] >= 0) keys[hpos[s]] = -1;
+    for (int q = lane; q < ns; q += 32)
+      if (hpos[q] >= 0) keys[hpos[q]] = -1;
     __syncwarp();
   }
 }
@@ -714,7 +981,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
     DBuf<T> wvals(nwarps * vmax, s);
     Workspace ws{keys.p, hpos.p, scol.p, soff.p, sstate.p, sf2.p, ht, smax, vmax};
     DBuf<int32_t> lcol(lbcap, s), ucol(ubcap, s), lcnt(p, s), ucnt(p, s), done(p, s);
-    DBuf<int64_t> lvo(lbcap, s), uvo(ubcap, s), lstart(p, s), ustart(p, s);
+    DBuf<int64_t> lvo(lbcap, s), uvo(ubcap, s), lstart(p, s), ustart(p, s), uvstart(p, s), uvlen(p, s);
     DBuf<T> lval(lvcap, s), uval(uvcap, s);
     DBuf<unsigned long long> ctr(8, s);
     DBuf<int> abort(1, s);
@@ -722,9 +989,11 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
     done.zero();
     abort.zero();
     X.piv.zero();
-    Pools P{lcol.p, lvo.p, ucol.p, uvo.p, lstart.p, lcnt.p, ustart.p, ucnt.p, ctr.p,
-            lbcap,  lvcap, ubcap,  uvcap, done.p,  abort.p};
-    launch(k_ilut<T>, (unsigned)nblocks, IW * 32, 0, s, A.view(), ws, wvals.p, P, lval.p, uval.p, X.Dg.voff.p,
+    Pools P{lcol.p, lvo.p,  ucol.p, uvo.p,  lstart.p, lcnt.p,  ustart.p,  ucnt.p,   ctr.p,
+            lbcap,  lvcap,  ubcap,  uvcap,  done.p,   abort.p, uvstart.p, uvlen.p};
+    VB_CUDA(cudaFuncSetAttribute(k_ilut<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ilut_smem()));
+    launch(k_ilut<T>, (unsigned)nblocks, IW * 32, ilut_smem(), s, A.view(), ws, wvals.p, P, lval.p, uval.p,
+           X.Dg.voff.p,
                                                      X.Dg.val.p, mixed ? X.Dg32.val.p : nullptr, X.piv.p,
                                                      mixed ? X.ptag.p : nullptr, mixed ? 1 : 0, cond_thr, t, lfil,
                                                      (unsigned long long)wait_limit, dst);

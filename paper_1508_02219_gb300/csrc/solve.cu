@@ -134,38 +134,53 @@ __global__ void k_rowblk(int64_t nbr, const int64_t* __restrict__ roff, int64_t*
     for (int64_t q = roff[I] + lane; q < roff[I + 1]; q += 32) rowblk[q] = I;
 }
 
-// Bounded spin until done[k] is set; false when the wait ran out or another
-// row failed (a failed row raises abort before it publishes).
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Bounded spin until done[k] is set (acquire load: the row's published values
+// are visible afterwards); false when the wait ran out or another row failed
+// (a failed row raises abort before it publishes).
 __device__ __forceinline__ bool wait_row(const int32_t* done, int64_t k, int* abort, unsigned long long limit,
                                          int* st) {
-  unsigned long long it = 0;
+  if (ld_acquire_gpu(done + k) != 0) return *((volatile int*)abort) == 0;
+  const unsigned long long t_start = global_ns();
   unsigned ns = 32;
-  while (*((volatile const int32_t*)&done[k]) == 0) {
+  while (ld_acquire_gpu(done + k) == 0) {
     if (*((volatile int*)abort)) return false;
-    if (++it > limit) {
+    if (global_ns() - t_start > limit) {  // limit is a time budget in ns
       dev_fail(st, DEV_ETIMEOUT);
       atomicExch(abort, 1);
       return false;
     }
     __nanosleep(ns);  // exponential backoff keeps waiting warps off the L2
-    if (ns < 512) ns <<= 1;
+    if (ns < 256) ns <<= 1;
   }
-  if (*((volatile int*)abort)) return false;
-  __threadfence();
-  return true;
+  return *((volatile int*)abort) == 0;
 }
 
-constexpr int TRI_MR = 16;  // block rows up to this size use the lane-per-block path
+constexpr int TRI_MR = 16;      // block rows up to this size use the lane-per-block path
+constexpr int TRI_STAGE = 1024;  // values of a row staged in shared memory per warp
+constexpr int TRI_XQ = 16;       // dependency values loaded in one batch
+
+template <typename T>
+constexpr size_t tri_smem() {
+  return (size_t)SW * TRI_STAGE * sizeof(T) + (size_t)SW * 32 * TRI_R * sizeof(double);
+}
 
 // Sync-free block triangular sweep over the last-level factors, one warp per
 // block row, rows handed out in level order (order[ticket]): every dependency
 // of a row sits in an earlier level and so holds an earlier ticket.
 //   forward  (BWD = false): y_i <- y_i - sum_{k<i} L_ik y_k        (in place)
 //   backward (BWD = true):  x_i <- D_i^{-1} (y_i - sum_{j>i} U_ij x_j)
-// Rows of up to TRI_MR scalars: every lane owns some blocks of the row, waits
-// for its own dependency and accumulates its products privately; a warp
-// reduction forms the update, so the row's latency is that of its slowest
-// dependency plus one block product.  Larger rows use lanes over scalar rows.
+// Rows of up to TRI_MR scalars: the row's block values (static) are staged in
+// shared memory before any wait; every lane then owns some blocks of the row,
+// waits for its own dependency, loads that dependency's values in one batch
+// and accumulates its products privately; a warp reduction forms the update.
+// The row's latency is its slowest dependency plus one batched load and a
+// reduction.  Larger rows use lanes over scalar rows.
 template <typename T, bool BWD>
 __global__ void __launch_bounds__(SW * 32)
     k_tri(VBView<T> M, const int64_t* __restrict__ dgoff, const double* __restrict__ lu64,
@@ -173,8 +188,10 @@ __global__ void __launch_bounds__(SW * 32)
           const double* __restrict__ rhs, double* __restrict__ out, const int32_t* __restrict__ order,
           int32_t* __restrict__ done, unsigned long long* ticket, int* abort, unsigned long long wait_limit,
           int* st) {
-  __shared__ double sv[SW][32 * TRI_R];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ __align__(16) unsigned char tri_sm[];
+  T* stage = (T*)tri_sm + (size_t)(threadIdx.x >> 5) * TRI_STAGE;
+  double* sv = (double*)(tri_sm + (size_t)SW * TRI_STAGE * sizeof(T)) + (size_t)(threadIdx.x >> 5) * 32 * TRI_R;
+  const int lane = threadIdx.x & 31;
   for (;;) {
     long long t0 = 0;
     if (lane == 0) t0 = (long long)atomicAdd(ticket, 1ULL);
@@ -185,23 +202,39 @@ __global__ void __launch_bounds__(SW * 32)
     const int64_t r0 = M.roff[i];
     bool failed = false;
     if (ni <= TRI_MR) {
+      const int64_t b0 = M.bptr[i], b1 = M.bptr[i + 1];
+      const int64_t v0 = M.voff[b0];
+      const int64_t nv = M.voff[b1] - v0;
+      const bool staged = nv <= TRI_STAGE;
+      if (staged) {
+#pragma unroll 4
+        for (int64_t e = lane; e < nv; e += 32) stage[e] = M.val[v0 + e];
+      }
+      const double r_self = lane < ni ? rhs[r0 + lane] : 0.0;
+      __syncwarp();
       double part[TRI_MR];
 #pragma unroll
       for (int a = 0; a < TRI_MR; ++a) part[a] = 0.0;
-      for (int64_t b = M.bptr[i] + lane; b < M.bptr[i + 1]; b += 32) {
+      for (int64_t b = b0 + lane; b < b1; b += 32) {
         const int32_t k = M.bcol[b];
+        const int nk = M.csz[k];
+        const T* v = staged ? stage + (M.voff[b] - v0) : M.val + M.voff[b];
         if (!wait_row(done, k, abort, wait_limit, st)) {
           failed = true;
           break;
         }
-        const int nk = M.csz[k];
-        const T* v = M.val + M.voff[b];
         const double* xk = out + M.coff[k];
-        for (int q = 0; q < nk; ++q) {
-          const double xq = __ldcg(xk + q);
+        for (int q0 = 0; q0 < nk; q0 += TRI_XQ) {
+          double xq[TRI_XQ];
 #pragma unroll
-          for (int a = 0; a < TRI_MR; ++a)
-            if (a < ni) part[a] = fma(ld(v + a * nk + q), xq, part[a]);
+          for (int q = 0; q < TRI_XQ; ++q) xq[q] = q0 + q < nk ? __ldcg(xk + q0 + q) : 0.0;
+#pragma unroll
+          for (int q = 0; q < TRI_XQ; ++q) {
+            if (q0 + q >= nk) break;
+#pragma unroll
+            for (int a = 0; a < TRI_MR; ++a)
+              if (a < ni) part[a] = fma(ld(v + a * nk + q0 + q), xq[q], part[a]);
+          }
         }
       }
       failed = __any_sync(0xffffffffu, failed);
@@ -213,7 +246,7 @@ __global__ void __launch_bounds__(SW * 32)
 #pragma unroll
         for (int a = 0; a < TRI_MR; ++a)
           if (a == lane) sa = part[a];
-        sv[warp][lane] = rhs[r0 + lane] - sa;
+        sv[lane] = r_self - sa;
       }
     } else {
       double s[TRI_R];
@@ -242,22 +275,21 @@ __global__ void __launch_bounds__(SW * 32)
       }
 #pragma unroll
       for (int t = 0; t < TRI_R; ++t)
-        if (!failed && lane + 32 * t < ni) sv[warp][lane + 32 * t] = s[t];
+        if (!failed && lane + 32 * t < ni) sv[lane + 32 * t] = s[t];
     }
     __syncwarp();
     if (!failed) {
       if (BWD && lane == 0) {
-        double* u = sv[warp];
         if (lu32 && !ptag[i]) {
-          pivot_forward<float>(lu32 + dgoff[i], piv + r0, ni, u);
-          pivot_backward<float>(lu32 + dgoff[i], ni, u);
+          pivot_forward<float>(lu32 + dgoff[i], piv + r0, ni, sv);
+          pivot_backward<float>(lu32 + dgoff[i], ni, sv);
         } else {
-          pivot_forward<double>(lu64 + dgoff[i], piv + r0, ni, u);
-          pivot_backward<double>(lu64 + dgoff[i], ni, u);
+          pivot_forward<double>(lu64 + dgoff[i], piv + r0, ni, sv);
+          pivot_backward<double>(lu64 + dgoff[i], ni, sv);
         }
       }
       __syncwarp();
-      for (int a = lane; a < ni; a += 32) out[r0 + a] = sv[warp][a];
+      for (int a = lane; a < ni; a += 32) out[r0 + a] = sv[a];
     }
     __threadfence();  // every lane's writes before the flag
     __syncwarp();
@@ -420,8 +452,22 @@ template void build_level_maps<float>(const LevelDev<float>&, const int32_t*, co
                                       cudaStream_t);
 
 // --------------------------------------------------------------------------
+// The sweeps use more than 48 KB of dynamic shared memory: opt in once per
+// device for each instantiation.
+template <typename T>
+void tri_attributes() {
+  static bool set_on[64] = {};
+  int dev = 0;
+  VB_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && set_on[dev]) return;
+  VB_CUDA(cudaFuncSetAttribute(k_tri<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem<T>()));
+  VB_CUDA(cudaFuncSetAttribute(k_tri<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem<T>()));
+  if (dev >= 0 && dev < 64) set_on[dev] = true;
+}
+
 template <typename T>
 void PrecDev<T>::prepare_apply() {
+  tri_attributes<T>();
   if (prepared) return;
   const int nl = (int)lev.size();
   int64_t total = 0;
@@ -487,9 +533,10 @@ void PrecDev<T>::apply_perm(const double* x, double* y) {
       VB_CUDA(cudaMemsetAsync(tick.p, 0, 2 * sizeof(unsigned long long), s));
       VB_CUDA(cudaMemsetAsync(abort_flag.p, 0, sizeof(int), s));
       const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 2, (p + SW - 1) / SW));
-      launch(k_tri<T, false>, nb, SW * 32, 0, s, last.L.view(), nullptr, nullptr, nullptr, nullptr, nullptr, yy,
-             yy, last.lorder.p, flags.p, tick.p, abort_flag.p, (unsigned long long)wait_limit, status.p);
-      launch(k_tri<T, true>, nb, SW * 32, 0, s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
+      launch(k_tri<T, false>, nb, SW * 32, tri_smem<T>(), s, last.L.view(), nullptr, nullptr, nullptr, nullptr,
+             nullptr, yy, yy, last.lorder.p, flags.p, tick.p, abort_flag.p, (unsigned long long)wait_limit,
+             status.p);
+      launch(k_tri<T, true>, nb, SW * 32, tri_smem<T>(), s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
              mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx, last.uorder.p, flags.p + p,
              tick.p + 1, abort_flag.p, (unsigned long long)wait_limit, status.p);
       launch(k_mul, grid_for(nlast, 256), 256, 0, s, nlast, last.c.p, xx, z);
@@ -561,6 +608,7 @@ size_t PrecDev<T>::scratch_bytes() const {
 
 template <typename T>
 void PrecDev<T>::apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm_dev) {
+  tri_attributes<T>();
   const ScratchPlan sp = plan_scratch(*this);
   double* xp = (double*)(scratch + sp.xp);
   double* yp = (double*)(scratch + sp.yp);
@@ -621,9 +669,9 @@ void PrecDev<T>::apply_with_scratch(const double* x, double* y, unsigned char* s
       VB_CUDA(cudaMemsetAsync(tk, 0, 2 * sizeof(unsigned long long), s));
       VB_CUDA(cudaMemsetAsync(ab, 0, sizeof(int), s));
       const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm_dev * 2, (p + SW - 1) / SW));
-      launch(k_tri<T, false>, nb, SW * 32, 0, s, last.L.view(), nullptr, nullptr, nullptr, nullptr, nullptr, yy,
-             yy, last.lorder.p, fl, tk, ab, (unsigned long long)wait_limit, status.p);
-      launch(k_tri<T, true>, nb, SW * 32, 0, s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
+      launch(k_tri<T, false>, nb, SW * 32, tri_smem<T>(), s, last.L.view(), nullptr, nullptr, nullptr, nullptr,
+             nullptr, yy, yy, last.lorder.p, fl, tk, ab, (unsigned long long)wait_limit, status.p);
+      launch(k_tri<T, true>, nb, SW * 32, tri_smem<T>(), s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
              mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx, last.uorder.p, fl + p, tk + 1,
              ab, (unsigned long long)wait_limit, status.p);
       launch(k_mul, grid_for(nl_last, 256), 256, 0, s, nl_last, last.c.p, xx, z);
