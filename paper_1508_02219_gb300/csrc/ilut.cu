@@ -211,11 +211,24 @@ __device__ __forceinline__ double fro2_batched(const T* __restrict__ v, int n) {
   return s;
 }
 
+// Squared Frobenius norm accumulated in FP32 (mixed factor).
+template <typename T>
+__device__ __forceinline__ float fro2_f32(const T* __restrict__ v, int n) {
+  float s = 0.f;
+#pragma unroll 4
+  for (int e = 0; e < n; ++e) {
+    const float x = (float)v[e];
+    s = __fmaf_rn(x, x, s);
+  }
+  return s;
+}
+
 constexpr int LCAP = 128;          // pending L columns tracked in shared memory per warp
 constexpr int USTAGE_BYTES = 6144;  // U row of a dependency staged in shared memory per warp
 
 struct IlutShared {
-  double lu[IW][SMB * SMB];     // pivot block of the dependency (FP64 values)
+  double lu[IW][SMB * SMB];     // FP64 pivot block (the dependency's, then the row's own)
+  float lu32[IW][SMB * SMB];    // FP32 pivot block of the mixed factor
   double mult[IW][SMB * SMB];   // multiplier block (T values, in place)
   int pv[IW][SMB];
   int64_t qoff[IW][32];  // workspace value offset of each staged U block's target
@@ -232,10 +245,10 @@ struct IlutShared {
 
 constexpr size_t ilut_smem() { return sizeof(IlutShared); }
 
-// x (one row of length m) <- x (P^T L U)^{-1} from a staged pivot block; x
-// lives in shared memory.
-template <typename T, typename TL>
-__device__ void ainv_right_row_sh(const double* lu, const int* pv, int m, T* x) {
+// x (one row of length m) <- x (P^T L U)^{-1} from a staged pivot block
+// (values of type TS, arithmetic in TL); x lives in shared memory.
+template <typename T, typename TL, typename TS>
+__device__ void ainv_right_row_sh(const TS* lu, const int* pv, int m, T* x) {
   for (int j = 0; j < m; ++j) {
     TL s = (TL)x[j];
     for (int q = 0; q < j; ++q) s = msub<TL>(s, (TL)x[q], (TL)lu[q * m + j]);
@@ -254,6 +267,110 @@ __device__ void ainv_right_row_sh(const double* lu, const int* pv, int m, T* x) 
       x[p] = t;
     }
   }
+}
+
+// |x| as an integer key: non-negative IEEE values order like their bit
+// patterns, so pivot searches compare integers.
+__device__ __forceinline__ long long abs_key(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+__device__ __forceinline__ long long abs_key(float x) { return (long long)(__float_as_int(x) & 0x7fffffff); }
+
+template <typename TL>
+__device__ __forceinline__ TL div_rn(TL a, TL b);
+template <>
+__device__ __forceinline__ double div_rn<double>(double a, double b) {
+  return __ddiv_rn(a, b);
+}
+template <>
+__device__ __forceinline__ float div_rn<float>(float a, float b) {
+  return __fdiv_rn(a, b);
+}
+
+// GEPP of the n x n row-major block a (max-abs pivot, ties to the lowest
+// row), one warp: each elimination step finds its pivot by a warp reduction,
+// then the lanes form the multipliers and update the trailing block, so every
+// element receives the operations of the sequential algorithm in its order.
+// Pivot rows go to gpiv (and pvs when not null).  Returns false when a pivot
+// column is exactly zero.
+template <typename TL>
+__device__ bool gepp_warp(TL* a, int n, int* pvs, int32_t* gpiv, int lane) {
+  for (int kk = 0; kk < n; ++kk) {
+    long long key = -1;
+    int idx = 0x7fffffff;
+    for (int ii = kk + lane; ii < n; ii += 32) {
+      const long long v = abs_key(a[ii * n + kk]);
+      if (v > key) {
+        key = v;
+        idx = ii;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ok > key || (ok == key && oi < idx)) {
+        key = ok;
+        idx = oi;
+      }
+    }
+    if (key <= 0) return false;
+    const int pr = idx;
+    if (lane == 0) {
+      gpiv[kk] = pr;
+      if (pvs) pvs[kk] = pr;
+    }
+    if (pr != kk)
+      for (int jj = lane; jj < n; jj += 32) {
+        const TL t = a[kk * n + jj];
+        a[kk * n + jj] = a[pr * n + jj];
+        a[pr * n + jj] = t;
+      }
+    __syncwarp();
+    const TL d = a[kk * n + kk];
+    const int w = n - kk - 1;
+    for (int r = lane; r < w; r += 32) {
+      TL* l = a + (kk + 1 + r) * n + kk;
+      *l = div_rn<TL>(*l, d);
+    }
+    __syncwarp();
+    for (int e = lane; e < w * w; e += 32) {
+      const int r = e / w, c = e - r * w;
+      const int ii = kk + 1 + r, jj = kk + 1 + c;
+      a[ii * n + jj] = msub<TL>(a[ii * n + jj], a[ii * n + kk], a[kk * n + jj]);
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// ||B^{-1}||_1 of a GEPP-factored FP32 block (n <= 32): lane c solves
+// B x = e_c through the interchanges, L and U; the result is the largest
+// column sum, on every lane.
+__device__ float inv_norm1_f32(const float* a, int n, const int* pv, int lane) {
+  float cs = 0.f;
+  if (lane < n) {
+    float x[32];
+    for (int ii = 0; ii < n; ++ii) x[ii] = ii == lane ? 1.f : 0.f;
+    for (int kk = 0; kk < n; ++kk) {
+      const int pk = pv[kk];
+      if (pk != kk) {
+        const float t = x[kk];
+        x[kk] = x[pk];
+        x[pk] = t;
+      }
+    }
+    for (int ii = 1; ii < n; ++ii) {
+      float sum = x[ii];
+      for (int kk = 0; kk < ii; ++kk) sum = __fmaf_rn(-a[ii * n + kk], x[kk], sum);
+      x[ii] = sum;
+    }
+    for (int ii = n - 1; ii >= 0; --ii) {
+      float sum = x[ii];
+      for (int kk = ii + 1; kk < n; ++kk) sum = __fmaf_rn(-a[ii * n + kk], x[kk], sum);
+      x[ii] = __fdiv_rn(sum, a[ii * n + ii]);
+    }
+    for (int ii = 0; ii < n; ++ii) cs += fabsf(x[ii]);
+  }
+  for (int o = 16; o > 0; o >>= 1) cs = fmaxf(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+  return cs;
 }
 
 __device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
@@ -413,7 +530,10 @@ __global__ void __launch_bounds__(IW * 32)
       // copy is the rounding of these values), the pivots, the precision tag,
       // the extent of U row k and the multiplier block
       if (staged) {
-        for (int e = lane; e < nk * nk; e += 32) sh.lu[warp][e] = __ldcg(dg + dgoff[k] + e);
+        if (sizeof(T) == sizeof(double))
+          for (int e = lane; e < nk * nk; e += 32) sh.lu[warp][e] = __ldcg(dg + dgoff[k] + e);
+        else
+          for (int e = lane; e < nk * nk; e += 32) sh.lu32[warp][e] = __ldcg(dg32 + dgoff[k] + e);
         if (lane < nk) sh.pv[warp][lane] = __ldcg(piv + A.roff[k] + lane);
         for (int e = lane; e < ni * nk; e += 32) mult[e] = m[e];
       }
@@ -425,12 +545,16 @@ __global__ void __launch_bounds__(IW * 32)
       __syncwarp();
       const bool use64 = sizeof(T) == sizeof(double) || sh.tag[warp] != 0;
       T* mm = staged ? mult : m;
+      if (staged && use64 && sizeof(T) != sizeof(double)) {  // an FP64 pivot block of the mixed factor
+        for (int e = lane; e < nk * nk; e += 32) sh.lu[warp][e] = __ldcg(dg + dgoff[k] + e);
+        __syncwarp();
+      }
       if (staged) {
         if (lane < ni) {
           if (use64)
             ainv_right_row_sh<T, double>(sh.lu[warp], sh.pv[warp], nk, mm + lane * nk);
           else
-            ainv_right_row_sh<T, float>(sh.lu[warp], sh.pv[warp], nk, mm + lane * nk);
+            ainv_right_row_sh<T, float>(sh.lu32[warp], sh.pv[warp], nk, mm + lane * nk);
         }
       } else {
         for (int a = lane; a < ni; a += 32) {
@@ -442,8 +566,18 @@ __global__ void __launch_bounds__(IW * 32)
       }
       __syncwarp();
       double f2 = 0.0;
-      if (lane == 0) f2 = fro2_seq(mm, ni * nk);
-      f2 = __shfl_sync(0xffffffffu, f2, 0);
+      if (sizeof(T) == sizeof(double)) {  // the oracle's summation order
+        if (lane == 0) f2 = fro2_seq(mm, ni * nk);
+        f2 = __shfl_sync(0xffffffffu, f2, 0);
+      } else {  // mixed factor: FP32 squares summed by a warp reduction
+        float sf = 0.f;
+        for (int e = lane; e < ni * nk; e += 32) {
+          const float x = (float)mm[e];
+          sf = __fmaf_rn(x, x, sf);
+        }
+        for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
+        f2 = (double)sf;
+      }
       if (drop_rule(f2, ni, nk, t)) {
         if (lane == 0) sstate[sk] = SL_DEAD;
         __syncwarp();
@@ -615,7 +749,8 @@ __global__ void __launch_bounds__(IW * 32)
         const int c = COL(q);
         if (ST(q) == SL_LIVE && c > i) {
           const int nc = A.rsz[c];
-          const double f2 = fro2_batched(wv + OFF(q), ni * nc);
+          const double f2 = sizeof(T) == sizeof(double) ? fro2_batched(wv + OFF(q), ni * nc)
+                                                          : (double)fro2_f32(wv + OFF(q), ni * nc);
           if (msh) mf2[q] = f2; else sf2[q] = f2;
           if (drop_rule(f2, ni, nc, t)) {
             if (msh) mst[q] = SL_DEAD; else sstate[q] = SL_DEAD;
@@ -680,91 +815,55 @@ __global__ void __launch_bounds__(IW * 32)
              (int64_t)(uvv + vu) <= P.uvcap;
       if (!fits) status_local = DEV_OVERFLOW;
       if (status_local == 0) {
-        // GEPP of the diagonal block (FP64, the oracle's order), in shared
-        // memory when it fits
-        const bool gsh = ni <= SMB;
-        double* a = gsh ? sh.lu[warp] : dg + dgoff[i];
+        // GEPP of the diagonal block, in shared memory when it fits.  FP64
+        // factor: FP64 in the oracle's operation order.  Mixed factor: FP32
+        // GEPP and 1-norm condition estimate (explicit inverse columns); a
+        // block above the threshold, larger than 32, or singular in FP32 is
+        // factored again in FP64 and tagged.
         const T* srcd = wv + OFF(dslot);
-        for (int e = lane; e < ni * ni; e += 32) a[e] = (double)srcd[e];
-        __syncwarp();
-        double norm1 = 0.0;
-        if (lane == 0) {
-          if (mixed)
-            for (int jj = 0; jj < ni; ++jj) {
-              double sum = 0.0;
-              for (int ii = 0; ii < ni; ++ii) sum += fabs(a[ii * ni + jj]);
-              norm1 = fmax(norm1, sum);
-            }
-          int* pv = sh.pv[warp];
-          bool singular = false;
-          for (int kk = 0; kk < ni; ++kk) {
-            int pr = kk;
-            double bestv = fabs(a[kk * ni + kk]);
-            for (int ii = kk + 1; ii < ni; ++ii) {
-              const double v = fabs(a[ii * ni + kk]);
-              if (v > bestv) {
-                bestv = v;
-                pr = ii;
+        const bool gsh = ni <= SMB;
+        int* pvs = gsh ? sh.pv[warp] : nullptr;
+        int32_t* gpiv = piv + A.roff[i];
+        bool ok = true, tag64 = true;
+        if (sizeof(T) == sizeof(float)) {
+          float* a = gsh ? sh.lu32[warp] : dg32 + dgoff[i];
+          for (int e = lane; e < ni * ni; e += 32) a[e] = (float)srcd[e];
+          __syncwarp();
+          float norm1 = 0.f;
+          for (int jj = lane; jj < ni; jj += 32) {
+            float sum = 0.f;
+            for (int ii = 0; ii < ni; ++ii) sum += fabsf(a[ii * ni + jj]);
+            norm1 = fmaxf(norm1, sum);
+          }
+          for (int o = 16; o > 0; o >>= 1) norm1 = fmaxf(norm1, __shfl_xor_sync(0xffffffffu, norm1, o));
+          __syncwarp();
+          if (ni <= 32 && gepp_warp<float>(a, ni, pvs, gpiv, lane)) {
+            const float kappa = norm1 * inv_norm1_f32(a, ni, gsh ? pvs : gpiv, lane);
+            tag64 = !(kappa <= (float)cond_thr);
+            if (!tag64) {
+              for (int e = lane; e < ni * ni; e += 32) {
+                if (gsh) dg32[dgoff[i] + e] = a[e];
+                dg[dgoff[i] + e] = (double)a[e];
               }
-            }
-            if (bestv == 0.0) {
-              singular = true;
-              break;
-            }
-            if (kk < SMB) pv[kk] = pr;
-            piv[A.roff[i] + kk] = pr;
-            if (pr != kk)
-              for (int jj = 0; jj < ni; ++jj) {
-                const double tt = a[kk * ni + jj];
-                a[kk * ni + jj] = a[pr * ni + jj];
-                a[pr * ni + jj] = tt;
-              }
-            const double d = a[kk * ni + kk];
-            for (int ii = kk + 1; ii < ni; ++ii) {
-              const double l = __ddiv_rn(a[ii * ni + kk], d);
-              a[ii * ni + kk] = l;
-              for (int jj = kk + 1; jj < ni; ++jj)
-                a[ii * ni + jj] = __dsub_rn(a[ii * ni + jj], __dmul_rn(l, a[kk * ni + jj]));
             }
           }
-          if (singular) *vflag = 3;
+          __syncwarp();
         }
-        __syncwarp();
-        if (*vflag == 3) status_local = DEV_ESINGULAR;
-        if (status_local == 0) {
-          if (gsh)
-            for (int e = lane; e < ni * ni; e += 32) dg[dgoff[i] + e] = a[e];
-          if (mixed) {
-            // 1-norm condition estimate with the explicit inverse: lane jj
-            // solves for column jj (blocks up to 32; larger ones stay FP64)
-            double cs = 0.0;
-            if (ni <= 32 && lane < ni) {
-              const int* pvs = gsh ? sh.pv[warp] : nullptr;
-              double x[32];
-              for (int ii = 0; ii < ni; ++ii) x[ii] = ii == lane ? 1.0 : 0.0;
-              for (int kk = 0; kk < ni; ++kk) {
-                const int pk = pvs ? pvs[kk] : piv[A.roff[i] + kk];
-                if (pk != kk) {
-                  const double tt = x[kk];
-                  x[kk] = x[pk];
-                  x[pk] = tt;
-                }
-              }
-              for (int ii = 1; ii < ni; ++ii)
-                for (int kk = 0; kk < ii; ++kk) x[ii] -= a[ii * ni + kk] * x[kk];
-              for (int ii = ni - 1; ii >= 0; --ii) {
-                double sum = x[ii];
-                for (int kk = ii + 1; kk < ni; ++kk) sum -= a[ii * ni + kk] * x[kk];
-                x[ii] = sum / a[ii * ni + ii];
-              }
-              for (int ii = 0; ii < ni; ++ii) cs += fabs(x[ii]);
+        if (tag64) {
+          double* a = gsh ? sh.lu[warp] : dg + dgoff[i];
+          for (int e = lane; e < ni * ni; e += 32) a[e] = (double)srcd[e];
+          __syncwarp();
+          ok = gepp_warp<double>(a, ni, pvs, gpiv, lane);
+          if (ok)
+            for (int e = lane; e < ni * ni; e += 32) {
+              if (gsh) dg[dgoff[i] + e] = a[e];
+              if (mixed) dg32[dgoff[i] + e] = (float)a[e];
             }
-            for (int o = 16; o > 0; o >>= 1) cs = fmax(cs, __shfl_xor_sync(0xffffffffu, cs, o));
-            norm1 = __shfl_sync(0xffffffffu, norm1, 0);
-            if (lane == 0) ptag[i] = (ni > 32 || norm1 * cs > cond_thr) ? 1 : 0;
-            for (int e = lane; e < ni * ni; e += 32) dg32[dgoff[i] + e] = (float)a[e];
-          }
         }
+        if (!ok)
+          status_local = DEV_ESINGULAR;
+        else if (mixed && lane == 0)
+          ptag[i] = tag64 ? 1 : 0;
       }
     }
     // Write the kept blocks of one part in column order: per chunk of 32

@@ -621,15 +621,233 @@ __global__ void __launch_bounds__(LW * 32)
   }
 }
 
-// Numeric phase, one warp per block row r of S.  Every element receives its
-// updates in the oracle's order: C value, then the G blocks ascending, each
-// contributing its k terms in order.
+// Numeric phase.  One warp per block row r of S.  The row's values are one
+// contiguous run of S (blocks ascending, each row-major), and S has C's row
+// partition, so the warp
+//   1. stages the row plan in shared memory: S block columns and offsets, the
+//      C block feeding each S block, and the (G block, W block) pairs of the
+//      row with the S block each pair updates;
+//   2. streams the C values into the S run (zero for fill blocks) with
+//      coalesced loads and stores;
+//   3. for each G block (r, Y) ascending, subtracts G_rY W_Ys from every S
+//      block s of W row Y: one lane per column of the W row, the column of W
+//      held in registers, the S rows i in batches;
+// so every element sees the C value, then the G blocks ascending, each with
+// its k terms ascending: the oracle's order.  The run just written stays in
+// L2 for the updates.  Rows that exceed the plan's capacities are listed for
+// k_schur_numeric_rows.
+constexpr int SN_WARPS = 8;   // warps per block
+constexpr int SN_NQ = 160;    // S blocks of one row
+constexpr int SN_NG = 32;     // G blocks of one row
+constexpr int SN_NP = 224;    // (G block, W block) pairs of one row
+constexpr int SN_RB = 8;      // S rows updated together
+constexpr int SN_MK = 8;      // W column length held in registers
+
+struct SnPlan {
+  int64_t gvo[SN_NG];     // value offset of G block g
+  int64_t wb0[SN_NG];     // first W block of W row Y_g
+  int64_t pwv[SN_NP];     // value offset of the W block of pair t
+  int32_t sb[SN_NQ];      // S block columns
+  int32_t soff[SN_NQ + 1];  // S block offsets within the run; soff[nq] = run length
+  int32_t csrc[SN_NQ];    // C block offset relative to the C row start, or -1
+  int32_t lst[SN_NG + 1];   // pairs of G block g: [lst[g], lst[g+1])
+  int32_t gm[SN_NG];      // n_Y
+  int32_t pq[SN_NP];      // S block of pair t
+  int32_t cpre[SN_NP + 1];  // W-row column prefix over the pairs
+};
+
+__device__ __forceinline__ int sn_find(const int32_t* a, int n, int32_t key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int32_t v = a[mid];
+    if (v == key) return mid;
+    if (v < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SN_WARPS * 32)
+    k_schur_numeric(VBView<T> C, VBView<T> G, VBView<T> W, VBView<T> S, int32_t* __restrict__ slow,
+                    int* __restrict__ nslow, int* st) {
+  extern __shared__ __align__(16) unsigned char sn_raw[];
+  const int lane = threadIdx.x & 31;
+  SnPlan& P = reinterpret_cast<SnPlan*>(sn_raw)[threadIdx.x >> 5];
+  const T* __restrict__ Cv = C.val;
+  const T* __restrict__ Gv = G.val;
+  const T* __restrict__ Wv = W.val;
+  for (int64_t r = (int64_t)blockIdx.x * SN_WARPS + (threadIdx.x >> 5); r < S.nbr;
+       r += (int64_t)gridDim.x * SN_WARPS) {
+    __syncwarp();
+    const int64_t s0 = S.bptr[r], s1 = S.bptr[r + 1];
+    const int64_t c0 = C.bptr[r], c1 = C.bptr[r + 1];
+    const int64_t g0 = G.bptr[r], g1 = G.bptr[r + 1];
+    const int nr = S.rsz[r];
+    const int64_t vbase = S.voff[s0], vend = S.voff[s1];
+    const int64_t cbase = C.voff[c0], cend = C.voff[c1];
+    if (s1 - s0 > SN_NQ || g1 - g0 > SN_NG || vend - vbase > INT32_MAX || cend - cbase > INT32_MAX) {
+      if (lane == 0) slow[atomicAdd(nslow, 1)] = (int32_t)r;
+      continue;
+    }
+    const int nq = (int)(s1 - s0), ng = (int)(g1 - g0);
+    for (int q = lane; q <= nq; q += 32) {
+      P.soff[q] = (int32_t)(S.voff[s0 + q] - vbase);
+      if (q < nq) {
+        P.sb[q] = S.bcol[s0 + q];
+        P.csrc[q] = -1;
+      }
+    }
+    int cnt = 0;
+    if (lane < ng) {
+      const int32_t Y = G.bcol[g0 + lane];
+      P.gm[lane] = G.csz[Y];
+      P.gvo[lane] = G.voff[g0 + lane];
+      const int64_t a = W.bptr[Y];
+      P.wb0[lane] = a;
+      cnt = (int)(W.bptr[Y + 1] - a);
+    }
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int np = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane < ng) P.lst[lane] = incl - cnt;
+    if (lane == 0) P.lst[ng] = np;
+    if (np > SN_NP) {
+      if (lane == 0) slow[atomicAdd(nslow, 1)] = (int32_t)r;
+      continue;
+    }
+    __syncwarp();
+    for (int64_t cb = c0 + lane; cb < c1; cb += 32) {
+      const int q = sn_find(P.sb, nq, C.bcol[cb]);
+      if (q >= 0)
+        P.csrc[q] = (int32_t)(C.voff[cb] - cbase);
+      else
+        dev_fail(st, DEV_INTERNAL);
+    }
+    int carry = 0;
+    for (int base = 0; base < np; base += 32) {
+      const int t = base + lane;
+      int ns = 0;
+      if (t < np) {
+        int lo = 0, hi = ng - 1;  // last g with lst[g] <= t
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (P.lst[mid] <= t)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        const int64_t wb = P.wb0[lo] + (t - P.lst[lo]);
+        int q = sn_find(P.sb, nq, W.bcol[wb]);
+        if (q < 0) {
+          dev_fail(st, DEV_INTERNAL);
+          q = 0;
+        }
+        P.pq[t] = q;
+        P.pwv[t] = W.voff[wb];
+        ns = (P.soff[q + 1] - P.soff[q]) / nr;
+      }
+      int sc = ns;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, sc, o);
+        if (lane >= o) sc += v;
+      }
+      if (t < np) P.cpre[t + 1] = carry + sc;
+      carry += __shfl_sync(0xffffffffu, sc, 31);
+    }
+    if (lane == 0) P.cpre[0] = 0;
+    __syncwarp();
+    // 2. C values (zero for fill) into the run
+    T* __restrict__ run = S.val + vbase;
+    const int vlen = P.soff[nq];
+    {
+      int q = 0;
+      for (int e0 = 0; e0 < vlen; e0 += 128) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * 32 + lane;
+          v[u] = (T)0;
+          if (e < vlen) {
+            while (P.soff[q + 1] <= e) ++q;
+            const int src = P.csrc[q];
+            if (src >= 0) v[u] = Cv[cbase + src + (e - P.soff[q])];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * 32 + lane;
+          if (e < vlen) run[e] = v[u];
+        }
+      }
+    }
+    __syncwarp();
+    // 3. the G W products, G blocks ascending
+    for (int g = 0; g < ng; ++g) {
+      const int t0 = P.lst[g], t1 = P.lst[g + 1];
+      if (t0 == t1) continue;
+      const int m = P.gm[g];
+      const T* __restrict__ gp = Gv + P.gvo[g];
+      const int cB = P.cpre[t1];
+      int t = t0;
+      for (int c = P.cpre[t0] + lane; c < cB; c += 32) {
+        while (P.cpre[t + 1] <= c) ++t;
+        const int j = c - P.cpre[t];
+        const int ns = P.cpre[t + 1] - P.cpre[t];
+        const T* __restrict__ wv = Wv + P.pwv[t] + j;
+        T* __restrict__ dst = run + P.soff[P.pq[t]] + j;
+        if (m <= SN_MK) {
+          T wr[SN_MK];
+#pragma unroll
+          for (int k = 0; k < SN_MK; ++k) wr[k] = k < m ? wv[k * ns] : (T)0;
+          for (int i0 = 0; i0 < nr; i0 += SN_RB) {
+            T a[SN_RB];
+#pragma unroll
+            for (int u = 0; u < SN_RB; ++u)
+              if (i0 + u < nr) a[u] = dst[(i0 + u) * ns];
+#pragma unroll
+            for (int u = 0; u < SN_RB; ++u) {
+              if (i0 + u < nr) {
+                const T* gi = gp + (i0 + u) * m;
+#pragma unroll
+                for (int k = 0; k < SN_MK; ++k)
+                  if (k < m) a[u] = msub<T>(a[u], gi[k], wr[k]);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < SN_RB; ++u)
+              if (i0 + u < nr) dst[(i0 + u) * ns] = a[u];
+          }
+        } else {
+          for (int i = 0; i < nr; ++i) {
+            T a = dst[i * ns];
+            for (int k = 0; k < m; ++k) a = msub<T>(a, gp[i * m + k], wv[k * ns]);
+            dst[i * ns] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Rows beyond the plan capacities: the same order of operations, one warp per
+// listed row, with the row's blocks located by binary search in global memory.
 template <typename T>
 __global__ void __launch_bounds__(LW * 32)
-    k_schur_numeric(VBView<T> C, VBView<T> G, VBView<T> W, VBView<T> S) {
+    k_schur_numeric_rows(VBView<T> C, VBView<T> G, VBView<T> W, VBView<T> S, const int32_t* __restrict__ rows,
+                         const int* __restrict__ nrows, int* st) {
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
-  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < S.nbr; r += (int64_t)gridDim.x * wpb) {
+  const int64_t total = *nrows;
+  for (int64_t t = blockIdx.x * wpb + (threadIdx.x >> 5); t < total; t += (int64_t)gridDim.x * wpb) {
+    const int64_t r = rows[t];
     const int nr = S.rsz[r];
     const int64_t s0 = S.bptr[r], s1 = S.bptr[r + 1];
     for (int64_t q = s0; q < s1; ++q) {
@@ -648,7 +866,10 @@ __global__ void __launch_bounds__(LW * 32)
         const int32_t sc = W.bcol[wb];
         const int ns = W.csz[sc];
         const int64_t q = bsearch_i32(S.bcol, s0, s1, sc);
-        if (q < 0) continue;  // cannot happen: the symbolic phase put every W column in the row
+        if (q < 0) {
+          if (lane == 0) dev_fail(st, DEV_INTERNAL);
+          continue;
+        }
         const T* wv = W.val + W.voff[wb];
         T* dst = S.val + S.voff[q];
         for (int e = lane; e < nr * ns; e += 32) {
@@ -936,6 +1157,9 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
   check_status(dst, s, "vbarms_factor: Schur pattern");
   finish_offsets(Sf, s);
   if (nC) {
+    DBuf<int32_t> slow(nC, s);
+    DBuf<int> nslow(1, s);
+    nslow.zero();
     if (rec) {
       // algorithmic work of the numeric phase: read C, G, W and write S once
       // (values and their index arrays); flops = sum over (r, Y, s) of
@@ -955,10 +1179,17 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
       VB_CUDA(cudaEventCreate(&rec->e1));
       VB_CUDA(cudaEventRecord(rec->e0, s));
     }
-    launch(k_schur_numeric<T>, grid_for(nC, LW, 152LL * 32), LW * 32, 0, s, C.view(), G.view(), W.view(), Sf.view());
+    const size_t psmem = (size_t)SN_WARPS * sizeof(SnPlan);
+    VB_CUDA(cudaFuncSetAttribute(k_schur_numeric<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+    launch(k_schur_numeric<T>, grid_for(nC, SN_WARPS, 152LL * 16), SN_WARPS * 32, psmem, s, C.view(), G.view(),
+           W.view(), Sf.view(), slow.p, nslow.p, dst);
+    VB_LAUNCH_CHECK();
+    launch(k_schur_numeric_rows<T>, 152u * 4, LW * 32, 0, s, C.view(), G.view(), W.view(), Sf.view(), slow.p,
+           nslow.p, dst);
     VB_LAUNCH_CHECK();
     if (rec) VB_CUDA(cudaEventRecord(rec->e1, s));
   }
+  check_status(dst, s, "vbarms_factor: Schur numeric");
   if (last_reduction && nC) {
     DBuf<int8_t> keep(Sf.nnzb, s);
     launch(k_schur_drop<T>, grid_for(nC, LW), LW * 32, 0, s, Sf.view(), t, keep.p);
