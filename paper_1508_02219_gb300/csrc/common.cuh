@@ -64,6 +64,44 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Default time budget of a bounded device wait: 30 s.
 constexpr unsigned long long kDefaultWaitNs = 30ull * 1000 * 1000 * 1000;
 
+__device__ __forceinline__ int ld_relaxed_gpu(const int32_t* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Publication flags of the sync-free kernels: a producer writes its data,
+// fences (__threadfence) and sets the flag to 1, or to 2 when it failed.  A
+// consumer waits here: relaxed polls with exponential backoff, the shared
+// abort word and the time budget looked at only every 16th poll (so that
+// waiting warps do not crowd one L2 line), then one acquire fence, which pairs
+// with the producer's fence.  Returns the flag, or 0 when the wait gave up:
+// abort raised elsewhere, or limit ns passed (then DEV_ETIMEOUT is recorded
+// and abort raised).
+__device__ __forceinline__ int wait_flag(const int32_t* flag, int* abort, unsigned long long limit, int* st) {
+  int v = ld_relaxed_gpu(flag);
+  if (v == 0) {
+    const unsigned long long t0 = global_ns();
+    unsigned nsl = 32;
+    for (unsigned it = 1;; ++it) {
+      __nanosleep(nsl);
+      if (nsl < 256) nsl <<= 1;
+      v = ld_relaxed_gpu(flag);
+      if (v != 0) break;
+      if ((it & 15) == 0) {
+        if (*((volatile int*)abort) != 0) return 0;
+        if (global_ns() - t0 > limit) {
+          dev_fail(st, DEV_ETIMEOUT);
+          atomicExch(abort, 1);
+          return 0;
+        }
+      }
+    }
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  return v;
+}
+
 // --------------------------------------------------------------------------
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
 template <typename T>

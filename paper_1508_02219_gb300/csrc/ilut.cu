@@ -5,16 +5,23 @@
 // Row i is processed by one warp that took ticket i (tickets are handed out
 // in row order, so every row a warp waits for is already owned by a running
 // warp).  The warp keeps its working row in a private workspace (hash table
-// column -> slot, dense values), eliminates its L part in ascending column
-// order including fill -- waiting, with a bounded spin, until row k is
-// published -- then drops and trims, factors its diagonal block (GEPP) and
-// publishes its L and U rows to global pools.  Per element, the operation
-// order is the oracle's, so FP64 results match it bit for bit.
+// column -> slot, dense values): in shared memory when the row fits, else in
+// global memory (a shared row whose fill outgrows the buffer starts again in
+// the global one).  It eliminates its L part in ascending column order
+// including fill -- waiting, with a bounded spin, until row k is published,
+// then staging row k's pivot block and U row in shared memory -- drops and
+// trims, factors its diagonal block (GEPP) and publishes its L and U rows to
+// global pools.  Per element, the operation order is the oracle's, so FP64
+// results match it bit for bit; the mixed factor keeps its drop sums, drop
+// tests and diagonal GEPP in FP32 (a block whose condition estimate exceeds
+// the threshold is factored again in FP64).
 //
-// A wait that runs out sets VB_ETIMEOUT and an abort flag that every other
-// warp checks; overflowing a pool or a workspace sets an overflow code and the
+// A wait that runs out sets VB_ETIMEOUT and raises an abort flag; a row that
+// failed publishes the flag value 2 so that its dependants stop too.
+// Overflowing a pool or the global workspace sets an overflow code and the
 // host repeats the kernel with larger buffers.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 #include "level.cuh"
@@ -49,9 +56,9 @@ struct Workspace {
   int* keys;      // [HT] per warp
   int* hpos;      // [SMAX]
   int* scol;      // [SMAX]
-  int64_t* soff;  // [SMAX]
+  int* soff;      // [SMAX]
   int* sstate;    // [SMAX]
-  double* sf2;    // [SMAX]
+  long long* sf2;  // [SMAX] norm key of each slot
   int ht, smax;
   int64_t vmax;
 };
@@ -71,6 +78,20 @@ __device__ __forceinline__ bool drop_rule(double f2, int m, int n, double t) {
   const double thr = __dmul_rn(__dmul_rn(t, (double)m), (double)n);
   return f2 < __dmul_rn(thr, thr);
 }
+
+// The same rule in FP32 for the mixed factor (FP64 operations are slow on
+// this part and would sit on the critical path of every elimination step).
+__device__ __forceinline__ bool drop_rule_f(float f2, int m, int n, float t) {
+  const float thr = t * (float)m * (float)n;
+  return f2 < thr * thr;
+}
+
+// Squared Frobenius norms are ranked (lfil) by their bit patterns: for
+// non-negative IEEE values the integer order is the value order, so the
+// comparisons stay on the integer pipes.  FP64 factor: the double's bits;
+// mixed factor: the float's bits.
+__device__ __forceinline__ long long norm_key(double f2) { return __double_as_longlong(f2); }
+__device__ __forceinline__ long long norm_key(float f2) { return (long long)__float_as_int(f2); }
 
 template <typename T>
 __device__ __forceinline__ double fro2_seq(const T* v, int n) {
@@ -131,23 +152,23 @@ __device__ __forceinline__ int ws_lookup(const int* keys, const int* scol, uint3
 }
 
 // Claim a new slot of sz values for column col; returns the slot or -1.
-template <typename T>
-__device__ __forceinline__ int ws_new_slot(const Workspace& ws, int* keys, int* hpos, int* scol, int64_t* soff,
+__device__ __forceinline__ int ws_new_slot(int smax, int64_t vmax, int* keys, int* hpos, int* scol, int* soff,
                                            int* sstate, int* nslots, unsigned long long* nvals, uint32_t hmask,
                                            int col, int sz) {
   const int slot = atomicAdd(nslots, 1);
   const long long off = (long long)atomicAdd(nvals, (unsigned long long)sz);
-  if (slot >= ws.smax) return -1;
+  if (slot >= smax) return -1;
   hpos[slot] = -1;  // the end-of-row reset skips slots that were never placed
-  if (off + sz > ws.vmax) return -1;
+  if (off + sz > vmax) return -1;
   scol[slot] = col;
-  soff[slot] = off;
+  soff[slot] = (int)off;
   sstate[slot] = SL_LIVE;
   hpos[slot] = ws_place(keys, hmask, slot, col);
   return hpos[slot] < 0 ? -1 : slot;
 }
 
-constexpr int SMB = 16;         // pivot blocks up to SMB x SMB are staged in shared memory
+constexpr int SMB = 16;         // pivot blocks up to SMB x SMB have their own shared buffer
+constexpr int PVMAX = 64;       // larger ones up to PVMAX are staged in free workspace space
 constexpr int MAX_SLOTS = 4096;  // largest workspace (blocks of one working row)
 
 // x (one row of length m) <- x (P^T L U)^{-1} from a staged pivot block
@@ -223,27 +244,46 @@ __device__ __forceinline__ float fro2_f32(const T* __restrict__ v, int n) {
   return s;
 }
 
-constexpr int LCAP = 128;          // pending L columns tracked in shared memory per warp
-constexpr int USTAGE_BYTES = 6144;  // U row of a dependency staged in shared memory per warp
+constexpr int LCAP = 128;           // pending L columns tracked in shared memory per warp
+constexpr int USTAGE_BYTES = 2048;  // U row of a dependency staged in shared memory per warp
+constexpr int WS_SLOTS = 64;        // working rows held in shared memory: blocks,
+constexpr int WS_HASH = 128;        //   hash positions,
+constexpr int WS_VBYTES = 4096;     //   value bytes
+constexpr int MSH = 96;             // slot metadata of a global working row staged for the finish
 
-struct IlutShared {
-  double lu[IW][SMB * SMB];     // FP64 pivot block (the dependency's, then the row's own)
-  float lu32[IW][SMB * SMB];    // FP32 pivot block of the mixed factor
-  double mult[IW][SMB * SMB];   // multiplier block (T values, in place)
-  int pv[IW][SMB];
-  int64_t qoff[IW][32];  // workspace value offset of each staged U block's target
-  int64_t quo[IW][32];   // value offset of the U block within the staged row
-  int qnj[IW][32];
-  int qpre[IW][33];      // element prefix of the staged U blocks
-  int lc[IW][LCAP];      // pending L columns (INT_MAX when processed)
-  int ls[IW][LCAP];      // their slots
-  int nl[IW];
-  int64_t hdr[IW][4];    // ustart, ucnt, uvstart, uvlen of the dependency
-  int tag[IW];
-  __align__(16) unsigned char ustage[IW][USTAGE_BYTES];
+// Per-warp shared memory: the working row when it fits (hash table, slot
+// metadata, values), the dependency's pivot block and U row, and the
+// bookkeeping of one elimination step.
+struct IlutWarp {
+  __align__(16) unsigned char vals[WS_VBYTES];
+  __align__(16) unsigned char ustage[USTAGE_BYTES];
+  __align__(16) unsigned char lu[SMB * SMB * sizeof(double)];  // FP64 or FP32 pivot block
+  long long sf2[WS_SLOTS];
+  long long wdst[32];  // pool value offset of each written block of a chunk
+  int keys[WS_HASH];
+  int hpos[WS_SLOTS];
+  int scol[WS_SLOTS];
+  int soff[WS_SLOTS];
+  int sstate[WS_SLOTS];
+  int pv[PVMAX];
+  int qoff[32];  // workspace value offset of each U block's target
+  int quo[32];   // value offset of the U block within the U row
+  int qnj[32];
+  int qpre[33];  // element prefix of the chunk's U blocks
+  int lc[LCAP];  // pending L columns (INT_MAX when processed)
+  int ls[LCAP];  // their slots
+  int nl, nslots, flag, pad;
+  unsigned long long nvals;
 };
 
-constexpr size_t ilut_smem() { return sizeof(IlutShared); }
+constexpr size_t ilut_smem() { return IW * sizeof(IlutWarp); }
+static_assert(MSH * (3 * sizeof(int) + sizeof(long long)) <= USTAGE_BYTES, "finish staging exceeds the U-row buffer");
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // x (one row of length m) <- x (P^T L U)^{-1} from a staged pivot block
 // (values of type TS, arithmetic in TL); x lives in shared memory.
@@ -373,41 +413,27 @@ __device__ float inv_norm1_f32(const float* a, int n, const int* pv, int lane) {
   return cs;
 }
 
-__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 template <typename T>
-__global__ void __launch_bounds__(IW * 32)
+__global__ void __launch_bounds__(IW * 32, 2)
     k_ilut(VBView<T> A, Workspace ws, T* __restrict__ wvals_all, Pools P, T* __restrict__ lval,
            T* __restrict__ uval, const int64_t* __restrict__ dgoff, double* __restrict__ dg,
            float* __restrict__ dg32, int32_t* __restrict__ piv, int32_t* __restrict__ ptag, int mixed,
            double cond_thr, double t, int lfil, unsigned long long wait_limit, int* st) {
-  __shared__ int s_nslots[IW];
-  __shared__ unsigned long long s_nvals[IW];
-  __shared__ int s_flag[IW];
   extern __shared__ __align__(16) unsigned char ilut_sm[];
-  IlutShared& sh = *reinterpret_cast<IlutShared*>(ilut_sm);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  IlutWarp& W = reinterpret_cast<IlutWarp*>(ilut_sm)[warp];
   const int64_t wid = (int64_t)blockIdx.x * IW + warp;
-  int* keys = ws.keys + wid * ws.ht;
-  int* hpos = ws.hpos + wid * ws.smax;
-  int* scol = ws.scol + wid * ws.smax;
-  int64_t* soff = ws.soff + wid * ws.smax;
-  int* sstate = ws.sstate + wid * ws.smax;
-  double* sf2 = ws.sf2 + wid * ws.smax;
-  T* wv = wvals_all + wid * ws.vmax;
-  T* mult = reinterpret_cast<T*>(sh.mult[warp]);
-  const T* ustage = reinterpret_cast<const T*>(sh.ustage[warp]);
-  T* ustage_w = reinterpret_cast<T*>(sh.ustage[warp]);
   constexpr int USTAGE = USTAGE_BYTES / (int)sizeof(T);
-  const uint32_t hmask = (uint32_t)ws.ht - 1;
-  volatile int* vflag = &s_flag[warp];
-  volatile int* vns = &s_nslots[warp];
-  volatile int* vnl = &sh.nl[warp];
-  for (int k = lane; k < ws.ht; k += 32) keys[k] = -1;
+  constexpr int VSH = WS_VBYTES / (int)sizeof(T);
+  T* const ustage = reinterpret_cast<T*>(W.ustage);
+  const float tf = (float)t, condf = (float)cond_thr;
+  volatile int* vflag = &W.flag;
+  volatile int* vns = &W.nslots;
+  volatile int* vnl = &W.nl;
+  int* const gkeys = ws.keys + wid * ws.ht;
+  for (int k = lane; k < ws.ht; k += 32) gkeys[k] = -1;
+  for (int k = lane; k < WS_HASH; k += 32) W.keys[k] = -1;
   __syncwarp();
 
   for (;;) {
@@ -417,21 +443,46 @@ __global__ void __launch_bounds__(IW * 32)
     if (row >= A.nbr) break;
     const int64_t i = row;
     const int ni = A.rsz[i];
-    if (lane == 0) {
-      s_nslots[warp] = 0;
-      s_nvals[warp] = 0;
-      s_flag[warp] = 0;
-      sh.nl[warp] = 0;
-    }
-    __syncwarp();
-    // ---- load row i of A into the workspace: slot q is the row's block q and
-    // the values arrive as one contiguous copy; columns left of the diagonal
-    // enter the shared list of pending L columns
-    {
-      const int64_t b0 = A.bptr[i], b1 = A.bptr[i + 1];
-      const int64_t v0 = A.voff[b0], nv = A.voff[b1] - v0;
-      const int nb = (int)(b1 - b0);
-      if (nb > ws.smax || nv > ws.vmax) {
+    const int64_t b0 = A.bptr[i], b1 = A.bptr[i + 1];
+    const int64_t v0 = A.voff[b0], nv = A.voff[b1] - v0;
+    const int nb = (int)(b1 - b0);
+    // The working row lives in shared memory when it leaves room for fill; a
+    // row whose fill outgrows that restarts in the warp's global workspace
+    // (nothing of it is visible before its finish, so the restart is exact).
+    bool in_sh = nb <= WS_SLOTS / 2 && nv <= VSH / 2;
+    int status_local = 0;
+    int* keys;
+    int* hpos;
+    int* scol;
+    int* soff;
+    int* sstate;
+    long long* sf2;
+    T* wv;
+    int smax_c;
+    int64_t vmax_c;
+    uint32_t hmask;
+    for (;;) {
+      if (in_sh) {
+        keys = W.keys, hpos = W.hpos, scol = W.scol, soff = W.soff, sstate = W.sstate, sf2 = W.sf2;
+        wv = reinterpret_cast<T*>(W.vals);
+        smax_c = WS_SLOTS, vmax_c = VSH, hmask = WS_HASH - 1;
+      } else {
+        keys = gkeys, hpos = ws.hpos + wid * ws.smax, scol = ws.scol + wid * ws.smax;
+        soff = ws.soff + wid * ws.smax, sstate = ws.sstate + wid * ws.smax, sf2 = ws.sf2 + wid * ws.smax;
+        wv = wvals_all + wid * ws.vmax;
+        smax_c = ws.smax, vmax_c = ws.vmax, hmask = (uint32_t)ws.ht - 1;
+      }
+      if (lane == 0) {
+        W.nslots = 0;
+        W.nvals = 0;
+        W.flag = 0;
+        W.nl = 0;
+      }
+      __syncwarp();
+      // ---- load row i of A into the workspace: slot q is the row's block q
+      // and the values arrive as one contiguous copy; columns left of the
+      // diagonal enter the list of pending L columns
+      if (nb > smax_c || nv > vmax_c) {
         if (lane == 0) {
           *vflag = 1;
           atomicMax(P.ctr + 5, (unsigned long long)nv);
@@ -442,282 +493,331 @@ __global__ void __launch_bounds__(IW * 32)
           const int slot = (int)(b - b0);
           const int32_t J = A.bcol[b];
           scol[slot] = J;
-          soff[slot] = A.voff[b] - v0;
+          soff[slot] = (int)(A.voff[b] - v0);
           sstate[slot] = SL_LIVE;
           hpos[slot] = ws_place(keys, hmask, slot, J);  // the table holds 2 smax positions
           if (J < i) {
-            const int q = atomicAdd(&sh.nl[warp], 1);
+            const int q = atomicAdd(&W.nl, 1);
             if (q < LCAP) {
-              sh.lc[warp][q] = J;
-              sh.ls[warp][q] = slot;
+              W.lc[q] = J;
+              W.ls[q] = slot;
             }
           }
         }
         warp_copy(wv, A.val + v0, nv, lane);
         if (lane == 0) {
-          s_nslots[warp] = nb;
-          s_nvals[warp] = (unsigned long long)nv;
+          W.nslots = nb;
+          W.nvals = (unsigned long long)nv;
         }
       }
-    }
-    __syncwarp();
-    int status_local = *vflag ? DEV_OVERFLOW : 0;
-    int64_t last = -1;
-    // ---- eliminate the L part in ascending column order (including fill)
-    while (status_local == 0) {
-      // next pending L column: from the shared list while it has not
-      // overflowed, else by a scan of the workspace slots
-      int best = 0x7fffffff, bslot = -1, bpos = -1;
-      const int nlist = *vnl;
-      if (nlist <= LCAP) {
-        for (int q = lane; q < nlist; q += 32) {
-          const int c = sh.lc[warp][q];
-          if (c < best) {
-            best = c;
-            bslot = sh.ls[warp][q];
-            bpos = q;
+      __syncwarp();
+      status_local = *vflag ? DEV_OVERFLOW : 0;
+      int64_t last = -1;
+      // ---- eliminate the L part in ascending column order (including fill)
+      while (status_local == 0) {
+        // next pending L column: from the list while it has not overflowed,
+        // else by a scan of the workspace slots
+        int best = 0x7fffffff, bslot = -1, bpos = -1;
+        const int nlist = *vnl;
+        if (nlist <= LCAP) {
+          for (int q = lane; q < nlist; q += 32) {
+            const int c = W.lc[q];
+            if (c < best) {
+              best = c;
+              bslot = W.ls[q];
+              bpos = q;
+            }
+          }
+        } else {
+          const int ns = min(*vns, smax_c);
+          for (int sidx = lane; sidx < ns; sidx += 32) {
+            const int c = scol[sidx];
+            if (sstate[sidx] == SL_LIVE && c > last && c < i && c < best) {
+              best = c;
+              bslot = sidx;
+            }
           }
         }
-      } else {
-        const int ns = min(*vns, ws.smax);
-        for (int sidx = lane; sidx < ns; sidx += 32) {
-          const int c = scol[sidx];
-          if (sstate[sidx] == SL_LIVE && c > last && c < i && c < best) {
-            best = c;
-            bslot = sidx;
+        const int kmin = warp_min_i(best);
+        if (kmin == 0x7fffffff) break;
+        const unsigned who = __ballot_sync(0xffffffffu, bslot >= 0 && best == kmin);
+        const int owner = __ffs(who) - 1;
+        const int sk = __shfl_sync(0xffffffffu, bslot, owner);
+        if (lane == owner && bpos >= 0) W.lc[bpos] = 0x7fffffff;
+        const int64_t k = kmin;
+        last = k;
+        // static data of row k: loaded before the wait, used after it
+        const int nk = A.rsz[k];
+        const int64_t dgk = dgoff[k];
+        const int64_t rk = A.roff[k];
+        // bounded wait until row k is published; a row that failed publishes
+        // 2 (its factors must not be used)
+        if (lane == 0 && wait_flag(P.done + k, P.abort, wait_limit, st) != 1) *vflag = 2;
+        __syncwarp();
+        if (*vflag == 2) {
+          status_local = DEV_ETIMEOUT;
+          break;
+        }
+        T* m = wv + soff[sk];
+        // the pivot block of k goes to shared memory: its own buffer when
+        // small, else the free tail of the value buffer (new slots are only
+        // created after the multiplier), sized for FP64
+        unsigned char* lus = nullptr;
+        if (nk <= SMB) {
+          lus = W.lu;
+        } else if (nk <= PVMAX) {
+          const long long used = in_sh ? ((long long)W.nvals * (long long)sizeof(T) + 15) / 16 * 16 : 0;
+          if (used + (long long)nk * nk * (long long)sizeof(double) <= WS_VBYTES) lus = W.vals + used;
+        }
+        const bool staged = lus != nullptr;
+        double* const luD = reinterpret_cast<double*>(lus);
+        float* const luF = reinterpret_cast<float*>(lus);
+        // round A: the precision tag and the extent of U row k (lanes 0-4),
+        // the pivot block of k and its pivots
+        long long hv = 0;
+        if (lane == 0)
+          hv = ptag ? __ldcg(ptag + k) : 1;
+        else if (lane == 1)
+          hv = __ldcg(P.ustart + k);
+        else if (lane == 2)
+          hv = __ldcg(P.ucnt + k);
+        else if (lane == 3)
+          hv = __ldcg(P.uvstart + k);
+        else if (lane == 4)
+          hv = __ldcg(P.uvlen + k);
+        if (staged && nk <= SMB) {  // every load issued before the first store
+          constexpr int LV = SMB * SMB / 32;
+          using TS = typename std::conditional<sizeof(T) == sizeof(double), double, float>::type;
+          const TS* src = sizeof(T) == sizeof(double) ? reinterpret_cast<const TS*>(dg) : reinterpret_cast<const TS*>(dg32);
+          TS* dstl = reinterpret_cast<TS*>(lus);
+          TS lv[LV];
+#pragma unroll
+          for (int u = 0; u < LV; ++u) {
+            const int e = lane + 32 * u;
+            lv[u] = e < nk * nk ? __ldcg(src + dgk + e) : (TS)0;
+          }
+          const int pvv = lane < nk ? __ldcg(piv + rk + lane) : 0;
+#pragma unroll
+          for (int u = 0; u < LV; ++u) {
+            const int e = lane + 32 * u;
+            if (e < nk * nk) dstl[e] = lv[u];
+          }
+          if (lane < nk) W.pv[lane] = pvv;
+        } else if (staged) {
+          if (sizeof(T) == sizeof(double))
+            for (int e = lane; e < nk * nk; e += 32) luD[e] = __ldcg(dg + dgk + e);
+          else
+            for (int e = lane; e < nk * nk; e += 32) luF[e] = __ldcg(dg32 + dgk + e);
+          if (lane < nk) W.pv[lane] = __ldcg(piv + rk + lane);
+        }
+        const int tag = (int)__shfl_sync(0xffffffffu, hv, 0);
+        const int64_t u0 = __shfl_sync(0xffffffffu, hv, 1);
+        const int uc = (int)__shfl_sync(0xffffffffu, hv, 2);
+        const int64_t uvs = __shfl_sync(0xffffffffu, hv, 3);
+        const int64_t uvl = __shfl_sync(0xffffffffu, hv, 4);
+        if (u0 < 0 || uc < 0 || u0 + uc > P.ubcap || uvs < 0 || uvl < 0 || uvs + uvl > P.uvcap) {
+          status_local = DEV_INTERNAL;  // never true for a published row: record and skip
+          break;
+        }
+        // round B, in flight during the multiplier: U row k into shared memory
+        // (16-byte asynchronous copies; U rows start 16-byte aligned in the
+        // pool and their padding is reserved) and the columns and offsets of
+        // its first 32 blocks
+        const bool ust = uvl <= USTAGE && ((uvs * (int64_t)sizeof(T)) & 15) == 0;
+        if (ust) {
+          const int nch = (int)((uvl * (int64_t)sizeof(T) + 15) / 16);
+          const unsigned char* src = reinterpret_cast<const unsigned char*>(uval + uvs);
+          for (int c = lane; c < nch; c += 32) cp_async16(W.ustage + 16 * c, src + 16 * c);
+        }
+        int32_t pj = -1;
+        int64_t puo = 0;
+        if (lane < uc) {
+          pj = __ldcg(P.ucol + u0 + lane);
+          puo = __ldcg(P.uvo + u0 + lane);
+        }
+        const bool use64 = sizeof(T) == sizeof(double) || tag != 0;
+        if (staged && use64 && sizeof(T) != sizeof(double))  // an FP64 pivot block of the mixed factor
+          for (int e = lane; e < nk * nk; e += 32) luD[e] = __ldcg(dg + dgk + e);
+        __syncwarp();
+        // the multiplier m = a_ik (P^T L U)_k^{-1}, in place, one lane per row
+        if (staged) {
+          for (int a = lane; a < ni; a += 32) {
+            if (use64)
+              ainv_right_row_sh<T, double>(luD, W.pv, nk, m + a * nk);
+            else
+              ainv_right_row_sh<T, float>(luF, W.pv, nk, m + a * nk);
+          }
+        } else {
+          for (int a = lane; a < ni; a += 32) {
+            if (use64)
+              ainv_right_row<T, double>(dg + dgk, piv + rk, nk, m + a * nk);
+            else
+              ainv_right_row<T, float>(dg32 + dgk, piv + rk, nk, m + a * nk);
           }
         }
-      }
-      const int kmin = warp_min_i(best);
-      if (kmin == 0x7fffffff) break;
-      const unsigned who = __ballot_sync(0xffffffffu, bslot >= 0 && best == kmin);
-      const int owner = __ffs(who) - 1;
-      const int sk = __shfl_sync(0xffffffffu, bslot, owner);
-      if (lane == owner && bpos >= 0) sh.lc[warp][bpos] = 0x7fffffff;
-      const int64_t k = kmin;
-      last = k;
-      const int nk = A.rsz[k];
-      // bounded wait (acquire) until row k is published
-      if (lane == 0) {
-        const unsigned long long t_start = global_ns();
-        unsigned nsl = 32;
-        while (ld_acquire_gpu(P.done + k) == 0) {
-          if (*((volatile int*)P.abort) != 0) {
-            *vflag = 2;
+        __syncwarp();
+        long long key = 0;
+        bool dropped;
+        if (sizeof(T) == sizeof(double)) {  // the oracle's summation order
+          double f2 = 0.0;
+          if (lane == 0) f2 = fro2_seq(m, ni * nk);
+          f2 = __shfl_sync(0xffffffffu, f2, 0);
+          dropped = drop_rule(f2, ni, nk, t);
+          key = norm_key(f2);
+        } else {  // mixed factor: FP32 squares summed by a warp reduction
+          float sf = 0.f;
+          for (int e = lane; e < ni * nk; e += 32) {
+            const float x = (float)m[e];
+            sf = __fmaf_rn(x, x, sf);
+          }
+          for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
+          dropped = drop_rule_f(sf, ni, nk, tf);
+          key = norm_key(sf);
+        }
+        if (ust) cp_async_wait_all();
+        if (dropped) {
+          if (lane == 0) sstate[sk] = SL_DEAD;
+          __syncwarp();
+          continue;
+        }
+        if (lane == 0) {
+          sstate[sk] = SL_LKEPT;
+          sf2[sk] = key;
+        }
+        __syncwarp();
+        // U row k in chunks of 32 blocks: look up or create the target blocks
+        // (probe, then place, separated by __syncwarp), then update all
+        // elements of the chunk with lanes spread over the flattened elements.
+        for (int q0 = 0; q0 < uc && status_local == 0; q0 += 32) {
+          const int q = q0 + lane;
+          int32_t j = -1;
+          int slot = -1;
+          int64_t uo = 0;
+          bool missing = false;
+          if (q < uc) {
+            if (q0 == 0) {
+              j = pj;
+              uo = puo;
+            } else {
+              j = __ldcg(P.ucol + u0 + q);
+              uo = __ldcg(P.uvo + u0 + q);
+            }
+            if (j <= k || j >= A.nbr || uo < uvs || uo + (int64_t)nk * A.rsz[j] > uvs + uvl) {
+              *vflag = 4;  // a published U block lies right of k inside its row's extent
+              j = -1;
+            } else {
+              slot = ws_lookup(keys, scol, hmask, j);
+              missing = slot < 0;
+            }
+          }
+          __syncwarp();
+          if (missing) {
+            const int sz = ni * A.rsz[j];
+            slot = ws_new_slot(smax_c, vmax_c, keys, hpos, scol, soff, sstate, &W.nslots, &W.nvals, hmask, j, sz);
+            if (slot < 0) {
+              *vflag = 1;
+            } else {
+              T* z = wv + soff[slot];
+#pragma unroll 4
+              for (int e = 0; e < sz; ++e) z[e] = (T)0;
+              if (j < i) {  // fill in the L part: pending for a later step
+                const int pq = atomicAdd(&W.nl, 1);
+                if (pq < LCAP) {
+                  W.lc[pq] = j;
+                  W.ls[pq] = slot;
+                }
+              }
+            }
+          }
+          __syncwarp();
+          if (*vflag == 1) {
+            status_local = DEV_OVERFLOW;
             break;
           }
-          if (global_ns() - t_start > wait_limit) {  // wait_limit is a time budget in ns
-            dev_fail(st, DEV_ETIMEOUT);
-            atomicExch(P.abort, 1);
-            *vflag = 2;
+          if (*vflag == 4) {
+            status_local = DEV_INTERNAL;
             break;
           }
-          __nanosleep(nsl);  // exponential backoff keeps waiting warps off the L2
-          if (nsl < 256) nsl <<= 1;
+          const int nj = j >= 0 ? A.rsz[j] : 0;
+          const int sz = ni * nj;
+          int incl = sz;
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+          }
+          const int total = __shfl_sync(0xffffffffu, incl, 31);
+          W.qpre[lane] = incl - sz;
+          if (lane == 31) W.qpre[32] = total;
+          W.qoff[lane] = slot >= 0 ? soff[slot] : 0;
+          W.quo[lane] = (int)(uo - uvs);
+          W.qnj[lane] = nj;
+          __syncwarp();
+          const int nq = min(32, uc - q0);
+          const T* Ubase = ust ? ustage : uval + uvs;
+          // four elements per lane in flight
+          for (int e0 = lane; e0 < total; e0 += 128) {
+            T acc[4];
+            T* dst[4];
+            int a4[4], jj4[4], nj4[4], uo4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int e = e0 + 32 * u;
+              dst[u] = nullptr;
+              if (e < total) {
+                int lo = 0, hi = nq - 1;  // block tq with qpre[tq] <= e < qpre[tq + 1]
+                while (lo < hi) {
+                  const int mid = (lo + hi + 1) >> 1;
+                  if (W.qpre[mid] <= e)
+                    lo = mid;
+                  else
+                    hi = mid - 1;
+                }
+                const int njt = W.qnj[lo];
+                const int local = e - W.qpre[lo];
+                a4[u] = local / njt;
+                jj4[u] = local - a4[u] * njt;
+                nj4[u] = njt;
+                uo4[u] = W.quo[lo];
+                dst[u] = wv + W.qoff[lo] + local;
+                acc[u] = *dst[u];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (!dst[u]) continue;
+              const T* U = Ubase + uo4[u];
+              T av = acc[u];
+              if (ust) {
+                for (int r = 0; r < nk; ++r) av = msub<T>(av, m[a4[u] * nk + r], U[r * nj4[u] + jj4[u]]);
+              } else {
+                for (int r = 0; r < nk; ++r) av = msub<T>(av, m[a4[u] * nk + r], __ldcg(U + r * nj4[u] + jj4[u]));
+              }
+              *dst[u] = av;
+            }
+          }
+          __syncwarp();
         }
-        // a row that failed still publishes (so no one waits forever) but
-        // raises abort first: its factors must not be used
-        if (*((volatile int*)P.abort) != 0) *vflag = 2;
       }
-      __syncwarp();
-      if (*vflag == 2) {
-        status_local = DEV_ETIMEOUT;
-        break;
-      }
-      T* m = wv + soff[sk];
-      const bool staged = nk <= SMB && ni <= SMB;
-      // one batch of independent loads: the pivot block of k (FP64; its FP32
-      // copy is the rounding of these values), the pivots, the precision tag,
-      // the extent of U row k and the multiplier block
-      if (staged) {
-        if (sizeof(T) == sizeof(double))
-          for (int e = lane; e < nk * nk; e += 32) sh.lu[warp][e] = __ldcg(dg + dgoff[k] + e);
-        else
-          for (int e = lane; e < nk * nk; e += 32) sh.lu32[warp][e] = __ldcg(dg32 + dgoff[k] + e);
-        if (lane < nk) sh.pv[warp][lane] = __ldcg(piv + A.roff[k] + lane);
-        for (int e = lane; e < ni * nk; e += 32) mult[e] = m[e];
-      }
-      if (lane == 0) sh.tag[warp] = ptag ? __ldcg(ptag + k) : 1;
-      if (lane == 1) sh.hdr[warp][0] = __ldcg(P.ustart + k);
-      if (lane == 2) sh.hdr[warp][1] = __ldcg(P.ucnt + k);
-      if (lane == 3) sh.hdr[warp][2] = __ldcg(P.uvstart + k);
-      if (lane == 4) sh.hdr[warp][3] = __ldcg(P.uvlen + k);
-      __syncwarp();
-      const bool use64 = sizeof(T) == sizeof(double) || sh.tag[warp] != 0;
-      T* mm = staged ? mult : m;
-      if (staged && use64 && sizeof(T) != sizeof(double)) {  // an FP64 pivot block of the mixed factor
-        for (int e = lane; e < nk * nk; e += 32) sh.lu[warp][e] = __ldcg(dg + dgoff[k] + e);
+      if (status_local == DEV_OVERFLOW && in_sh) {
+        // the fill outgrew the shared workspace: start the row again in the
+        // global one
+        for (int q = lane; q < WS_HASH; q += 32) W.keys[q] = -1;
         __syncwarp();
-      }
-      if (staged) {
-        if (lane < ni) {
-          if (use64)
-            ainv_right_row_sh<T, double>(sh.lu[warp], sh.pv[warp], nk, mm + lane * nk);
-          else
-            ainv_right_row_sh<T, float>(sh.lu32[warp], sh.pv[warp], nk, mm + lane * nk);
-        }
-      } else {
-        for (int a = lane; a < ni; a += 32) {
-          if (use64)
-            ainv_right_row<T, double>(dg + dgoff[k], piv + A.roff[k], nk, m + a * nk);
-          else
-            ainv_right_row<T, float>(dg32 + dgoff[k], piv + A.roff[k], nk, m + a * nk);
-        }
-      }
-      __syncwarp();
-      double f2 = 0.0;
-      if (sizeof(T) == sizeof(double)) {  // the oracle's summation order
-        if (lane == 0) f2 = fro2_seq(mm, ni * nk);
-        f2 = __shfl_sync(0xffffffffu, f2, 0);
-      } else {  // mixed factor: FP32 squares summed by a warp reduction
-        float sf = 0.f;
-        for (int e = lane; e < ni * nk; e += 32) {
-          const float x = (float)mm[e];
-          sf = __fmaf_rn(x, x, sf);
-        }
-        for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
-        f2 = (double)sf;
-      }
-      if (drop_rule(f2, ni, nk, t)) {
-        if (lane == 0) sstate[sk] = SL_DEAD;
-        __syncwarp();
+        in_sh = false;
         continue;
       }
-      if (lane == 0) {
-        sstate[sk] = SL_LKEPT;
-        sf2[sk] = f2;
-      }
-      if (staged)
-        for (int e = lane; e < ni * nk; e += 32) m[e] = mm[e];  // the kept multiplier is an L block
-      const int64_t u0 = sh.hdr[warp][0];
-      const int uc = (int)sh.hdr[warp][1];
-      const int64_t uvs = sh.hdr[warp][2];
-      const int64_t uvl = sh.hdr[warp][3];
-      if (u0 < 0 || uc < 0 || u0 + uc > P.ubcap || uvs < 0 || uvl < 0 || uvs + uvl > P.uvcap) {
-        status_local = DEV_INTERNAL;  // never true for a published row: record and skip
-        break;
-      }
-      // stage U row k (contiguous in the pool) when it fits
-      const bool ust = uvl <= USTAGE;
-      if (ust) {
-#pragma unroll 4
-        for (int64_t e = lane; e < uvl; e += 32) ustage_w[e] = __ldcg(uval + uvs + e);
-      }
-      // U row k in chunks of 32 blocks: look up or create the target blocks
-      // (probe, then place, separated by __syncwarp), then update all
-      // elements of the chunk with lanes spread over the flattened elements.
-      for (int q0 = 0; q0 < uc && status_local == 0; q0 += 32) {
-        const int q = q0 + lane;
-        int32_t j = -1;
-        int slot = -1;
-        int64_t uo = 0;
-        bool missing = false;
-        if (q < uc) {
-          j = __ldcg(P.ucol + u0 + q);
-          uo = __ldcg(P.uvo + u0 + q);
-          if (j <= k || j >= A.nbr || uo < uvs || uo + (int64_t)nk * A.rsz[j] > uvs + uvl) {
-            *vflag = 4;  // a published U block lies right of k inside its row's extent
-            j = -1;
-          } else {
-            slot = ws_lookup(keys, scol, hmask, j);
-            missing = slot < 0;
-          }
-        }
-        __syncwarp();
-        if (missing) {
-          const int sz = ni * A.rsz[j];
-          slot = ws_new_slot<T>(ws, keys, hpos, scol, soff, sstate, &s_nslots[warp], &s_nvals[warp], hmask, j, sz);
-          if (slot < 0) {
-            *vflag = 1;
-          } else {
-            T* z = wv + soff[slot];
-#pragma unroll 4
-            for (int e = 0; e < sz; ++e) z[e] = (T)0;
-            if (j < i) {  // fill in the L part: pending for a later step
-              const int pq = atomicAdd(&sh.nl[warp], 1);
-              if (pq < LCAP) {
-                sh.lc[warp][pq] = j;
-                sh.ls[warp][pq] = slot;
-              }
-            }
-          }
-        }
-        __syncwarp();
-        if (*vflag == 1) {
-          status_local = DEV_OVERFLOW;
-          break;
-        }
-        if (*vflag == 4) {
-          status_local = DEV_INTERNAL;
-          break;
-        }
-        const int nj = j >= 0 ? A.rsz[j] : 0;
-        const int sz = ni * nj;
-        int incl = sz;
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        sh.qpre[warp][lane] = incl - sz;
-        if (lane == 31) sh.qpre[warp][32] = total;
-        sh.qoff[warp][lane] = slot >= 0 ? soff[slot] : 0;
-        sh.quo[warp][lane] = uo - uvs;
-        sh.qnj[warp][lane] = nj;
-        __syncwarp();
-        const int nq = min(32, uc - q0);
-        const T* Ubase = ust ? ustage : uval + uvs;
-        // four elements per lane in flight: their workspace loads overlap
-        for (int e0 = lane; e0 < total; e0 += 128) {
-          T acc[4];
-          T* dst[4];
-          int a4[4], jj4[4], nj4[4];
-          int64_t uo4[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int e = e0 + 32 * u;
-            dst[u] = nullptr;
-            if (e < total) {
-              int lo = 0, hi = nq - 1;  // block tq with qpre[tq] <= e < qpre[tq + 1]
-              while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sh.qpre[warp][mid] <= e)
-                  lo = mid;
-                else
-                  hi = mid - 1;
-              }
-              const int njt = sh.qnj[warp][lo];
-              const int local = e - sh.qpre[warp][lo];
-              a4[u] = local / njt;
-              jj4[u] = local - a4[u] * njt;
-              nj4[u] = njt;
-              uo4[u] = sh.quo[warp][lo];
-              dst[u] = wv + sh.qoff[warp][lo] + local;
-              acc[u] = *dst[u];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (!dst[u]) continue;
-            const T* U = Ubase + uo4[u];
-            T av = acc[u];
-            for (int r = 0; r < nk; ++r) av = msub<T>(av, mm[a4[u] * nk + r], U[r * nj4[u] + jj4[u]]);
-            *dst[u] = av;
-          }
-        }
-        __syncwarp();
-      }
+      break;
     }
-    const int ns = min(*vns, ws.smax);
-    // ---- finish the row.  The slot metadata is staged in shared memory (the
-    // U-row stage buffer is free now) so that the scans below read on-chip
-    // data; rows with more than MSH slots read the workspace directly.
-    constexpr int MSH = USTAGE_BYTES / 24;
-    int* mcol = reinterpret_cast<int*>(sh.ustage[warp]);
+    const int ns = min(*vns, smax_c);
+    // ---- finish the row.  A row in the global workspace has its slot
+    // metadata staged in shared memory (the U-row stage buffer is free now)
+    // so that the scans below read on-chip data; rows with more than MSH
+    // slots read the workspace directly.
+    int* mcol = reinterpret_cast<int*>(W.ustage);
     int* mst = mcol + MSH;
-    int64_t* moff = reinterpret_cast<int64_t*>(mst + MSH);
-    double* mf2 = reinterpret_cast<double*>(moff + MSH);
-    const bool msh = ns <= MSH;
+    int* moff = mst + MSH;
+    long long* mf2 = reinterpret_cast<long long*>(moff + MSH);
+    const bool msh = !in_sh && ns <= MSH;
     if (msh)
       for (int q = lane; q < ns; q += 32) {
         mcol[q] = scol[q];
@@ -749,10 +849,19 @@ __global__ void __launch_bounds__(IW * 32)
         const int c = COL(q);
         if (ST(q) == SL_LIVE && c > i) {
           const int nc = A.rsz[c];
-          const double f2 = sizeof(T) == sizeof(double) ? fro2_batched(wv + OFF(q), ni * nc)
-                                                          : (double)fro2_f32(wv + OFF(q), ni * nc);
-          if (msh) mf2[q] = f2; else sf2[q] = f2;
-          if (drop_rule(f2, ni, nc, t)) {
+          bool drop;
+          long long key;
+          if (sizeof(T) == sizeof(double)) {
+            const double f2 = fro2_batched(wv + OFF(q), ni * nc);
+            drop = drop_rule(f2, ni, nc, t);
+            key = norm_key(f2);
+          } else {
+            const float f2 = fro2_f32(wv + OFF(q), ni * nc);
+            drop = drop_rule_f(f2, ni, nc, tf);
+            key = norm_key(f2);
+          }
+          if (msh) mf2[q] = key; else sf2[q] = key;
+          if (drop) {
             if (msh) mst[q] = SL_DEAD; else sstate[q] = SL_DEAD;
           }
         }
@@ -767,13 +876,13 @@ __global__ void __launch_bounds__(IW * 32)
           if (q >= ns) continue;
           const bool isL = IS_L(q), isU = IS_U(q);
           if (!isL && !isU) continue;
-          const double fq = F2(q);
+          const long long fq = F2(q);
           const int cq = COL(q);
           int rank = 0;
           for (int r2 = 0; r2 < ns; ++r2) {
             const bool same = isL ? IS_L(r2) : IS_U(r2);
             if (same) {
-              const double fr = F2(r2);
+              const long long fr = F2(r2);
               if (fr > fq || (fr == fq && COL(r2) < cq)) ++rank;
             }
           }
@@ -801,18 +910,22 @@ __global__ void __launch_bounds__(IW * 32)
       nu = warp_sum_i(nu);
       vl = warp_sum_ll(vl);
       vu = warp_sum_ll(vu);
+      // U rows are reserved in whole 16-byte units so that every row starts
+      // 16-byte aligned (the readers stage them with 16-byte copies)
+      constexpr long long UQ = 16 / (long long)sizeof(T);
+      const long long vu_pad = (vu + UQ - 1) / UQ * UQ;
       if (lane == 0) {
         lb = atomicAdd(P.ctr + 0, (unsigned long long)nl);
         lvv = atomicAdd(P.ctr + 1, (unsigned long long)vl);
         ub = atomicAdd(P.ctr + 2, (unsigned long long)nu);
-        uvv = atomicAdd(P.ctr + 3, (unsigned long long)vu);
+        uvv = atomicAdd(P.ctr + 3, (unsigned long long)vu_pad);
       }
       lb = __shfl_sync(0xffffffffu, lb, 0);
       lvv = __shfl_sync(0xffffffffu, lvv, 0);
       ub = __shfl_sync(0xffffffffu, ub, 0);
       uvv = __shfl_sync(0xffffffffu, uvv, 0);
       fits = (int64_t)(lb + nl) <= P.lbcap && (int64_t)(lvv + vl) <= P.lvcap && (int64_t)(ub + nu) <= P.ubcap &&
-             (int64_t)(uvv + vu) <= P.uvcap;
+             (int64_t)(uvv + vu_pad) <= P.uvcap;
       if (!fits) status_local = DEV_OVERFLOW;
       if (status_local == 0) {
         // GEPP of the diagonal block, in shared memory when it fits.  FP64
@@ -821,12 +934,25 @@ __global__ void __launch_bounds__(IW * 32)
         // block above the threshold, larger than 32, or singular in FP32 is
         // factored again in FP64 and tagged.
         const T* srcd = wv + OFF(dslot);
-        const bool gsh = ni <= SMB;
-        int* pvs = gsh ? sh.pv[warp] : nullptr;
+        // staging: the small-block buffer, else the U-row buffer (free now)
+        // of a shared working row or the value buffer of a global one
+        unsigned char* gb = nullptr;
+        int gcap = 0;
+        if (ni <= SMB) {
+          gb = W.lu, gcap = (int)sizeof(W.lu);
+        } else if (ni <= PVMAX) {
+          if (in_sh)
+            gb = W.ustage, gcap = USTAGE_BYTES;
+          else
+            gb = W.vals, gcap = WS_VBYTES;
+        }
+        const bool gs32 = gb && ni * ni * 4 <= gcap, gs64 = gb && ni * ni * 8 <= gcap;
+        int* pvs = gb ? W.pv : nullptr;
         int32_t* gpiv = piv + A.roff[i];
         bool ok = true, tag64 = true;
         if (sizeof(T) == sizeof(float)) {
-          float* a = gsh ? sh.lu32[warp] : dg32 + dgoff[i];
+          const bool gsh = gs32;
+          float* a = gsh ? reinterpret_cast<float*>(gb) : dg32 + dgoff[i];
           for (int e = lane; e < ni * ni; e += 32) a[e] = (float)srcd[e];
           __syncwarp();
           float norm1 = 0.f;
@@ -838,8 +964,8 @@ __global__ void __launch_bounds__(IW * 32)
           for (int o = 16; o > 0; o >>= 1) norm1 = fmaxf(norm1, __shfl_xor_sync(0xffffffffu, norm1, o));
           __syncwarp();
           if (ni <= 32 && gepp_warp<float>(a, ni, pvs, gpiv, lane)) {
-            const float kappa = norm1 * inv_norm1_f32(a, ni, gsh ? pvs : gpiv, lane);
-            tag64 = !(kappa <= (float)cond_thr);
+            const float kappa = norm1 * inv_norm1_f32(a, ni, pvs ? pvs : gpiv, lane);
+            tag64 = !(kappa <= condf);
             if (!tag64) {
               for (int e = lane; e < ni * ni; e += 32) {
                 if (gsh) dg32[dgoff[i] + e] = a[e];
@@ -850,7 +976,8 @@ __global__ void __launch_bounds__(IW * 32)
           __syncwarp();
         }
         if (tag64) {
-          double* a = gsh ? sh.lu[warp] : dg + dgoff[i];
+          const bool gsh = gs64;
+          double* a = gsh ? reinterpret_cast<double*>(gb) : dg + dgoff[i];
           for (int e = lane; e < ni * ni; e += 32) a[e] = (double)srcd[e];
           __syncwarp();
           ok = gepp_warp<double>(a, ni, pvs, gpiv, lane);
@@ -899,9 +1026,9 @@ __global__ void __launch_bounds__(IW * 32)
           if (lane >= o) incl += v;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        sh.qpre[warp][lane] = incl - sz;
-        sh.qoff[warp][lane] = src;
-        sh.quo[warp][lane] = dstv;
+        W.qpre[lane] = incl - sz;
+        W.qoff[lane] = (int)src;
+        W.wdst[lane] = dstv;
         __syncwarp();
         for (int e0 = lane; e0 < total; e0 += 32 * 8) {
           T v[8];
@@ -914,16 +1041,16 @@ __global__ void __launch_bounds__(IW * 32)
               int lo = 0, hi = 31;
               while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (sh.qpre[warp][mid] <= e)
+                if (W.qpre[mid] <= e)
                   lo = mid;
                 else
                   hi = mid - 1;
               }
               // skip empty entries that share the same prefix
-              while (lo < 31 && sh.qpre[warp][lo + 1] <= e) ++lo;
-              const int local = e - sh.qpre[warp][lo];
-              v[u] = wv[sh.qoff[warp][lo] + local];
-              d8[u] = sh.quo[warp][lo] + local;
+              while (lo < 31 && W.qpre[lo + 1] <= e) ++lo;
+              const int local = e - W.qpre[lo];
+              v[u] = wv[W.qoff[lo] + local];
+              d8[u] = W.wdst[lo] + local;
             }
           }
 #pragma unroll
@@ -953,14 +1080,14 @@ __global__ void __launch_bounds__(IW * 32)
       P.uvlen[i] = 0;
     }
     if (lane == 0) {  // what the row asked for, to size a retry
-      atomicMax(P.ctr + 5, s_nvals[warp]);
-      atomicMax(P.ctr + 6, (unsigned long long)s_nslots[warp]);
+      atomicMax(P.ctr + 5, W.nvals);
+      atomicMax(P.ctr + 6, (unsigned long long)W.nslots);
     }
     // publish the row (its U part and pivot block): every lane's writes are
     // made visible device-wide before lane 0 raises the flag
     __threadfence();
     __syncwarp();
-    if (lane == 0) atomicExch(&P.done[i], 1);
+    if (lane == 0) atomicExch(&P.done[i], status_local == 0 ? 1 : 2);
     // the L part is read by no other row: written after publishing
     if (status_local == 0) {
       write_part(true, lb, lvv, P.lcol, P.lvo, lval);
@@ -970,8 +1097,12 @@ __global__ void __launch_bounds__(IW * 32)
       }
     }
     // clear the hash positions this row used
-    for (int q = lane; q < ns; q += 32)
-      if (hpos[q] >= 0) keys[hpos[q]] = -1;
+    if (in_sh) {
+      for (int q = lane; q < WS_HASH; q += 32) W.keys[q] = -1;
+    } else {
+      for (int q = lane; q < ns; q += 32)
+        if (hpos[q] >= 0) keys[hpos[q]] = -1;
+    }
     __syncwarp();
   }
 }
@@ -1065,18 +1196,18 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   int nsm = 0;
   VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   int64_t lbcap = std::max<int64_t>(4 * A.nnzb, 1024), lvcap = std::max<int64_t>(4 * A.nval, 1 << 16);
-  int64_t ubcap = lbcap, uvcap = lvcap;
+  int64_t ubcap = lbcap, uvcap = lvcap + 2 * p;  // U rows are padded to 16 bytes
   int smax = 1024;
   int64_t vmax = 32768;
-  int blocks_per_sm = 2;
+  const int blocks_per_sm = 2;  // two blocks of IW warps share the shared memory of an SM
   for (int attempt = 0; attempt < 6; ++attempt) {
     const int64_t nblocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * blocks_per_sm, (p + IW - 1) / IW));
     const int64_t nwarps = nblocks * IW;
     int ht = 1;
     while (ht < 2 * smax) ht <<= 1;
     DBuf<int> keys(nwarps * ht, s), hpos(nwarps * smax, s), scol(nwarps * smax, s), sstate(nwarps * smax, s);
-    DBuf<int64_t> soff(nwarps * smax, s);
-    DBuf<double> sf2(nwarps * smax, s);
+    DBuf<int> soff(nwarps * smax, s);
+    DBuf<long long> sf2(nwarps * smax, s);
     DBuf<T> wvals(nwarps * vmax, s);
     Workspace ws{keys.p, hpos.p, scol.p, soff.p, sstate.p, sf2.p, ht, smax, vmax};
     DBuf<int32_t> lcol(lbcap, s), ucol(ubcap, s), lcnt(p, s), ucnt(p, s), done(p, s);

@@ -134,31 +134,11 @@ __global__ void k_rowblk(int64_t nbr, const int64_t* __restrict__ roff, int64_t*
     for (int64_t q = roff[I] + lane; q < roff[I + 1]; q += 32) rowblk[q] = I;
 }
 
-__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Bounded spin until done[k] is set (acquire load: the row's published values
-// are visible afterwards); false when the wait ran out or another row failed
-// (a failed row raises abort before it publishes).
+// Bounded wait until row k is published (wait_flag); false when the wait gave
+// up or row k failed (a failed row publishes 2).
 __device__ __forceinline__ bool wait_row(const int32_t* done, int64_t k, int* abort, unsigned long long limit,
                                          int* st) {
-  if (ld_acquire_gpu(done + k) != 0) return *((volatile int*)abort) == 0;
-  const unsigned long long t_start = global_ns();
-  unsigned ns = 32;
-  while (ld_acquire_gpu(done + k) == 0) {
-    if (*((volatile int*)abort)) return false;
-    if (global_ns() - t_start > limit) {  // limit is a time budget in ns
-      dev_fail(st, DEV_ETIMEOUT);
-      atomicExch(abort, 1);
-      return false;
-    }
-    __nanosleep(ns);  // exponential backoff keeps waiting warps off the L2
-    if (ns < 256) ns <<= 1;
-  }
-  return *((volatile int*)abort) == 0;
+  return wait_flag(done + k, abort, limit, st) == 1;
 }
 
 constexpr int TRI_MR = 16;      // block rows up to this size use the lane-per-block path
@@ -293,7 +273,7 @@ __global__ void __launch_bounds__(SW * 32)
     }
     __threadfence();  // every lane's writes before the flag
     __syncwarp();
-    if (lane == 0) atomicExch(&done[i], 1);
+    if (lane == 0) atomicExch(&done[i], failed ? 2 : 1);
   }
 }
 
