@@ -123,9 +123,35 @@ vb_status vbarms_vbsr_export(vbarms_vbsr A, int32_t* perm, int32_t* bsz, int64_t
 vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil,
                         const vbarms_opts* opt, vbarms_prec* out);
 
+/* Batched factorization of nmat independent matrices (the paper factors one
+ * matrix; batching is an interface of this library).  Matrices that share
+ * (nlev[m], droptol[m], lfil[m]) are factored together as their
+ * block-diagonal union, one launch per phase for the whole group; since
+ * every step of the method stays inside a connected component, each
+ * matrix's factors are those vbarms_factor would give it, operation for
+ * operation.  out[m] receives a handle per matrix; the handles of one group
+ * share the group's factorization (freed with the last of them).  With such
+ * a handle, vbarms_apply and fgmres_solve act on the matrix's own vectors
+ * but apply the whole group's preconditioner (zero outside the matrix's
+ * rows); vbarms_apply_batched applies it once for many matrices;
+ * vbarms_prec_stats / _export / _vector / _kernel_stats describe the group;
+ * vbarms_apply_static rejects it.  A: handles of vbarms_compress or
+ * vbarms_vbsr_from_blocks (inputs, not consumed); a group runs on the stream
+ * of its first matrix after the others' streams are synchronized.  Errors:
+ * as vbarms_factor; VB_EINVAL when a group exceeds 2^31 rows or blocks; on
+ * error no handle is returned.                                              */
+vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev, const double* droptol,
+                                const int* lfil, const vbarms_opts* opt, vbarms_prec* out);
+
 /* y = M^{-1} x (Alg. 2).  x, y: device double[n], original numbering, must
  * not alias.  Runs on the stream of the matrix the handle was built from.   */
 vb_status vbarms_apply(vbarms_prec M, const double* x, double* y);
+
+/* y[m] = M[m]^{-1} x[m] for m < nmat (Alg. 2 per matrix).  Handles of one
+ * batched factorization are served by a single application of the batch's
+ * preconditioner.  x[m], y[m]: device double[n_m], original numbering, not
+ * aliased.                                                                  */
+vb_status vbarms_apply_batched(int nmat, const vbarms_prec* M, const double* const* x, double* const* y);
 
 /* y = M^{-1} x like vbarms_apply, but allocating nothing: for callers that
  * cannot allocate device memory when they apply the preconditioner (while a

@@ -67,6 +67,10 @@ vb_status vbarms_apply_static(vbarms_prec M, const double* x, double* y) {
     vb::set_last_error("vbarms_apply_static: x and y must not alias");
     return VB_EINVAL;
   }
+  if (M->len >= 0) {
+    vb::set_last_error("vbarms_apply_static: a handle of a batched factorization; use vbarms_apply");
+    return VB_EINVAL;
+  }
   try {
     vb::PrecBase& P = *M->impl;
     const size_t need = P.scratch_bytes();

@@ -324,16 +324,120 @@ vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil, const
   return VB_OK;
 }
 
+vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev, const double* droptol,
+                                const int* lfil, const vbarms_opts* opt, vbarms_prec* out) {
+  if (nmat < 0 || (nmat > 0 && (!A || !nlev || !droptol || !lfil || !out)))
+    return set_err(VB_EINVAL, "NULL argument or nmat < 0");
+  for (int m = 0; m < nmat; ++m) {
+    if (!A[m]) return set_err(VB_EINVAL, "NULL matrix handle");
+    if (nlev[m] < 0 || !(droptol[m] >= 0.0)) return set_err(VB_EINVAL, "nlev < 0 or droptol < 0");
+  }
+  vbarms_opts d;
+  vbarms_opts_default(&d);
+  if (!opt) opt = &d;
+  if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
+  std::vector<std::unique_ptr<vbarms_prec_st>> res(nmat);
+  vb_status st = guarded([&] {
+    // matrices with the same (nlev, droptol, lfil) form one batch: one
+    // factorization of their block-diagonal union
+    std::vector<char> taken(nmat, 0);
+    for (int m0 = 0; m0 < nmat; ++m0) {
+      if (taken[m0]) continue;
+      std::vector<int> members;
+      for (int m = m0; m < nmat; ++m)
+        if (!taken[m] && nlev[m] == nlev[m0] && droptol[m] == droptol[m0] && lfil[m] == lfil[m0]) {
+          members.push_back(m);
+          taken[m] = 1;
+        }
+      cudaStream_t s = A[members[0]]->s;
+      for (int m : members)
+        if (A[m]->s != s) VB_CUDA(cudaStreamSynchronize(A[m]->s));
+      vbarms_vbsr_st U;
+      U.s = s;
+      std::vector<const Compressed*> parts;
+      for (int m : members) parts.push_back(&A[m]->C);
+      compressed_union(parts, s, U.C);
+      FactorOpts o{nlev[m0], droptol[m0], lfil[m0], opt->precision, opt->fp64_pivot_cond, opt->ddtol,
+                   opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs};
+      std::shared_ptr<PrecBase> P;
+      if (o.precision == VB_FP64)
+        P = factor_impl<double>(U, o);
+      else
+        P = factor_impl<float>(U, o);
+      int64_t off = 0;
+      for (int m : members) {
+        res[m] = std::make_unique<vbarms_prec_st>();
+        res[m]->impl = P;
+        res[m]->off = off;
+        res[m]->len = A[m]->C.n;
+        off += A[m]->C.n;
+      }
+      VB_CUDA(cudaStreamSynchronize(s));
+    }
+  });
+  if (st != VB_OK) return st;
+  for (int m = 0; m < nmat; ++m) out[m] = res[m].release();
+  return VB_OK;
+}
+
 vb_status vbarms_apply(vbarms_prec M, const double* x, double* y) {
   if (!M || !x || !y) return set_err(VB_EINVAL, "NULL argument");
   if (x == y) return set_err(VB_EINVAL, "x and y must not alias");
   return guarded([&] {
     PrecBase& P = *M->impl;
     DBuf<double> xp(P.n, P.s), yp(P.n, P.s);
-    gather_dev(xp.p, x, P.perm.p, P.n, P.s);
-    P.apply_perm(xp.p, yp.p);
-    scatter_dev(y, yp.p, P.perm.p, P.n, P.s);
+    if (M->len < 0) {
+      gather_dev(xp.p, x, P.perm.p, P.n, P.s);
+      P.apply_perm(xp.p, yp.p);
+      scatter_dev(y, yp.p, P.perm.p, P.n, P.s);
+    } else {
+      // one matrix of a batch: the batch's preconditioner is block diagonal,
+      // so it acts on x placed in the matrix's rows and zero elsewhere
+      DBuf<double> xu(P.n, P.s), yu(P.n, P.s);
+      xu.zero();
+      if (M->len)
+        VB_CUDA(cudaMemcpyAsync(xu.p + M->off, x, M->len * sizeof(double), cudaMemcpyDeviceToDevice, P.s));
+      gather_dev(xp.p, xu.p, P.perm.p, P.n, P.s);
+      P.apply_perm(xp.p, yp.p);
+      scatter_dev(yu.p, yp.p, P.perm.p, P.n, P.s);
+      if (M->len)
+        VB_CUDA(cudaMemcpyAsync(y, yu.p + M->off, M->len * sizeof(double), cudaMemcpyDeviceToDevice, P.s));
+    }
     check_status(P.status.p, P.s, "vbarms_apply");
+  });
+}
+
+vb_status vbarms_apply_batched(int nmat, const vbarms_prec* M, const double* const* x, double* const* y) {
+  if (nmat < 0 || (nmat > 0 && (!M || !x || !y))) return set_err(VB_EINVAL, "NULL argument or nmat < 0");
+  for (int m = 0; m < nmat; ++m) {
+    if (!M[m] || !x[m] || !y[m]) return set_err(VB_EINVAL, "NULL handle or vector");
+    if (x[m] == y[m]) return set_err(VB_EINVAL, "x and y must not alias");
+  }
+  return guarded([&] {
+    // one application per shared factorization: every matrix's x goes to its
+    // rows of the batch vector
+    std::vector<char> done(nmat, 0);
+    for (int m0 = 0; m0 < nmat; ++m0) {
+      if (done[m0]) continue;
+      PrecBase& P = *M[m0]->impl;
+      DBuf<double> xu(P.n, P.s), yu(P.n, P.s), xp(P.n, P.s), yp(P.n, P.s);
+      xu.zero();
+      for (int m = m0; m < nmat; ++m) {
+        if (done[m] || M[m]->impl.get() != &P) continue;
+        const int64_t off = M[m]->len < 0 ? 0 : M[m]->off, len = M[m]->size();
+        if (len) VB_CUDA(cudaMemcpyAsync(xu.p + off, x[m], len * sizeof(double), cudaMemcpyDeviceToDevice, P.s));
+      }
+      gather_dev(xp.p, xu.p, P.perm.p, P.n, P.s);
+      P.apply_perm(xp.p, yp.p);
+      scatter_dev(yu.p, yp.p, P.perm.p, P.n, P.s);
+      for (int m = m0; m < nmat; ++m) {
+        if (done[m] || M[m]->impl.get() != &P) continue;
+        const int64_t off = M[m]->len < 0 ? 0 : M[m]->off, len = M[m]->size();
+        if (len) VB_CUDA(cudaMemcpyAsync(y[m], yu.p + off, len * sizeof(double), cudaMemcpyDeviceToDevice, P.s));
+        done[m] = 1;
+      }
+      check_status(P.status.p, P.s, "vbarms_apply_batched");
+    }
   });
 }
 
@@ -341,7 +445,7 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
                        int maxit, int* iters, double* relres) {
   if (!A || !b || !x) return set_err(VB_EINVAL, "NULL argument");
   if (restart < 1 || maxit < 0 || !(rtol >= 0.0)) return set_err(VB_EINVAL, "restart < 1, maxit < 0 or rtol < 0");
-  if (M && M->impl->n != A->C.n) return set_err(VB_EINVAL, "preconditioner and matrix sizes differ");
+  if (M && M->size() != A->C.n) return set_err(VB_EINVAL, "preconditioner and matrix sizes differ");
   bool conv = false;
   vb_status st = guarded([&] {
     cudaStream_t s = A->s;
@@ -367,6 +471,16 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
     }
     const double target = rtol * bnorm;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m);
+    // one matrix of a batch: the batch preconditioner acts on v placed in the
+    // matrix's rows (its permuted rows are the same contiguous range) and
+    // zero elsewhere
+    const bool view = M && M->len >= 0;
+    DBuf<double> vu, zu;
+    if (view) {
+      vu.alloc(M->impl->n, s);
+      zu.alloc(M->impl->n, s);
+      vu.zero();
+    }
     for (;;) {
       // true residual r = b - A x
       spmv_vb(A->C.A, A->rowblk.p, n, xp.p, w.p, s);
@@ -383,7 +497,11 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
         double* vj = V.p + (size_t)j * n;
         double* zj = Z.p + (size_t)j * n;
         // flexible step: z_j = M^{-1} v_j, w = A z_j, modified Gram-Schmidt
-        if (M)
+        if (view) {
+          if (n) VB_CUDA(cudaMemcpyAsync(vu.p + M->off, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+          M->impl->apply_perm(vu.p, zu.p);
+          if (n) VB_CUDA(cudaMemcpyAsync(zj, zu.p + M->off, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        } else if (M)
           M->impl->apply_perm(vj, zj);
         else
           VB_CUDA(cudaMemcpyAsync(zj, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -16,6 +16,11 @@ struct Compressed {
 void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau,
                      cudaStream_t s, int* dstatus, Compressed& out);
 
+// The block-diagonal union of several compressed matrices, for batched
+// factorization: parts keep their order, their block and scalar rows are
+// numbered consecutively.
+void compressed_union(const std::vector<const Compressed*>& parts, cudaStream_t s, Compressed& out);
+
 // One reduction level (Steps 2-4) on the device.
 template <typename T>
 struct LevelDev {

@@ -97,7 +97,12 @@ void scatter_dev(double* y, const double* x, const int32_t* idx, int64_t n, cuda
 
 }  // namespace vb
 
-// Opaque handle of the C ABI: the factorization of one precision.
+// Opaque handle of the C ABI: a factorization, or one matrix of a batched
+// factorization (then its rows are [off, off + len) of the batch's original
+// numbering and impl is shared by the batch).
 struct vbarms_prec_st {
-  std::unique_ptr<vb::PrecBase> impl;
+  std::shared_ptr<vb::PrecBase> impl;
+  int64_t off = 0;
+  int64_t len = -1;  // -1: the whole factorization
+  int64_t size() const { return len < 0 ? impl->n : len; }
 };

@@ -66,6 +66,8 @@ def lib():
                 "vbarms_vbsr_export": (i32, [vp, vp, vp, vp, vp, vp, vp]),
                 "vbarms_factor": (i32, [vp, i32, d, i32, P(Opts), P(vp)]),
                 "vbarms_apply": (i32, [vp, vp, vp]),
+                "vbarms_factor_batched": (i32, [i32, vp, vp, vp, vp, P(Opts), vp]),
+                "vbarms_apply_batched": (i32, [i32, vp, vp, vp]),
                 "fgmres_solve": (i32, [vp, vp, vp, vp, d, i32, i32, P(i32), P(d)]),
                 "vbarms_prec_stats": (i32, [vp, P(i32), P(d), vp]),
                 "vbarms_prec_export": (i32, [vp, i32, i32, P(i64), P(i64), P(i64), P(i64), vp, vp, vp, vp, vp,
@@ -241,6 +243,33 @@ def vbarms_factor(A: VBSR, nlev: int, droptol: float, lfil: int, precision="fp64
     h = C.c_void_p()
     _check(lib().vbarms_factor(A.h, int(nlev), float(droptol), int(lfil), C.byref(o), C.byref(h)))
     return Prec(h.value, A)
+
+
+def vbarms_factor_batched(As, nlev, droptol, lfil, precision="fp64", **kw) -> list:
+    """Factor several matrices at once (their block-diagonal union, one
+    launch per phase); nlev, droptol, lfil are scalars or per-matrix lists."""
+    nm = len(As)
+    def per(v, t):
+        return [t(x) for x in v] if isinstance(v, (list, tuple, np.ndarray)) else [t(v)] * nm
+    nl = np.asarray(per(nlev, int), np.int32)
+    dt = np.asarray(per(droptol, float), np.float64)
+    lf = np.asarray(per(lfil, int), np.int32)
+    hs = (C.c_void_p * max(nm, 1))(*[A.h for A in As])
+    out = (C.c_void_p * max(nm, 1))()
+    o = make_opts(precision, **kw)
+    _check(lib().vbarms_factor_batched(nm, C.cast(hs, C.c_void_p), _hp(nl), _hp(dt), _hp(lf), C.byref(o),
+                                       C.cast(out, C.c_void_p)))
+    return [Prec(out[m], As[m]) for m in range(nm)]
+
+
+def vbarms_apply_batched(Ms, xs, ys):
+    """ys[m] = Ms[m]^{-1} xs[m]; handles of one batched factorization share one
+    application."""
+    nm = len(Ms)
+    hs = (C.c_void_p * max(nm, 1))(*[M.h for M in Ms])
+    xp = (C.c_void_p * max(nm, 1))(*[_dp(x) for x in xs])
+    yp = (C.c_void_p * max(nm, 1))(*[_dp(y) for y in ys])
+    _check(lib().vbarms_apply_batched(nm, C.cast(hs, C.c_void_p), C.cast(xp, C.c_void_p), C.cast(yp, C.c_void_p)))
 
 
 def vbarms_apply(M: Prec, x, y):
