@@ -195,6 +195,28 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_1508_02219_gb300 import synth
+    if args.workload in synth.BATCHES:
+        # a batch: the oracle on one 10k-node ell=5 matrix of the generator,
+        # scaled by the batch's node count
+        bw = synth.BATCHES[args.workload]
+        total = sum(n for n, _ in synth.batch_shapes(args.workload, args.seed, args.scale))
+        ms = synth.geometric(10000, 5, seed=args.seed)
+        times = []
+        for i in range(args.warmup + args.steps):
+            r = oracle_setup_seconds(ms, dict(tau=bw["tau"], nlev=bw["nlev"], droptol=bw["droptol"],
+                                              lfil=bw["lfil"]))
+            if i >= args.warmup:
+                times.append((r["compress_s"] + r["factor_s"]) * total / 10000)
+        v = statistics.mean(times)
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": args.workload, "scale": args.scale},
+                          "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                                           "sample": f"one 10000-node ell=5 matrix, scaled by {total} nodes"},
+                          "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+              flush=True)
+        return
     m_full_nnz_est = None
     m, w, nodes, full_nodes = cpu_sample(args.workload, args.seed, args.cpu_sample_nodes)
     full = synth.WORKLOADS[args.workload]
@@ -220,10 +242,121 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args):
+    """Batched factorization of a named batch of independent matrices: one
+    step = compress every matrix + one vbarms_factor_batched call (one launch
+    per phase for the whole batch).  No solve is timed in this mode."""
+    import torch
+    from paper_1508_02219_gb300 import build, synth, vbarms as V
+    dist, rank, ws = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    bw = synth.BATCHES[args.workload]
+    mats = synth.make_batch(args.workload, seed=args.seed, scale=args.scale)
+    prec = "fp32" if bw["precision"] == "fp32" else "fp64"
+    dev = torch.device("cuda", local)
+    dmats = [(torch.from_numpy(m.rowptr).to(dev), torch.from_numpy(m.colind).to(dev),
+              torch.from_numpy(m.val).to(dev)) for m in mats]
+    torch.cuda.synchronize()
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        As = [V.vbarms_compress(m.n, rp, ci, vv, bw["tau"]) for m, (rp, ci, vv) in zip(mats, dmats)]
+        e[1].record()
+        Ps = V.vbarms_factor_batched(As, bw["nlev"], bw["droptol"], bw["lfil"], precision=prec)
+        e[2].record()
+        torch.cuda.synchronize()
+        r = dict(compress_s=e[0].elapsed_time(e[1]) / 1e3, factor_s=e[1].elapsed_time(e[2]) / 1e3,
+                 stats=Ps[0].stats(), kstats=Ps[0].kernel_stats(0))
+        del Ps, As
+        return r
+
+    for _ in range(args.warmup):
+        step()
+    barrier(dist)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = V.launch_count()
+    res = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    launches = V.launch_count() - l0
+    clocks = clk.stop()
+    barrier(dist)
+    setup = max_over_ranks(dist, statistics.mean(r["compress_s"] + r["factor_s"] for r in res))
+    kb = sum(r["kstats"]["bytes"] for r in res)
+    kms = sum(r["kstats"]["ms"] for r in res)
+    kl = sum(r["kstats"]["launches"] for r in res)
+    peak, peak_kind = peaks()
+    achieved = kb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": "k_schur_numeric", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": None, "launches_per_step": kl / max(1, len(res)),
+            "algorithmic_bytes_per_launch": kb / max(1, kl), "avg_launch_ms": kms / max(1, kl)}
+    e2e = None
+    if not args.no_e2e:
+        pins = [(torch.from_numpy(m.rowptr).pin_memory(), torch.from_numpy(m.colind).pin_memory(),
+                 torch.from_numpy(m.val).pin_memory()) for m in mats]
+        ets = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            As = [V.vbarms_compress(m.n, a.numpy(), b.numpy(), c.numpy(), bw["tau"])
+                  for m, (a, b, c) in zip(mats, pins)]
+            Ps = V.vbarms_factor_batched(As, bw["nlev"], bw["droptol"], bw["lfil"], precision=prec)
+            st = Ps[0].stats()  # device-to-host read of the batch's result summary
+            ev[1].record()
+            torch.cuda.synchronize()
+            ets.append(ev[0].elapsed_time(ev[1]) / 1e3)
+            del Ps, As
+        e2e = {"value": max_over_ranks(dist, statistics.mean(ets)), "unit": "s",
+               "h2d_bytes_per_step": int(sum(m.rowptr.nbytes + m.colind.nbytes + m.val.nbytes for m in mats)),
+               "d2h_bytes_per_step": 8 * 10,
+               "note": "compress every matrix from pinned host CSR (copied inside the calls) + the batched factor"}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        nodes = 10000
+        ms = synth.geometric(nodes, 5, seed=args.seed)
+        r = oracle_setup_seconds(ms, dict(tau=bw["tau"], nlev=bw["nlev"], droptol=bw["droptol"],
+                                          lfil=bw["lfil"]))
+        total_nodes = sum(m.meta.get("nodes", m.n) for m in mats)
+        cpu = {"value": (r["compress_s"] + r["factor_s"]) * total_nodes / nodes, "unit": "s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"one {nodes}-node ell=5 matrix of the same generator; oracle compress+factor seconds "
+                         f"scaled by the batch's node count {total_nodes}",
+               "host_cpus": os.cpu_count()}
+    if rank == 0:
+        last = res[-1]
+        out = {
+            "metric": METRIC, "value": setup, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": setup * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "scale": args.scale, "matrices": len(mats),
+                       "nodes": [m.meta.get("nodes") for m in mats], "ell": [m.meta.get("ell") for m in mats],
+                       "n": sum(m.n for m in mats), "nnz": sum(m.nnz for m in mats), "tau": bw["tau"],
+                       "nlev": bw["nlev"], "droptol": bw["droptol"], "lfil": bw["lfil"], "factor_precision": prec,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (CSR %.2f GB)" % (sum(m.nnz * 12 + m.n * 8 for m in mats) / 1e9)},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "detail": {"compress_s": statistics.mean(r["compress_s"] for r in res),
+                       "factor_s": statistics.mean(r["factor_s"] for r in res), "levels": last["stats"]["levels"],
+                       "phase_s": last["stats"]["phase_s"], "solve": "not timed in batch mode"},
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    from paper_1508_02219_gb300 import synth as _synth
+    if args.workload in _synth.BATCHES:
+        return run_batch(args)
     import torch
     from paper_1508_02219_gb300 import build, synth, vbarms as V
     dist, rank, ws = dist_init()

@@ -294,3 +294,29 @@ def make_workload(name: str, seed: int = 0, scale: float = 1.0) -> CSR:
     nn = max(2, int(round(w["n_nodes"] * scale)))
     return geometric(nn, w["ell"], seed=seed, dominance=w.get("dominance"),
                      ill_frac=w.get("ill_frac", 0.0))
+
+
+# Named batches of independent matrices (batched factorization): count
+# matrices from the geometric generator, node counts log-uniform in
+# [min_nodes, max_nodes], unknowns per node drawn from ells, matrix k built
+# with seed k.
+BATCHES = {
+    "batch32": dict(count=32, min_nodes=20_000, max_nodes=300_000, ells=(4, 5, 6), tau=0.8, nlev=4,
+                    droptol=1e-4, lfil=30, precision="fp32"),
+}
+
+
+def batch_shapes(name: str, seed: int = 0, scale: float = 1.0) -> list[tuple[int, int]]:
+    """(nodes, ell) of every matrix of a named batch; ``scale`` shrinks the
+    node counts."""
+    b = BATCHES[name]
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(b["min_nodes"]), np.log(b["max_nodes"])
+    nodes = np.exp(rng.uniform(lo, hi, b["count"]))
+    ells = rng.choice(np.asarray(b["ells"]), b["count"])
+    return [(max(2, int(round(n * scale))), int(e)) for n, e in zip(nodes, ells)]
+
+
+def make_batch(name: str, seed: int = 0, scale: float = 1.0) -> list[CSR]:
+    """The matrices of a named batch (matrix k uses seed ``seed + k``)."""
+    return [geometric(n, e, seed=seed + k) for k, (n, e) in enumerate(batch_shapes(name, seed, scale))]
