@@ -642,6 +642,7 @@ constexpr int SN_NG = 32;     // G blocks of one row
 constexpr int SN_NP = 224;    // (G block, W block) pairs of one row
 constexpr int SN_RB = 8;      // S rows updated together
 constexpr int SN_MK = 8;      // W column length held in registers
+constexpr int SN_CU = 16;     // copy loads in flight per lane
 
 struct SnPlan {
   int64_t gvo[SN_NG];     // value offset of G block g
@@ -670,18 +671,60 @@ __device__ __forceinline__ int sn_find(const int32_t* a, int n, int32_t key) {
   return -1;
 }
 
+// One G block's update of the S run with a compile-time pivot size MK = n_Y
+// (any number nr of S rows): lane per W-row column, the column of W in
+// registers, k ascending per element.
+template <typename T, int MK>
+__device__ __forceinline__ void sn_update_m(const SnPlan& P, int t0, int cA, int cB, int nr, int lane,
+                                            const T* gp, const T* __restrict__ Wv, T* run) {
+  int t = t0;
+  for (int c = cA + lane; c < cB; c += 32) {
+    while (P.cpre[t + 1] <= c) ++t;
+    const int j = c - P.cpre[t];
+    const int ns = P.cpre[t + 1] - P.cpre[t];
+    const T* __restrict__ wv = Wv + P.pwv[t] + j;
+    T* dst = run + P.soff[P.pq[t]] + j;
+    T wr[MK];
+#pragma unroll
+    for (int k = 0; k < MK; ++k) wr[k] = wv[k * ns];
+    int u = 0;
+    for (; u + 2 <= nr; u += 2) {
+      T a0 = dst[u * ns], a1 = dst[(u + 1) * ns];
+      const T* g0 = gp + u * MK;
+#pragma unroll
+      for (int k = 0; k < MK; ++k) {
+        a0 = msub<T>(a0, g0[k], wr[k]);
+        a1 = msub<T>(a1, g0[MK + k], wr[k]);
+      }
+      dst[u * ns] = a0;
+      dst[(u + 1) * ns] = a1;
+    }
+    if (u < nr) {
+      T a0 = dst[u * ns];
+      const T* g0 = gp + u * MK;
+#pragma unroll
+      for (int k = 0; k < MK; ++k) a0 = msub<T>(a0, g0[k], wr[k]);
+      dst[u * ns] = a0;
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SN_WARPS * 32)
     k_schur_numeric(VBView<T> C, VBView<T> G, VBView<T> W, VBView<T> S, int32_t* __restrict__ slow,
-                    int* __restrict__ nslow, int* st) {
+                    int* __restrict__ nslow, unsigned long long* __restrict__ rowctr, int* st) {
   extern __shared__ __align__(16) unsigned char sn_raw[];
   const int lane = threadIdx.x & 31;
   SnPlan& P = reinterpret_cast<SnPlan*>(sn_raw)[threadIdx.x >> 5];
   const T* __restrict__ Cv = C.val;
   const T* __restrict__ Gv = G.val;
   const T* __restrict__ Wv = W.val;
-  for (int64_t r = (int64_t)blockIdx.x * SN_WARPS + (threadIdx.x >> 5); r < S.nbr;
-       r += (int64_t)gridDim.x * SN_WARPS) {
+  for (;;) {
+    // rows are handed out one at a time to whichever warp is free
+    long long rr = 0;
+    if (lane == 0) rr = (long long)atomicAdd(rowctr, 1ULL);
+    const int64_t r = __shfl_sync(0xffffffffu, rr, 0);
+    if (r >= S.nbr) break;
     __syncwarp();
     const int64_t s0 = S.bptr[r], s1 = S.bptr[r + 1];
     const int64_t c0 = C.bptr[r], c1 = C.bptr[r + 1];
@@ -763,25 +806,30 @@ __global__ void __launch_bounds__(SN_WARPS * 32)
     }
     if (lane == 0) P.cpre[0] = 0;
     __syncwarp();
-    // 2. C values (zero for fill) into the run
+    // 2. C values (zero for fill) into the run, SN_CU loads in flight per lane
     T* __restrict__ run = S.val + vbase;
     const int vlen = P.soff[nq];
     {
-      int q = 0;
-      for (int e0 = 0; e0 < vlen; e0 += 128) {
-        T v[4];
+      // the lane's current block: its start, end and C source in registers
+      int q = 0, qb = 0, qe = P.soff[1], src = P.csrc[0];
+      for (int e0 = 0; e0 < vlen; e0 += 32 * SN_CU) {
+        T v[SN_CU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < SN_CU; ++u) {
           const int e = e0 + u * 32 + lane;
           v[u] = (T)0;
           if (e < vlen) {
-            while (P.soff[q + 1] <= e) ++q;
-            const int src = P.csrc[q];
-            if (src >= 0) v[u] = Cv[cbase + src + (e - P.soff[q])];
+            while (qe <= e) {
+              ++q;
+              qb = qe;
+              qe = P.soff[q + 1];
+              src = P.csrc[q];
+            }
+            if (src >= 0) v[u] = Cv[cbase + src + (e - qb)];
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < SN_CU; ++u) {
           const int e = e0 + u * 32 + lane;
           if (e < vlen) run[e] = v[u];
         }
@@ -795,6 +843,23 @@ __global__ void __launch_bounds__(SN_WARPS * 32)
       const int m = P.gm[g];
       const T* __restrict__ gp = Gv + P.gvo[g];
       const int cB = P.cpre[t1];
+      // compile-time pivot sizes for the blocks of 4-6 unknowns per node
+      // and their merges
+      if (m >= 4 && m <= 6) {
+        if (m == 6)
+          sn_update_m<T, 6>(P, t0, P.cpre[t0], cB, nr, lane, gp, Wv, run);
+        else if (m == 5)
+          sn_update_m<T, 5>(P, t0, P.cpre[t0], cB, nr, lane, gp, Wv, run);
+        else
+          sn_update_m<T, 4>(P, t0, P.cpre[t0], cB, nr, lane, gp, Wv, run);
+        __syncwarp();
+        continue;
+      }
+      if (m == 12) {
+        sn_update_m<T, 12>(P, t0, P.cpre[t0], cB, nr, lane, gp, Wv, run);
+        __syncwarp();
+        continue;
+      }
       int t = t0;
       for (int c = P.cpre[t0] + lane; c < cB; c += 32) {
         while (P.cpre[t + 1] <= c) ++t;
@@ -1181,8 +1246,14 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
     }
     const size_t psmem = (size_t)SN_WARPS * sizeof(SnPlan);
     VB_CUDA(cudaFuncSetAttribute(k_schur_numeric<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
-    launch(k_schur_numeric<T>, grid_for(nC, SN_WARPS, 152LL * 16), SN_WARPS * 32, psmem, s, C.view(), G.view(),
-           W.view(), Sf.view(), slow.p, nslow.p, dst);
+    int dev = 0, nsm = 0, per_sm = 0;
+    VB_CUDA(cudaGetDevice(&dev));
+    VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    VB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_schur_numeric<T>, SN_WARPS * 32, psmem));
+    DBuf<unsigned long long> rowctr(1, s);
+    rowctr.zero();
+    launch(k_schur_numeric<T>, grid_for(nC, SN_WARPS, (int64_t)nsm * std::max(per_sm, 1)), SN_WARPS * 32, psmem, s,
+           C.view(), G.view(), W.view(), Sf.view(), slow.p, nslow.p, rowctr.p, dst);
     VB_LAUNCH_CHECK();
     launch(k_schur_numeric_rows<T>, 152u * 4, LW * 32, 0, s, C.view(), G.view(), W.view(), Sf.view(), slow.p,
            nslow.p, dst);
