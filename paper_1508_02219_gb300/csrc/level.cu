@@ -45,40 +45,83 @@ __device__ __forceinline__ float msub<float>(float acc, float a, float b) {
 }
 
 // ---- A5: Step 2 scaling ----------------------------------------------------
+// |x| maxima: exact in any precision and any order.  FP64 values are
+// compared by their bit patterns (integer maxima, no FP64 pipe); FP32 ones by
+// fmaxf.
+__device__ __forceinline__ double absmax_acc(double m, double x) {
+  const long long a = __double_as_longlong(m), b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  return __longlong_as_double(a > b ? a : b);
+}
+__device__ __forceinline__ float absmax_acc(float m, float x) { return fmaxf(m, fabsf(x)); }
+
+// Row maxima, one warp per block row: lane (a, g) takes scalar row a of the
+// blocks g, g + G, ... of the block row (G = 32 / m groups), then the groups
+// combine by shuffles.  Rows of more than 16 scalars use lanes over rows.
 template <typename TA>
 __global__ void k_rowmax(VBView<TA> A, double* __restrict__ r) {
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
   for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < A.nbr; I += (int64_t)gridDim.x * wpb) {
     const int m = A.rsz[I];
-    for (int a = lane; a < m; a += 32) {
-      double mx = 0.0;
-      for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
-        const int nc = A.csz[A.bcol[b]];
-        const TA* v = A.val + A.voff[b] + (int64_t)a * nc;
-        for (int j = 0; j < nc; ++j) mx = fmax(mx, fabs((double)v[j]));
+    const int64_t b0 = A.bptr[I], b1 = A.bptr[I + 1];
+    if (m <= 16) {
+      const int G = 32 / m, a = lane % m, g = lane / m;
+      TA mx = (TA)0;
+      if (g < G)
+        for (int64_t b = b0 + g; b < b1; b += G) {
+          const int nc = A.csz[A.bcol[b]];
+          const TA* v = A.val + A.voff[b] + (int64_t)a * nc;
+          for (int j = 0; j < nc; ++j) mx = absmax_acc(mx, v[j]);
+        }
+      for (int k = 1; k < G; ++k) {
+        const TA o = __shfl_sync(0xffffffffu, mx, (a + k * m) & 31);
+        if (lane < m) mx = absmax_acc(mx, o);
       }
-      r[A.roff[I] + a] = mx > 0.0 ? __ddiv_rn(1.0, mx) : 1.0;
+      if (lane < m) {
+        const double d = (double)mx;
+        r[A.roff[I] + a] = d > 0.0 ? __ddiv_rn(1.0, d) : 1.0;
+      }
+    } else {
+      for (int a = lane; a < m; a += 32) {
+        TA mx = (TA)0;
+        for (int64_t b = b0; b < b1; ++b) {
+          const int nc = A.csz[A.bcol[b]];
+          const TA* v = A.val + A.voff[b] + (int64_t)a * nc;
+          for (int j = 0; j < nc; ++j) mx = absmax_acc(mx, v[j]);
+        }
+        const double d = (double)mx;
+        r[A.roff[I] + a] = d > 0.0 ? __ddiv_rn(1.0, d) : 1.0;
+      }
     }
   }
 }
 
+// Products r_a * a_aj in the value type's arithmetic: FP64 (exact IEEE
+// products, the oracle's) for FP64 values, FP32 for the FP32 levels of the
+// mixed factor.
+__device__ __forceinline__ double rprod(double r, double v) { return __dmul_rn(r, v); }
+__device__ __forceinline__ float rprod(double r, float v) { return __fmul_rn((float)r, v); }
+
+// Column maxima of the row-scaled matrix, one warp per block row: lane
+// (g, j) takes column j (then j + 8, ...) of the blocks g, g + 4, ...; one
+// atomicMax per block column on the bit pattern of the non-negative maximum.
 template <typename TA>
 __global__ void k_colmax(VBView<TA> A, const double* __restrict__ r, unsigned long long* __restrict__ cmax) {
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
+  const int g = lane >> 3, j0 = lane & 7;
   for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < A.nbr; I += (int64_t)gridDim.x * wpb) {
     const int m = A.rsz[I];
     const int64_t r0 = A.roff[I];
-    for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
+    for (int64_t b = A.bptr[I] + g; b < A.bptr[I + 1]; b += 4) {
       const int J = A.bcol[b];
       const int nc = A.csz[J];
       const int64_t c0 = A.coff[J];
       const TA* v = A.val + A.voff[b];
-      for (int e = lane; e < m * nc; e += 32) {
-        const int a = e / nc, j = e - a * nc;
-        const double x = fabs(__dmul_rn(r[r0 + a], (double)v[e]));
-        atomicMax(&cmax[c0 + j], (unsigned long long)__double_as_longlong(x));
+      for (int j = j0; j < nc; j += 8) {
+        TA mx = (TA)0;
+        for (int a = 0; a < m; ++a) mx = absmax_acc(mx, rprod(r[r0 + a], v[a * nc + j]));
+        atomicMax(&cmax[c0 + j], (unsigned long long)__double_as_longlong((double)mx));
       }
     }
   }
@@ -91,45 +134,77 @@ __global__ void k_colinv(int64_t n, const unsigned long long* __restrict__ cmax,
   }
 }
 
+__device__ __forceinline__ double rcprod(double r, double v, double c) { return __dmul_rn(__dmul_rn(r, v), c); }
+__device__ __forceinline__ float rcprod(double r, float v, double c) {
+  return __fmul_rn(__fmul_rn((float)r, v), (float)c);
+}
+
+// a_ij <- r_i a_ij c_j, one warp per block row, lanes (g, j) as in k_colmax.
 template <typename TA>
 __global__ void k_apply_scale(VBView<TA> A, const double* __restrict__ r, const double* __restrict__ c) {
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
+  const int g = lane >> 3, j0 = lane & 7;
   for (int64_t I = blockIdx.x * wpb + (threadIdx.x >> 5); I < A.nbr; I += (int64_t)gridDim.x * wpb) {
     const int m = A.rsz[I];
     const int64_t r0 = A.roff[I];
-    for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
+    for (int64_t b = A.bptr[I] + g; b < A.bptr[I + 1]; b += 4) {
       const int J = A.bcol[b];
       const int nc = A.csz[J];
       const int64_t c0 = A.coff[J];
       TA* v = A.val + A.voff[b];
-      for (int e = lane; e < m * nc; e += 32) {
-        const int a = e / nc, j = e - a * nc;
-        v[e] = (TA)__dmul_rn(__dmul_rn(r[r0 + a], (double)v[e]), c[c0 + j]);
+      for (int j = j0; j < nc; j += 8) {
+        const double cj = c[c0 + j];
+        for (int a = 0; a < m; ++a) v[a * nc + j] = (TA)rcprod(r[r0 + a], v[a * nc + j], cj);
       }
     }
   }
 }
 
 // ---- A6: Step 3 ----------------------------------------------------------
+// Weights, one warp per block row: lane k forms ||A_Yb||_F of the row's
+// blocks k, k + 32, ... (row-major sum of squares, the oracle's order for
+// FP64 values), then lane 0 adds the norms in block order.
+__device__ __forceinline__ double sq_acc(double s, double x) { return __dadd_rn(s, __dmul_rn(x, x)); }
+__device__ __forceinline__ float sq_acc(float s, float x) { return __fmaf_rn(x, x, s); }
+__device__ __forceinline__ double sqrt_rn(double x) { return __dsqrt_rn(x); }
+__device__ __forceinline__ float sqrt_rn(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
 template <typename TA>
 __global__ void k_weights(VBView<TA> A, double* __restrict__ w) {
-  for (int64_t Y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; Y < A.nbr; Y += (int64_t)gridDim.x * blockDim.x) {
-    double dsum = 0.0, diag = 0.0;
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t Y = blockIdx.x * wpb + (threadIdx.x >> 5); Y < A.nbr; Y += (int64_t)gridDim.x * wpb) {
     const int m = A.rsz[Y];
-    for (int64_t b = A.bptr[Y]; b < A.bptr[Y + 1]; ++b) {
-      const int nc = A.csz[A.bcol[b]];
-      const TA* v = A.val + A.voff[b];
-      double s = 0.0;
-      for (int e = 0; e < m * nc; ++e) {
-        const double x = (double)v[e];
-        s = __dadd_rn(s, __dmul_rn(x, x));
+    const int64_t b0 = A.bptr[Y], b1 = A.bptr[Y + 1];
+    TA dsum = (TA)0, diag = (TA)0;
+    for (int64_t c0 = b0; c0 < b1; c0 += 32) {
+      const int64_t b = c0 + lane;
+      TA f = (TA)0;
+      bool isdiag = false;
+      if (b < b1) {
+        const int J = A.bcol[b];
+        const int nc = A.csz[J];
+        const TA* v = A.val + A.voff[b];
+        TA s = (TA)0;
+        for (int e = 0; e < m * nc; ++e) s = sq_acc(s, v[e]);
+        f = sqrt_rn(s);
+        isdiag = J == Y;
       }
-      const double f = __dsqrt_rn(s);
-      dsum = __dadd_rn(dsum, f);
-      if (A.bcol[b] == Y) diag = f;
+      const int cnt = b1 - c0 < 32 ? (int)(b1 - c0) : 32;
+      for (int k = 0; k < cnt; ++k) {
+        const TA fk = __shfl_sync(0xffffffffu, f, k);
+        dsum = add_rn(dsum, fk);
+      }
+      const unsigned dm = __ballot_sync(0xffffffffu, isdiag);
+      if (dm) diag = __shfl_sync(0xffffffffu, f, __ffs(dm) - 1);
     }
-    w[Y] = dsum > 0.0 ? __ddiv_rn(diag, dsum) : 0.0;
+    if (lane == 0) {
+      const double ds = (double)dsum, dg = (double)diag;
+      w[Y] = ds > 0.0 ? __ddiv_rn(dg, ds) : 0.0;
+    }
   }
 }
 
@@ -1019,7 +1094,7 @@ int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t
   newpos.alloc(p, s);
   if (!p) return 0;
   const unsigned g = grid_for(p, 256);
-  launch(k_weights<TA>, g, 256, 0, s, A.view(), w.p);
+  launch(k_weights<TA>, grid_for(p, LW), LW * 32, 0, s, A.view(), w.p);
   VB_LAUNCH_CHECK();
   DBuf<int32_t> tcnt(p, s), trow(A.nnzb, s), pending(p, s), state(p, s);
   DBuf<int64_t> tptr(p + 1, s);
