@@ -4,6 +4,7 @@
 //
 // Vectors are FP64.  FP64 factors are applied in the oracle's operation
 // order; FP32 factors are promoted to FP64 as they are read.
+#include <type_traits>
 #include "prec.cuh"
 #include "vbsr_ops.cuh"
 
@@ -63,6 +64,30 @@ __device__ void pivot_backward(const TL* lu, int m, double* u) {
   }
 }
 
+// u <- U^{-1} L^{-1} P u for an FP32 pivot block in FP32 arithmetic (the
+// mixed factor applies its FP32 factors in FP32; vectors stay FP64).  m <= 32.
+__device__ void pivot_solve_f32(const float* lu, const int32_t* pv, int m, double* u) {
+  float x[32];
+  for (int k = 0; k < m; ++k) x[k] = (float)u[k];
+  for (int k = 0; k < m; ++k)
+    if (pv[k] != k) {
+      const float t = x[k];
+      x[k] = x[pv[k]];
+      x[pv[k]] = t;
+    }
+  for (int i = 1; i < m; ++i) {
+    float s = x[i];
+    for (int k = 0; k < i; ++k) s = __fmaf_rn(-lu[i * m + k], x[k], s);
+    x[i] = s;
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    float s = x[i];
+    for (int k = i + 1; k < m; ++k) s = __fmaf_rn(-lu[i * m + k], x[k], s);
+    x[i] = __fdiv_rn(s, lu[i * m + i]);
+  }
+  for (int k = 0; k < m; ++k) u[k] = (double)x[k];
+}
+
 __global__ void k_pivot_fwd(int64_t nD, const int32_t* __restrict__ sz, const int64_t* __restrict__ roff,
                             const int64_t* __restrict__ voff, const double* __restrict__ lu64,
                             const float* __restrict__ lu32, const int32_t* __restrict__ ptag,
@@ -97,6 +122,19 @@ __global__ void k_bsr_sub(VBView<T> M, const int64_t* __restrict__ rowblk, int64
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nrows; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t I = rowblk[q];
     const int a = (int)(q - M.roff[I]);
+    if (sizeof(T) == sizeof(float)) {
+      // FP32 factor blocks: products summed in FP32, the result in FP64
+      float acc = 0.f;
+      for (int64_t b = M.bptr[I]; b < M.bptr[I + 1]; ++b) {
+        const int32_t J = M.bcol[b];
+        const int nc = M.csz[J];
+        const T* v = M.val + M.voff[b] + (int64_t)a * nc;
+        const double* xj = x + M.coff[J];
+        for (int k = 0; k < nc; ++k) acc = __fmaf_rn((float)v[k], (float)xj[k], acc);
+      }
+      y[q] = y[q] - (double)acc;
+      continue;
+    }
     double s = y[q];
     for (int64_t b = M.bptr[I]; b < M.bptr[I + 1]; ++b) {
       const int32_t J = M.bcol[b];
@@ -192,7 +230,10 @@ __global__ void __launch_bounds__(SW * 32)
       }
       const double r_self = lane < ni ? rhs[r0 + lane] : 0.0;
       __syncwarp();
-      double part[TRI_MR];
+      // FP32 factors are applied in FP32 (the products and their sums), FP64
+      // ones in FP64; the row's result is formed in FP64
+      using TA = typename std::conditional<sizeof(T) == sizeof(float), float, double>::type;
+      TA part[TRI_MR];
 #pragma unroll
       for (int a = 0; a < TRI_MR; ++a) part[a] = 0.0;
       for (int64_t b = b0 + lane; b < b1; b += 32) {
@@ -205,15 +246,15 @@ __global__ void __launch_bounds__(SW * 32)
         }
         const double* xk = out + M.coff[k];
         for (int q0 = 0; q0 < nk; q0 += TRI_XQ) {
-          double xq[TRI_XQ];
+          TA xq[TRI_XQ];
 #pragma unroll
-          for (int q = 0; q < TRI_XQ; ++q) xq[q] = q0 + q < nk ? __ldcg(xk + q0 + q) : 0.0;
+          for (int q = 0; q < TRI_XQ; ++q) xq[q] = q0 + q < nk ? (TA)__ldcg(xk + q0 + q) : (TA)0;
 #pragma unroll
           for (int q = 0; q < TRI_XQ; ++q) {
             if (q0 + q >= nk) break;
 #pragma unroll
             for (int a = 0; a < TRI_MR; ++a)
-              if (a < ni) part[a] = fma(ld(v + a * nk + q0 + q), xq[q], part[a]);
+              if (a < ni) part[a] = fma((TA)v[a * nk + q0 + q], xq[q], part[a]);
           }
         }
       }
@@ -260,7 +301,9 @@ __global__ void __launch_bounds__(SW * 32)
     __syncwarp();
     if (!failed) {
       if (BWD && lane == 0) {
-        if (lu32 && !ptag[i]) {
+        if (lu32 && !ptag[i] && ni <= 32) {
+          pivot_solve_f32(lu32 + dgoff[i], piv + r0, ni, sv);
+        } else if (lu32 && !ptag[i]) {
           pivot_forward<float>(lu32 + dgoff[i], piv + r0, ni, sv);
           pivot_backward<float>(lu32 + dgoff[i], ni, sv);
         } else {
