@@ -1195,8 +1195,10 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   VB_CUDA(cudaGetDevice(&dev));
   int nsm = 0;
   VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  int64_t lbcap = std::max<int64_t>(4 * A.nnzb, 1024), lvcap = std::max<int64_t>(4 * A.nval, 1 << 16);
-  int64_t ubcap = lbcap, uvcap = lvcap + 2 * p;  // U rows are padded to 16 bytes
+  // L and U each hold about half of the last-level matrix on the configured
+  // workloads; the pools start at its full size and grow on overflow (retry)
+  int64_t lbcap = std::max<int64_t>(A.nnzb, 1024), lvcap = std::max<int64_t>(A.nval, 1 << 16);
+  int64_t ubcap = lbcap, uvcap = lvcap + 4 * p;  // U rows are padded to 16 bytes
   int smax = 1024;
   int64_t vmax = 32768;
   const int blocks_per_sm = 2;  // two blocks of IW warps share the shared memory of an SM

@@ -696,6 +696,27 @@ __global__ void __launch_bounds__(LW * 32)
   }
 }
 
+// Upper bound on the distinct columns of the listed S rows (C row plus the
+// W rows reached from G), to size the global hash tables of those rows.
+__global__ void k_schur_row_bound(int nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ Cbptr,
+                                  const int64_t* __restrict__ Gbptr, const int32_t* __restrict__ Gbcol,
+                                  const int64_t* __restrict__ Wbptr, int64_t ncols,
+                                  unsigned long long* __restrict__ maxb) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t t = blockIdx.x * wpb + (threadIdx.x >> 5); t < nrows; t += (int64_t)gridDim.x * wpb) {
+    const int32_t r = rows[t];
+    long long b = 0;
+    for (int64_t g = Gbptr[r] + lane; g < Gbptr[r + 1]; g += 32) {
+      const int32_t Y = Gbcol[g];
+      b += Wbptr[Y + 1] - Wbptr[Y];
+    }
+    b = warp_sum_ll(b) + (Cbptr[r + 1] - Cbptr[r]);
+    if (b > ncols) b = ncols;
+    if (lane == 0) atomicMax(maxb, (unsigned long long)b);
+  }
+}
+
 // Numeric phase.  One warp per block row r of S.  The row's values are one
 // contiguous run of S (blocks ascending, each row-major), and S has C's row
 // partition, so the warp
@@ -1267,8 +1288,15 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
   int64_t hb = 0;
   DBuf<int> gtab;
   if (nh > 0) {
+    // tables sized by the heaviest listed row, not by the matrix width
+    DBuf<unsigned long long> bound(1, s);
+    bound.zero();
+    launch(k_schur_row_bound, grid_for(nh, LW), LW * 32, 0, s, nh, heavy.p, C.bptr.p, G.bptr.p, G.bcol.p, W.bptr.p,
+           nC, bound.p);
+    VB_LAUNCH_CHECK();
+    const int64_t maxb = (int64_t)d2h(bound.p, s);
     gcap = 1024;
-    while ((int64_t)gcap < 2 * nC + 64) gcap <<= 1;
+    while ((int64_t)gcap < 2 * maxb + 64) gcap <<= 1;
     int64_t warps = std::max<int64_t>(1, (256LL << 20) / ((int64_t)gcap * 4));
     warps = std::min<int64_t>(warps, nh);
     hb = (warps + LW - 1) / LW;

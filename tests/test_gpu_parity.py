@@ -83,6 +83,9 @@ FACTOR_CASES = {
     "geo_lfil": (lambda: synth.geometric(2000, 5, seed=8), 0.8, 2, 1e-3, 6),
     "geo_pivoting": (lambda: synth.geometric(1500, 6, seed=9, dominance=1.5, ill_frac=0.01), 0.8, 3, 1e-4, 30),
     "geo_ilut_only": (lambda: synth.geometric(800, 3, seed=10), 0.75, 0, 1e-3, 10),
+    # the largest configuration's regime at small size: tau = 0.9 fragments the
+    # node blocks (block sizes 1-12), 5 levels, t = 1e-5, lfil 40
+    "geo_tau09_l5": (lambda: synth.make_workload("geo2m_l6", seed=3, scale=0.002), 0.9, 5, 1e-5, 40),
 }
 
 
@@ -97,7 +100,7 @@ def test_fp64_factor_bit_exact(case):
     compare_factor(P, Po)
 
 
-@pytest.mark.parametrize("case", ["grid10_l5", "geo_3lev", "geo_pivoting"])
+@pytest.mark.parametrize("case", ["grid10_l5", "geo_3lev", "geo_pivoting", "geo_tau09_l5"])
 def test_apply_and_fgmres_fp64(case):
     gen, tau, nlev, t, lfil = FACTOR_CASES[case]
     m = gen()
