@@ -211,7 +211,7 @@ __global__ void k_pending(int64_t n, const int64_t* __restrict__ simstart, const
     for (int64_t q = lane; q < simcnt[i]; q += 32) atomicAdd(&pending[simbuf[simstart[i] + q]], 1);
 }
 
-// state: 0 undecided, 1 leader, 2 claimed this round, 3 claimed.
+// state: 0 undecided, 1 leader, 2 claimed in the current MIS round, 3 claimed.
 __global__ void k_round_a(int64_t n, const int64_t* __restrict__ simstart, const int32_t* __restrict__ simcnt,
                           const int32_t* __restrict__ simbuf, const int32_t* __restrict__ pending,
                           int32_t* __restrict__ state, unsigned long long* remaining) {

@@ -231,7 +231,7 @@ __device__ __forceinline__ bool better(const double* w, int64_t u, int64_t v) {
   return w[u] > w[v] || (w[u] == w[v] && u < v);
 }
 
-// state: 0 undecided, 1 in D, 2 out (this round), 3 out.
+// state: 0 undecided, 1 in D, 2 out (in the current MIS round), 3 out.
 __global__ void k_is_init(int64_t p, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
                           const int64_t* __restrict__ tptr, const int32_t* __restrict__ trow,
                           const double* __restrict__ w, double ddtol, int32_t* __restrict__ pending,
