@@ -64,9 +64,14 @@ __global__ void k_col_fill(int64_t n, const int64_t* __restrict__ rowptr, const 
 }
 
 // ---- A2 ------------------------------------------------------------------
-// One warp per row i.  GLOBAL = false: table in shared memory (SIM_CAP);
-// rows whose candidate set outgrows SIM_LIMIT are deferred to a list.
-// GLOBAL = true: table in global memory (gcap per warp), rows from the list.
+// One warp per row i.  The row's columns are taken 32 at a time: one round of
+// loads gives their extents in the CSC, then the lanes walk the chunk's
+// (column, row j) entries flattened, eight loads in flight per lane, and
+// count |P_i n P_j| for j > i in a hash table (atomic inserts and counts, so
+// entries of different columns may meet in one pass).  GLOBAL = false: table
+// in shared memory (SIM_CAP); rows whose candidate set outgrows SIM_LIMIT are
+// deferred to a list.  GLOBAL = true: table in global memory (gcap per warp),
+// rows from the list.
 template <bool GLOBAL>
 __global__ void __launch_bounds__(CW * 32)
     k_similar(int64_t nrows, const int32_t* __restrict__ rows, const int64_t* __restrict__ rowptr,
@@ -77,6 +82,8 @@ __global__ void __launch_bounds__(CW * 32)
               int32_t* __restrict__ heavy, int* nheavy, int* st) {
   extern __shared__ int smem[];
   __shared__ int nfresh[CW];
+  __shared__ int64_t ccs[CW][32];  // CSC start of each column of the chunk
+  __shared__ int cpre[CW][33];     // entry prefix over the chunk's columns
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int *keys, *cnt;
   uint32_t cap;
@@ -109,27 +116,55 @@ __global__ void __launch_bounds__(CW * 32)
     if (lane == 0) nfresh[warp] = 0;
     __syncwarp();
     bool over = false;
-    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      const int32_t c = colind[p];
+    const int64_t pe = rowptr[i + 1];
+    for (int64_t p0 = rowptr[i]; p0 < pe && !over; p0 += 32) {
+      int64_t cs = 0, ce = 0;
+      if (p0 + lane < pe) {
+        const int32_t c = colind[p0 + lane];
+        cs = cptr[c];
+        ce = cptr[c + 1];
+      }
+      const int lc = (int)(ce - cs);
+      int incl = lc;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      ccs[warp][lane] = cs;
+      cpre[warp][lane] = incl - lc;
+      if (lane == 31) cpre[warp][32] = tot;
+      __syncwarp();
       bool full = false;
-      for (int64_t q = cptr[c] + lane; q < cptr[c + 1]; q += 32) {
-        const int32_t j = crow[q];
-        if (j <= i) continue;
-        bool fresh;
-        const int slot = hset_insert(keys, cap - 1, j, &fresh);
-        if (slot < 0) {
-          full = true;
-          break;
+      int tc = 0;  // column of the lane's current entry (entries only move forward)
+      for (int e0 = lane; e0 < tot && !full; e0 += 32 * 8) {
+        int32_t jv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + 32 * u;
+          jv[u] = -1;
+          if (e < tot) {
+            while (cpre[warp][tc + 1] <= e) ++tc;
+            jv[u] = crow[ccs[warp][tc] + (e - cpre[warp][tc])];
+          }
         }
-        atomicAdd(&cnt[slot], 1);
-        if (fresh) atomicAdd(&nfresh[warp], 1);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int32_t j = jv[u];
+          if (j <= i || full) continue;
+          bool fresh;
+          const int slot = hset_insert(keys, cap - 1, j, &fresh);
+          if (slot < 0) {
+            full = true;
+            continue;
+          }
+          atomicAdd(&cnt[slot], 1);
+          if (fresh) atomicAdd(&nfresh[warp], 1);
+        }
       }
       __syncwarp();
       const int nf = *((volatile int*)&nfresh[warp]);
-      if (__any_sync(0xffffffffu, full) || nf > limit) {
-        over = true;
-        break;
-      }
+      if (__any_sync(0xffffffffu, full) || nf > limit) over = true;
     }
     if (over) {
       if (lane == 0) {
