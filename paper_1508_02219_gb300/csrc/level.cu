@@ -530,13 +530,12 @@ __device__ __forceinline__ double fro2_d(const double* v, int n) {
   for (int e = 0; e < n; ++e) s = __dadd_rn(s, __dmul_rn(v[e], v[e]));
   return s;
 }
+// FP32 blocks (the FP32 levels of the mixed factor): the sum of squares in
+// FP32, returned as a double
 __device__ __forceinline__ double fro2_d(const float* v, int n) {
-  double s = 0.0;
-  for (int e = 0; e < n; ++e) {
-    const double x = (double)v[e];
-    s = __dadd_rn(s, __dmul_rn(x, x));
-  }
-  return s;
+  float s = 0.f;
+  for (int e = 0; e < n; ++e) s = __fmaf_rn(v[e], v[e], s);
+  return (double)s;
 }
 
 __device__ __forceinline__ bool drop_rule(double f2, int m, int n, double t) {
@@ -751,6 +750,7 @@ struct SnPlan {
   int32_t gm[SN_NG];      // n_Y
   int32_t pq[SN_NP];      // S block of pair t
   int32_t cpre[SN_NP + 1];  // W-row column prefix over the pairs
+  unsigned long long fl;     // flops of the rows this warp did (2 n_r n_Y n_s per pair)
 };
 
 __device__ __forceinline__ int sn_find(const int32_t* a, int n, int32_t key) {
@@ -805,22 +805,32 @@ __device__ __forceinline__ void sn_update_m(const SnPlan& P, int t0, int cA, int
   }
 }
 
+// Blocks per SM the register budget aims for: four for FP32 (64 registers),
+// two for FP64.
 template <typename T>
-__global__ void __launch_bounds__(SN_WARPS * 32)
+constexpr int kSnMinBlocks = sizeof(T) == sizeof(float) ? 4 : 2;
+
+template <typename T>
+__global__ void __launch_bounds__(SN_WARPS * 32, kSnMinBlocks<T>)
     k_schur_numeric(VBView<T> C, VBView<T> G, VBView<T> W, VBView<T> S, int32_t* __restrict__ slow,
-                    int* __restrict__ nslow, unsigned long long* __restrict__ rowctr, int* st) {
+                    int* __restrict__ nslow, unsigned long long* __restrict__ rowctr,
+                    unsigned long long* __restrict__ flops, int* st) {
   extern __shared__ __align__(16) unsigned char sn_raw[];
   const int lane = threadIdx.x & 31;
   SnPlan& P = reinterpret_cast<SnPlan*>(sn_raw)[threadIdx.x >> 5];
   const T* __restrict__ Cv = C.val;
   const T* __restrict__ Gv = G.val;
   const T* __restrict__ Wv = W.val;
+  if (lane == 0) P.fl = 0;
   for (;;) {
     // rows are handed out one at a time to whichever warp is free
     long long rr = 0;
     if (lane == 0) rr = (long long)atomicAdd(rowctr, 1ULL);
     const int64_t r = __shfl_sync(0xffffffffu, rr, 0);
-    if (r >= S.nbr) break;
+    if (r >= S.nbr) {
+      if (lane == 0 && flops && P.fl) atomicAdd(flops, P.fl);
+      break;
+    }
     __syncwarp();
     const int64_t s0 = S.bptr[r], s1 = S.bptr[r + 1];
     const int64_t c0 = C.bptr[r], c1 = C.bptr[r + 1];
@@ -870,6 +880,7 @@ __global__ void __launch_bounds__(SN_WARPS * 32)
         dev_fail(st, DEV_INTERNAL);
     }
     int carry = 0;
+    long long pf = 0;
     for (int base = 0; base < np; base += 32) {
       const int t = base + lane;
       int ns = 0;
@@ -891,6 +902,7 @@ __global__ void __launch_bounds__(SN_WARPS * 32)
         P.pq[t] = q;
         P.pwv[t] = W.voff[wb];
         ns = (P.soff[q + 1] - P.soff[q]) / nr;
+        pf += 2LL * nr * P.gm[lo] * ns;
       }
       int sc = ns;
       for (int o = 1; o < 32; o <<= 1) {
@@ -901,6 +913,8 @@ __global__ void __launch_bounds__(SN_WARPS * 32)
       carry += __shfl_sync(0xffffffffu, sc, 31);
     }
     if (lane == 0) P.cpre[0] = 0;
+    pf = warp_sum_ll(pf);
+    if (lane == 0) P.fl += (unsigned long long)pf;
     __syncwarp();
     // 2. C values (zero for fill) into the run, SN_CU loads in flight per lane
     T* __restrict__ run = S.val + vbase;
@@ -1003,10 +1017,11 @@ __global__ void __launch_bounds__(SN_WARPS * 32)
 template <typename T>
 __global__ void __launch_bounds__(LW * 32)
     k_schur_numeric_rows(VBView<T> C, VBView<T> G, VBView<T> W, VBView<T> S, const int32_t* __restrict__ rows,
-                         const int* __restrict__ nrows, int* st) {
+                         const int* __restrict__ nrows, unsigned long long* __restrict__ flops, int* st) {
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
   const int64_t total = *nrows;
+  unsigned long long wfl = 0;
   for (int64_t t = blockIdx.x * wpb + (threadIdx.x >> 5); t < total; t += (int64_t)gridDim.x * wpb) {
     const int64_t r = rows[t];
     const int nr = S.rsz[r];
@@ -1033,6 +1048,7 @@ __global__ void __launch_bounds__(LW * 32)
         }
         const T* wv = W.val + W.voff[wb];
         T* dst = S.val + S.voff[q];
+        if (lane == 0) wfl += 2ull * (unsigned long long)nr * (unsigned long long)m * (unsigned long long)ns;
         for (int e = lane; e < nr * ns; e += 32) {
           const int i = e / ns, j = e - i * ns;
           T acc = dst[e];
@@ -1043,26 +1059,7 @@ __global__ void __launch_bounds__(LW * 32)
       __syncwarp();
     }
   }
-}
-
-// Flop count of the numeric phase: 2 n_r n_Y (sum of n_s over W row Y) per
-// G block (r, Y).
-template <typename T>
-__global__ void k_schur_flops(VBView<T> G, const int64_t* __restrict__ Wbptr, const int32_t* __restrict__ Wbcol,
-                              const int32_t* __restrict__ Wcsz, unsigned long long* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wpb = blockDim.x >> 5;
-  unsigned long long acc = 0;
-  for (int64_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < G.nbr; r += (int64_t)gridDim.x * wpb) {
-    const unsigned long long nr = G.rsz[r];
-    for (int64_t g = G.bptr[r] + lane; g < G.bptr[r + 1]; g += 32) {
-      const int32_t Y = G.bcol[g];
-      unsigned long long ws = 0;
-      for (int64_t b = Wbptr[Y]; b < Wbptr[Y + 1]; ++b) ws += Wcsz[Wbcol[b]];
-      acc += 2ULL * nr * (unsigned long long)G.csz[Y] * ws;
-    }
-  }
-  atomicAdd(out, acc);
+  if (lane == 0 && flops && wfl) atomicAdd(flops, wfl);
 }
 
 // Last reduction: drop off-diagonal blocks of S below the threshold.
@@ -1328,6 +1325,8 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
     DBuf<int32_t> slow(nC, s);
     DBuf<int> nslow(1, s);
     nslow.zero();
+    DBuf<unsigned long long> fl(1, s);  // flops of the numeric phase, counted by its kernels
+    fl.zero();
     if (rec) {
       // algorithmic work of the numeric phase: read C, G, W and write S once
       // (values and their index arrays); flops = sum over (r, Y, s) of
@@ -1337,12 +1336,6 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
       };
       rec->bytes = (double)sizeof(T) * (double)(C.nval + G.nval + W.nval + Sf.nval) + idx(C) + idx(G) + idx(W) +
                    idx(Sf);
-      DBuf<unsigned long long> fl(1, s);
-      fl.zero();
-      if (G.nnzb) launch(k_schur_flops<T>, grid_for(G.nbr, LW), LW * 32, 0, s, G.view(), W.bptr.p, W.bcol.p,
-                         W.csz_p(), fl.p);
-      VB_LAUNCH_CHECK();
-      rec->flops = (double)d2h(fl.p, s);
       VB_CUDA(cudaEventCreate(&rec->e0));
       VB_CUDA(cudaEventCreate(&rec->e1));
       VB_CUDA(cudaEventRecord(rec->e0, s));
@@ -1356,12 +1349,15 @@ void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_re
     DBuf<unsigned long long> rowctr(1, s);
     rowctr.zero();
     launch(k_schur_numeric<T>, grid_for(nC, SN_WARPS, (int64_t)nsm * std::max(per_sm, 1)), SN_WARPS * 32, psmem, s,
-           C.view(), G.view(), W.view(), Sf.view(), slow.p, nslow.p, rowctr.p, dst);
+           C.view(), G.view(), W.view(), Sf.view(), slow.p, nslow.p, rowctr.p, fl.p, dst);
     VB_LAUNCH_CHECK();
     launch(k_schur_numeric_rows<T>, 152u * 4, LW * 32, 0, s, C.view(), G.view(), W.view(), Sf.view(), slow.p,
-           nslow.p, dst);
+           nslow.p, fl.p, dst);
     VB_LAUNCH_CHECK();
-    if (rec) VB_CUDA(cudaEventRecord(rec->e1, s));
+    if (rec) {
+      VB_CUDA(cudaEventRecord(rec->e1, s));
+      rec->flops = (double)d2h(fl.p, s);
+    }
   }
   check_status(dst, s, "vbarms_factor: Schur numeric");
   if (last_reduction && nC) {
