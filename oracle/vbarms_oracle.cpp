@@ -10,7 +10,7 @@
 // Every floating-point operation is a separate IEEE round-to-nearest step
 // (build with -ffp-contract=off), evaluated in the order written here.
 //
-// Readings of points the paper leaves open (numbered as in the design notes):
+// Readings of points the paper leaves open (R1-R9):
 //  R1  similarity of rows i,j (Section 2.1): cos = |P_i n P_j| / sqrt(|P_i||P_j|)
 //      on the stored pattern of the rows; j joins i's group iff cos >= tau,
 //      tested exactly as (double)(c*c) >= (tau*tau) * (double)(|P_i||P_j|).
