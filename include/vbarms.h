@@ -55,10 +55,14 @@ typedef struct vbarms_prec_st* vbarms_prec; /* multilevel VBARMS factorization *
 enum { VB_FP64 = 0, VB_FP32_MIXED = 1 };
 
 typedef struct {
-  /* VB_FP64: every factor in FP64.  VB_FP32_MIXED: W, G, Schur complements and
-   * last-level factors stored and computed in FP32 (FP32 accumulation); pivot
-   * blocks whose 1-norm condition estimate exceeds fp64_pivot_cond keep FP64
-   * LU factors and are applied in FP64.                                      */
+  /* VB_FP64: every factor in FP64.  VB_FP32_MIXED: the first level is scaled
+   * and ordered from the FP64 matrix; W, G, Schur complements and last-level
+   * factors are stored and computed in FP32 (FP32 accumulation) and applied
+   * in FP32 arithmetic into FP64 vectors.  Pivot blocks whose 1-norm
+   * condition estimate exceeds fp64_pivot_cond keep FP64 LU factors and are
+   * applied in FP64 (reduction levels: factored in FP64, the others used as
+   * their FP32 rounding; last level: factored in FP32 and refactored in FP64
+   * when the estimate exceeds the threshold).                              */
   int precision;
   double fp64_pivot_cond; /* default 1e4                                     */
   double ddtol;           /* Step 3: supernodes with weight < ddtol go to C
