@@ -69,6 +69,10 @@ typedef struct {
                              (default 0 = off)                               */
   uint64_t wait_limit;    /* nanoseconds one bounded device wait may last
                              before VB_ETIMEOUT (0 = default, 30 s)          */
+  int schur_drop_all;     /* nonzero: apply the drop threshold to the Schur
+                             complement at every reduction (the ARMS habit);
+                             0 (default): only at the last one, as Section 3
+                             prescribes                                      */
 } vbarms_opts;
 
 /* Fill *opt with the defaults above. */

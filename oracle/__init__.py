@@ -61,7 +61,7 @@ def lib():
                 "or_is_order": (i64, [vp, d, vp, vp]),
                 "or_gepp": (i32, [vp, i32, vp]),
                 "or_dropped": (i32, [vp, i32, i32, d]),
-                "or_factor": (vp, [vp, i32, d, i32, d]),
+                "or_factor": (vp, [vp, i32, d, i32, d, i32]),
                 "or_prec_free": (None, [vp]),
                 "or_prec_levels": (i32, [vp]),
                 "or_prec_fill": (d, [vp]),
@@ -244,11 +244,12 @@ IVEC = dict(pI=3, piv=4)
 class Prec:
     """Multilevel factorization (Steps 2-4 repeated, Eq. 7-8, last-level ILUT)."""
 
-    def __init__(self, A: VBMat, nlev: int, droptol: float, lfil: int, ddtol: float = 0.0):
+    def __init__(self, A: VBMat, nlev: int, droptol: float, lfil: int, ddtol: float = 0.0,
+                 schur_drop_all: bool = False):
         self._A = _VBHandle(A)
         self.n = int(A.rsz.sum())
         L = lib()
-        self.h = L.or_factor(self._A.h, int(nlev), float(droptol), int(lfil), float(ddtol))
+        self.h = L.or_factor(self._A.h, int(nlev), float(droptol), int(lfil), float(ddtol), int(bool(schur_drop_all)))
         if not self.h:
             raise OracleError(L.or_last_status(), "factor")
         self.levels = L.or_prec_levels(self.h)

@@ -595,7 +595,9 @@ int ilut_last(Last& X, double t, int lfil) {
   return OK;
 }
 
-int factor(const VB& A0, int nlev, double t, int lfil, double ddtol, Prec& P) {
+// drop_all: the threshold is applied to the Schur complement at every
+// reduction (the ARMS habit) instead of only at the last one (Section 3).
+int factor(const VB& A0, int nlev, double t, int lfil, double ddtol, bool drop_all, Prec& P) {
   if (A0.nbr != A0.nbc || nlev < 0 || !(t >= 0.0)) return EINVAL;
   P.n = A0.roff[A0.nbr];
   VB cur = A0;
@@ -605,7 +607,7 @@ int factor(const VB& A0, int nlev, double t, int lfil, double ddtol, Prec& P) {
     scale(L.A, L.r, L.c);
     is_order(L.A, ddtol, L.pI, L.nD, L.w);
     if (L.nD == 0) break;  // nothing to eliminate: cur becomes the last level
-    const bool last_red = (l == nlev - 1);
+    const bool last_red = (l == nlev - 1) || drop_all;
     int st = factor_level(L, last_red, t, lfil);
     if (st != OK) return st;
     cur = L.S;
@@ -912,9 +914,9 @@ int64_t or_is_order(const void* h, double ddtol, int32_t* pI, double* w) {
 int or_gepp(double* a, int m, int32_t* piv) { return gepp(a, m, piv); }
 int or_dropped(const double* a, int m, int n, double t) { return dropped(a, m, n, t) ? 1 : 0; }
 
-void* or_factor(const void* A, int nlev, double droptol, int lfil, double ddtol) {
+void* or_factor(const void* A, int nlev, double droptol, int lfil, double ddtol, int drop_all) {
   auto* P = new Prec();
-  g_last_status = factor(*(const VB*)A, nlev, droptol, lfil, ddtol, *P);
+  g_last_status = factor(*(const VB*)A, nlev, droptol, lfil, ddtol, drop_all != 0, *P);
   if (g_last_status != OK) {
     delete P;
     return nullptr;

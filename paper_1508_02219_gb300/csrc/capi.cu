@@ -119,7 +119,7 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
     KernelRec rec;
     rec.kernel = 0;
     rec.level = l;
-    schur<T>(L.C, L.G, L.W, l == o.nlev - 1, o.droptol, L.S, s, dst, &rec);
+    schur<T>(L.C, L.G, L.W, l == o.nlev - 1 || o.schur_drop_all, o.droptol, L.S, s, dst, &rec);
     P->krec.push_back(rec);
     tm.mark(PH_SCHUR);
     fill += (double)(L.D.nval + L.W.nval + L.G.nval);
@@ -172,6 +172,7 @@ void vbarms_opts_default(vbarms_opts* opt) {
   opt->fp64_pivot_cond = 1e4;
   opt->ddtol = 0.0;
   opt->wait_limit = 0;
+  opt->schur_drop_all = 0;
 }
 
 const char* vbarms_last_error(void) { return g_err.c_str(); }
@@ -308,7 +309,7 @@ vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil, const
   if (!opt) opt = &d;
   if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
   FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
-               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs};
+               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
     if (o.precision == VB_FP64)
@@ -358,7 +359,7 @@ vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev,
       for (int m : members) parts.push_back(&A[m]->C);
       compressed_union(parts, s, U.C);
       FactorOpts o{nlev[m0], droptol[m0], lfil[m0], opt->precision, opt->fp64_pivot_cond, opt->ddtol,
-                   opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs};
+                   opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
       std::shared_ptr<PrecBase> P;
       if (o.precision == VB_FP64)
         P = factor_impl<double>(U, o);

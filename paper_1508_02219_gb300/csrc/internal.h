@@ -63,6 +63,7 @@ struct FactorOpts {
   double fp64_pivot_cond;
   double ddtol;
   uint64_t wait_limit;
+  bool schur_drop_all;
 };
 
 // Step 2: two-sided max-abs scaling in place (FP64 values).

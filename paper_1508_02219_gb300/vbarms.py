@@ -39,7 +39,7 @@ class VbarmsError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("fp64_pivot_cond", C.c_double), ("ddtol", C.c_double),
-                ("wait_limit", C.c_uint64)]
+                ("wait_limit", C.c_uint64), ("schur_drop_all", C.c_int)]
 
 
 def library_path() -> str:
@@ -227,13 +227,14 @@ class Prec:
         return out
 
 
-def make_opts(precision="fp64", fp64_pivot_cond=1e4, ddtol=0.0, wait_limit=0) -> Opts:
+def make_opts(precision="fp64", fp64_pivot_cond=1e4, ddtol=0.0, wait_limit=0, schur_drop_all=False) -> Opts:
     o = Opts()
     lib().vbarms_opts_default(C.byref(o))
     o.precision = VB_FP64 if precision in ("fp64", VB_FP64) else VB_FP32_MIXED
     o.fp64_pivot_cond = float(fp64_pivot_cond)
     o.ddtol = float(ddtol)
     o.wait_limit = int(wait_limit)
+    o.schur_drop_all = int(bool(schur_drop_all))
     return o
 
 

@@ -100,6 +100,25 @@ def test_fp64_factor_bit_exact(case):
     compare_factor(P, Po)
 
 
+@pytest.mark.parametrize("case", ["geo_3lev", "geo_pivoting", "geo_tau09_l5"])
+def test_fp64_factor_schur_drop_all_bit_exact(case):
+    """The ARMS-style variant (threshold on S at every reduction) against the
+    oracle's, bit for bit, and its application."""
+    gen, tau, nlev, t, lfil = FACTOR_CASES[case]
+    m = gen()
+    V = vb()
+    A, c = compress_both(m, tau)
+    P = V.vbarms_factor(A, nlev, t, lfil, precision="fp64", schur_drop_all=True)
+    Po = oracle.Prec(c.A, nlev, t, lfil, 0.0, True)
+    compare_factor(P, Po)
+    x = np.random.default_rng(2).standard_normal(m.n)
+    yo = np.empty(m.n)
+    yo[c.perm] = Po.apply(x[c.perm])
+    yd = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    V.vbarms_apply(P, torch.from_numpy(x).cuda(), yd)
+    assert rel_fro(yd.cpu().numpy(), yo) <= 1e-12
+
+
 @pytest.mark.parametrize("case", ["grid10_l5", "geo_3lev", "geo_pivoting", "geo_tau09_l5"])
 def test_apply_and_fgmres_fp64(case):
     gen, tau, nlev, t, lfil = FACTOR_CASES[case]

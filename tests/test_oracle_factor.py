@@ -332,3 +332,49 @@ def test_singular_pivot_block_reported():
     with pytest.raises(oracle.OracleError) as e:
         oracle.Prec(vb, 1, 0.0, -1)
     assert e.value.status == oracle.ESINGULAR
+
+
+@pytest.mark.parametrize("t,lfil", [(1e-3, -1), (5e-3, 3)])
+def test_schur_drop_all_drops_at_every_reduction(t, lfil):
+    """ARMS-style variant (Section 3 applies the threshold to S only at the
+    last reduction; the variant applies it at every one): the first level's
+    D, W, G are unchanged, its S is the default S less exactly the
+    off-diagonal blocks below the threshold, and every level's S keeps
+    C - G W on its stored blocks."""
+    m, c = compressed(90, 4, seed=11)
+    P0 = oracle.Prec(c.A, 3, t, lfil)
+    P1 = oracle.Prec(c.A, 3, t, lfil, 0.0, True)
+    for name in ("D", "W", "G", "C"):
+        a, b = P0.mat(0, name), P1.mat(0, name)
+        assert np.array_equal(a.bcol, b.bcol) and np.array_equal(a.val, b.val), name
+    S0, S1 = _block_map(P0.mat(0, "S")), _block_map(P1.mat(0, "S"))
+    assert set(S1) <= set(S0)
+    for key, blk in S0.items():
+        keep = key[0] == key[1] or np.linalg.norm(blk) >= t * blk.size
+        assert (key in S1) == keep, key
+        if keep:
+            assert np.array_equal(S1[key], blk)
+    assert len(S1) < len(S0), "nothing was dropped: the case pins nothing"
+    for lev in range(P1.levels):
+        B = level_dense(P1, lev)
+        nf = int(P1.mat(lev, "D").rsz.sum())
+        Cd = B[nf:, nf:]
+        S = P1.mat(lev, "S")
+        S_ref = Cd - P1.mat(lev, "G").dense() @ P1.mat(lev, "W").dense()
+        Sd, ro = S.dense(), _offsets(S.rsz)
+        for (I, J), blk in _blocks_of_dense(S_ref, S.rsz, S.csz).items():
+            got = Sd[ro[I]:ro[I + 1], ro[J]:ro[J + 1]]
+            if np.abs(got).any() or I == J:
+                np.testing.assert_allclose(got, blk, rtol=1e-10, atol=1e-14)
+            else:
+                assert np.linalg.norm(blk) < t * blk.size * (1 + 1e-12)
+
+
+def test_schur_drop_all_one_level_is_the_default():
+    """With one level the only reduction is the last: the variant changes
+    nothing."""
+    m, c = compressed(70, 4, seed=2)
+    P0 = oracle.Prec(c.A, 1, 1e-3, 4)
+    P1 = oracle.Prec(c.A, 1, 1e-3, 4, 0.0, True)
+    for lev, name in [(0, "S"), (0, "W"), (1, "L"), (1, "U"), (1, "D")]:
+        assert np.array_equal(P0.mat(lev, name).val, P1.mat(lev, name).val), name
