@@ -70,6 +70,14 @@ def lib():
                 "or_prec_vec": (i64, [vp, i32, i32, vp, vp]),
                 "or_apply": (None, [vp, vp, vp]),
                 "or_fgmres": (i32, [vp, vp, vp, vp, d, i32, i32, P(i32), P(d)]),
+                "or_dd_build": (vp, [vp, i32, i32, i32, i32, d, i32, d, i32]),
+                "or_dd_free": (None, [vp]),
+                "or_dd_part": (i64, [vp, vp]),
+                "or_dd_rows": (i64, [vp, i32, vp]),
+                "or_dd_local": (vp, [vp, i32]),
+                "or_dd_local_prec": (vp, [vp, i32]),
+                "or_dd_apply": (None, [vp, vp, vp]),
+                "or_dd_fgmres": (i32, [vp, vp, vp, vp, d, i32, i32, P(i32), P(d)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -294,12 +302,72 @@ class Prec:
         return x
 
 
-def fgmres(A: VBMat, prec: Prec | None, b, x0=None, rtol=1e-8, restart=50, maxit=1000):
-    """Right-preconditioned FGMRES(m) on the block-permuted system."""
+class _LocalPrec(Prec):
+    """A local factorization owned by a DD (not freed on its own)."""
+
+    def __init__(self, h, n, owner):
+        self.h, self.n, self._owner = h, n, owner
+        self.levels = lib().or_prec_levels(h)
+
+    def __del__(self):
+        pass
+
+
+class DD:
+    """Section 5 global preconditioners with VBARMS local solvers: block
+    Jacobi (overlap 0), additive Schwarz, restricted additive Schwarz."""
+
+    def __init__(self, A: VBMat, nparts: int, overlap: int, restricted: bool, nlev: int, droptol: float,
+                 lfil: int, ddtol: float = 0.0, schur_drop_all: bool = False):
+        self._A = _VBHandle(A)
+        self.n = int(A.rsz.sum())
+        self.nparts = int(nparts)
+        L = lib()
+        self.h = L.or_dd_build(self._A.h, int(nparts), int(overlap), int(bool(restricted)), int(nlev),
+                               float(droptol), int(lfil), float(ddtol), int(bool(schur_drop_all)))
+        if not self.h:
+            raise OracleError(L.or_last_status(), "dd_build")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_dd_free(self.h)
+            self.h = None
+
+    def part(self) -> np.ndarray:
+        L = lib()
+        out = np.zeros(L.or_dd_part(self.h, None), np.int32)
+        L.or_dd_part(self.h, _p(out))
+        return out
+
+    def rows(self, i: int) -> np.ndarray:
+        """W_i^delta: the block rows of subdomain i with its overlap."""
+        L = lib()
+        out = np.zeros(L.or_dd_rows(self.h, i, None), np.int32)
+        L.or_dd_rows(self.h, i, _p(out))
+        return out
+
+    def local(self, i: int) -> VBMat:
+        return _export(lib().or_dd_local(self.h, i))
+
+    def local_prec(self, i: int) -> Prec:
+        m = self.local(i)
+        return _LocalPrec(lib().or_dd_local_prec(self.h, i), int(m.rsz.sum()), self)
+
+    def apply(self, b: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.zeros(self.n)
+        lib().or_dd_apply(self.h, _p(b), _p(x))
+        return x
+
+
+def fgmres(A: VBMat, prec, b, x0=None, rtol=1e-8, restart=50, maxit=1000):
+    """Right-preconditioned FGMRES(m) on the block-permuted system; prec is a
+    Prec, a DD or None."""
     h = _VBHandle(A)
     b = np.ascontiguousarray(b, np.float64)
     x = np.zeros_like(b) if x0 is None else np.ascontiguousarray(x0, np.float64).copy()
     it, rr = C.c_int(), C.c_double()
-    st = lib().or_fgmres(h.h, prec.h if prec is not None else None, _p(b), _p(x), float(rtol),
-                         int(restart), int(maxit), C.byref(it), C.byref(rr))
+    f = lib().or_dd_fgmres if isinstance(prec, DD) else lib().or_fgmres
+    st = f(h.h, prec.h if prec is not None else None, _p(b), _p(x), float(rtol),
+           int(restart), int(maxit), C.byref(it), C.byref(rr))
     return x, it.value, rr.value, st

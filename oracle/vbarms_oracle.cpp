@@ -10,7 +10,7 @@
 // Every floating-point operation is a separate IEEE round-to-nearest step
 // (build with -ffp-contract=off), evaluated in the order written here.
 //
-// Readings of points the paper leaves open (R1-R9):
+// Readings of points the paper leaves open (R1-R9; D1-D3 for Section 5):
 //  R1  similarity of rows i,j (Section 2.1): cos = |P_i n P_j| / sqrt(|P_i||P_j|)
 //      on the stored pattern of the rows; j joins i's group iff cos >= tau,
 //      tested exactly as (double)(c*c) >= (tau*tau) * (double)(|P_i||P_j|).
@@ -29,10 +29,20 @@
 //  R8  last level: block ILUT in natural order (block IKJ form of Alg. 3).
 //  R9  FGMRES(m) with right preconditioning, MGS Arnoldi, Givens rotations,
 //      true residual at every restart, stop at ||r|| <= rtol ||b||.
+//  D1  Section 5 subdomains on one address space: the compressed block rows
+//      are split into N contiguous ranges, part(I) = floor(N * roff_I / n)
+//      (the locality-preserving row order stands in for a graph partitioner).
+//  D2  overlap: W_i^d = adj(W_i^{d-1}), adj(S) = S plus every block row
+//      coupled to S by a stored block of A or A^T; A_i keeps the blocks of A
+//      with row and column in W_i^delta, numbered in ascending order.
+//  D3  block Jacobi (delta = 0) and additive Schwarz add R_i^T A_i^{-1} R_i
+//      over the subdomains in order; the restricted variant keeps from
+//      subdomain i only the rows of W_i^0.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <numeric>
 #include <vector>
@@ -755,8 +765,98 @@ double dot(const std::vector<double>& a, const std::vector<double>& b) {
   return s;
 }
 
+// ---------------------------------------------------------------------------
+// Section 5: global preconditioners with VBARMS as the local solver (block
+// Jacobi, Schwarz), all subdomains in one address space (D1-D3).
+struct DD {
+  int nparts = 0, delta = 0;
+  bool restricted = true;
+  int64_t n = 0;
+  std::vector<int64_t> roff;            // scalar offsets of A's block rows
+  std::vector<int32_t> part;            // W_i^0 membership of each block row
+  std::vector<std::vector<int32_t>> W;  // W_i^delta, ascending block rows of A
+  std::vector<VB> Aloc;                 // A_i = R_i A R_i on W_i^delta
+  std::vector<Prec> loc;                // VBARMS of A_i
+};
+
+int dd_build(const VB& A, int nparts, int delta, bool restricted, int nlev, double t, int lfil, double ddtol,
+             bool drop_all, DD& D) {
+  if (A.nbr != A.nbc || nparts < 1 || delta < 0) return EINVAL;
+  const int64_t p = A.nbr, n = A.roff[p];
+  D.nparts = nparts;
+  D.delta = delta;
+  D.restricted = restricted;
+  D.n = n;
+  D.roff = A.roff;
+  // D1: contiguous ranges of block rows of near-equal scalar size
+  D.part.assign(p, 0);
+  for (int64_t I = 0; I < p; ++I) D.part[I] = (int32_t)(((int64_t)nparts * A.roff[I]) / n);
+  // D2: the block graph of A + A^T
+  std::vector<std::vector<int32_t>> adj(p);
+  for (int64_t I = 0; I < p; ++I)
+    for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
+      adj[I].push_back(A.bcol[b]);
+      adj[A.bcol[b]].push_back((int32_t)I);
+    }
+  D.W.assign(nparts, {});
+  D.Aloc.assign(nparts, VB());
+  D.loc.assign(nparts, Prec());
+  for (int i = 0; i < nparts; ++i) {
+    std::vector<char> in(p, 0);
+    for (int64_t I = 0; I < p; ++I) in[I] = D.part[I] == i;
+    for (int d = 0; d < delta; ++d) {  // W_i^d = adj(W_i^{d-1})
+      std::vector<char> next = in;
+      for (int64_t I = 0; I < p; ++I)
+        if (in[I])
+          for (int32_t J : adj[I]) next[J] = 1;
+      in.swap(next);
+    }
+    std::vector<int32_t>& Wi = D.W[i];
+    std::vector<int32_t> local(p, -1);
+    for (int64_t I = 0; I < p; ++I)
+      if (in[I]) {
+        local[I] = (int32_t)Wi.size();
+        Wi.push_back((int32_t)I);
+      }
+    std::vector<int32_t> sz;
+    for (int32_t I : Wi) sz.push_back(A.rsz[I]);
+    VB& Ai = D.Aloc[i];
+    Ai.init(sz, sz);
+    for (int32_t I : Wi) {
+      for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b)
+        if (local[A.bcol[b]] >= 0) Ai.push(local[A.bcol[b]], A.blk(b));
+      Ai.end_row();
+    }
+    if (Wi.empty()) continue;
+    const int st = factor(Ai, nlev, t, lfil, ddtol, drop_all, D.loc[i]);
+    if (st != OK) return st;
+  }
+  return OK;
+}
+
+// D3: y = sum_i Q_i^T A_i^{-1} R_i x with A_i^{-1} the local VBARMS solve;
+// Q_i = R_i (additive Schwarz; block Jacobi when delta = 0) or the restriction
+// to W_i^0 (restricted additive Schwarz).  Subdomains are added in order.
+void dd_apply(const DD& D, const double* x, double* y) {
+  for (int64_t j = 0; j < D.n; ++j) y[j] = 0.0;
+  for (int i = 0; i < D.nparts; ++i) {
+    const std::vector<int32_t>& Wi = D.W[i];
+    if (Wi.empty()) continue;
+    const VB& Ai = D.Aloc[i];
+    std::vector<double> xi(Ai.roff[Ai.nbr]), zi(Ai.roff[Ai.nbr]);
+    for (size_t k = 0; k < Wi.size(); ++k)
+      for (int a = 0; a < Ai.rsz[k]; ++a) xi[Ai.roff[k] + a] = x[D.roff[Wi[k]] + a];
+    solve_level(D.loc[i], 0, xi.data(), zi.data());
+    for (size_t k = 0; k < Wi.size(); ++k) {
+      if (D.restricted && D.part[Wi[k]] != i) continue;
+      for (int a = 0; a < Ai.rsz[k]; ++a) y[D.roff[Wi[k]] + a] = y[D.roff[Wi[k]] + a] + zi[Ai.roff[k] + a];
+    }
+  }
+}
+
 // R9: flexible GMRES(m) with right preconditioning (FGMRES, Saad 1993).
-int fgmres(const VB& A, const Prec* P, const double* b, double* x, double rtol, int m, int maxit, int* iters,
+using PrecFn = std::function<void(const double*, double*)>;  // z = M^{-1} v; empty: M = I
+int fgmres(const VB& A, const PrecFn& P, const double* b, double* x, double rtol, int m, int maxit, int* iters,
            double* relres) {
   const int64_t n = A.roff[A.nbr];
   std::vector<double> bv(b, b + n), r(n), w(n);
@@ -783,7 +883,7 @@ int fgmres(const VB& A, const Prec* P, const double* b, double* x, double rtol, 
     int j = 0;
     for (; j < m && it < maxit; ++j) {
       if (P)
-        solve_level(*P, 0, V[j].data(), Z[j].data());
+        P(V[j].data(), Z[j].data());
       else
         Z[j] = V[j];
       spmv(A, Z[j].data(), w.data());
@@ -984,7 +1084,40 @@ int64_t or_prec_vec(void* h, int l, int which, double* dout, int32_t* iout) {
 void or_apply(void* h, const double* b, double* x) { solve_level(*(Prec*)h, 0, b, x); }
 int or_fgmres(const void* A, void* prec, const double* b, double* x, double rtol, int m, int maxit, int* iters,
               double* relres) {
-  return fgmres(*(const VB*)A, (const Prec*)prec, b, x, rtol, m, maxit, iters, relres);
+  PrecFn M;
+  if (prec) M = [prec](const double* v, double* z) { solve_level(*(const Prec*)prec, 0, v, z); };
+  return fgmres(*(const VB*)A, M, b, x, rtol, m, maxit, iters, relres);
+}
+
+void* or_dd_build(const void* A, int nparts, int delta, int restricted, int nlev, double t, int lfil, double ddtol,
+                  int drop_all) {
+  auto* D = new DD();
+  g_last_status = dd_build(*(const VB*)A, nparts, delta, restricted != 0, nlev, t, lfil, ddtol, drop_all != 0, *D);
+  if (g_last_status != OK) {
+    delete D;
+    return nullptr;
+  }
+  return D;
+}
+void or_dd_free(void* h) { delete (DD*)h; }
+int64_t or_dd_part(void* h, int32_t* part) {
+  const DD* D = (const DD*)h;
+  if (part) std::copy(D->part.begin(), D->part.end(), part);
+  return (int64_t)D->part.size();
+}
+int64_t or_dd_rows(void* h, int i, int32_t* rows) {
+  const DD* D = (const DD*)h;
+  if (rows) std::copy(D->W[i].begin(), D->W[i].end(), rows);
+  return (int64_t)D->W[i].size();
+}
+const void* or_dd_local(void* h, int i) { return &((DD*)h)->Aloc[i]; }
+void* or_dd_local_prec(void* h, int i) { return &((DD*)h)->loc[i]; }
+void or_dd_apply(void* h, const double* x, double* y) { dd_apply(*(const DD*)h, x, y); }
+int or_dd_fgmres(const void* A, void* h, const double* b, double* x, double rtol, int m, int maxit, int* iters,
+                 double* relres) {
+  const DD* D = (const DD*)h;
+  PrecFn M = [D](const double* v, double* z) { dd_apply(*D, v, z); };
+  return fgmres(*(const VB*)A, M, b, x, rtol, m, maxit, iters, relres);
 }
 
 }  // extern "C"
