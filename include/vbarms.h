@@ -151,6 +151,36 @@ vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil,
 vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev, const double* droptol,
                                 const int* lfil, const vbarms_opts* opt, vbarms_prec* out);
 
+/* Global preconditioners of Section 5 with VBARMS as the local solver, all
+ * subdomains on one GPU: block Jacobi (overlap 0), additive Schwarz
+ * (restricted = 0) and restricted additive Schwarz (restricted != 0).
+ * Subdomain i (0 <= i < nparts) owns the compressed block rows I with
+ * floor(nparts * roff_I / n) = i (contiguous ranges of near-equal scalar
+ * size; roff_I is the first scalar row of block row I in the P_B
+ * numbering), extended overlap times by the block graph of A + A^T
+ * (W_i^d = adj(W_i^{d-1})).  Its local matrix A_i = R_i A R_i holds the
+ * blocks of A with row and column in W_i^overlap, rows ascending.  Every A_i
+ * is factored by VBARMS with (nlev, droptol, lfil, opt) -- all of them as
+ * one block-diagonal union, one launch per phase -- and the handle applies
+ *   M^{-1} x = sum_i Q_i^T A_i^{-1} R_i x,
+ * Q_i = R_i (additive) or the restriction to the owned rows (restricted).
+ * The handle works with vbarms_apply, vbarms_apply_static, fgmres_solve and
+ * vbarms_prec_stats; vbarms_prec_export / _vector / _kernel_stats describe
+ * the union's factorization.  A: handle of vbarms_compress or
+ * vbarms_vbsr_from_blocks (input, not consumed).  Errors: VB_EINVAL (nparts
+ * outside [1, 4096], overlap < 0, nlev < 0, droptol < 0, a union above 2^31
+ * rows), then as vbarms_factor.                                             */
+vb_status vbarms_dd_factor(vbarms_vbsr A, int nparts, int overlap, int restricted, int nlev, double droptol,
+                           int lfil, const vbarms_opts* opt, vbarms_prec* out);
+
+/* Layout of a vbarms_dd_factor handle: part[nblk(A)] = the subdomain owning
+ * each block row, dstart[nparts + 1] = first union block row of each
+ * subdomain, rows[*union_blocks] = the block row of A behind each union
+ * block row (subdomain-major, ascending within a subdomain).  Any pointer
+ * may be NULL.  VB_EINVAL for a handle of another kind.                      */
+vb_status vbarms_dd_layout(vbarms_prec M, int* nparts, int* overlap, int* restricted, int64_t* union_blocks,
+                           int32_t* part, int64_t* dstart, int32_t* rows);
+
 /* y = M^{-1} x (Alg. 2).  x, y: device double[n], original numbering, must
  * not alias.  Runs on the stream of the matrix the handle was built from.   */
 vb_status vbarms_apply(vbarms_prec M, const double* x, double* y);

@@ -302,6 +302,24 @@ class Prec:
         return x
 
 
+def block_diag(mats) -> VBMat:
+    """The block-diagonal concatenation of square-partitioned VBMats."""
+    rsz, bcol, val = [], [], []
+    bptr, voff = [0], [0]
+    r0 = 0
+    for M in mats:
+        rsz.append(M.rsz)
+        bptr.extend((M.bptr[1:] + bptr[-1]).tolist())
+        bcol.append(M.bcol + r0)
+        voff.extend((M.voff[1:] + voff[-1]).tolist())
+        val.append(M.val)
+        r0 += M.nbr
+    cat = lambda xs, t: np.concatenate(xs).astype(t) if xs else np.zeros(0, t)
+    rs = cat(rsz, np.int32)
+    return VBMat(rs, rs.copy(), np.asarray(bptr, np.int64), cat(bcol, np.int32), np.asarray(voff, np.int64),
+                 cat(val, np.float64))
+
+
 class _LocalPrec(Prec):
     """A local factorization owned by a DD (not freed on its own)."""
 

@@ -90,7 +90,7 @@ vb_status vbarms_apply_static(vbarms_prec M, const double* x, double* y) {
     const vb_status st = setup_device(dev, &scratch, &nsm);
     if (st != VB_OK) return st;
     P.apply_with_scratch(x, y, scratch, nsm);
-    vb::check_status(P.status.p, P.s, "vbarms_apply_static");
+    vb::check_status(P.status_dev(), P.s, "vbarms_apply_static");
   } catch (const vb::Error& err) {
     vb::set_last_error(err.msg);
     return err.st;

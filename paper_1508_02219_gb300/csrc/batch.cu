@@ -57,7 +57,35 @@ void cat(const std::vector<const V*>& src, const std::vector<int64_t>& counts, c
   VB_CUDA(cudaStreamSynchronize(s));
 }
 
+__global__ void k_part_ids(int nparts, const int64_t* __restrict__ start, int32_t* __restrict__ dom) {
+  const int64_t total = start[nparts];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nparts - 1;  // last part with start <= e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= e)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    dom[e] = lo;
+  }
+}
+
 }  // namespace
+
+void union_part_ids(const std::vector<const Compressed*>& parts, cudaStream_t s, DBuf<int32_t>& dom) {
+  const int np = (int)parts.size();
+  std::vector<int64_t> start(np + 1, 0);
+  for (int m = 0; m < np; ++m) start[m + 1] = start[m] + parts[m]->A.nbr;
+  dom.alloc(std::max<int64_t>(start[np], 1), s);
+  if (start[np] == 0) return;
+  DBuf<int64_t> dstart(np + 1, s);
+  h2d(dstart.p, start.data(), np + 1, s);
+  launch(k_part_ids, grid_for(start[np], 256), 256, 0, s, np, dstart.p, dom.p);
+  VB_LAUNCH_CHECK();
+  VB_CUDA(cudaStreamSynchronize(s));  // the host array must outlive the copy
+}
 
 void compressed_union(const std::vector<const Compressed*>& parts, cudaStream_t s, Compressed& out) {
   const int np = (int)parts.size();

@@ -64,8 +64,12 @@ struct PhaseTimer {
   }
 };
 
+// dom (device, may be NULL): for a matrix made of ndom independent diagonal
+// blocks, the block of each block row (nondecreasing); it follows the rows
+// through the levels so that the last-level ILUT can interleave the blocks.
 template <typename T>
-std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts& o) {
+std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts& o, const int32_t* dom = nullptr,
+                                      int ndom = 0) {
   auto P = std::make_unique<PrecDev<T>>();
   cudaStream_t s = Ah.s;
   P->s = s;
@@ -86,6 +90,12 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
   VBDev<T> curT;
   bool cur_is64 = true;
   double fill = 0;
+  const bool track = dom && ndom > 1 && ndom <= kTicketMaxDom && Ah.C.A.nbr > 0;
+  DBuf<int32_t> dcur;
+  if (track) {
+    dcur.alloc(Ah.C.A.nbr, s);
+    VB_CUDA(cudaMemcpyAsync(dcur.p, dom, Ah.C.A.nbr * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  }
   for (int l = 0; l < o.nlev; ++l) {
     const int64_t p = cur_is64 ? cur64->nbr : curT.nbr;
     if (p == 0) break;
@@ -110,6 +120,11 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
       gather_parts<T, T>(L.AT, L.pI, newpos, nD, L, s, dst);
     }
     tm.mark(PH_GATHER);
+    if (track) {  // the next level's rows are the C rows, in P_I order
+      DBuf<int32_t> dn(std::max<int64_t>(p - nD, 1), s);
+      take_i32(dcur.p, L.pI.p + nD, p - nD, dn.p, s);
+      dcur = std::move(dn);
+    }
     pivot_lu(L.D, L.piv, L.ptag, L.D32, mixed, o.fp64_pivot_cond, s, dst);
     tm.mark(PH_PIVOT);
     w_or_g<T>(L.F, 0, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.W, s);
@@ -142,7 +157,9 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
   else
     X.A = std::move(curT);
   scale_level_t<T>(X.A, X.r, X.c, s);
-  ilut_last<T>(X, o.droptol, o.lfil, mixed, o.fp64_pivot_cond, o.wait_limit, s, dst);
+  DBuf<int32_t> tickets;
+  if (track) ticket_order(dcur.p, X.A.nbr, ndom, tickets, s);
+  ilut_last<T>(X, o.droptol, o.lfil, mixed, o.fp64_pivot_cond, o.wait_limit, s, dst, tickets.p);
   tm.mark(PH_ILUT);
   level_order<T>(X.L, false, X.lorder, X.ldepth, s);
   level_order<T>(X.U, true, X.uorder, X.udepth, s);
@@ -358,13 +375,15 @@ vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev,
       std::vector<const Compressed*> parts;
       for (int m : members) parts.push_back(&A[m]->C);
       compressed_union(parts, s, U.C);
+      DBuf<int32_t> dom;
+      union_part_ids(parts, s, dom);
       FactorOpts o{nlev[m0], droptol[m0], lfil[m0], opt->precision, opt->fp64_pivot_cond, opt->ddtol,
                    opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
       std::shared_ptr<PrecBase> P;
       if (o.precision == VB_FP64)
-        P = factor_impl<double>(U, o);
+        P = factor_impl<double>(U, o, dom.p, (int)parts.size());
       else
-        P = factor_impl<float>(U, o);
+        P = factor_impl<float>(U, o, dom.p, (int)parts.size());
       int64_t off = 0;
       for (int m : members) {
         res[m] = std::make_unique<vbarms_prec_st>();
@@ -379,6 +398,73 @@ vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev,
   if (st != VB_OK) return st;
   for (int m = 0; m < nmat; ++m) out[m] = res[m].release();
   return VB_OK;
+}
+
+vb_status vbarms_dd_factor(vbarms_vbsr A, int nparts, int overlap, int restricted, int nlev, double droptol, int lfil,
+                           const vbarms_opts* opt, vbarms_prec* out) {
+  if (!A || !out) return set_err(VB_EINVAL, "NULL handle");
+  if (nlev < 0 || !(droptol >= 0.0)) return set_err(VB_EINVAL, "nlev < 0 or droptol < 0");
+  if (nparts < 1 || nparts > kDDMaxParts || overlap < 0)
+    return set_err(VB_EINVAL, "nparts must lie in [1, 4096] and overlap must be >= 0");
+  vbarms_opts d;
+  vbarms_opts_default(&d);
+  if (!opt) opt = &d;
+  if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
+  FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
+               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
+  auto h = std::make_unique<vbarms_prec_st>();
+  vb_status st = guarded([&] {
+    cudaStream_t s = A->s;
+    auto D = std::make_unique<PrecDD>();
+    D->s = s;
+    D->n = A->C.n;
+    D->precision = o.precision;
+    D->wait_limit = o.wait_limit;
+    D->perm.alloc(std::max<int64_t>(A->C.n, 1), s);
+    if (A->C.n)
+      VB_CUDA(cudaMemcpyAsync(D->perm.p, A->C.perm.p, A->C.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    D->status.alloc(1, s);
+    D->status.zero();
+    // the subdomains' block-diagonal union, factored once; its rows carry
+    // their subdomain so that the last-level ILUT interleaves the subdomains
+    vbarms_vbsr_st U;
+    U.s = s;
+    dd_build(A->C, nparts, overlap, restricted != 0, s, D->L, U.C);
+    if (o.precision == VB_FP64)
+      D->inner = factor_impl<double>(U, o, D->L.ud.p, nparts);
+    else
+      D->inner = factor_impl<float>(U, o, D->L.ud.p, nparts);
+    for (int i = 0; i < PH_COUNT; ++i) D->phase_s[i] = D->inner->phase_s[i];
+    D->mem_ratio = D->inner->mem_ratio;
+    D->krec = std::move(D->inner->krec);
+    D->inner->krec.clear();
+    h->impl = std::move(D);
+  });
+  if (st != VB_OK) {
+    cudaStreamSynchronize(A->s);
+    return st;
+  }
+  *out = h.release();
+  return VB_OK;
+}
+
+vb_status vbarms_dd_layout(vbarms_prec M, int* nparts, int* overlap, int* restricted, int64_t* union_blocks,
+                           int32_t* part, int64_t* dstart, int32_t* rows) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  auto* D = dynamic_cast<PrecDD*>(M->impl.get());
+  if (!D) return set_err(VB_EINVAL, "not a domain-decomposition preconditioner");
+  return guarded([&] {
+    const DDLayout& L = D->L;
+    if (nparts) *nparts = L.nparts;
+    if (overlap) *overlap = L.overlap;
+    if (restricted) *restricted = L.restricted ? 1 : 0;
+    if (union_blocks) *union_blocks = L.m;
+    if (part && L.p) VB_CUDA(cudaMemcpyAsync(part, L.part.p, L.p * sizeof(int32_t), cudaMemcpyDeviceToHost, D->s));
+    if (dstart)
+      VB_CUDA(cudaMemcpyAsync(dstart, L.dstart.p, (L.nparts + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, D->s));
+    if (rows && L.m) VB_CUDA(cudaMemcpyAsync(rows, L.ug.p, L.m * sizeof(int32_t), cudaMemcpyDeviceToHost, D->s));
+    VB_CUDA(cudaStreamSynchronize(D->s));
+  });
 }
 
 vb_status vbarms_apply(vbarms_prec M, const double* x, double* y) {
@@ -404,7 +490,7 @@ vb_status vbarms_apply(vbarms_prec M, const double* x, double* y) {
       if (M->len)
         VB_CUDA(cudaMemcpyAsync(y, yu.p + M->off, M->len * sizeof(double), cudaMemcpyDeviceToDevice, P.s));
     }
-    check_status(P.status.p, P.s, "vbarms_apply");
+    check_status(P.status_dev(), P.s, "vbarms_apply");
   });
 }
 
@@ -437,7 +523,7 @@ vb_status vbarms_apply_batched(int nmat, const vbarms_prec* M, const double* con
         if (len) VB_CUDA(cudaMemcpyAsync(y[m], yu.p + off, len * sizeof(double), cudaMemcpyDeviceToDevice, P.s));
         done[m] = 1;
       }
-      check_status(P.status.p, P.s, "vbarms_apply_batched");
+      check_status(P.status_dev(), P.s, "vbarms_apply_batched");
     }
   });
 }
@@ -513,7 +599,7 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
         }
         dot_dev(w.p, w.p, n, hcol.p + j + 1, red.p, s);
         std::vector<double> hc = d2h_vec(hcol.p, j + 2, s);
-        if (M) check_status(M->impl->status.p, s, "fgmres_solve: preconditioner");
+        if (M) check_status(M->impl->status_dev(), s, "fgmres_solve: preconditioner");
         const double hn = std::sqrt(hc[j + 1]);
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
         H[(size_t)(j + 1) * m + j] = hn;

@@ -4,7 +4,10 @@
 //
 // Row i is processed by one warp that took ticket i (tickets are handed out
 // in row order, so every row a warp waits for is already owned by a running
-// warp).  The warp keeps its working row in a private workspace (hash table
+// warp).  A matrix made of independent diagonal blocks (a batch, or the
+// subdomains of a domain decomposition) may instead hand out its rows
+// interleaved across the blocks, each block's rows in ascending order: the
+// blocks' dependency chains then advance side by side.  The warp keeps its working row in a private workspace (hash table
 // column -> slot, dense values): in shared memory when the row fits, else in
 // global memory (a shared row whose fill outgrows the buffer starts again in
 // the global one).  It eliminates its L part in ascending column order
@@ -50,6 +53,9 @@ struct Pools {
   int* abort;
   int64_t* uvstart;  // value offset of the first U block of each row
   int64_t* uvlen;    // values of the U row (its blocks are contiguous)
+  // ticket -> row (nullptr: ticket t is row t); every row's dependencies
+  // must come earlier in it
+  const int32_t* order;
 };
 
 struct Workspace {
@@ -438,7 +444,10 @@ __global__ void __launch_bounds__(IW * 32, 2)
 
   for (;;) {
     long long row = 0;
-    if (lane == 0) row = (long long)atomicAdd(P.ctr + 4, 1ULL);
+    if (lane == 0) {
+      row = (long long)atomicAdd(P.ctr + 4, 1ULL);
+      if (P.order && row < A.nbr) row = P.order[row];
+    }
     row = __shfl_sync(0xffffffffu, row, 0);
     if (row >= A.nbr) break;
     const int64_t i = row;
@@ -1151,7 +1160,7 @@ __global__ void k_iota(int64_t n, int64_t* __restrict__ bptr, int32_t* __restric
 
 template <typename T>
 void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, uint64_t wait_limit, cudaStream_t s,
-               int* dst) {
+               int* dst, const int32_t* order) {
   const VBDev<T>& A = X.A;
   const int64_t p = A.nbr;
   const int64_t n = p ? d2h(A.roff.p + p, s) : 0;
@@ -1222,7 +1231,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
     abort.zero();
     X.piv.zero();
     Pools P{lcol.p, lvo.p,  ucol.p, uvo.p,  lstart.p, lcnt.p,  ustart.p,  ucnt.p,   ctr.p,
-            lbcap,  lvcap,  ubcap,  uvcap,  done.p,   abort.p, uvstart.p, uvlen.p};
+            lbcap,  lvcap,  ubcap,  uvcap,  done.p,   abort.p, uvstart.p, uvlen.p, order};
     VB_CUDA(cudaFuncSetAttribute(k_ilut<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ilut_smem()));
     launch(k_ilut<T>, (unsigned)nblocks, IW * 32, ilut_smem(), s, A.view(), ws, wvals.p, P, lval.p, uval.p,
            X.Dg.voff.p,
@@ -1275,8 +1284,72 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   fail(VB_ENOMEM, "vbarms_factor: last-level ILUT workspace could not be sized");
 }
 
-template void ilut_last<double>(LastDev<double>&, double, int, bool, double, uint64_t, cudaStream_t, int*);
-template void ilut_last<float>(LastDev<float>&, double, int, bool, double, uint64_t, cudaStream_t, int*);
+namespace {
+__global__ void k_dom_start(int64_t p, int ndom, const int32_t* __restrict__ dom, int64_t* __restrict__ start) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d <= ndom; d += gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = p;  // first row with dom >= d
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (dom[mid] < d)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    start[d] = lo;
+  }
+}
+
+// Row r, the j-th of block d, goes to position
+//   sum_{d'} min(len_d', j) + #{d' < d : len_d' > j},
+// its place when the blocks' rows are dealt out one per block in turn.
+__global__ void k_ticket_pos(int64_t p, int ndom, const int32_t* __restrict__ dom, const int64_t* __restrict__ start,
+                             int32_t* __restrict__ order) {
+  extern __shared__ int64_t lens[];
+  for (int d = threadIdx.x; d < ndom; d += blockDim.x) lens[d] = start[d + 1] - start[d];
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < p; r += (int64_t)gridDim.x * blockDim.x) {
+    const int d = dom[r];
+    const int64_t j = r - start[d];
+    int64_t pos = 0;
+    for (int e = 0; e < ndom; ++e) {
+      const int64_t le = lens[e];
+      pos += le < j ? le : j;
+      if (e < d && le > j) ++pos;
+    }
+    order[pos] = (int32_t)r;
+  }
+}
+
+__global__ void k_take_i32(int64_t n, const int32_t* __restrict__ src, const int32_t* __restrict__ idx,
+                           int32_t* __restrict__ dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = src[idx[k]];
+}
+}  // namespace
+
+void ticket_order(const int32_t* dom, int64_t p, int ndom, DBuf<int32_t>& order, cudaStream_t s) {
+  if (p == 0 || ndom <= 1 || ndom > kTicketMaxDom) {
+    order = DBuf<int32_t>();
+    return;
+  }
+  DBuf<int64_t> start(ndom + 1, s);
+  launch(k_dom_start, grid_for(ndom + 1, 256), 256, 0, s, p, ndom, dom, start.p);
+  VB_LAUNCH_CHECK();
+  order.alloc(p, s);
+  launch(k_ticket_pos, grid_for(p, 256), 256, (size_t)ndom * sizeof(int64_t), s, p, ndom, dom, start.p, order.p);
+  VB_LAUNCH_CHECK();
+}
+
+void take_i32(const int32_t* src, const int32_t* idx, int64_t n, int32_t* dst, cudaStream_t s) {
+  if (n == 0) return;
+  launch(k_take_i32, grid_for(n, 256), 256, 0, s, n, src, idx, dst);
+  VB_LAUNCH_CHECK();
+}
+
+template void ilut_last<double>(LastDev<double>&, double, int, bool, double, uint64_t, cudaStream_t, int*,
+                                 const int32_t*);
+template void ilut_last<float>(LastDev<float>&, double, int, bool, double, uint64_t, cudaStream_t, int*,
+                                const int32_t*);
 
 }  // namespace vb
 

@@ -20,6 +20,8 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
 // factorization: parts keep their order, their block and scalar rows are
 // numbered consecutively.
 void compressed_union(const std::vector<const Compressed*>& parts, cudaStream_t s, Compressed& out);
+// dom[k] = the part that block row k of the union comes from.
+void union_part_ids(const std::vector<const Compressed*>& parts, cudaStream_t s, DBuf<int32_t>& dom);
 
 // One reduction level (Steps 2-4) on the device.
 template <typename T>

@@ -40,10 +40,21 @@ template <typename T>
 void schur(const VBDev<T>& C, const VBDev<T>& G, const VBDev<T>& W, bool last_reduction, double t, VBDev<T>& S,
            cudaStream_t s, int* dst, KernelRec* rec);
 
-// Last level: block ILUT in natural order (Alg. 3 in block form).
+// Last level: block ILUT in natural order (Alg. 3 in block form).  order
+// (may be NULL) hands the rows out in another sequence that keeps every
+// row's dependencies before it (ticket_order).
 template <typename T>
 void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, uint64_t wait_limit, cudaStream_t s,
-               int* dst);
+               int* dst, const int32_t* order = nullptr);
+
+// For a matrix of independent diagonal blocks (dom[r]: the block of row r,
+// nondecreasing, values in [0, ndom)): the rows interleaved round-robin over
+// the blocks, each block's rows ascending.  Leaves order empty when ndom is
+// above kTicketMaxDom.
+constexpr int kTicketMaxDom = 4096;
+void ticket_order(const int32_t* dom, int64_t p, int ndom, DBuf<int32_t>& order, cudaStream_t s);
+// dst[k] = src[idx[k]]
+void take_i32(const int32_t* src, const int32_t* idx, int64_t n, int32_t* dst, cudaStream_t s);
 
 // Solve phase (Alg. 2) helpers.
 template <typename T>

@@ -46,6 +46,8 @@ struct PrecBase {
   // (256-byte aligned, scratch_bytes() long): allocates nothing.
   virtual void apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm) = 0;
   virtual void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) = 0;
+  // The device status word the solve kernels report to.
+  virtual int* status_dev() { return status.p; }
 };
 
 template <typename T>
@@ -69,6 +71,58 @@ struct PrecDev : PrecBase {
   void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval, int32_t* rsz,
                   int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) override;
   void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) override;
+};
+
+// Section 5 global preconditioners (dd.cu): the subdomains of A, their
+// block-diagonal union and the maps between union and global vectors.
+constexpr int kDDMaxParts = 4096;
+
+struct DDLayout {
+  int nparts = 0, overlap = 0;
+  bool restricted = true;
+  int64_t n = 0, p = 0;    // scalar and block rows of A
+  int64_t m = 0, nu = 0;   // block and scalar rows of the union
+  DBuf<int32_t> part;      // subdomain owning each block row of A
+  DBuf<int32_t> rsz;       // block sizes of A
+  DBuf<int64_t> roff;      // scalar offsets of A's block rows
+  DBuf<int32_t> ug, ud;    // per union block row: block row of A, subdomain
+  DBuf<int64_t> dstart;    // first union block row of each subdomain (nparts + 1)
+  DBuf<int64_t> uroff;     // scalar offsets of the union's block rows
+  DBuf<int32_t> gidx;      // union scalar row -> scalar row of A
+  DBuf<int32_t> src;       // scalar row of A -> its row in the owning subdomain
+  DBuf<int64_t> cptr;      // additive: copies of each block row of A ...
+  DBuf<int32_t> clist;     // ... as union block rows, in subdomain order
+};
+
+void dd_build(const Compressed& A, int nparts, int overlap, bool restricted, cudaStream_t s, DDLayout& L,
+              Compressed& U);
+void dd_apply(const DDLayout& L, PrecBase& inner, const double* x, double* y, double* xu, double* yu,
+              cudaStream_t s);
+
+// Block Jacobi / (restricted) additive Schwarz with the factorization of the
+// subdomains' union as the local solver.
+struct PrecDD : PrecBase {
+  std::unique_ptr<PrecBase> inner;
+  DDLayout L;
+  DBuf<double> xu, yu;
+  int levels() const override { return inner->levels(); }
+  void apply_perm(const double* x, double* y) override {
+    if (!xu.p && L.nu) {
+      xu.alloc(L.nu, s);
+      yu.alloc(L.nu, s);
+    }
+    dd_apply(L, *inner, x, y, xu.p, yu.p, s);
+  }
+  size_t scratch_bytes() const override;
+  void apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm) override;
+  void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval, int32_t* rsz,
+                  int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) override {
+    inner->export_mat(lev, which, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+  }
+  void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) override {
+    inner->export_vec(lev, which, d, iv, len);
+  }
+  int* status_dev() override { return inner->status_dev(); }
 };
 
 // Record the message vbarms_last_error() returns on this thread.

@@ -68,6 +68,8 @@ def lib():
                 "vbarms_apply": (i32, [vp, vp, vp]),
                 "vbarms_factor_batched": (i32, [i32, vp, vp, vp, vp, P(Opts), vp]),
                 "vbarms_apply_batched": (i32, [i32, vp, vp, vp]),
+                "vbarms_dd_factor": (i32, [vp, i32, i32, i32, i32, d, i32, P(Opts), P(vp)]),
+                "vbarms_dd_layout": (i32, [vp, P(i32), P(i32), P(i32), P(i64), vp, vp, vp]),
                 "fgmres_solve": (i32, [vp, vp, vp, vp, d, i32, i32, P(i32), P(d)]),
                 "vbarms_prec_stats": (i32, [vp, P(i32), P(d), vp]),
                 "vbarms_prec_export": (i32, [vp, i32, i32, P(i64), P(i64), P(i64), P(i64), vp, vp, vp, vp, vp,
@@ -261,6 +263,29 @@ def vbarms_factor_batched(As, nlev, droptol, lfil, precision="fp64", **kw) -> li
     _check(lib().vbarms_factor_batched(nm, C.cast(hs, C.c_void_p), _hp(nl), _hp(dt), _hp(lf), C.byref(o),
                                        C.cast(out, C.c_void_p)))
     return [Prec(out[m], As[m]) for m in range(nm)]
+
+
+def vbarms_dd_factor(A: VBSR, nparts: int, overlap: int, restricted: bool, nlev: int, droptol: float, lfil: int,
+                     precision="fp64", **kw) -> Prec:
+    """Section 5 global preconditioner (block Jacobi / additive Schwarz /
+    restricted additive Schwarz) with VBARMS local solvers on every subdomain."""
+    o = make_opts(precision, **kw)
+    h = C.c_void_p()
+    _check(lib().vbarms_dd_factor(A.h, int(nparts), int(overlap), int(bool(restricted)), int(nlev), float(droptol),
+                                  int(lfil), C.byref(o), C.byref(h)))
+    return Prec(h.value, A)
+
+
+def dd_layout(M: Prec):
+    """(part per block row of A, dstart[nparts + 1], union rows -> block rows of A)."""
+    L = lib()
+    npart, ov, rs, nu = C.c_int(), C.c_int(), C.c_int(), C.c_int64()
+    _check(L.vbarms_dd_layout(M.h, C.byref(npart), C.byref(ov), C.byref(rs), C.byref(nu), None, None, None))
+    part = np.zeros(max(M.A.query()["nblk"], 1), np.int32)
+    dstart = np.zeros(npart.value + 1, np.int64)
+    rows = np.zeros(max(nu.value, 1), np.int32)
+    _check(L.vbarms_dd_layout(M.h, None, None, None, None, _hp(part), _hp(dstart), _hp(rows)))
+    return part[:M.A.query()["nblk"]], dstart, rows[:nu.value]
 
 
 def vbarms_apply_batched(Ms, xs, ys):

@@ -161,3 +161,23 @@ def test_dd_fgmres_converges():
         x, its, rr, st = oracle.fgmres(A, D, b, rtol=1e-8)
         assert st == oracle.OK and rr <= 1e-8
         assert np.linalg.norm(b - oracle.spmv(A, x)) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("t,lfil", [(1e-3, 10), (1e-4, -1)])
+def test_union_factorization_is_the_local_ones(t, lfil):
+    """Every step of the method stays inside a connected component, so one
+    factorization of the subdomains' block-diagonal union applies, row for
+    row, exactly what the separate local factorizations apply (the layout the
+    library factors)."""
+    A = _case(300, 4, seed=8)
+    D = oracle.DD(A, 5, 1, True, 3, t, lfil)
+    locs = [D.local(i) for i in range(5)]
+    U = oracle.block_diag(locs)
+    Pu = oracle.Prec(U, 3, t, lfil)
+    xu = np.random.default_rng(5).standard_normal(int(U.rsz.sum()))
+    yu = Pu.apply(xu)
+    o = 0
+    for i, M in enumerate(locs):
+        ni = int(M.rsz.sum())
+        assert np.array_equal(yu[o:o + ni], D.local_prec(i).apply(xu[o:o + ni])), f"subdomain {i}"
+        o += ni
