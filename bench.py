@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator factor")
     p.add_argument("--cpu-sample-nodes", type=int, default=0, help="oracle sample size (0 = auto)")
+    p.add_argument("--dd", type=int, default=0,
+                   help="domain decomposition (Section 5) with this many subdomains; 0 = one global VBARMS")
+    p.add_argument("--overlap", type=int, default=1, help="subdomain overlap levels with --dd (0 = block Jacobi)")
+    p.add_argument("--additive", action="store_true", help="with --dd: additive instead of restricted Schwarz")
     return p.parse_args()
 
 
@@ -165,13 +169,27 @@ def workload(name, scale, seed):
     return m, w
 
 
-def oracle_setup_seconds(m, w, restart=50):
+def dd_config(args):
+    """(nparts, overlap, restricted) of a Section 5 run, or None."""
+    return (args.dd, args.overlap, not args.additive) if getattr(args, "dd", 0) else None
+
+
+def dd_name(dd):
+    if dd is None:
+        return "vbarms"
+    return "bj" if dd[1] == 0 else ("ras" if dd[2] else "asm")
+
+
+def oracle_setup_seconds(m, w, restart=50, dd=None):
     """The CPU oracle (single-threaded) on matrix m: setup seconds and FGMRES."""
     import oracle
     t0 = time.perf_counter()
     c = oracle.compress(m.n, m.rowptr, m.colind, m.val, w["tau"])
     t1 = time.perf_counter()
-    P = oracle.Prec(c.A, w["nlev"], w["droptol"], w["lfil"])
+    if dd is None:
+        P = oracle.Prec(c.A, w["nlev"], w["droptol"], w["lfil"])
+    else:
+        P = oracle.DD(c.A, dd[0], dd[1], dd[2], w["nlev"], w["droptol"], w["lfil"])
     t2 = time.perf_counter()
     from paper_1508_02219_gb300 import synth
     b = synth.ones_rhs(m)
@@ -223,8 +241,9 @@ def run_reference(args):
     # full-size nnz: the generator's nnz scales with the node count
     scale_f = full_nodes / nodes
     times = []
+    dd = dd_config(args)
     for i in range(args.warmup + args.steps):
-        r = oracle_setup_seconds(m, w)
+        r = oracle_setup_seconds(m, w, dd=dd)
         if i >= args.warmup:
             times.append(r["compress_s"] + r["factor_s"])
     v = statistics.mean(times) * scale_f
@@ -233,7 +252,8 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "nodes": full_nodes, "ell": full["ell"], "tau": full["tau"],
-                   "nlev": full["nlev"], "droptol": full["droptol"], "lfil": full["lfil"]},
+                   "nlev": full["nlev"], "droptol": full["droptol"], "lfil": full["lfil"],
+                   **({"precond": dd_name(dd), "nparts": dd[0], "overlap": dd[1]} if dd else {})},
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"{nodes} of {full_nodes} nodes of the same generator, oracle setup "
                                    f"(compress+factor) seconds scaled by the node ratio {scale_f:.1f}"},
@@ -374,13 +394,19 @@ def main():
     bd = torch.from_numpy(b).to(dev)
     xd = torch.zeros(m.n, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
+    dd = dd_config(args)
+
+    def factor(A, precision):
+        if dd is None:
+            return V.vbarms_factor(A, w["nlev"], w["droptol"], w["lfil"], precision=precision)
+        return V.vbarms_dd_factor(A, dd[0], dd[1], dd[2], w["nlev"], w["droptol"], w["lfil"], precision=precision)
 
     def step(precision, solve=True, record=None):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record()
         A = V.vbarms_compress(m.n, rp, ci, vv, w["tau"])
         e[1].record()
-        P = V.vbarms_factor(A, w["nlev"], w["droptol"], w["lfil"], precision=precision)
+        P = factor(A, precision)
         e[2].record()
         its = rr = None
         if solve:
@@ -452,7 +478,7 @@ def main():
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             ev[0].record()
             A = V.vbarms_compress(m.n, prp.numpy(), pci.numpy(), pvv.numpy(), w["tau"])
-            P = V.vbarms_factor(A, w["nlev"], w["droptol"], w["lfil"], precision=prec)
+            P = factor(A, prec)
             # device-to-host read of the step's result: the last level's
             # per-block precision tags of the factor
             tags = P.vector(P.levels, "ptag")
@@ -476,7 +502,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ms, wl, nodes, full_nodes = cpu_sample(args.workload, args.seed, args.cpu_sample_nodes)
-        r = oracle_setup_seconds(ms, wl)
+        r = oracle_setup_seconds(ms, wl, dd=dd)
         cpu = {"value": (r["compress_s"] + r["factor_s"]) * (full_nodes / nodes), "unit": "s", "cores": 1,
                "kind": "oracle",
                "sample": f"{nodes} of {full_nodes} nodes of the same generator; oracle compress+factor seconds "
@@ -494,6 +520,7 @@ def main():
                        "nnz": m.nnz, "tau": w["tau"], "nlev": w["nlev"], "droptol": w["droptol"],
                        "lfil": w["lfil"], "factor_precision": prec, "fgmres": "FGMRES(50) rtol 1e-8",
                        "parallelism": "replicas" if ws > 1 else "single",
+                       **({"precond": dd_name(dd), "nparts": dd[0], "overlap": dd[1]} if dd else {}),
                        "l2": "inputs larger than L2 (CSR %.2f GB)" % ((m.nnz * 12 + m.n * 8) / 1e9)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
