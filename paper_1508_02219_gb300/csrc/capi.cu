@@ -161,8 +161,7 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
   if (track) ticket_order(dcur.p, X.A.nbr, ndom, tickets, s);
   ilut_last<T>(X, o.droptol, o.lfil, mixed, o.fp64_pivot_cond, o.wait_limit, s, dst, tickets.p);
   tm.mark(PH_ILUT);
-  level_order<T>(X.L, false, X.lorder, X.ldepth, s);
-  level_order<T>(X.U, true, X.uorder, X.udepth, s);
+  level_orders<T>(X, o.wait_limit, dst, s);
   fill += (double)(X.Dg.nval + X.L.nval + X.U.nval);
   tm.accumulate(P->phase_s);
   for (auto& r : P->krec) {

@@ -1355,38 +1355,182 @@ template void ilut_last<float>(LastDev<float>&, double, int, bool, double, uint6
 
 namespace vb {
 
-// Level order of a static triangular block pattern, computed on the host from
-// the block structure (one pass in dependency order), uploaded as a row list.
-template <typename T>
-void level_order(const VBDev<T>& M, bool backward, DBuf<int32_t>& order, int64_t& depth, cudaStream_t s) {
-  const int64_t p = M.nbr;
-  order.alloc(std::max<int64_t>(p, 1), s);
-  depth = 0;
-  if (p == 0) return;
-  std::vector<int64_t> bptr = d2h_vec(M.bptr.p, p + 1, s);
-  std::vector<int32_t> bcol = d2h_vec(M.bcol.p, M.nnzb, s);
-  std::vector<int32_t> lev(p, 0);
-  for (int64_t t = 0; t < p; ++t) {
-    const int64_t i = backward ? p - 1 - t : t;
-    int32_t l = 0;
-    for (int64_t b = bptr[i]; b < bptr[i + 1]; ++b) l = std::max(l, lev[bcol[b]] + 1);
-    lev[i] = l;
-    depth = std::max<int64_t>(depth, l + 1);
+namespace {
+
+// Level of every row in the dependency DAG of a triangular block pattern:
+// lev[i] = 1 + max lev[k] over the row's block columns k (0 without
+// blocks).  Warps of a persistent grid take the rows in dependency order
+// (forward, for L: ascending, every column below the row; backward, for U:
+// descending, every column above) and spin, bounded, on the columns' words:
+// a row publishes lev + 1 (-1 when it failed) in its word with one atomic
+// store, so the word is both flag and value and needs no fence.  The first
+// half of the grid does L, the second U, at the same time.
+struct DagSide {
+  int64_t p;
+  const int64_t* bptr;
+  const int32_t* bcol;
+  int32_t* word;  // 0 until published, then lev + 1 (or -1)
+  unsigned long long* tick;
+  int* depth;
+};
+
+// The published word, or 0 when the wait gave up (abort raised elsewhere, or
+// limit ns passed: DEV_ETIMEOUT recorded and abort raised).
+__device__ __forceinline__ int dag_wait(const int32_t* w, int* abort, unsigned long long limit, int* st) {
+  int v = ld_relaxed_gpu(w);
+  if (v == 0) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+      v = ld_relaxed_gpu(w);
+      if (v != 0) break;
+      if ((it & 63) == 0) {
+        if (*((volatile int*)abort) != 0) return 0;
+        if (global_ns() - t0 > limit) {
+          dev_fail(st, DEV_ETIMEOUT);
+          atomicExch(abort, 1);
+          return 0;
+        }
+      }
+    }
   }
-  // counting sort by level, rows ascending (forward) / descending (backward)
-  std::vector<int64_t> start(depth + 1, 0);
-  for (int64_t i = 0; i < p; ++i) start[lev[i] + 1]++;
-  for (int64_t l = 0; l < depth; ++l) start[l + 1] += start[l];
-  std::vector<int32_t> ord(p);
-  for (int64_t t = 0; t < p; ++t) {
-    const int64_t i = backward ? p - 1 - t : t;
-    ord[start[lev[i]]++] = (int32_t)i;
-  }
-  h2d(order.p, ord.data(), p, s);
-  VB_CUDA(cudaStreamSynchronize(s));
+  return v;
 }
 
-template void level_order<double>(const VBDev<double>&, bool, DBuf<int32_t>&, int64_t&, cudaStream_t);
-template void level_order<float>(const VBDev<float>&, bool, DBuf<int32_t>&, int64_t&, cudaStream_t);
+__global__ void k_dag_level(DagSide fw, DagSide bw, unsigned half, int* __restrict__ abort, unsigned long long limit,
+                            int* st) {
+  const bool back = blockIdx.x >= half;
+  const DagSide D = back ? bw : fw;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    long long t = 0;
+    if (lane == 0) t = (long long)atomicAdd(D.tick, 1ULL);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= D.p) break;
+    const int64_t i = back ? D.p - 1 - t : t;
+    int l = 0, bad = 0;
+    for (int64_t b = D.bptr[i] + lane; b < D.bptr[i + 1]; b += 32) {
+      const int v = dag_wait(D.word + D.bcol[b], abort, limit, st);
+      if (v <= 0)
+        bad = 1;
+      else
+        l = max(l, v);  // v = lev[k] + 1
+    }
+    l = warp_max_i(l);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      if (!bad) atomicMax(D.depth, l + 1);
+      atomicExch(D.word + i, bad ? -1 : l + 1);
+    }
+  }
+}
+
+// word = lev + 1 -> lev
+__global__ void k_dag_unword(int64_t n, int32_t* __restrict__ w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] -= 1;
+}
+
+// Stable least-significant-digit radix sort of row ids by their level, 8
+// bits a pass: per block of RS_T ids a digit histogram, one scan over
+// (digit, block), then every id goes to its digit's range after the ids of
+// earlier blocks and of earlier warps and lanes of its own block.
+constexpr int RS_T = 256;
+
+__global__ void k_rs_init(int64_t n, bool descending, int32_t* __restrict__ v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (int32_t)(descending ? n - 1 - i : i);
+}
+
+__global__ void __launch_bounds__(RS_T) k_rs_hist(int64_t n, const int32_t* __restrict__ v,
+                                                  const int32_t* __restrict__ key, int shift, int64_t nblk,
+                                                  int32_t* __restrict__ hist) {
+  __shared__ int h[256];
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)RS_T + threadIdx.x;
+  if (e < n) atomicAdd(&h[(key[v[e]] >> shift) & 255], 1);
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * nblk + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(int64_t n, const int32_t* __restrict__ v,
+                                                     const int32_t* __restrict__ key, int shift, int64_t nblk,
+                                                     const int64_t* __restrict__ base, int32_t* __restrict__ out) {
+  __shared__ int cnt[RS_T / 32][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int x = threadIdx.x; x < (RS_T / 32) * 256; x += blockDim.x) (&cnt[0][0])[x] = 0;
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)RS_T + threadIdx.x;
+  const bool has = e < n;
+  const int32_t id = has ? v[e] : 0;
+  const int d = has ? (key[id] >> shift) & 255 : 256;
+  const unsigned peers = __match_any_sync(0xffffffffu, d);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  if (has && rank == 0) cnt[warp][d] = __popc(peers);
+  __syncthreads();
+  if (has) {
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += cnt[w][d];
+    out[base[(int64_t)d * nblk + blockIdx.x] + off + rank] = id;
+  }
+}
+
+}  // namespace
+
+// Level orders of the last level's L (forward sweep) and U (backward sweep)
+// on the device: the levels of both dependency DAGs (k_dag_level), then each
+// side's rows sorted by level, rows ascending (L) / descending (U) within a
+// level.
+template <typename T>
+void level_orders(LastDev<T>& X, uint64_t wait_limit, int* dst, cudaStream_t s) {
+  const int64_t p = X.L.nbr;
+  X.lorder.alloc(std::max<int64_t>(p, 1), s);
+  X.uorder.alloc(std::max<int64_t>(p, 1), s);
+  X.ldepth = X.udepth = 0;
+  if (p == 0) return;
+  DBuf<int32_t> lev(2 * p, s);
+  DBuf<unsigned long long> tick(2, s);
+  DBuf<int> abort(1, s), dmax(2, s);
+  lev.zero();
+  tick.zero();
+  abort.zero();
+  dmax.zero();
+  int dev = 0, nsm = 0;
+  VB_CUDA(cudaGetDevice(&dev));
+  VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned half = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 4, (p + 7) / 8));
+  DagSide fw{p, X.L.bptr.p, X.L.bcol.p, lev.p, tick.p, dmax.p};
+  DagSide bw{p, X.U.bptr.p, X.U.bcol.p, lev.p + p, tick.p + 1, dmax.p + 1};
+  launch(k_dag_level, 2 * half, 256, 0, s, fw, bw, half, abort.p, (unsigned long long)wait_limit, dst);
+  VB_LAUNCH_CHECK();
+  check_status(dst, s, "vbarms_factor: level order of the triangular sweeps");
+  launch(k_dag_unword, grid_for(2 * p, 256), 256, 0, s, 2 * p, lev.p);
+  VB_LAUNCH_CHECK();
+  const std::vector<int> dd = d2h_vec(dmax.p, 2, s);
+  X.ldepth = dd[0];
+  X.udepth = dd[1];
+  const int64_t nblk = (p + RS_T - 1) / RS_T;
+  DBuf<int32_t> hist(256 * nblk, s);
+  DBuf<int64_t> base(256 * nblk + 1, s);
+  for (int side = 0; side < 2; ++side) {
+    const int32_t* key = lev.p + side * p;
+    const int64_t depth = side == 0 ? X.ldepth : X.udepth;
+    DBuf<int32_t> a(p, s), b(p, s);
+    launch(k_rs_init, grid_for(p, 256), 256, 0, s, p, side == 1, a.p);
+    VB_LAUNCH_CHECK();
+    for (int shift = 0; shift < 31 && (1LL << shift) < depth; shift += 8) {
+      launch(k_rs_hist, (unsigned)nblk, RS_T, 0, s, p, a.p, key, shift, nblk, hist.p);
+      VB_LAUNCH_CHECK();
+      scan_i32_to_i64(hist.p, base.p, 256 * nblk, s);
+      launch(k_rs_scatter, (unsigned)nblk, RS_T, 0, s, p, a.p, key, shift, nblk, base.p, b.p);
+      VB_LAUNCH_CHECK();
+      std::swap(a, b);
+    }
+    (side == 0 ? X.lorder : X.uorder) = std::move(a);
+  }
+}
+
+template void level_orders<double>(LastDev<double>&, uint64_t, int*, cudaStream_t);
+template void level_orders<float>(LastDev<float>&, uint64_t, int*, cudaStream_t);
 
 }  // namespace vb

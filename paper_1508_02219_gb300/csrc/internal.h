@@ -52,10 +52,11 @@ struct LastDev {
   int64_t ldepth = 0, udepth = 0;
 };
 
-// Level order of the rows of a triangular block pattern (forward: row i
-// depends on its columns k < i; backward: on its columns j > i).
+// Level orders of the last level's triangular sweeps (L forward: row i
+// depends on its columns k < i; U backward: on its columns j > i), computed
+// on the device with bounded waits (wait_limit ns; failures go to dst).
 template <typename T>
-void level_order(const VBDev<T>& M, bool backward, DBuf<int32_t>& order, int64_t& depth, cudaStream_t s);
+void level_orders(LastDev<T>& X, uint64_t wait_limit, int* dst, cudaStream_t s);
 
 struct FactorOpts {
   int nlev;
