@@ -47,6 +47,7 @@ def lib():
             sig = {
                 "or_last_status": (i32, []),
                 "or_compress": (vp, [i64, vp, vp, vp, d]),
+                "or_graph_compress": (vp, [i64, vp, vp, vp, d]),
                 "or_cmp_free": (None, [vp]),
                 "or_cmp_nblk": (i64, [vp]),
                 "or_cmp_perm": (None, [vp, vp, vp]),
@@ -175,13 +176,23 @@ class Compressed:
 
 def compress(n, rowptr, colind, val, tau) -> Compressed:
     """Step 1: angle-based compression (Section 2.1) and P_B A P_B^T (Eq. 3)."""
+    return _compressed(lib().or_compress, "compress", n, rowptr, colind, val, tau)
+
+
+def graph_compress(n, rowptr, colind, val, mu) -> Compressed:
+    """Graph-based compression with minimum block density mu (Section 2.2,
+    Alg. 1) and P_B A P_B^T."""
+    return _compressed(lib().or_graph_compress, "graph_compress", n, rowptr, colind, val, mu)
+
+
+def _compressed(fn, what, n, rowptr, colind, val, param) -> Compressed:
     L = lib()
     rowptr = np.ascontiguousarray(rowptr, np.int64)
     colind = np.ascontiguousarray(colind, np.int32)
     val = np.ascontiguousarray(val, np.float64)
-    h = L.or_compress(int(n), _p(rowptr), _p(colind), _p(val), float(tau))
+    h = fn(int(n), _p(rowptr), _p(colind), _p(val), float(param))
     if not h:
-        raise OracleError(L.or_last_status(), "compress")
+        raise OracleError(L.or_last_status(), what)
     p = L.or_cmp_nblk(h)
     perm = np.zeros(int(n), np.int32)
     bsz = np.zeros(p, np.int32)

@@ -10,7 +10,8 @@
 // Every floating-point operation is a separate IEEE round-to-nearest step
 // (build with -ffp-contract=off), evaluated in the order written here.
 //
-// Readings of points the paper leaves open (R1-R9; D1-D3 for Section 5):
+// Readings of points the paper leaves open (R1-R9; G1-G5 for Section 2.2 at graph_compress;
+// D1-D3 for Section 5):
 //  R1  similarity of rows i,j (Section 2.1): cos = |P_i n P_j| / sqrt(|P_i||P_j|)
 //      on the stored pattern of the rows; j joins i's group iff cos >= tau,
 //      tested exactly as (double)(c*c) >= (tau*tau) * (double)(|P_i||P_j|).
@@ -224,17 +225,25 @@ struct Compressed {
   double av_bd = 0, av_bs = 0;
 };
 
-int compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau,
-             Compressed& out) {
-  if (n < 0 || !(tau > 0.0 && tau <= 1.0)) return EINVAL;
-  if (n > 0 && rowptr[0] != 0) return EINVAL;
+bool csr_ok(int64_t n, const int64_t* rowptr, const int32_t* colind) {
+  if (n < 0) return false;
+  if (n > 0 && rowptr[0] != 0) return false;
   for (int64_t i = 0; i < n; ++i) {
-    if (rowptr[i + 1] < rowptr[i]) return EINVAL;
+    if (rowptr[i + 1] < rowptr[i]) return false;
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      if (colind[p] < 0 || colind[p] >= n) return EINVAL;
-      if (p > rowptr[i] && colind[p] <= colind[p - 1]) return EINVAL;
+      if (colind[p] < 0 || colind[p] >= n) return false;
+      if (p > rowptr[i] && colind[p] <= colind[p - 1]) return false;
     }
   }
+  return true;
+}
+
+void assemble(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+              const std::vector<std::vector<int32_t>>& members, Compressed& out);
+
+int compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau,
+             Compressed& out) {
+  if (!(tau > 0.0 && tau <= 1.0) || !csr_ok(n, rowptr, colind)) return EINVAL;
   // Column lists of the pattern matrix C (rows having a stored entry in col c).
   std::vector<int64_t> cptr(n + 1, 0);
   for (int64_t p = 0; p < (n ? rowptr[n] : 0); ++p) cptr[colind[p] + 1]++;
@@ -277,6 +286,15 @@ int compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const doub
     if (leader[i] == i) blk_of_leader[i] = p++;
   std::vector<std::vector<int32_t>> members(p);
   for (int64_t i = 0; i < n; ++i) members[blk_of_leader[leader[i]]].push_back((int32_t)i);
+  assemble(n, rowptr, colind, val, members, out);
+  return OK;
+}
+
+// The block permutation of the given groups (in the given order, members in
+// the given order) and the VBCSR of P_B A P_B^T, with av_bd and av_bs.
+void assemble(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+              const std::vector<std::vector<int32_t>>& members, Compressed& out) {
+  const int32_t p = (int32_t)members.size();
   out.perm.clear();
   out.bsz.assign(p, 0);
   std::vector<int32_t> blk(n), off(n);
@@ -318,6 +336,130 @@ int compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const doub
   const double nnz = n ? (double)rowptr[n] : 0.0;
   out.av_bd = padded > 0 ? nnz / padded : 0.0;
   out.av_bs = p > 0 ? (double)n / (double)p : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Graph-based compression (Section 2.2, Alg. 1), readings G1-G5:
+//  G1 adj(i) is the closed neighbourhood of i in the graph of A + A^T
+//     ({i} plus every j with a stored a_ij or a_ji); the key of i is
+//     chk(i) = sum of adj(i).
+//  G2 supernodes: vertices scanned by (key, index); the first unassigned
+//     vertex of a key opens a supernode and takes every later vertex of the
+//     same key with an identical adj (so a supernode's first vertex is its
+//     smallest).
+//  G3 merge phase: supernodes visited in ascending order of their smallest
+//     vertex; X's candidates are the supernodes (as they are when X's turn
+//     starts) whose adjacency meets X, i.e. the owners of adj(X), X excluded,
+//     in ascending order of their smallest vertex, each tried once.
+//  G4 X and Z merge iff the density of the merged supernode's block row and
+//     column, N / T with T and N of Section 2.2, is at least mu, tested as
+//     (double)N >= mu * (double)T.
+//  G5 blocks in ascending order of their smallest vertex, vertices ascending.
+struct GNode {
+  std::vector<int32_t> v;    // vertices, ascending
+  std::vector<int32_t> adj;  // union of adj(v), ascending
+  int64_t deg = 0;           // sum of |adj(v)|
+  int64_t inner = 0;         // sum of |adj(v) n X|
+  bool alive = true;
+};
+
+// T and N of a vertex set S with union adjacency a, degree sum deg and inner
+// count inner (Section 2.2): rows and columns spanned, nonzeros spanned.
+inline int64_t span_T(int64_t s, int64_t a) { return 2 * a * s - s * s; }
+inline int64_t span_N(int64_t deg, int64_t inner) { return 2 * deg - inner; }
+
+int graph_compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double mu,
+                   Compressed& out) {
+  if (!(mu >= 0.0) || !csr_ok(n, rowptr, colind)) return EINVAL;
+  // G1: closed neighbourhoods in A + A^T
+  std::vector<std::vector<int32_t>> adj(n);
+  for (int64_t i = 0; i < n; ++i) {
+    adj[i].push_back((int32_t)i);
+    for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+      adj[i].push_back(colind[q]);
+      adj[colind[q]].push_back((int32_t)i);
+    }
+  }
+  std::vector<int64_t> key(n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    std::sort(adj[i].begin(), adj[i].end());
+    adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
+    for (int32_t j : adj[i]) key[i] += j;
+  }
+  // G2: the checksum scan
+  std::vector<int32_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  std::vector<char> done(n, 0);
+  std::vector<GNode> V;
+  for (int64_t x = 0; x < n; ++x) {
+    const int32_t i = order[x];
+    if (done[i]) continue;
+    GNode Y;
+    Y.v.push_back(i);
+    done[i] = 1;
+    for (int64_t y = x + 1; y < n && key[order[y]] == key[i]; ++y) {
+      const int32_t j = order[y];
+      if (!done[j] && adj[j] == adj[i]) {
+        Y.v.push_back(j);
+        done[j] = 1;
+      }
+    }
+    V.push_back(std::move(Y));
+  }
+  // G3: supernodes by their smallest vertex
+  std::sort(V.begin(), V.end(), [](const GNode& a, const GNode& b) { return a.v[0] < b.v[0]; });
+  std::vector<int32_t> owner(n);
+  for (size_t z = 0; z < V.size(); ++z) {
+    GNode& Z = V[z];
+    std::sort(Z.v.begin(), Z.v.end());
+    for (int32_t v : Z.v) owner[v] = (int32_t)z;
+    Z.adj = adj[Z.v[0]];  // identical for every vertex of Z
+    for (int32_t v : Z.v) Z.deg += (int64_t)adj[v].size();
+  }
+  for (size_t z = 0; z < V.size(); ++z) {
+    V[z].inner = 0;
+    for (int32_t v : V[z].v)
+      for (int32_t u : adj[v]) V[z].inner += owner[u] == (int32_t)z ? 1 : 0;
+  }
+  for (size_t x = 0; x < V.size(); ++x) {
+    if (!V[x].alive) continue;
+    std::vector<int32_t> cand;
+    for (int32_t u : V[x].adj)
+      if (owner[u] != (int32_t)x) cand.push_back(owner[u]);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) { return V[a].v[0] < V[b].v[0]; });
+    for (int32_t z : cand) {
+      GNode& X = V[x];
+      GNode& Z = V[z];
+      std::vector<int32_t> un;
+      std::set_union(X.adj.begin(), X.adj.end(), Z.adj.begin(), Z.adj.end(), std::back_inserter(un));
+      int64_t cross = 0;  // sum over v in Z of |adj(v) n X|
+      for (int32_t v : Z.v)
+        for (int32_t u : adj[v]) cross += owner[u] == (int32_t)x ? 1 : 0;
+      const int64_t sz = (int64_t)(X.v.size() + Z.v.size());
+      const int64_t T = span_T(sz, (int64_t)un.size());
+      const int64_t N = span_N(X.deg + Z.deg, X.inner + Z.inner + 2 * cross);
+      if ((double)N >= mu * (double)T) {
+        for (int32_t v : Z.v) owner[v] = (int32_t)x;
+        std::vector<int32_t> mv;
+        std::merge(X.v.begin(), X.v.end(), Z.v.begin(), Z.v.end(), std::back_inserter(mv));
+        X.v.swap(mv);
+        X.adj.swap(un);
+        X.deg += Z.deg;
+        X.inner += Z.inner + 2 * cross;
+        Z.alive = false;
+      }
+    }
+  }
+  // G5
+  std::vector<std::vector<int32_t>> members;
+  for (auto& X : V)
+    if (X.alive) members.push_back(X.v);
+  std::sort(members.begin(), members.end(),
+            [](const std::vector<int32_t>& a, const std::vector<int32_t>& b) { return a[0] < b[0]; });
+  assemble(n, rowptr, colind, val, members, out);
   return OK;
 }
 
@@ -944,6 +1086,15 @@ int or_last_status() { return g_last_status; }
 void* or_compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau) {
   auto* c = new Compressed();
   g_last_status = compress(n, rowptr, colind, val, tau, *c);
+  if (g_last_status != OK) {
+    delete c;
+    return nullptr;
+  }
+  return c;
+}
+void* or_graph_compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double mu) {
+  auto* c = new Compressed();
+  g_last_status = graph_compress(n, rowptr, colind, val, mu, *c);
   if (g_last_status != OK) {
     delete c;
     return nullptr;
