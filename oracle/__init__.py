@@ -48,6 +48,7 @@ def lib():
                 "or_last_status": (i32, []),
                 "or_compress": (vp, [i64, vp, vp, vp, d]),
                 "or_graph_compress": (vp, [i64, vp, vp, vp, d]),
+                "or_compress_two_pass": (vp, [i64, vp, vp, vp, d]),
                 "or_cmp_free": (None, [vp]),
                 "or_cmp_nblk": (i64, [vp]),
                 "or_cmp_perm": (None, [vp, vp, vp]),
@@ -177,6 +178,12 @@ class Compressed:
 def compress(n, rowptr, colind, val, tau) -> Compressed:
     """Step 1: angle-based compression (Section 2.1) and P_B A P_B^T (Eq. 3)."""
     return _compressed(lib().or_compress, "compress", n, rowptr, colind, val, tau)
+
+
+def compress_two_pass(n, rowptr, colind, val, tau) -> Compressed:
+    """The two-pass variant of the angle method (Section 2.1): identical
+    patterns grouped first, then unassigned rows added to a group by angle."""
+    return _compressed(lib().or_compress_two_pass, "compress_two_pass", n, rowptr, colind, val, tau)
 
 
 def graph_compress(n, rowptr, colind, val, mu) -> Compressed:

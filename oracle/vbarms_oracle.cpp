@@ -10,8 +10,8 @@
 // Every floating-point operation is a separate IEEE round-to-nearest step
 // (build with -ffp-contract=off), evaluated in the order written here.
 //
-// Readings of points the paper leaves open (R1-R9; G1-G5 for Section 2.2 at graph_compress;
-// D1-D3 for Section 5):
+// Readings of points the paper leaves open (R1-R9; T1-T3 at compress_two_pass and G1-G5
+// at graph_compress; D1-D3 for Section 5):
 //  R1  similarity of rows i,j (Section 2.1): cos = |P_i n P_j| / sqrt(|P_i||P_j|)
 //      on the stored pattern of the rows; j joins i's group iff cos >= tau,
 //      tested exactly as (double)(c*c) >= (tau*tau) * (double)(|P_i||P_j|).
@@ -336,6 +336,86 @@ void assemble(int64_t n, const int64_t* rowptr, const int32_t* colind, const dou
   const double nnz = n ? (double)rowptr[n] : 0.0;
   out.av_bd = padded > 0 ? nnz / padded : 0.0;
   out.av_bs = p > 0 ? (double)n / (double)p : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Two-pass variant of the angle method (Section 2.1), readings T1-T3:
+//  T1 pass 1 groups rows with identical stored patterns P_i (the rows of the
+//     pattern matrix); a class of two or more rows is a group, the rows of
+//     one-row classes are unassigned.
+//  T2 pass 2 takes the unassigned rows in natural order; each joins the first
+//     group (groups in ascending order of their smallest row) whose common
+//     pattern P_g passes the angle test of R1 against P_j; the groups keep
+//     their pattern; a row that fits no group (and an empty row) stays alone.
+//  T3 blocks in ascending order of their smallest row, rows ascending.
+int compress_two_pass(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau,
+                      Compressed& out) {
+  if (!(tau > 0.0 && tau <= 1.0) || !csr_ok(n, rowptr, colind)) return EINVAL;
+  // T1: classes of identical patterns (rows compared after sorting by pattern)
+  std::vector<int32_t> rows(n);
+  std::iota(rows.begin(), rows.end(), 0);
+  auto pat_less = [&](int32_t a, int32_t b) {
+    return std::lexicographical_compare(colind + rowptr[a], colind + rowptr[a + 1], colind + rowptr[b],
+                                        colind + rowptr[b + 1]);
+  };
+  auto pat_eq = [&](int32_t a, int32_t b) {
+    return rowptr[a + 1] - rowptr[a] == rowptr[b + 1] - rowptr[b] &&
+           std::equal(colind + rowptr[a], colind + rowptr[a + 1], colind + rowptr[b]);
+  };
+  std::stable_sort(rows.begin(), rows.end(), pat_less);
+  std::vector<std::vector<int32_t>> groups;  // pass-1 groups (two or more rows)
+  std::vector<char> assigned(n, 0);
+  for (int64_t a = 0; a < n;) {
+    int64_t b = a + 1;
+    while (b < n && pat_eq(rows[a], rows[b])) ++b;
+    if (b - a >= 2 && rowptr[rows[a] + 1] > rowptr[rows[a]]) {
+      std::vector<int32_t> g(rows.begin() + a, rows.begin() + b);
+      std::sort(g.begin(), g.end());
+      for (int32_t r : g) assigned[r] = 1;
+      groups.push_back(std::move(g));
+    }
+    a = b;
+  }
+  std::sort(groups.begin(), groups.end(),
+            [](const std::vector<int32_t>& x, const std::vector<int32_t>& y) { return x[0] < y[0]; });
+  const size_t ng = groups.size();
+  std::vector<int32_t> ref(ng);  // a row carrying each group's pattern
+  for (size_t g = 0; g < ng; ++g) ref[g] = groups[g][0];
+  // T2: unassigned rows against the groups, R1's exact test
+  const double tau2 = tau * tau;
+  std::vector<std::vector<int32_t>> joined(ng);
+  std::vector<std::vector<int32_t>> members;
+  std::vector<char> mark(n, 0);
+  for (int64_t j = 0; j < n; ++j) {
+    if (assigned[j]) continue;
+    const int64_t nj = rowptr[j + 1] - rowptr[j];
+    int64_t hit = -1;
+    if (nj > 0) {
+      for (int64_t q = rowptr[j]; q < rowptr[j + 1]; ++q) mark[colind[q]] = 1;
+      for (size_t g = 0; g < ng && hit < 0; ++g) {
+        const int32_t r = ref[g];
+        const int64_t nr = rowptr[r + 1] - rowptr[r];
+        int64_t c = 0;
+        for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) c += mark[colind[q]];
+        if ((double)(c * c) >= tau2 * (double)(nj * nr)) hit = (int64_t)g;
+      }
+      for (int64_t q = rowptr[j]; q < rowptr[j + 1]; ++q) mark[colind[q]] = 0;
+    }
+    if (hit >= 0)
+      joined[hit].push_back((int32_t)j);
+    else
+      members.push_back({(int32_t)j});
+  }
+  for (size_t g = 0; g < ng; ++g) {
+    std::vector<int32_t> m;
+    std::merge(groups[g].begin(), groups[g].end(), joined[g].begin(), joined[g].end(), std::back_inserter(m));
+    members.push_back(std::move(m));
+  }
+  // T3
+  std::sort(members.begin(), members.end(),
+            [](const std::vector<int32_t>& x, const std::vector<int32_t>& y) { return x[0] < y[0]; });
+  assemble(n, rowptr, colind, val, members, out);
+  return OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1086,6 +1166,15 @@ int or_last_status() { return g_last_status; }
 void* or_compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau) {
   auto* c = new Compressed();
   g_last_status = compress(n, rowptr, colind, val, tau, *c);
+  if (g_last_status != OK) {
+    delete c;
+    return nullptr;
+  }
+  return c;
+}
+void* or_compress_two_pass(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau) {
+  auto* c = new Compressed();
+  g_last_status = compress_two_pass(n, rowptr, colind, val, tau, *c);
   if (g_last_status != OK) {
     delete c;
     return nullptr;
