@@ -36,3 +36,15 @@ def test_invalid_arguments_rejected_on_host():
     with pytest.raises(vbarms.VbarmsError) as e:
         vbarms.vbarms_compress(-1, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), 1.0)
     assert e.value.status == vbarms.VB_EINVAL
+    # NULL handles of the other entry points, rejected before any device work
+    import ctypes as C
+    L = vbarms.lib()
+    h = C.c_void_p()
+    o = vbarms.make_opts()
+    assert L.vbarms_factor(None, 2, 1e-3, -1, C.byref(o), C.byref(h)) == vbarms.VB_EINVAL
+    assert L.vbarms_dd_factor(None, 4, 1, 1, 2, 1e-3, -1, C.byref(o), C.byref(h)) == vbarms.VB_EINVAL
+    assert L.vbarms_dd_layout(None, None, None, None, None, None, None, None) == vbarms.VB_EINVAL
+    assert L.vbarms_apply(None, None, None) == vbarms.VB_EINVAL
+    assert L.vbarms_factor_batched(-1, None, None, None, None, C.byref(o), None) == vbarms.VB_EINVAL
+    assert L.fgmres_solve(None, None, None, None, 1e-8, 50, 1000, None, None) == vbarms.VB_EINVAL
+    assert h.value is None
