@@ -174,10 +174,13 @@ def geometric(n_nodes: int, ell: int = 6, seed: int = 0, approx: bool = True,
     every kept entry gets additive N(0, noise_var) noise, so node blocks are
     only approximately dense.
 
-    ``dominance`` (e.g. 1.5) replaces each diagonal block by s_a * Z_a with
-    Z_a ~ N(0, 1) (same drop mask) and s_a = dominance * sum_b ||A_ab||_F /
-    ||Z_a||_F; a seeded fraction ``ill_frac`` of nodes instead get a dense
-    Z_a = U diag(1, ..., 1, 1/ill_cond) V^T with random orthogonal U, V.
+    ``dominance`` (e.g. 1.5) replaces each diagonal block by a dense
+    D_a = s_a U diag(sig) V^T with random orthogonal U, V, sig ~ U[1, 2] and
+    s_a = dominance * sum_b ||A_ab||_F / min(sig), so that
+    sigma_min(D_a) = dominance * sum_b ||A_ab||_F (block diagonal dominance in
+    the 2-norm); a seeded fraction ``ill_frac`` of nodes instead get
+    sig = (1, ..., 1, 1/ill_cond) and s_a = dominance * sum_b ||A_ab||_F, so
+    kappa_2(D_a) = ill_cond exactly.
     """
     from scipy.spatial import cKDTree
     rng = np.random.default_rng(seed)
