@@ -181,18 +181,18 @@ __global__ void k_dd_copies(int64_t p, int nparts, int nw, const uint32_t* __res
     int c = 0;
     for (int w = 0; w < nw; ++w) {
       uint32_t word = mask[I * nw + w];
-      if (!FILL) {
+      if constexpr (!FILL) {
         c += __popc(word);
-        continue;
-      }
-      while (word) {
-        const int i = w * 32 + __ffs(word) - 1;
-        word &= word - 1;
-        clist[cptr[I] + c] = (int32_t)bsearch_i32(ug, dstart[i], dstart[i + 1], (int32_t)I);
-        ++c;
+      } else {
+        while (word) {
+          const int i = w * 32 + __ffs(word) - 1;
+          word &= word - 1;
+          clist[cptr[I] + c] = (int32_t)bsearch_i32(ug, dstart[i], dstart[i + 1], (int32_t)I);
+          ++c;
+        }
       }
     }
-    if (!FILL) ccnt[I] = c;
+    if constexpr (!FILL) ccnt[I] = c;
   }
 }
 
