@@ -181,3 +181,28 @@ def test_union_factorization_is_the_local_ones(t, lfil):
         ni = int(M.rsz.sum())
         assert np.array_equal(yu[o:o + ni], D.local_prec(i).apply(xu[o:o + ni])), f"subdomain {i}"
         o += ni
+
+
+def test_more_subdomains_than_block_rows():
+    """Empty subdomains are skipped; with exact local solves the restricted sum
+    over the non-empty ones is the dense formula, and the ranges still cover
+    every block row once."""
+    A = _case(20, 3, seed=6)
+    nparts = 2 * A.nbr
+    D = oracle.DD(A, nparts, 1, True, 2, 0.0, -1)
+    part = D.part()
+    assert len(part) == A.nbr and len(set(part.tolist())) < nparts, "some subdomains are empty"
+    assert sum(len(np.flatnonzero(part == i)) for i in range(nparts)) == A.nbr
+    Ad = A.dense()
+    x = np.random.default_rng(7).standard_normal(Ad.shape[0])
+    ref = np.zeros_like(x)
+    for i in range(nparts):
+        W = D.rows(i)
+        if len(W) == 0:
+            continue
+        s = _scalar_rows(A, W)
+        z = np.linalg.solve(Ad[np.ix_(s, s)], x[s])
+        keep = np.isin(s, _scalar_rows(A, np.flatnonzero(part == i)))
+        ref[s[keep]] += z[keep]
+    y = D.apply(x)
+    assert np.linalg.norm(y - ref) <= 1e-10 * np.linalg.norm(ref)
