@@ -378,3 +378,116 @@ def test_schur_drop_all_one_level_is_the_default():
     P1 = oracle.Prec(c.A, 1, 1e-3, 4, 0.0, True)
     for lev, name in [(0, "S"), (0, "W"), (1, "L"), (1, "U"), (1, "D")]:
         assert np.array_equal(P0.mat(lev, name).val, P1.mat(lev, name).val), name
+
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def test_ilut_hand_derived_three_block_rows():
+    """Block ILUT (Section 3 dropping rule, Alg. 3 in block form) on a case
+    whose kept and dropped blocks straddle t m n, every value derived by hand
+    in tests/golden/ilut_three_block_rows.json."""
+    import json
+    g = json.load(open(__import__("os").path.join(GOLDEN, "ilut_three_block_rows.json")))
+    from conftest import vb_from_dense_blocks
+    vb = vb_from_dense_blocks(np.array(g["A"], dtype=float), g["block_sizes"])
+    P = oracle.Prec(vb, 0, g["t"], -1)
+    assert P.levels == 0
+    assert np.array_equal(P.vec(0, "r"), np.ones(4)) and np.array_equal(P.vec(0, "c"), np.ones(4))
+    for name in ("L", "U"):
+        M = P.mat(0, name)
+        assert M.bptr.tolist() == g[name]["bptr"], name
+        assert M.bcol.tolist() == g[name]["bcol"], name
+        np.testing.assert_allclose(M.val, g[name]["val"], rtol=0, atol=1e-15, err_msg=name)
+    from fractions import Fraction
+    np.testing.assert_allclose(P.mat(0, "D").val, [float(Fraction(x)) for x in g["D_exact"]], rtol=0, atol=1e-15)
+    assert P.vec(0, "piv").tolist() == g["D"]["piv"]
+
+
+def _pivot_dense(P, lev, A):
+    """P^T L U of every last-level pivot block, as a dict of dense blocks."""
+    Dg, piv = P.mat(lev, "D"), P.vec(lev, "piv")
+    off = _offsets(A.rsz)
+    out = {}
+    for i in range(Dg.nbr):
+        lu = Dg.val[Dg.voff[Dg.bptr[i]]:Dg.voff[Dg.bptr[i] + 1]].reshape(A.rsz[i], A.rsz[i])
+        L, U = lu_parts(lu)
+        pp = piv_perm(piv[off[i]:off[i + 1]])
+        out[i] = np.eye(len(pp))[:, pp] @ L @ U
+    return out
+
+
+@pytest.mark.parametrize("dominance", [None, 1.5])
+@pytest.mark.parametrize("t,lfil", [(1e-3, -1), (1e-2, -1), (1e-2, 5), (3e-2, 3)])
+def test_ilut_kept_set_row_by_row(t, lfil, dominance):
+    """Which blocks the block ILUT keeps (Section 3 dropping rule, Alg. 3):
+    with R = (I + L)(D + U) - A, on every row whose L part was not trimmed
+    by lfil,
+      - a stored U block has ||U_ij||_F >= t n_i n_j, and an unstored U
+        position carries the dropped working-row block, ||R_ij||_F < t n_i n_j
+        (or, when lfil trimmed the U part, ranks after every stored block by
+        norm descending, column ascending);
+      - a stored L block has ||L_ik||_F >= t n_i n_k, and at an unstored L
+        position the multiplier that was dropped, -R_ik D_k^{-1}, has norm
+        < t n_i n_k;
+      - the diagonal block and every stored block have R = 0."""
+    m, c = compressed(60, 3, seed=4, dominance=dominance)
+    P = oracle.Prec(c.A, 0, t, lfil)
+    A, LU, Lm, Um = last_level_dense(P)
+    R = LU - A.dense()
+    off = _offsets(A.rsz)
+    Dk = _pivot_dense(P, 0, A)
+    Lb, Ub = _block_map(Lm), _block_map(Um)
+    nL, nU = np.diff(Lm.bptr), np.diff(Um.bptr)
+    slack = 1 + 1e-9
+    checked = dropped_u = dropped_m = near_u = near_m = 0
+    noise = 1e-13
+    for i in range(A.nbr):
+        if lfil >= 0 and nL[i] >= lfil:
+            continue  # its L part may have been trimmed after use
+        checked += 1
+        ni = A.rsz[i]
+        blk = lambda j: R[off[i]:off[i + 1], off[j]:off[j + 1]]
+        assert np.abs(blk(i)).max() <= 1e-12, (i, "diagonal")
+        stored_u = []
+        for j in range(i + 1, A.nbr):
+            thr = t * ni * A.rsz[j]
+            if (i, j) in Ub:
+                u = Ub[(i, j)]
+                assert np.linalg.norm(u) >= thr / slack, (i, j, "stored U below threshold")
+                assert np.abs(blk(j)).max() <= 1e-12, (i, j, "stored U block not exact")
+                stored_u.append((np.linalg.norm(u), j))
+                near_u += np.linalg.norm(u) < 3 * thr
+        trimmed_u = lfil >= 0 and nU[i] == lfil
+        for j in range(i + 1, A.nbr):
+            if (i, j) in Ub:
+                continue
+            r = np.linalg.norm(blk(j))
+            if r <= noise:
+                continue
+            dropped_u += 1
+            thr = t * ni * A.rsz[j]
+            if r >= thr * slack:
+                assert trimmed_u, (i, j, f"unstored U block of norm {r:.3e} >= {thr:.3e}")
+                for (sn, sj) in stored_u:
+                    assert sn > r * slack or (abs(sn - r) <= 1e-12 * r and sj < j), (i, j, "lfil rank")
+        for k in range(i):
+            thr = t * ni * A.rsz[k]
+            if (i, k) in Lb:
+                lk = Lb[(i, k)]
+                assert np.linalg.norm(lk) >= thr / slack, (i, k, "stored multiplier below threshold")
+                assert np.abs(blk(k)).max() <= 1e-12, (i, k, "stored L block not exact")
+                near_m += np.linalg.norm(lk) < 2 * thr
+            else:
+                r = blk(k)
+                if np.linalg.norm(r) <= noise:
+                    continue
+                mult = -r @ np.linalg.inv(Dk[k])
+                dropped_m += 1
+                assert np.linalg.norm(mult) < thr * slack, (i, k, "unstored multiplier above threshold")
+    # the case pins something: dropped blocks of both kinds, and kept blocks
+    # close enough to the threshold that a threshold 3x (U) or 2x (multiplier)
+    # larger would drop them
+    print(f"rows {checked}, dropped U {dropped_u}, dropped multipliers {dropped_m}, near U {near_u}, near L {near_m}")
+    assert checked >= 20 and dropped_u >= 5 and dropped_m >= 5 and near_u >= 1 and near_m >= 1, \
+        (checked, dropped_u, dropped_m, near_u, near_m)
