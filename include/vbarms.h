@@ -23,6 +23,12 @@
  *  - Device work is enqueued on the stream given at creation (a cudaStream_t
  *    passed as void*, NULL = the legacy default stream).  Calls that return
  *    sizes or statuses synchronize that stream.
+ *  - A handle belongs to the device that was current when it was created
+ *    (vbarms_compress, vbarms_vbsr_from_blocks; a factorization takes its
+ *    matrix's device), and its stream must belong to that device.  Every
+ *    later call with the handle runs on that device whatever device is
+ *    current, and restores the caller's current device before returning.
+ *    Calls that combine handles of different devices return VB_EINVAL.
  *  - Vectors given to vbarms_apply / fgmres_solve are caller-owned device
  *    arrays of doubles in the ORIGINAL (unpermuted) numbering.
  *
@@ -192,27 +198,36 @@ vb_status vbarms_apply(vbarms_prec M, const double* x, double* y);
 vb_status vbarms_apply_batched(int nmat, const vbarms_prec* M, const double* const* x, double* const* y);
 
 /* y = M^{-1} x like vbarms_apply, but allocating nothing: for callers that
- * cannot allocate device memory when they apply the preconditioner (while a
- * stream is being recorded into a CUDA graph, in solver loops that forbid
- * allocator calls after set-up, or when device memory belongs to another
- * runtime's pool).  The paper has no counterpart; this is an interface
- * convenience.
+ * cannot allocate device memory when they apply the preconditioner -- solver
+ * loops with a fixed memory budget that forbid allocator calls once set-up
+ * is over, or applications whose device memory belongs to another runtime's
+ * pool and that give this library no allocator.  The paper has no
+ * counterpart; this is an interface convenience.
  * All scratch comes from one file-scope device array of
  * vbarms_apply_static_max_bytes() bytes (64 MiB) that every GPU loading the
  * library holds until the process exits.  A factorization that needs more
- * (roughly n above 500k unknowns) is rejected with VB_EINVAL; use
- * vbarms_apply then.  x, y: device double[n], original numbering, no
- * aliasing; the call synchronizes the handle's stream before returning.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current: make that first call
+ * is rejected with VB_EINVAL (use vbarms_apply then); the need grows with
+ * the scalar sizes of all levels and with the last level's block rows, and
+ * vbarms_apply_static_need tells it for a given handle.  x, y: device
+ * double[n] on the handle's device, original numbering, no aliasing; the
+ * call synchronizes the handle's stream before returning.  The first call on
+ * a device does a set-up: it looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call shares the same array and it keeps
  * the previous call's contents (the call clears what must start at zero):
  * calls that overlap on the GPU -- from several host threads, or on several
- * streams -- race and must be serialized by the caller.                   */
+ * streams -- race and must be serialized by the caller.  Handles of a
+ * batched factorization are rejected (VB_EINVAL).                          */
 vb_status vbarms_apply_static(vbarms_prec M, const double* x, double* y);
 
 /* Size in bytes of the fixed scratch array of vbarms_apply_static. */
 uint64_t vbarms_apply_static_max_bytes(void);
+
+/* *bytes = the scratch vbarms_apply_static needs for M (no device work); a
+ * handle fits when it is at most vbarms_apply_static_max_bytes().  The paper
+ * has no counterpart.  VB_EINVAL for NULL arguments or a handle of a batched
+ * factorization.                                                            */
+vb_status vbarms_apply_static_need(vbarms_prec M, uint64_t* bytes);
 
 /* Right-preconditioned flexible GMRES(restart) on A x = b (FP64 Arnoldi with
  * modified Gram-Schmidt, Givens rotations, true residual at every restart).
@@ -259,6 +274,11 @@ vb_status vbarms_prec_kernel_stats(vbarms_prec M, int kernel, int* launches, dou
  * threads, all handles); read it before and after a call to count the
  * launches of that call.                                                   */
 uint64_t vbarms_launch_count(void);
+
+/* Number of device allocations this library has made since it was loaded
+ * (all threads, all handles; every allocation of the library is counted).
+ * Read it before and after a call to see whether that call allocated.      */
+uint64_t vbarms_alloc_count(void);
 
 void vbarms_vbsr_destroy(vbarms_vbsr A);
 void vbarms_prec_destroy(vbarms_prec M);

@@ -1,10 +1,10 @@
 // vbarms_apply_static: the preconditioner solve with no device allocation.
 //
 // Some callers cannot allocate device memory at the point where they apply
-// the preconditioner: code that runs while a stream is being recorded into a
-// CUDA graph (allocation calls are not allowed there), real-time solver loops
-// that forbid allocator calls after set-up, or hosts whose device memory is
-// owned by another runtime's pool.  For them this entry point runs the same
+// the preconditioner: solver loops with a fixed memory budget that forbid
+// allocator calls once set-up is over, and hosts whose device memory belongs
+// to another runtime's pool (an embedding application that hands this
+// library no allocator of its own).  For them this entry point runs the same
 // solve as vbarms_apply, with all of its scratch in one fixed-size device
 // array defined in this file.
 #include <mutex>
@@ -26,9 +26,14 @@ std::mutex g_mu;
 unsigned char* g_addr[kMaxDevices] = {};
 int g_nsm[kMaxDevices] = {};
 
-// Set-up, once per device and with that device current: the device address
-// of the scratch array (return code checked) and the device's SM count.
+// Set-up, once per device and with that device current (the caller makes the
+// handle's device current first): the device address of the scratch array
+// (return code checked) and the device's SM count.
 vb_status setup_device(int dev, unsigned char** addr, int* nsm) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    vb::set_last_error("vbarms_apply_static: device ordinal beyond the supported 64");
+    return VB_ECUDA;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {
     void* p = nullptr;
@@ -58,6 +63,20 @@ extern "C" {
 
 uint64_t vbarms_apply_static_max_bytes(void) { return VB_APPLY_STATIC_BYTES; }
 
+vb_status vbarms_apply_static_need(vbarms_prec M, uint64_t* bytes) {
+  if (!M || !bytes) {
+    vb::set_last_error("vbarms_apply_static_need: NULL argument");
+    return VB_EINVAL;
+  }
+  if (M->len >= 0) {
+    vb::set_last_error("vbarms_apply_static_need: a handle of a batched factorization");
+    return VB_EINVAL;
+  }
+  *bytes = (uint64_t)M->impl->scratch_bytes();
+  vb::set_last_error("");
+  return VB_OK;
+}
+
 vb_status vbarms_apply_static(vbarms_prec M, const double* x, double* y) {
   if (!M || !x || !y) {
     vb::set_last_error("vbarms_apply_static: NULL argument");
@@ -80,14 +99,12 @@ vb_status vbarms_apply_static(vbarms_prec M, const double* x, double* y) {
                          " bytes; use vbarms_apply");
       return VB_EINVAL;
     }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-      vb::set_last_error("vbarms_apply_static: no usable current device");
-      return VB_ECUDA;
-    }
+    // the handle's device, whatever device is current: the scratch address
+    // belongs to it
+    vb::DeviceScope ds(P.dev);
     unsigned char* scratch = nullptr;
     int nsm = 0;
-    const vb_status st = setup_device(dev, &scratch, &nsm);
+    const vb_status st = setup_device(P.dev, &scratch, &nsm);
     if (st != VB_OK) return st;
     P.apply_with_scratch(x, y, scratch, nsm);
     vb::check_status(P.status_dev(), P.s, "vbarms_apply_static");

@@ -12,6 +12,7 @@ using namespace vb;
 
 struct vbarms_vbsr_st {
   cudaStream_t s = nullptr;
+  int dev = 0;  // the device current when the handle was created
   Compressed C;
   DBuf<int> status;
   DBuf<int64_t> rowblk;  // scalar row -> block row, for the SpMV
@@ -73,6 +74,7 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
   auto P = std::make_unique<PrecDev<T>>();
   cudaStream_t s = Ah.s;
   P->s = s;
+  P->dev = Ah.dev;
   P->n = Ah.C.n;
   P->precision = o.precision;
   P->wait_limit = o.wait_limit;
@@ -205,6 +207,7 @@ vb_status vbarms_compress(int64_t n, const int64_t* rowptr, const int32_t* colin
   vb_status st = guarded([&] {
     cudaStream_t s = (cudaStream_t)stream;
     h->s = s;
+    h->dev = current_device();
     h->status.alloc(1, s);
     h->status.zero();
     const int64_t* d_rowptr = rowptr;
@@ -247,6 +250,7 @@ vb_status vbarms_vbsr_from_blocks(int64_t nblk, const int32_t* bsz, const int64_
   vb_status st = guarded([&] {
     cudaStream_t s = (cudaStream_t)stream;
     h->s = s;
+    h->dev = current_device();
     h->status.alloc(1, s);
     h->status.zero();
     int64_t n = 0;
@@ -310,6 +314,7 @@ vb_status vbarms_vbsr_export(vbarms_vbsr A, int32_t* perm, int32_t* bsz, int64_t
                              int64_t* voff, double* val) {
   if (!A) return set_err(VB_EINVAL, "NULL handle");
   return guarded([&] {
+    DeviceScope ds(A->dev);
     cudaStream_t s = A->s;
     if (perm && A->C.n) VB_CUDA(cudaMemcpyAsync(perm, A->C.perm.p, A->C.n * 4, cudaMemcpyDeviceToHost, s));
     export_vb(A->C.A, s, nullptr, nullptr, nullptr, nullptr, bsz, nullptr, bptr, bcol, voff, val);
@@ -328,6 +333,7 @@ vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil, const
                opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
+    DeviceScope ds(A->dev);
     if (o.precision == VB_FP64)
       h->impl = factor_impl<double>(*A, o);
     else
@@ -348,6 +354,7 @@ vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev,
   for (int m = 0; m < nmat; ++m) {
     if (!A[m]) return set_err(VB_EINVAL, "NULL matrix handle");
     if (nlev[m] < 0 || !(droptol[m] >= 0.0)) return set_err(VB_EINVAL, "nlev < 0 or droptol < 0");
+    if (A[m]->dev != A[0]->dev) return set_err(VB_EINVAL, "the matrices of a batch live on different devices");
   }
   vbarms_opts d;
   vbarms_opts_default(&d);
@@ -366,11 +373,13 @@ vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev,
           members.push_back(m);
           taken[m] = 1;
         }
+      DeviceScope ds(A[members[0]]->dev);
       cudaStream_t s = A[members[0]]->s;
       for (int m : members)
         if (A[m]->s != s) VB_CUDA(cudaStreamSynchronize(A[m]->s));
       vbarms_vbsr_st U;
       U.s = s;
+      U.dev = A[members[0]]->dev;
       std::vector<const Compressed*> parts;
       for (int m : members) parts.push_back(&A[m]->C);
       compressed_union(parts, s, U.C);
@@ -413,9 +422,11 @@ vb_status vbarms_dd_factor(vbarms_vbsr A, int nparts, int overlap, int restricte
                opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
+    DeviceScope ds(A->dev);
     cudaStream_t s = A->s;
     auto D = std::make_unique<PrecDD>();
     D->s = s;
+    D->dev = A->dev;
     D->n = A->C.n;
     D->precision = o.precision;
     D->wait_limit = o.wait_limit;
@@ -428,6 +439,7 @@ vb_status vbarms_dd_factor(vbarms_vbsr A, int nparts, int overlap, int restricte
     // their subdomain so that the last-level ILUT interleaves the subdomains
     vbarms_vbsr_st U;
     U.s = s;
+    U.dev = A->dev;
     dd_build(A->C, nparts, overlap, restricted != 0, s, D->L, U.C);
     if (o.precision == VB_FP64)
       D->inner = factor_impl<double>(U, o, D->L.ud.p, nparts);
@@ -453,6 +465,7 @@ vb_status vbarms_dd_layout(vbarms_prec M, int* nparts, int* overlap, int* restri
   auto* D = dynamic_cast<PrecDD*>(M->impl.get());
   if (!D) return set_err(VB_EINVAL, "not a domain-decomposition preconditioner");
   return guarded([&] {
+    DeviceScope ds(D->dev);
     const DDLayout& L = D->L;
     if (nparts) *nparts = L.nparts;
     if (overlap) *overlap = L.overlap;
@@ -471,6 +484,7 @@ vb_status vbarms_apply(vbarms_prec M, const double* x, double* y) {
   if (x == y) return set_err(VB_EINVAL, "x and y must not alias");
   return guarded([&] {
     PrecBase& P = *M->impl;
+    DeviceScope ds(P.dev);
     DBuf<double> xp(P.n, P.s), yp(P.n, P.s);
     if (M->len < 0) {
       gather_dev(xp.p, x, P.perm.p, P.n, P.s);
@@ -506,6 +520,7 @@ vb_status vbarms_apply_batched(int nmat, const vbarms_prec* M, const double* con
     for (int m0 = 0; m0 < nmat; ++m0) {
       if (done[m0]) continue;
       PrecBase& P = *M[m0]->impl;
+      DeviceScope ds(P.dev);
       DBuf<double> xu(P.n, P.s), yu(P.n, P.s), xp(P.n, P.s), yp(P.n, P.s);
       xu.zero();
       for (int m = m0; m < nmat; ++m) {
@@ -532,8 +547,10 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
   if (!A || !b || !x) return set_err(VB_EINVAL, "NULL argument");
   if (restart < 1 || maxit < 0 || !(rtol >= 0.0)) return set_err(VB_EINVAL, "restart < 1, maxit < 0 or rtol < 0");
   if (M && M->size() != A->C.n) return set_err(VB_EINVAL, "preconditioner and matrix sizes differ");
+  if (M && M->impl->dev != A->dev) return set_err(VB_EINVAL, "preconditioner and matrix live on different devices");
   bool conv = false;
   vb_status st = guarded([&] {
+    DeviceScope ds(A->dev);
     cudaStream_t s = A->s;
     const int64_t n = A->C.n;
     const int m = restart;
@@ -653,6 +670,8 @@ vb_status vbarms_prec_stats(vbarms_prec M, int* levels_used, double* mem_ratio, 
 
 uint64_t vbarms_launch_count(void) { return g_launch_count.load(); }
 
+uint64_t vbarms_alloc_count(void) { return g_alloc_count.load(); }
+
 vb_status vbarms_prec_kernel_stats(vbarms_prec M, int kernel, int* launches, double* ms, double* bytes,
                                    double* flops) {
   if (!M) return set_err(VB_EINVAL, "NULL handle");
@@ -676,24 +695,46 @@ vb_status vbarms_prec_export(vbarms_prec M, int lev, int which, int64_t* nbr, in
                              int64_t* nval, int32_t* rsz, int32_t* csz, int64_t* bptr, int32_t* bcol,
                              int64_t* voff, double* val) {
   if (!M) return set_err(VB_EINVAL, "NULL handle");
-  return guarded([&] { M->impl->export_mat(lev, which, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val); });
+  return guarded([&] {
+    DeviceScope ds(M->impl->dev);
+    M->impl->export_mat(lev, which, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+  });
 }
 
 vb_status vbarms_prec_vector(vbarms_prec M, int lev, int which, double* d, int32_t* iv, int64_t* len) {
   if (!M) return set_err(VB_EINVAL, "NULL handle");
-  return guarded([&] { M->impl->export_vec(lev, which, d, iv, len); });
+  return guarded([&] {
+    DeviceScope ds(M->impl->dev);
+    M->impl->export_vec(lev, which, d, iv, len);
+  });
 }
 
+// Destruction runs on the handle's device (its buffers are freed on its
+// stream); a failure to select that device still frees the host side.
 void vbarms_vbsr_destroy(vbarms_vbsr A) {
   if (!A) return;
-  cudaStreamSynchronize(A->s);
-  delete A;
+  try {
+    DeviceScope ds(A->dev);
+    cudaStreamSynchronize(A->s);
+    delete A;
+  } catch (const Error&) {
+    delete A;
+  }
 }
 
 void vbarms_prec_destroy(vbarms_prec M) {
   if (!M) return;
-  if (M->impl) cudaStreamSynchronize(M->impl->s);
-  delete M;
+  if (!M->impl) {
+    delete M;
+    return;
+  }
+  try {
+    DeviceScope ds(M->impl->dev);
+    cudaStreamSynchronize(M->impl->s);
+    delete M;
+  } catch (const Error&) {
+    delete M;
+  }
 }
 
 }  // extern "C"

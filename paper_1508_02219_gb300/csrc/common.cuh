@@ -35,6 +35,37 @@ struct Error {
 
 // Every kernel of the library is launched through launch(), which counts it.
 extern std::atomic<unsigned long long> g_launch_count;
+// Every device allocation of the library goes through DBuf::alloc, which
+// counts it.
+extern std::atomic<unsigned long long> g_alloc_count;
+
+// Makes device dev current for the lifetime of the object and restores the
+// device that was current before.  Handles remember the device they were
+// created on; every entry point that works with a handle runs inside one.
+struct DeviceScope {
+  int prev = -1, dev = 0;
+  explicit DeviceScope(int d) : dev(d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      (void)cudaGetLastError();
+      throw_cuda_error("cudaGetDevice");
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      prev = -1;
+      throw_cuda_error("cudaSetDevice");
+    }
+  }
+  ~DeviceScope() {
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+  [[noreturn]] static void throw_cuda_error(const char* what);
+};
+
+// The device current in this thread (VB_ECUDA when there is none).
+int current_device();
 
 template <typename... KArgs, typename... Args>
 inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
@@ -137,6 +168,7 @@ struct DBuf {
         (void)cudaGetLastError();
         fail(VB_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
       }
+      g_alloc_count.fetch_add(1, std::memory_order_relaxed);
     }
   }
   void zero() {

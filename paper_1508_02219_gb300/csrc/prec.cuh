@@ -19,6 +19,7 @@ struct LevelMaps {
 
 struct PrecBase {
   cudaStream_t s = nullptr;
+  int dev = 0;  // the device the factorization lives on
   int64_t n = 0;
   int precision = VB_FP64;
   uint64_t wait_limit = 0;

@@ -4,6 +4,17 @@
 namespace vb {
 
 std::atomic<unsigned long long> g_launch_count{0};
+std::atomic<unsigned long long> g_alloc_count{0};
+
+void DeviceScope::throw_cuda_error(const char* what) {
+  fail(VB_ECUDA, std::string(what) + " failed: no usable device for this handle");
+}
+
+int current_device() {
+  int d = 0;
+  VB_CUDA(cudaGetDevice(&d));
+  return d;
+}
 
 void check_status(int* dst, cudaStream_t s, const char* where) {
   int st = d2h(dst, s);

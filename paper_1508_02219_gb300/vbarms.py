@@ -79,6 +79,8 @@ def lib():
                 "vbarms_launch_count": (C.c_uint64, []),
                 "vbarms_apply_static": (i32, [vp, vp, vp]),
                 "vbarms_apply_static_max_bytes": (C.c_uint64, []),
+                "vbarms_apply_static_need": (i32, [vp, P(C.c_uint64)]),
+                "vbarms_alloc_count": (C.c_uint64, []),
                 "vbarms_vbsr_destroy": (None, [vp]),
                 "vbarms_prec_destroy": (None, [vp]),
             }
@@ -313,6 +315,13 @@ def apply_static_max_bytes() -> int:
     return int(lib().vbarms_apply_static_max_bytes())
 
 
+def vbarms_apply_static_need(M: Prec) -> int:
+    """Bytes of scratch vbarms_apply_static needs for M (no device work)."""
+    b = C.c_uint64()
+    _check(lib().vbarms_apply_static_need(M.h, C.byref(b)))
+    return int(b.value)
+
+
 def fgmres_solve(A: VBSR, M: Prec | None, b, x, rtol=1e-8, restart=50, maxit=1000, raise_noconv=False):
     """FGMRES(restart); returns (iters, relres, status).  x is updated in place."""
     it, rr = C.c_int(), C.c_double()
@@ -335,3 +344,8 @@ def exported_symbols() -> list[str]:
 def launch_count() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(lib().vbarms_launch_count())
+
+
+def alloc_count() -> int:
+    """Device allocations made by the library since it was loaded."""
+    return int(lib().vbarms_alloc_count())
