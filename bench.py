@@ -47,7 +47,6 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator factor")
-    p.add_argument("--cpu-sample-nodes", type=int, default=0, help="oracle sample size (0 = auto)")
     p.add_argument("--dd", type=int, default=0,
                    help="domain decomposition (Section 5) with this many subdomains; 0 = one global VBARMS")
     p.add_argument("--overlap", type=int, default=1, help="subdomain overlap levels with --dd (0 = block Jacobi)")
@@ -180,7 +179,45 @@ def dd_name(dd):
     return "bj" if dd[1] == 0 else ("ras" if dd[2] else "asm")
 
 
-def oracle_setup_seconds(m, w, restart=50, dd=None):
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+class OneCore:
+    """Pin the calling thread to one host core for the oracle (the oracle is
+    single-threaded; pinning keeps it on one core as the survey's taskset
+    -c 0 would), restoring the previous affinity afterwards."""
+
+    def __enter__(self):
+        self.prev = None
+        try:
+            self.prev = os.sched_getaffinity(0)
+            self.core = min(self.prev)
+            os.sched_setaffinity(0, {self.core})
+        except (AttributeError, OSError):
+            self.core = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.prev is not None:
+            os.sched_setaffinity(0, self.prev)
+
+
+def oracle_setup_seconds(m, w, restart=50, dd=None, keep=False):
     """The CPU oracle (single-threaded) on matrix m: setup seconds and FGMRES."""
     import oracle
     t0 = time.perf_counter()
@@ -195,17 +232,10 @@ def oracle_setup_seconds(m, w, restart=50, dd=None):
     b = synth.ones_rhs(m)
     x, its, rr, st = oracle.fgmres(c.A, P, b[c.perm], rtol=1e-8, restart=restart, maxit=1000)
     t3 = time.perf_counter()
-    return dict(compress_s=t1 - t0, factor_s=t2 - t1, solve_s=t3 - t2, its=its, relres=rr)
-
-
-def cpu_sample(name, seed, nodes):
-    from paper_1508_02219_gb300 import synth
-    w = dict(synth.WORKLOADS[name])
-    full_nodes = w.get("n_nodes", 1000)
-    if not nodes:
-        nodes = min(full_nodes, 20000)
-    m = synth.make_workload(name, seed=seed, scale=nodes / full_nodes)
-    return m, w, nodes, full_nodes
+    r = dict(compress_s=t1 - t0, factor_s=t2 - t1, solve_s=t3 - t2, its=its, relres=rr)
+    if keep:
+        r.update(c=c, P=P, x=x)
+    return r
 
 
 def run_reference(args):
@@ -235,29 +265,31 @@ def run_reference(args):
                           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
               flush=True)
         return
-    m_full_nnz_est = None
-    m, w, nodes, full_nodes = cpu_sample(args.workload, args.seed, args.cpu_sample_nodes)
+    # the oracle on the full matrix of the workload: one step, no warm-up
+    # (a step of the single-threaded oracle takes minutes; the line reports the
+    # steps it ran)
     full = synth.WORKLOADS[args.workload]
-    # full-size nnz: the generator's nnz scales with the node count
-    scale_f = full_nodes / nodes
-    times = []
+    m = synth.make_workload(args.workload, seed=args.seed, scale=args.scale)
     dd = dd_config(args)
-    for i in range(args.warmup + args.steps):
-        r = oracle_setup_seconds(m, w, dd=dd)
-        if i >= args.warmup:
-            times.append(r["compress_s"] + r["factor_s"])
-    v = statistics.mean(times) * scale_f
+    with OneCore() as oc:
+        r = oracle_setup_seconds(m, full, dd=dd)
+    v = r["compress_s"] + r["factor_s"]
     out = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": 1,
+        "warmup": 0, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "nodes": full_nodes, "ell": full["ell"], "tau": full["tau"],
-                   "nlev": full["nlev"], "droptol": full["droptol"], "lfil": full["lfil"],
+        "config": {"workload": args.workload, "nodes": m.meta.get("nodes"), "n": m.n, "nnz": m.nnz,
+                   "ell": full["ell"], "tau": full["tau"], "nlev": full["nlev"], "droptol": full["droptol"],
+                   "lfil": full["lfil"], "scale": args.scale,
                    **({"precond": dd_name(dd), "nparts": dd[0], "overlap": dd[1]} if dd else {})},
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": f"{nodes} of {full_nodes} nodes of the same generator, oracle setup "
-                                   f"(compress+factor) seconds scaled by the node ratio {scale_f:.1f}"},
+                         "sample": f"the whole {args.workload} matrix (n = {m.n}), one run of the oracle's "
+                                   f"compress + factor, pinned to one core",
+                         "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
+                         "requested_steps": args.steps, "requested_warmup": args.warmup},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "detail": {"compress_s": r["compress_s"], "factor_s": r["factor_s"], "solve_s": r["solve_s"],
+                   "fgmres_its": r["its"], "relres": r["relres"]},
     }
     print(json.dumps(out), flush=True)
 
@@ -371,6 +403,31 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def error_report(V, torch, m, r_gpu, r_or) -> dict:
+    """Relative Frobenius error of every result of the mixed factor against
+    the oracle's FP64 factorization of the same matrix: each level's W, G, S
+    and the last level's L, U (blocks matched by compressed block row), one
+    preconditioner application and the FGMRES solution."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import precision_report as pr
+    P, Po, c = r_gpu["P"], r_or["P"], r_or["c"]
+    rep = pr.factor_errors(P, Po)
+    out = {k: float(v) for k, v in pr.summary(rep).items()}
+    out["block_rel_median"] = {k: float(v) for k, v in pr.summary(rep, "block_rel_median").items()}
+    out["blocks_only_one_side"] = {f"{k}.{n}": [r["blocks_only_gpu"], r["blocks_only_oracle"]]
+                                   for k, v in rep.items() for n, r in v.items() if isinstance(r, dict)}
+    x = np.random.default_rng(5).standard_normal(m.n)
+    y = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    V.vbarms_apply(P, torch.from_numpy(x).cuda(), y)
+    yo = np.empty(m.n)
+    yo[c.perm] = Po.apply(x[c.perm])
+    out["apply"] = pr.rel(y.cpu().numpy(), yo)
+    xo = np.empty(m.n)
+    xo[c.perm] = r_or["x"]
+    out["solution"] = pr.rel(r_gpu["x"].cpu().numpy(), xo)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -401,7 +458,7 @@ def main():
             return V.vbarms_factor(A, w["nlev"], w["droptol"], w["lfil"], precision=precision)
         return V.vbarms_dd_factor(A, dd[0], dd[1], dd[2], w["nlev"], w["droptol"], w["lfil"], precision=precision)
 
-    def step(precision, solve=True, record=None):
+    def step(precision, solve=True, keep=False):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record()
         A = V.vbarms_compress(m.n, rp, ci, vv, w["tau"])
@@ -417,6 +474,8 @@ def main():
         r = dict(compress_s=e[0].elapsed_time(e[1]) / 1e3, factor_s=e[1].elapsed_time(e[2]) / 1e3,
                  solve_s=e[2].elapsed_time(e[3]) / 1e3, its=its, relres=rr, stats=P.stats(),
                  kstats=P.kernel_stats(0), av_bd=A.query()["av_bd"], av_bs=A.query()["av_bs"])
+        if keep:  # the factorization is kept for the error report (after timing)
+            r.update(P=P, A=A, x=xd.clone())
         del P, A
         return r
 
@@ -428,7 +487,7 @@ def main():
     clk.start()
     l0 = V.launch_count()
     t0 = time.perf_counter()
-    res = [step(prec) for _ in range(args.steps)]
+    res = [step(prec, keep=(k == args.steps - 1)) for k in range(args.steps)]
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     launches = V.launch_count() - l0
@@ -463,7 +522,9 @@ def main():
                 "fgmres_its": r64["its"], "relres": r64["relres"], "phase_s": r64["stats"]["phase_s"],
                 "schur_numeric": r64["kstats"]}
 
-    # end to end through the C ABI with host buffers (pinned), copies timed
+    # end to end through the C ABI with host buffers (pinned), copies timed:
+    # compress from the host CSR (copied inside the call), factor, upload b,
+    # FGMRES, download x -- the same work as a step plus its host copies
     e2e = None
     if not args.no_e2e:
         prp = torch.from_numpy(m.rowptr).pin_memory()
@@ -471,45 +532,47 @@ def main():
         pvv = torch.from_numpy(m.val).pin_memory()
         pb = torch.from_numpy(b).pin_memory()
         px = torch.empty(m.n, dtype=torch.float64).pin_memory()
-        ets = []
-        d2h = 0
-        for i in range(max(1, args.steps)):
+        ets, sets = [], []
+        its_e2e = None
+        n_e2e = max(1, min(args.steps, 5))
+        for i in range(n_e2e):
             torch.cuda.synchronize()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             ev[0].record()
             A = V.vbarms_compress(m.n, prp.numpy(), pci.numpy(), pvv.numpy(), w["tau"])
             P = factor(A, prec)
-            # device-to-host read of the step's result: the last level's
-            # per-block precision tags of the factor
-            tags = P.vector(P.levels, "ptag")
-            d2h = int(tags.nbytes)
             ev[1].record()
             bdev = pb.to(dev, non_blocking=True)
             xdev = torch.zeros(m.n, dtype=torch.float64, device=dev)
-            V.fgmres_solve(A, P, bdev, xdev, rtol=1e-8, restart=50, maxit=1000)
+            its_e2e, _, _ = V.fgmres_solve(A, P, bdev, xdev, rtol=1e-8, restart=50, maxit=1000)
             px.copy_(xdev, non_blocking=True)
             ev[2].record()
             torch.cuda.synchronize()
-            ets.append(ev[0].elapsed_time(ev[1]) / 1e3)
+            ets.append(ev[0].elapsed_time(ev[2]) / 1e3)
+            sets.append(ev[0].elapsed_time(ev[1]) / 1e3)
             del P, A
         e2e = {"value": max_over_ranks(dist, statistics.mean(ets)), "unit": "s",
-               "h2d_bytes_per_step": int(m.rowptr.nbytes + m.colind.nbytes + m.val.nbytes),
-               "d2h_bytes_per_step": d2h,
-               "note": "timed: compress from pinned host CSR (copied inside the call) + factor + read-back of the "
-                       "factor's last-level precision tags; the FGMRES solve with its b upload and x download "
-                       "follows untimed in the same step"}
+               "h2d_bytes_per_step": int(m.rowptr.nbytes + m.colind.nbytes + m.val.nbytes + b.nbytes),
+               "d2h_bytes_per_step": int(px.numel() * 8),
+               "setup_only_s": max_over_ranks(dist, statistics.mean(sets)), "fgmres_its": its_e2e, "steps": n_e2e,
+               "note": "timed per step: compress from pinned host CSR (copied inside the call) + factor + upload of "
+                       "b + FGMRES(50) to rtol 1e-8 + download of x; setup_only_s stops after the factor"}
 
+    # the CPU oracle on the whole matrix, once, pinned to one core; its FP64
+    # factorization is also the reference of the mixed factor's error report
     cpu = None
+    errors = None
     if rank == 0 and not args.no_cpu_baseline:
-        ms, wl, nodes, full_nodes = cpu_sample(args.workload, args.seed, args.cpu_sample_nodes)
-        r = oracle_setup_seconds(ms, wl, dd=dd)
-        cpu = {"value": (r["compress_s"] + r["factor_s"]) * (full_nodes / nodes), "unit": "s", "cores": 1,
-               "kind": "oracle",
-               "sample": f"{nodes} of {full_nodes} nodes of the same generator; oracle compress+factor seconds "
-                         f"{r['compress_s'] + r['factor_s']:.2f} scaled by the node ratio; oracle FGMRES its "
-                         f"{r['its']}",
-               "host_cpus": os.cpu_count()}
-
+        with OneCore():
+            r = oracle_setup_seconds(m, w, dd=dd, keep=True)
+        cpu = {"value": r["compress_s"] + r["factor_s"], "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"the whole {args.workload} matrix (n = {m.n}), one run of the oracle's compress + factor "
+                         f"(FP64, single thread, pinned to one core); its FGMRES took {r['solve_s']:.1f} s and "
+                         f"{r['its']} iterations",
+               "host_cpus": os.cpu_count(), "cpu_model": cpu_model()}
+        if dd is None and prec == "fp32":
+            errors = error_report(V, torch, m, res[-1], r)
+        del r
     last = res[-1]
     if rank == 0:
         out = {
@@ -530,7 +593,7 @@ def main():
                        "relres": last["relres"], "levels": last["stats"]["levels"],
                        "mem_ratio": last["stats"]["mem_ratio"], "phase_s": last["stats"]["phase_s"],
                        "av_bd": last["av_bd"], "av_bs": last["av_bs"], "wall_timed_s": wall,
-                       "fp64_factor": fp64},
+                       "fp64_factor": fp64, "error_vs_fp64_oracle": errors},
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

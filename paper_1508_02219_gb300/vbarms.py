@@ -203,6 +203,13 @@ class Prec:
     def levels(self) -> int:
         return self.stats()["levels"]
 
+    def shape(self, lev: int, which: str) -> dict:
+        """Sizes of one exported factor (nbr, nbc, nnzb, nval) without its arrays."""
+        nbr, nbc, nnzb, nval = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().vbarms_prec_export(self.h, lev, MAT[which], C.byref(nbr), C.byref(nbc), C.byref(nnzb),
+                                        C.byref(nval), None, None, None, None, None, None))
+        return dict(nbr=nbr.value, nbc=nbc.value, nnzb=nnzb.value, nval=nval.value)
+
     def export(self, lev: int, which: str) -> dict:
         w = MAT[which]
         nbr, nbc, nnzb, nval = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()

@@ -1,6 +1,6 @@
-"""bench.py's reference arm (the oracle on a bounded sample) on CPU: the
-JSON line of the contract, for the default method and for the Section 5
-preconditioners."""
+"""bench.py's reference arm (the oracle on the whole matrix of the workload,
+one step) on CPU, here on a small scale of the workload: the JSON line of the
+contract, for the default method and for the Section 5 preconditioners."""
 import json
 import os
 import subprocess
@@ -25,7 +25,7 @@ def _run(*args):
                                            (["--dd", "4", "--overlap", "0"], "bj"),
                                            (["--dd", "4", "--overlap", "1", "--additive"], "asm")])
 def test_reference_arm_line(extra, precond):
-    d = _run("--workload", "geo60k_l6", "--cpu-sample-nodes", "400", "--steps", "1", "--warmup", "0", *extra)
+    d = _run("--workload", "geo60k_l6", "--scale", "0.007", "--steps", "3", "--warmup", "2", *extra)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
               "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
@@ -33,6 +33,8 @@ def test_reference_arm_line(extra, precond):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"] == "geo60k_l6"
+    # one step of the oracle, reported as run (the requested counts are noted)
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["cpu_baseline"]["requested_steps"] == 3
     assert d["config"].get("precond") == precond
     if precond:
         assert d["config"]["nparts"] == 4

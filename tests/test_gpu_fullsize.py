@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+import precision_report
 from gpu_helpers import as_dict, compare_factor, compare_vb, cuda_ok, gpu_compress, torch, vb
 from paper_1508_02219_gb300 import synth
 
@@ -62,8 +63,21 @@ def test_fullsize_geo500k_mixed():
     xo, its_o, rr_o, st_o = oracle.fgmres(c.A, Po, b[c.perm], rtol=1e-8)
     assert st == V.VB_OK and st_o == oracle.OK
     assert rr <= 1e-8
-    assert its <= math.ceil(1.1 * its_o) + 1, f"mixed FGMRES {its} vs FP64 oracle {its_o}"
+    assert its <= math.floor(1.10 * its_o), f"mixed FGMRES {its} vs FP64 oracle {its_o}"
     # the true residual, recomputed here in FP64
     xg = x.cpu().numpy()
     r = b - m.matvec(xg)
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    # the error of every result against the FP64 oracle, reported
+    rep = precision_report.factor_errors(P, Po)
+    flat = precision_report.summary(rep)
+    print("median blockwise relative error per result:",
+          {k: f"{v:.2e}" for k, v in precision_report.summary(rep, "block_rel_median").items()})
+    xof = np.empty(m.n)
+    xof[c.perm] = xo
+    flat["solution"] = precision_report.rel(xg, xof)
+    print("geo500k_l6 mixed factor, relative error per result vs the FP64 oracle:",
+          {k: f"{v:.2e}" for k, v in flat.items()})
+    # both solutions meet rtol 1e-8; they differ by up to cond(A) times that
+    # (the workload plants pivot blocks of condition 1e6)
+    assert all(np.isfinite(v) for v in flat.values()) and flat["solution"] <= 1e-2

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+import precision_report
 from gpu_helpers import as_dict, cuda_ok, gpu_compress, rel_fro, torch, vb
 from paper_1508_02219_gb300 import synth
 
@@ -38,7 +39,8 @@ def test_mixed_factor_iteration_budget(case):
         assert true < 1e-5, f"{prec}: solution error {true:.2e}"
         res[prec] = (its, P)
     its64, its32 = res["fp64"][0], res["fp32"][0]
-    assert its32 <= math.ceil(1.10 * its64) + 1, f"mixed FP32 needs {its32} vs FP64 {its64} iterations"
+    # at most 10 % extra iterations: its32 <= floor(1.10 its64)
+    assert its32 <= math.floor(1.10 * its64), f"mixed FP32 needs {its32} vs FP64 {its64} iterations"
 
 
 def test_mixed_factor_error_against_fp64_oracle():
@@ -67,6 +69,31 @@ def test_mixed_factor_error_against_fp64_oracle():
             errs[w] = rel_fro(g["val"], o["val"])
             assert errs[w] <= 1e-5, f"{w}: {errs[w]:.2e}"
     print("per-component relative error of the FP32 factor vs the FP64 oracle (level 1):", errs)
+    # every level's W, G, S, the last level's L and U, one application of the
+    # preconditioner and the FGMRES solution, against the FP64 oracle
+    rep = precision_report.factor_errors(P, Po)
+    flat = precision_report.summary(rep)
+    x = np.random.default_rng(5).standard_normal(m.n)
+    y = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    V.vbarms_apply(P, torch.from_numpy(x).cuda(), y)
+    yo = np.empty(m.n)
+    yo[c.perm] = Po.apply(x[c.perm])
+    flat["apply"] = precision_report.rel(y.cpu().numpy(), yo)
+    b = synth.ones_rhs(m)
+    xs = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    V.fgmres_solve(A, P, torch.from_numpy(b).cuda(), xs, rtol=1e-8)
+    xo, _, _, _ = oracle.fgmres(c.A, Po, b[c.perm], rtol=1e-8)
+    xof = np.empty(m.n)
+    xof[c.perm] = xo
+    flat["solution"] = precision_report.rel(xs.cpu().numpy(), xof)
+    print("relative error of every result of the mixed factor vs the FP64 oracle:",
+          {k: f"{v:.2e}" for k, v in flat.items()})
+    print("median blockwise relative error per result:",
+          {k: f"{v:.2e}" for k, v in precision_report.summary(rep, "block_rel_median").items()})
+    print("blocks stored by one side only:", {f"{k}.{n}": (r["blocks_only_gpu"], r["blocks_only_oracle"])
+                                             for k, v in rep.items() for n, r in v.items() if isinstance(r, dict)})
+    assert all(np.isfinite(v) for v in flat.values())
+    assert flat["apply"] <= 1e-2 and flat["solution"] <= 1e-2, flat
 
 
 def test_near_singular_pivots_are_kept_in_fp64():

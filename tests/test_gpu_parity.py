@@ -159,7 +159,7 @@ def test_apply_and_fgmres_fp64(case):
 def test_no_drop_factor_is_exact_inverse():
     """t = 0, no lfil: M = A, so FGMRES converges in one iteration."""
     V = vb()
-    m = synth.geometric(500, 4, seed=11)
+    m = synth.geometric(1500, 4, seed=11)
     A = gpu_compress(m, 0.75)
     P = V.vbarms_factor(A, 2, 0.0, -1)
     b = torch.from_numpy(synth.ones_rhs(m)).cuda()
