@@ -7,23 +7,33 @@
 // warp).  A matrix made of independent diagonal blocks (a batch, or the
 // subdomains of a domain decomposition) may instead hand out its rows
 // interleaved across the blocks, each block's rows in ascending order: the
-// blocks' dependency chains then advance side by side.  The warp keeps its working row in a private workspace (hash table
-// column -> slot, dense values): in shared memory when the row fits, else in
-// global memory (a shared row whose fill outgrows the buffer starts again in
-// the global one).  It eliminates its L part in ascending column order
-// including fill -- waiting, with a bounded spin, until row k is published,
-// then staging row k's pivot block and U row in shared memory -- drops and
-// trims, factors its diagonal block (GEPP) and publishes its L and U rows to
-// global pools.  Per element, the operation order is the oracle's, so FP64
+// blocks' dependency chains then advance side by side.
+//
+// The warp keeps its working row in a private workspace (hash table column ->
+// slot, dense values): in shared memory when the row fits, else in global
+// memory (a shared row whose fill outgrows the buffer starts again in the
+// global one).  The size of the shared workspace is chosen at launch from the
+// last-level matrix (rows of a few large blocks, or rows of many small ones).
+// The warp eliminates its L part in ascending column order including fill.
+// For each column k it needs row k's factored pivot block and its U row:
+// row k publishes them as one record (below) and a 64-bit word in done[k]
+// telling where the record lies, so the dependant waits for one word and
+// brings the record on chip with one bulk asynchronous copy (completing on an
+// mbarrier); the record of the next pending column is fetched ahead while
+// the current step computes.  After the last column the warp thresholds its U
+// part, applies lfil to L and U (radix selection of the lfil largest norms),
+// sorts the kept blocks by column, factors its diagonal block (GEPP) and
+// publishes.  Per element, the operation order is the oracle's, so FP64
 // results match it bit for bit; the mixed factor keeps its drop sums, drop
 // tests and diagonal GEPP in FP32 (a block whose condition estimate exceeds
 // the threshold is factored again in FP64).
 //
 // A wait that runs out sets VB_ETIMEOUT and raises an abort flag; a row that
-// failed publishes the flag value 2 so that its dependants stop too.
-// Overflowing a pool or the global workspace sets an overflow code and the
-// host repeats the kernel with larger buffers.
+// failed publishes kRowFailed so that its dependants stop too.  Overflowing a
+// pool or the global workspace sets an overflow code and the host repeats the
+// kernel with larger buffers.
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "internal.h"
@@ -33,41 +43,92 @@
 namespace vb {
 namespace {
 
-constexpr int IW = 8;  // warps per block
-
 enum : int { SL_LIVE = 0, SL_LKEPT = 1, SL_DEAD = 2 };
 
+// ---------------------------------------------------------------------------
+// Published rows.  Row k's record, in the U pool, 16-byte aligned:
+//   int32 head[4]         ucnt (U blocks), nk, lu64 (1: the pivot LU is stored
+//                         in FP64, else in the factor's type), nval (U values)
+//   int32 piv[nk]         GEPP interchanges of the pivot block
+//   TL lu[nk * nk]        the factored pivot block, row-major
+//   int32 ucol[ucnt]      U block columns, ascending
+//   int32 urel[ucnt]      each U block's first value within val
+//   T val[nval]           the U blocks, row-major, in column order
+// every part starting on a 16-byte boundary.  done[k] = (offset << 24) |
+// length, both in 16-byte units, once the record is complete; kRowFailed when
+// the row failed; 0 before.
+constexpr unsigned long long kRowFailed = ~0ull;
+constexpr int64_t kRecMaxUnits = (1LL << 24) - 1;
+
+__host__ __device__ __forceinline__ int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }
+
+struct RecLayout {
+  int64_t piv, lu, ucol, urel, val, bytes;
+};
+
+__host__ __device__ __forceinline__ RecLayout rec_layout(int ucnt, int nk, int lu64, int64_t nval, int tsize) {
+  RecLayout L;
+  L.piv = 16;
+  L.lu = L.piv + pad16(4LL * nk);
+  L.ucol = L.lu + pad16((int64_t)nk * nk * (lu64 ? 8 : tsize));
+  L.urel = L.ucol + pad16(4LL * ucnt);
+  L.val = L.urel + pad16(4LL * ucnt);
+  L.bytes = L.val + pad16(nval * tsize);
+  return L;
+}
+
 struct Pools {
-  // L and U rows: blocks in pool order; per row the first block and count
+  // L rows: blocks in pool order; per row the first block and count
   int32_t* lcol;
   int64_t* lvo;  // value offset of each pool block
-  int32_t* ucol;
-  int64_t* uvo;
   int64_t* lstart;
   int32_t* lcnt;
-  int64_t* ustart;
-  int32_t* ucnt;
-  unsigned long long* ctr;  // [0] L blocks, [1] L values, [2] U blocks, [3] U values, [4] ticket, [5] max row need
-  int64_t lbcap, lvcap, ubcap, uvcap;
-  int32_t* done;
+  unsigned long long* done;  // per row: the published record word
+  unsigned long long* ctr;   // [0] L blocks, [1] L values, [2] U record units, [4] ticket,
+                             // [5] largest row values asked, [6] largest row slots asked
+  int64_t lbcap, lvcap, ucap16;
   int* abort;
-  int64_t* uvstart;  // value offset of the first U block of each row
-  int64_t* uvlen;    // values of the U row (its blocks are contiguous)
   // ticket -> row (nullptr: ticket t is row t); every row's dependencies
   // must come earlier in it
   const int32_t* order;
 };
 
+// Global fallback workspace, per warp.
 struct Workspace {
-  int* keys;      // [HT] per warp
-  int* hpos;      // [SMAX]
-  int* scol;      // [SMAX]
-  int* soff;      // [SMAX]
-  int* sstate;    // [SMAX]
-  long long* sf2;  // [SMAX] norm key of each slot
+  int* keys;       // [ht]
+  int* hpos;       // [smax]
+  int* scol;       // [smax]
+  int* soff;       // [smax]
+  int* sstate;     // [smax]
+  long long* sf2;  // [smax] norm key of each slot
+  int* fin;        // [2 smax] candidate lists of the finish
+  unsigned long long* srt;  // [4 smax] kept lists being sorted
   int ht, smax;
   int64_t vmax;
 };
+
+// Shared workspace of one warp, sized at launch (byte offsets in the warp's
+// region; every part 16-byte aligned).
+struct IlutGeom {
+  int slots, hash, vbytes, stage, lcap;
+  int o_misc, o_stage, o_vals, o_keys, o_hpos, o_scol, o_soff, o_sst, o_sf2, o_lc, o_ls;
+  int bytes;
+};
+
+constexpr int PVMAX = 64;
+struct IlutMisc {
+  unsigned long long mbar[2];  // completion of the bulk copy into stage buffer b
+  unsigned long long nvals;
+  long long wdst[32];  // destination offset of each block of a copied chunk
+  int hist[256];       // radix selection of the lfil cut
+  int qoff[32];        // workspace value offset of each U block's target
+  int quo[32];         // value offset of the U block within the record values
+  int qnj[32];
+  int qpre[33];        // element prefix of a chunk's blocks
+  int pv[PVMAX];       // GEPP interchanges of the row's own diagonal block
+  int nl, nslots, flag, pad;
+};
+
 
 template <typename T>
 __device__ __forceinline__ T msub(T acc, T a, T b);
@@ -173,33 +234,7 @@ __device__ __forceinline__ int ws_new_slot(int smax, int64_t vmax, int* keys, in
   return hpos[slot] < 0 ? -1 : slot;
 }
 
-constexpr int SMB = 16;         // pivot blocks up to SMB x SMB have their own shared buffer
-constexpr int PVMAX = 64;       // larger ones up to PVMAX are staged in free workspace space
 constexpr int MAX_SLOTS = 4096;  // largest workspace (blocks of one working row)
-
-// x (one row of length m) <- x (P^T L U)^{-1} from a staged pivot block
-// (values held as doubles; TL is the arithmetic type).
-template <typename T, typename TL>
-__device__ void ainv_right_row_s(const double* lu, const int* pv, int m, T* x) {
-  for (int j = 0; j < m; ++j) {
-    TL s = (TL)x[j];
-    for (int q = 0; q < j; ++q) s = msub<TL>(s, (TL)x[q], (TL)lu[q * m + j]);
-    x[j] = (T)(s / (TL)lu[j * m + j]);
-  }
-  for (int j = m - 1; j >= 0; --j) {
-    TL s = (TL)x[j];
-    for (int q = j + 1; q < m; ++q) s = msub<TL>(s, (TL)x[q], (TL)lu[q * m + j]);
-    x[j] = (T)s;
-  }
-  for (int k = m - 1; k >= 0; --k) {
-    const int p = pv[k];
-    if (p > k && p < m) {
-      const T t = x[k];
-      x[k] = x[p];
-      x[p] = t;
-    }
-  }
-}
 
 // Warp-cooperative copy with eight independent loads in flight per lane.
 template <typename T>
@@ -249,47 +284,6 @@ __device__ __forceinline__ float fro2_f32(const T* __restrict__ v, int n) {
   }
   return s;
 }
-
-constexpr int LCAP = 128;           // pending L columns tracked in shared memory per warp
-constexpr int USTAGE_BYTES = 2048;  // U row of a dependency staged in shared memory per warp
-constexpr int WS_SLOTS = 64;        // working rows held in shared memory: blocks,
-constexpr int WS_HASH = 128;        //   hash positions,
-constexpr int WS_VBYTES = 4096;     //   value bytes
-constexpr int MSH = 96;             // slot metadata of a global working row staged for the finish
-
-// Per-warp shared memory: the working row when it fits (hash table, slot
-// metadata, values), the dependency's pivot block and U row, and the
-// bookkeeping of one elimination step.
-struct IlutWarp {
-  __align__(16) unsigned char vals[WS_VBYTES];
-  __align__(16) unsigned char ustage[USTAGE_BYTES];
-  __align__(16) unsigned char lu[SMB * SMB * sizeof(double)];  // FP64 or FP32 pivot block
-  long long sf2[WS_SLOTS];
-  long long wdst[32];  // pool value offset of each written block of a chunk
-  int keys[WS_HASH];
-  int hpos[WS_SLOTS];
-  int scol[WS_SLOTS];
-  int soff[WS_SLOTS];
-  int sstate[WS_SLOTS];
-  int pv[PVMAX];
-  int qoff[32];  // workspace value offset of each U block's target
-  int quo[32];   // value offset of the U block within the U row
-  int qnj[32];
-  int qpre[33];  // element prefix of the chunk's U blocks
-  int lc[LCAP];  // pending L columns (INT_MAX when processed)
-  int ls[LCAP];  // their slots
-  int nl, nslots, flag, pad;
-  unsigned long long nvals;
-};
-
-constexpr size_t ilut_smem() { return IW * sizeof(IlutWarp); }
-static_assert(MSH * (3 * sizeof(int) + sizeof(long long)) <= USTAGE_BYTES, "finish staging exceeds the U-row buffer");
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // x (one row of length m) <- x (P^T L U)^{-1} from a staged pivot block
 // (values of type TS, arithmetic in TL); x lives in shared memory.
@@ -419,28 +413,306 @@ __device__ float inv_norm1_f32(const float* a, int n, const int* pv, int lane) {
   return cs;
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies into shared memory, completing on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Orders this thread's generic-proxy view of memory with the async proxy
+// (the bulk copies): taken by a producer after writing a record and by a
+// consumer after acquiring its flag, before issuing the copy.
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of bar to complete; false when limit ns
+// passed first.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long limit) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if ((it & 15) == 0 && global_ns() - t0 > limit) return false;
+  }
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The published word of a row, waiting for it as wait_flag does (relaxed
+// polls with backoff, the abort word and the time budget every 16th poll,
+// one acquire fence at the end).  0 when the wait gave up.
+__device__ __forceinline__ unsigned long long wait_word(const unsigned long long* w, int* abort,
+                                                        unsigned long long limit, int* st) {
+  unsigned long long v = ld_relaxed_u64(w);
+  if (v == 0) {
+    const unsigned long long t0 = global_ns();
+    unsigned nsl = 32;
+    for (unsigned it = 1;; ++it) {
+      __nanosleep(nsl);
+      if (nsl < 256) nsl <<= 1;
+      v = ld_relaxed_u64(w);
+      if (v != 0) break;
+      if ((it & 15) == 0) {
+        if (*((volatile int*)abort) != 0) return 0;
+        if (global_ns() - t0 > limit) {
+          dev_fail(st, DEV_ETIMEOUT);
+          atomicExch(abort, 1);
+          return 0;
+        }
+      }
+    }
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  return v;
+}
+
+// Ascending bitonic sort of a[0, n2) (n2 a power of two) by one warp.
+__device__ void warp_bitonic_sort(unsigned long long* a, int n2, int lane) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int x = lane; x < n2; x += 32) {
+        const int y = x ^ j;
+        if (y > x) {
+          const unsigned long long u = a[x], v = a[y];
+          if ((u > v) == ((x & k) == 0)) {
+            a[x] = v;
+            a[y] = u;
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
+// lfil (Section 3 dropping rule with the lfil bound of the paper's ARMS
+// parameters): of the n candidate slots cand[], keep the lfil with the
+// largest norm keys, lower column first on equal keys; the others become
+// SL_DEAD and cand[] is compacted to the kept ones.  The lfil-th largest key
+// is found by radix selection, 8 bits a pass from the top (keybytes passes:
+// the keys are the bit patterns of non-negative FP64 or FP32 norms, so their
+// integer order is their value order).  Returns the number kept.
+__device__ int lfil_cut(int* cand, int n, int lfil, const long long* sf2, const int* scol, int* sstate, int* hist,
+                        int keybytes, int lane) {
+  if (lfil < 0 || n <= lfil) return n;
+  if (lfil == 0) {
+    for (int c = lane; c < n; c += 32) sstate[cand[c]] = SL_DEAD;
+    __syncwarp();
+    return 0;
+  }
+  unsigned long long prefix = 0, pmask = 0;
+  int want = lfil;  // keys still to take at or below the current prefix
+  for (int d = keybytes - 1; d >= 0; --d) {
+    const int shift = 8 * d;
+    for (int b = lane; b < 256; b += 32) hist[b] = 0;
+    __syncwarp();
+    for (int c = lane; c < n; c += 32) {
+      const unsigned long long key = (unsigned long long)sf2[cand[c]];
+      if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255], 1);
+    }
+    __syncwarp();
+    // lane l holds bins 255 - 8 l - u, u = 0..7 (the highest bins first)
+    int cnt[8];
+    int s = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      cnt[u] = hist[255 - 8 * lane - u];
+      s += cnt[u];
+    }
+    int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int excl = incl - s;
+    int bin = -1, above = 0;
+    if (excl < want && want <= incl) {
+      int run = excl;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (bin < 0 && run + cnt[u] >= want) {
+          bin = 255 - 8 * lane - u;
+          above = run;
+        }
+        run += cnt[u];
+      }
+    }
+    const unsigned who = __ballot_sync(0xffffffffu, bin >= 0);
+    const int src = __ffs(who) - 1;
+    bin = __shfl_sync(0xffffffffu, bin, src);
+    above = __shfl_sync(0xffffffffu, above, src);
+    want -= above;
+    prefix |= (unsigned long long)bin << shift;
+    pmask |= 255ull << shift;
+    __syncwarp();
+  }
+  // keys above prefix are kept; of the keys equal to it, the `want` with the
+  // lowest columns
+  int kept = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int c = base + lane;
+    int q = -1;
+    bool keep = false;
+    if (c < n) {
+      q = cand[c];
+      const unsigned long long key = (unsigned long long)sf2[q];
+      if (key > prefix) {
+        keep = true;
+      } else if (key == prefix) {
+        const int col = scol[q];
+        int rank = 0;
+        for (int c2 = 0; c2 < n; ++c2) {
+          const int q2 = cand[c2];
+          if ((unsigned long long)sf2[q2] == prefix && scol[q2] < col) ++rank;
+        }
+        keep = rank < want;
+      }
+    }
+    __syncwarp();
+    const unsigned bk = __ballot_sync(0xffffffffu, keep);
+    if (keep) cand[kept + __popc(bk & ((1u << lane) - 1u))] = q;
+    else if (q >= 0) sstate[q] = SL_DEAD;
+    kept += __popc(bk);
+    __syncwarp();
+  }
+  return kept;
+}
+
+// The kept blocks of one part in column order: srt[p] = col << 32 | slot for
+// p < k (n2 = the next power of two, padded with ~0).  Returns n2.
+__device__ int sort_by_column(const int* cand, int k, const int* scol, unsigned long long* srt, int lane) {
+  int n2 = 1;
+  while (n2 < k) n2 <<= 1;
+  for (int p = lane; p < n2; p += 32)
+    srt[p] = p < k ? ((unsigned long long)(unsigned)scol[cand[p]] << 32) | (unsigned)cand[p] : ~0ull;
+  __syncwarp();
+  warp_bitonic_sort(srt, n2, lane);
+  return n2;
+}
+
+// Copy blocks to consecutive destinations, 32 blocks a round: block b of the
+// round has sz[b] values at src offset so[b] and goes to dst offset dof[b];
+// lanes walk the round's flattened values, eight loads in flight per lane.
+template <typename T>
+__device__ __forceinline__ void copy_round(IlutMisc& M, int sz, int so, long long dof, const T* __restrict__ src,
+                                           T* __restrict__ dst, int lane) {
+  int incl = sz;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  M.qpre[lane] = incl - sz;
+  if (lane == 31) M.qpre[32] = total;
+  M.qoff[lane] = so;
+  M.wdst[lane] = dof;
+  __syncwarp();
+  for (int e0 = lane; e0 < total; e0 += 32 * 8) {
+    T v[8];
+    long long d8[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + 32 * u;
+      d8[u] = -1;
+      if (e < total) {
+        int lo = 0, hi = 31;  // last block with qpre <= e (empty blocks share a prefix)
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (M.qpre[mid] <= e)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        const int local = e - M.qpre[lo];
+        v[u] = src[M.qoff[lo] + local];
+        d8[u] = M.wdst[lo] + local;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (d8[u] >= 0) dst[d8[u]] = v[u];
+  }
+  __syncwarp();
+}
+
+
 
 template <typename T>
-__global__ void __launch_bounds__(IW * 32, 2)
-    k_ilut(VBView<T> A, Workspace ws, T* __restrict__ wvals_all, Pools P, T* __restrict__ lval,
-           T* __restrict__ uval, const int64_t* __restrict__ dgoff, double* __restrict__ dg,
+__global__ void __launch_bounds__(256, 2)
+    k_ilut(VBView<T> A, IlutGeom g, Workspace ws, T* __restrict__ wvals_all, Pools P, T* __restrict__ lval,
+           unsigned char* __restrict__ upool, const int64_t* __restrict__ dgoff, double* __restrict__ dg,
            float* __restrict__ dg32, int32_t* __restrict__ piv, int32_t* __restrict__ ptag, int mixed,
            double cond_thr, double t, int lfil, unsigned long long wait_limit, int* st) {
-  extern __shared__ __align__(16) unsigned char ilut_sm[];
+  extern __shared__ __align__(128) unsigned char ilut_sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  IlutWarp& W = reinterpret_cast<IlutWarp*>(ilut_sm)[warp];
-  const int64_t wid = (int64_t)blockIdx.x * IW + warp;
-  constexpr int USTAGE = USTAGE_BYTES / (int)sizeof(T);
-  constexpr int VSH = WS_VBYTES / (int)sizeof(T);
-  T* const ustage = reinterpret_cast<T*>(W.ustage);
+  unsigned char* const wb = ilut_sm + (size_t)warp * g.bytes;
+  IlutMisc& M = *reinterpret_cast<IlutMisc*>(wb + g.o_misc);
+  unsigned char* const stage0 = wb + g.o_stage;
+  unsigned char* const stage1 = stage0 + g.stage;
+  T* const sh_vals = reinterpret_cast<T*>(wb + g.o_vals);
+  int* const sh_keys = reinterpret_cast<int*>(wb + g.o_keys);
+  int* const sh_hpos = reinterpret_cast<int*>(wb + g.o_hpos);
+  int* const sh_scol = reinterpret_cast<int*>(wb + g.o_scol);
+  int* const sh_soff = reinterpret_cast<int*>(wb + g.o_soff);
+  int* const sh_sst = reinterpret_cast<int*>(wb + g.o_sst);
+  long long* const sh_sf2 = reinterpret_cast<long long*>(wb + g.o_sf2);
+  int* const lc = reinterpret_cast<int*>(wb + g.o_lc);  // pending L columns (INT_MAX when processed)
+  int* const ls = reinterpret_cast<int*>(wb + g.o_ls);  // their slots
+  const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  const int VSH = g.vbytes / (int)sizeof(T);
   const float tf = (float)t, condf = (float)cond_thr;
-  volatile int* vflag = &W.flag;
-  volatile int* vns = &W.nslots;
-  volatile int* vnl = &W.nl;
+  constexpr int TS = (int)sizeof(T);
+  volatile int* vflag = &M.flag;
+  volatile int* vns = &M.nslots;
+  volatile int* vnl = &M.nl;
   int* const gkeys = ws.keys + wid * ws.ht;
   for (int k = lane; k < ws.ht; k += 32) gkeys[k] = -1;
-  for (int k = lane; k < WS_HASH; k += 32) W.keys[k] = -1;
+  for (int k = lane; k < g.hash; k += 32) sh_keys[k] = -1;
+  if (lane == 0) {
+    mbar_init(&M.mbar[0]);
+    mbar_init(&M.mbar[1]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
   __syncwarp();
+  // stage buffer bookkeeping, the same in every lane: the column whose record
+  // a buffer holds (-1: free), whether its copy still has to be waited for,
+  // and the parity of its mbarrier's next phase
+  int btag0 = -1, btag1 = -1;
+  bool bpend0 = false, bpend1 = false;
+  unsigned bph0 = 0, bph1 = 0;
+  auto drain = [&]() {  // wait (bounded) for copies in flight and free both buffers
+    if (bpend0) {
+      if (mbar_wait(&M.mbar[0], bph0, wait_limit)) bph0 ^= 1;
+      bpend0 = false;
+    }
+    if (bpend1) {
+      if (mbar_wait(&M.mbar[1], bph1, wait_limit)) bph1 ^= 1;
+      bpend1 = false;
+    }
+    btag0 = btag1 = -1;
+  };
 
   for (;;) {
     long long row = 0;
@@ -458,7 +730,7 @@ __global__ void __launch_bounds__(IW * 32, 2)
     // The working row lives in shared memory when it leaves room for fill; a
     // row whose fill outgrows that restarts in the warp's global workspace
     // (nothing of it is visible before its finish, so the restart is exact).
-    bool in_sh = nb <= WS_SLOTS / 2 && nv <= VSH / 2;
+    bool in_sh = nb <= g.slots / 2 && nv <= VSH / 2;
     int status_local = 0;
     int* keys;
     int* hpos;
@@ -472,9 +744,9 @@ __global__ void __launch_bounds__(IW * 32, 2)
     uint32_t hmask;
     for (;;) {
       if (in_sh) {
-        keys = W.keys, hpos = W.hpos, scol = W.scol, soff = W.soff, sstate = W.sstate, sf2 = W.sf2;
-        wv = reinterpret_cast<T*>(W.vals);
-        smax_c = WS_SLOTS, vmax_c = VSH, hmask = WS_HASH - 1;
+        keys = sh_keys, hpos = sh_hpos, scol = sh_scol, soff = sh_soff, sstate = sh_sst, sf2 = sh_sf2;
+        wv = sh_vals;
+        smax_c = g.slots, vmax_c = VSH, hmask = (uint32_t)g.hash - 1;
       } else {
         keys = gkeys, hpos = ws.hpos + wid * ws.smax, scol = ws.scol + wid * ws.smax;
         soff = ws.soff + wid * ws.smax, sstate = ws.sstate + wid * ws.smax, sf2 = ws.sf2 + wid * ws.smax;
@@ -482,10 +754,10 @@ __global__ void __launch_bounds__(IW * 32, 2)
         smax_c = ws.smax, vmax_c = ws.vmax, hmask = (uint32_t)ws.ht - 1;
       }
       if (lane == 0) {
-        W.nslots = 0;
-        W.nvals = 0;
-        W.flag = 0;
-        W.nl = 0;
+        M.nslots = 0;
+        M.nvals = 0;
+        M.flag = 0;
+        M.nl = 0;
       }
       __syncwarp();
       // ---- load row i of A into the workspace: slot q is the row's block q
@@ -506,17 +778,17 @@ __global__ void __launch_bounds__(IW * 32, 2)
           sstate[slot] = SL_LIVE;
           hpos[slot] = ws_place(keys, hmask, slot, J);  // the table holds 2 smax positions
           if (J < i) {
-            const int q = atomicAdd(&W.nl, 1);
-            if (q < LCAP) {
-              W.lc[q] = J;
-              W.ls[q] = slot;
+            const int q = atomicAdd(&M.nl, 1);
+            if (q < g.lcap) {
+              lc[q] = J;
+              ls[q] = slot;
             }
           }
         }
         warp_copy(wv, A.val + v0, nv, lane);
         if (lane == 0) {
-          W.nslots = nb;
-          W.nvals = (unsigned long long)nv;
+          M.nslots = nb;
+          M.nvals = (unsigned long long)nv;
         }
       }
       __syncwarp();
@@ -524,144 +796,174 @@ __global__ void __launch_bounds__(IW * 32, 2)
       int64_t last = -1;
       // ---- eliminate the L part in ascending column order (including fill)
       while (status_local == 0) {
-        // next pending L column: from the list while it has not overflowed,
-        // else by a scan of the workspace slots
-        int best = 0x7fffffff, bslot = -1, bpos = -1;
+        // the next pending L column and the one after it: from the list while
+        // it has not overflowed, else by a scan of the workspace slots
+        int c1 = INT_MAX, s1 = -1, p1 = -1, c2 = INT_MAX;
         const int nlist = *vnl;
-        if (nlist <= LCAP) {
+        if (nlist <= g.lcap) {
           for (int q = lane; q < nlist; q += 32) {
-            const int c = W.lc[q];
-            if (c < best) {
-              best = c;
-              bslot = W.ls[q];
-              bpos = q;
+            const int c = lc[q];
+            if (c < c1) {
+              c2 = c1;
+              c1 = c;
+              s1 = ls[q];
+              p1 = q;
+            } else if (c < c2) {
+              c2 = c;
             }
           }
         } else {
           const int ns = min(*vns, smax_c);
           for (int sidx = lane; sidx < ns; sidx += 32) {
             const int c = scol[sidx];
-            if (sstate[sidx] == SL_LIVE && c > last && c < i && c < best) {
-              best = c;
-              bslot = sidx;
+            if (sstate[sidx] == SL_LIVE && c > last && c < i) {
+              if (c < c1) {
+                c2 = c1;
+                c1 = c;
+                s1 = sidx;
+              } else if (c < c2) {
+                c2 = c;
+              }
             }
           }
         }
-        const int kmin = warp_min_i(best);
-        if (kmin == 0x7fffffff) break;
-        const unsigned who = __ballot_sync(0xffffffffu, bslot >= 0 && best == kmin);
+        const int kmin = warp_min_i(c1);
+        if (kmin == INT_MAX) break;
+        const unsigned who = __ballot_sync(0xffffffffu, s1 >= 0 && c1 == kmin);
         const int owner = __ffs(who) - 1;
-        const int sk = __shfl_sync(0xffffffffu, bslot, owner);
-        if (lane == owner && bpos >= 0) W.lc[bpos] = 0x7fffffff;
+        const int sk = __shfl_sync(0xffffffffu, s1, owner);
+        const int knext = warp_min_i(lane == owner ? c2 : c1);
+        if (lane == owner && p1 >= 0) lc[p1] = INT_MAX;
         const int64_t k = kmin;
         last = k;
-        // static data of row k: loaded before the wait, used after it
         const int nk = A.rsz[k];
-        const int64_t dgk = dgoff[k];
-        const int64_t rk = A.roff[k];
-        // bounded wait until row k is published; a row that failed publishes
-        // 2 (its factors must not be used)
-        if (lane == 0 && wait_flag(P.done + k, P.abort, wait_limit, st) != 1) *vflag = 2;
-        __syncwarp();
-        if (*vflag == 2) {
-          status_local = DEV_ETIMEOUT;
-          break;
-        }
-        T* m = wv + soff[sk];
-        // the pivot block of k goes to shared memory: its own buffer when
-        // small, else the free tail of the value buffer (new slots are only
-        // created after the multiplier), sized for FP64
-        unsigned char* lus = nullptr;
-        if (nk <= SMB) {
-          lus = W.lu;
-        } else if (nk <= PVMAX) {
-          const long long used = in_sh ? ((long long)W.nvals * (long long)sizeof(T) + 15) / 16 * 16 : 0;
-          if (used + (long long)nk * nk * (long long)sizeof(double) <= WS_VBYTES) lus = W.vals + used;
-        }
-        const bool staged = lus != nullptr;
-        double* const luD = reinterpret_cast<double*>(lus);
-        float* const luF = reinterpret_cast<float*>(lus);
-        // round A: the precision tag and the extent of U row k (lanes 0-4),
-        // the pivot block of k and its pivots
-        long long hv = 0;
-        if (lane == 0)
-          hv = ptag ? __ldcg(ptag + k) : 1;
-        else if (lane == 1)
-          hv = __ldcg(P.ustart + k);
-        else if (lane == 2)
-          hv = __ldcg(P.ucnt + k);
-        else if (lane == 3)
-          hv = __ldcg(P.uvstart + k);
-        else if (lane == 4)
-          hv = __ldcg(P.uvlen + k);
-        if (staged && nk <= SMB) {  // every load issued before the first store
-          constexpr int LV = SMB * SMB / 32;
-          using TS = typename std::conditional<sizeof(T) == sizeof(double), double, float>::type;
-          const TS* src = sizeof(T) == sizeof(double) ? reinterpret_cast<const TS*>(dg) : reinterpret_cast<const TS*>(dg32);
-          TS* dstl = reinterpret_cast<TS*>(lus);
-          TS lv[LV];
-#pragma unroll
-          for (int u = 0; u < LV; ++u) {
-            const int e = lane + 32 * u;
-            lv[u] = e < nk * nk ? __ldcg(src + dgk + e) : (TS)0;
+        // ---- row k's record: already fetched ahead into a stage buffer, or
+        // fetched now (a bounded wait for its word, then one bulk copy); a
+        // record too large for a buffer is read in place
+        int bi = btag0 == (int)k ? 0 : (btag1 == (int)k ? 1 : -1);
+        const unsigned char* rec = nullptr;
+        int64_t rlen = 0;
+        if (bi < 0) {
+          unsigned long long word = 0;
+          if (lane == 0) word = wait_word(P.done + k, P.abort, wait_limit, st);
+          word = __shfl_sync(0xffffffffu, word, 0);
+          if (word == 0 || word == kRowFailed) {
+            status_local = DEV_ETIMEOUT;
+            break;
           }
-          const int pvv = lane < nk ? __ldcg(piv + rk + lane) : 0;
-#pragma unroll
-          for (int u = 0; u < LV; ++u) {
-            const int e = lane + 32 * u;
-            if (e < nk * nk) dstl[e] = lv[u];
+          rlen = (int64_t)(word & 0xFFFFFFull) * 16;
+          const unsigned char* src = upool + (int64_t)(word >> 24) * 16;
+          if (rlen <= g.stage) {
+            // a free buffer, else one holding a record fetched ahead for a
+            // later column: its copy is waited for before the buffer is reused
+            bi = btag0 < 0 ? 0 : (btag1 < 0 ? 1 : 0);
+            bool ok = true;
+            if (bi == 0 && bpend0) {
+              ok = mbar_wait(&M.mbar[0], bph0, wait_limit);
+              if (ok) bph0 ^= 1;
+              bpend0 = !ok;
+            } else if (bi == 1 && bpend1) {
+              ok = mbar_wait(&M.mbar[1], bph1, wait_limit);
+              if (ok) bph1 ^= 1;
+              bpend1 = !ok;
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+              if (lane == 0) dev_fail(st, DEV_ETIMEOUT);
+              status_local = DEV_ETIMEOUT;
+              break;
+            }
+            if (lane == 0) {
+              fence_proxy_async_all();
+              bulk_load(bi ? stage1 : stage0, src, (unsigned)rlen, &M.mbar[bi]);
+            }
+            if (bi) {
+              btag1 = (int)k;
+              bpend1 = true;
+            } else {
+              btag0 = (int)k;
+              bpend0 = true;
+            }
+          } else {
+            rec = src;
           }
-          if (lane < nk) W.pv[lane] = pvv;
-        } else if (staged) {
-          if (sizeof(T) == sizeof(double))
-            for (int e = lane; e < nk * nk; e += 32) luD[e] = __ldcg(dg + dgk + e);
-          else
-            for (int e = lane; e < nk * nk; e += 32) luF[e] = __ldcg(dg32 + dgk + e);
-          if (lane < nk) W.pv[lane] = __ldcg(piv + rk + lane);
         }
-        const int tag = (int)__shfl_sync(0xffffffffu, hv, 0);
-        const int64_t u0 = __shfl_sync(0xffffffffu, hv, 1);
-        const int uc = (int)__shfl_sync(0xffffffffu, hv, 2);
-        const int64_t uvs = __shfl_sync(0xffffffffu, hv, 3);
-        const int64_t uvl = __shfl_sync(0xffffffffu, hv, 4);
-        if (u0 < 0 || uc < 0 || u0 + uc > P.ubcap || uvs < 0 || uvl < 0 || uvs + uvl > P.uvcap) {
+        // the next pending column's record, fetched ahead while this step
+        // computes, when its row is already published, no buffer holds it
+        // yet and a buffer is free (the current step's buffer holds k)
+        if (knext != INT_MAX && btag0 != knext && btag1 != knext) {
+          const int ob = btag0 < 0 ? 0 : (btag1 < 0 ? 1 : -1);
+          int go = 0;
+          unsigned long long w2 = 0;
+          if (ob >= 0 && lane == 0) {
+            w2 = ld_relaxed_u64(P.done + knext);
+            if (w2 != 0 && w2 != kRowFailed && (int64_t)(w2 & 0xFFFFFFull) * 16 <= g.stage) {
+              asm volatile("fence.acq_rel.gpu;" ::: "memory");
+              fence_proxy_async_all();
+              bulk_load(ob ? stage1 : stage0, upool + (int64_t)(w2 >> 24) * 16, (unsigned)((w2 & 0xFFFFFFull) * 16),
+                        &M.mbar[ob]);
+              go = 1;
+            }
+          }
+          go = __shfl_sync(0xffffffffu, go, 0);
+          if (go) {
+            if (ob) {
+              btag1 = knext;
+              bpend1 = true;
+            } else {
+              btag0 = knext;
+              bpend0 = true;
+            }
+          }
+        }
+        if (bi >= 0) {
+          bool ok = true;
+          if (bi == 0 && bpend0) {
+            ok = mbar_wait(&M.mbar[0], bph0, wait_limit);
+            if (ok) bph0 ^= 1;
+            bpend0 = !ok;
+          } else if (bi == 1 && bpend1) {
+            ok = mbar_wait(&M.mbar[1], bph1, wait_limit);
+            if (ok) bph1 ^= 1;
+            bpend1 = !ok;
+          }
+          if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) dev_fail(st, DEV_ETIMEOUT);
+            status_local = DEV_ETIMEOUT;
+            break;
+          }
+          rec = bi ? stage1 : stage0;
+        }
+        const bool staged = bi >= 0;
+        // header: U blocks, pivot size, pivot precision, U values
+        int hv = 0;
+        if (lane < 4) hv = staged ? reinterpret_cast<const int*>(rec)[lane] : __ldcg(reinterpret_cast<const int*>(rec) + lane);
+        const int ucnt = __shfl_sync(0xffffffffu, hv, 0);
+        const int hnk = __shfl_sync(0xffffffffu, hv, 1);
+        const int lu64 = __shfl_sync(0xffffffffu, hv, 2);
+        const int uval_n = __shfl_sync(0xffffffffu, hv, 3);
+        const RecLayout RL = rec_layout(ucnt, nk, lu64, uval_n, TS);
+        if (hnk != nk || ucnt < 0 || uval_n < 0 || (!staged && RL.bytes > rlen && rlen) ||
+            (staged && RL.bytes > g.stage)) {
           status_local = DEV_INTERNAL;  // never true for a published row: record and skip
           break;
         }
-        // round B, in flight during the multiplier: U row k into shared memory
-        // (16-byte asynchronous copies; U rows start 16-byte aligned in the
-        // pool and their padding is reserved) and the columns and offsets of
-        // its first 32 blocks
-        const bool ust = uvl <= USTAGE && ((uvs * (int64_t)sizeof(T)) & 15) == 0;
-        if (ust) {
-          const int nch = (int)((uvl * (int64_t)sizeof(T) + 15) / 16);
-          const unsigned char* src = reinterpret_cast<const unsigned char*>(uval + uvs);
-          for (int c = lane; c < nch; c += 32) cp_async16(W.ustage + 16 * c, src + 16 * c);
-        }
-        int32_t pj = -1;
-        int64_t puo = 0;
-        if (lane < uc) {
-          pj = __ldcg(P.ucol + u0 + lane);
-          puo = __ldcg(P.uvo + u0 + lane);
-        }
-        const bool use64 = sizeof(T) == sizeof(double) || tag != 0;
-        if (staged && use64 && sizeof(T) != sizeof(double))  // an FP64 pivot block of the mixed factor
-          for (int e = lane; e < nk * nk; e += 32) luD[e] = __ldcg(dg + dgk + e);
-        __syncwarp();
+        const int* rpiv = reinterpret_cast<const int*>(rec + RL.piv);
+        const int* rcol = reinterpret_cast<const int*>(rec + RL.ucol);
+        const int* rrel = reinterpret_cast<const int*>(rec + RL.urel);
+        const T* rval = reinterpret_cast<const T*>(rec + RL.val);
+        T* m = wv + soff[sk];
         // the multiplier m = a_ik (P^T L U)_k^{-1}, in place, one lane per row
-        if (staged) {
-          for (int a = lane; a < ni; a += 32) {
-            if (use64)
-              ainv_right_row_sh<T, double>(luD, W.pv, nk, m + a * nk);
+        for (int a = lane; a < ni; a += 32) {
+          if (staged) {
+            if (lu64)
+              ainv_right_row_sh<T, double, double>(reinterpret_cast<const double*>(rec + RL.lu), rpiv, nk, m + a * nk);
             else
-              ainv_right_row_sh<T, float>(luF, W.pv, nk, m + a * nk);
-          }
-        } else {
-          for (int a = lane; a < ni; a += 32) {
-            if (use64)
-              ainv_right_row<T, double>(dg + dgk, piv + rk, nk, m + a * nk);
+              ainv_right_row_sh<T, float, T>(reinterpret_cast<const T*>(rec + RL.lu), rpiv, nk, m + a * nk);
+          } else {
+            if (lu64)
+              ainv_right_row<T, double>(reinterpret_cast<const double*>(rec + RL.lu), rpiv, nk, m + a * nk);
             else
-              ainv_right_row<T, float>(dg32 + dgk, piv + rk, nk, m + a * nk);
+              ainv_right_row<T, T>(reinterpret_cast<const T*>(rec + RL.lu), rpiv, nk, m + a * nk);
           }
         }
         __syncwarp();
@@ -683,10 +985,11 @@ __global__ void __launch_bounds__(IW * 32, 2)
           dropped = drop_rule_f(sf, ni, nk, tf);
           key = norm_key(sf);
         }
-        if (ust) cp_async_wait_all();
         if (dropped) {
           if (lane == 0) sstate[sk] = SL_DEAD;
           __syncwarp();
+          if (bi == 0) btag0 = -1;
+          if (bi == 1) btag1 = -1;
           continue;
         }
         if (lane == 0) {
@@ -697,22 +1000,17 @@ __global__ void __launch_bounds__(IW * 32, 2)
         // U row k in chunks of 32 blocks: look up or create the target blocks
         // (probe, then place, separated by __syncwarp), then update all
         // elements of the chunk with lanes spread over the flattened elements.
-        for (int q0 = 0; q0 < uc && status_local == 0; q0 += 32) {
+        for (int q0 = 0; q0 < ucnt && status_local == 0; q0 += 32) {
           const int q = q0 + lane;
           int32_t j = -1;
           int slot = -1;
-          int64_t uo = 0;
+          int uo = 0;
           bool missing = false;
-          if (q < uc) {
-            if (q0 == 0) {
-              j = pj;
-              uo = puo;
-            } else {
-              j = __ldcg(P.ucol + u0 + q);
-              uo = __ldcg(P.uvo + u0 + q);
-            }
-            if (j <= k || j >= A.nbr || uo < uvs || uo + (int64_t)nk * A.rsz[j] > uvs + uvl) {
-              *vflag = 4;  // a published U block lies right of k inside its row's extent
+          if (q < ucnt) {
+            j = staged ? rcol[q] : __ldcg(rcol + q);
+            uo = staged ? rrel[q] : __ldcg(rrel + q);
+            if (j <= k || j >= A.nbr || uo < 0 || (int64_t)uo + (int64_t)nk * A.rsz[j] > uval_n) {
+              *vflag = 4;  // a published U block lies right of k inside its record
               j = -1;
             } else {
               slot = ws_lookup(keys, scol, hmask, j);
@@ -722,7 +1020,7 @@ __global__ void __launch_bounds__(IW * 32, 2)
           __syncwarp();
           if (missing) {
             const int sz = ni * A.rsz[j];
-            slot = ws_new_slot(smax_c, vmax_c, keys, hpos, scol, soff, sstate, &W.nslots, &W.nvals, hmask, j, sz);
+            slot = ws_new_slot(smax_c, vmax_c, keys, hpos, scol, soff, sstate, &M.nslots, &M.nvals, hmask, j, sz);
             if (slot < 0) {
               *vflag = 1;
             } else {
@@ -730,10 +1028,10 @@ __global__ void __launch_bounds__(IW * 32, 2)
 #pragma unroll 4
               for (int e = 0; e < sz; ++e) z[e] = (T)0;
               if (j < i) {  // fill in the L part: pending for a later step
-                const int pq = atomicAdd(&W.nl, 1);
-                if (pq < LCAP) {
-                  W.lc[pq] = j;
-                  W.ls[pq] = slot;
+                const int pq = atomicAdd(&M.nl, 1);
+                if (pq < g.lcap) {
+                  lc[pq] = j;
+                  ls[pq] = slot;
                 }
               }
             }
@@ -755,14 +1053,13 @@ __global__ void __launch_bounds__(IW * 32, 2)
             if (lane >= o) incl += v;
           }
           const int total = __shfl_sync(0xffffffffu, incl, 31);
-          W.qpre[lane] = incl - sz;
-          if (lane == 31) W.qpre[32] = total;
-          W.qoff[lane] = slot >= 0 ? soff[slot] : 0;
-          W.quo[lane] = (int)(uo - uvs);
-          W.qnj[lane] = nj;
+          M.qpre[lane] = incl - sz;
+          if (lane == 31) M.qpre[32] = total;
+          M.qoff[lane] = slot >= 0 ? soff[slot] : 0;
+          M.quo[lane] = uo;
+          M.qnj[lane] = nj;
           __syncwarp();
-          const int nq = min(32, uc - q0);
-          const T* Ubase = ust ? ustage : uval + uvs;
+          const int nq = min(32, ucnt - q0);
           // four elements per lane in flight
           for (int e0 = lane; e0 < total; e0 += 128) {
             T acc[4];
@@ -776,27 +1073,27 @@ __global__ void __launch_bounds__(IW * 32, 2)
                 int lo = 0, hi = nq - 1;  // block tq with qpre[tq] <= e < qpre[tq + 1]
                 while (lo < hi) {
                   const int mid = (lo + hi + 1) >> 1;
-                  if (W.qpre[mid] <= e)
+                  if (M.qpre[mid] <= e)
                     lo = mid;
                   else
                     hi = mid - 1;
                 }
-                const int njt = W.qnj[lo];
-                const int local = e - W.qpre[lo];
+                const int njt = M.qnj[lo];
+                const int local = e - M.qpre[lo];
                 a4[u] = local / njt;
                 jj4[u] = local - a4[u] * njt;
                 nj4[u] = njt;
-                uo4[u] = W.quo[lo];
-                dst[u] = wv + W.qoff[lo] + local;
+                uo4[u] = M.quo[lo];
+                dst[u] = wv + M.qoff[lo] + local;
                 acc[u] = *dst[u];
               }
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               if (!dst[u]) continue;
-              const T* U = Ubase + uo4[u];
+              const T* U = rval + uo4[u];
               T av = acc[u];
-              if (ust) {
+              if (staged) {
                 for (int r = 0; r < nk; ++r) av = msub<T>(av, m[a4[u] * nk + r], U[r * nj4[u] + jj4[u]]);
               } else {
                 for (int r = 0; r < nk; ++r) av = msub<T>(av, m[a4[u] * nk + r], __ldcg(U + r * nj4[u] + jj4[u]));
@@ -806,317 +1103,293 @@ __global__ void __launch_bounds__(IW * 32, 2)
           }
           __syncwarp();
         }
+        if (bi == 0) btag0 = -1;
+        if (bi == 1) btag1 = -1;
       }
       if (status_local == DEV_OVERFLOW && in_sh) {
         // the fill outgrew the shared workspace: start the row again in the
-        // global one
-        for (int q = lane; q < WS_HASH; q += 32) W.keys[q] = -1;
+        // global one (records fetched ahead stay valid)
+        for (int q = lane; q < g.hash; q += 32) sh_keys[q] = -1;
         __syncwarp();
         in_sh = false;
         continue;
       }
       break;
     }
+    drain();  // every record fetched ahead has been used, unless the row failed
     const int ns = min(*vns, smax_c);
-    // ---- finish the row.  A row in the global workspace has its slot
-    // metadata staged in shared memory (the U-row stage buffer is free now)
-    // so that the scans below read on-chip data; rows with more than MSH
-    // slots read the workspace directly.
-    int* mcol = reinterpret_cast<int*>(W.ustage);
-    int* mst = mcol + MSH;
-    int* moff = mst + MSH;
-    long long* mf2 = reinterpret_cast<long long*>(moff + MSH);
-    const bool msh = !in_sh && ns <= MSH;
-    if (msh)
-      for (int q = lane; q < ns; q += 32) {
-        mcol[q] = scol[q];
-        mst[q] = sstate[q];
-        moff[q] = soff[q];
-        mf2[q] = sf2[q];
-      }
-    __syncwarp();
-    auto COL = [&](int q) { return msh ? mcol[q] : scol[q]; };
-    auto ST = [&](int q) { return msh ? mst[q] : sstate[q]; };
-    auto OFF = [&](int q) { return msh ? moff[q] : soff[q]; };
-    auto F2 = [&](int q) { return msh ? mf2[q] : sf2[q]; };
-    auto IS_L = [&](int q) { return ST(q) == SL_LKEPT; };
-    auto IS_U = [&](int q) { return ST(q) == SL_LIVE && COL(q) > i; };
+    // ---- finish the row.
     int dslot = -1;
     if (status_local == 0) {
       for (int q = lane; q < ns; q += 32)
-        if (COL(q) == i && ST(q) == SL_LIVE) dslot = q;
+        if (scol[q] == i && sstate[q] == SL_LIVE) dslot = q;
       dslot = warp_max_i(dslot);
       if (dslot < 0) status_local = DEV_ESINGULAR;
     }
-    bool fits = false;
-    unsigned long long lb = 0, lvv = 0, ub = 0, uvv = 0;
-    int nl = 0, nu = 0;
-    long long vl = 0, vu = 0;
+    // GEPP of the diagonal block, in shared memory when it fits (the stage
+    // buffers are free now).  FP64 factor: FP64 in the oracle's operation
+    // order.  Mixed factor: FP32 GEPP and 1-norm condition estimate (explicit
+    // inverse columns); a block above the threshold, larger than 32, or
+    // singular in FP32 is factored again in FP64 and tagged.
+    bool tag64 = sizeof(T) == sizeof(double);
     if (status_local == 0) {
-      // U part: threshold on the blocks right of the diagonal
+      const T* srcd = wv + soff[dslot];
+      unsigned char* gb = stage0;
+      const int gcap = 2 * g.stage;
+      const bool gs32 = ni * ni * 4 <= gcap, gs64 = ni * ni * 8 <= gcap;
+      int* pvs = ni <= PVMAX ? M.pv : nullptr;
+      int32_t* gpiv = piv + A.roff[i];
+      bool ok = true;
+      if (sizeof(T) == sizeof(float)) {
+        tag64 = true;
+        float* a = gs32 ? reinterpret_cast<float*>(gb) : dg32 + dgoff[i];
+        for (int e = lane; e < ni * ni; e += 32) a[e] = (float)srcd[e];
+        __syncwarp();
+        float norm1 = 0.f;
+        for (int jj = lane; jj < ni; jj += 32) {
+          float sum = 0.f;
+          for (int ii = 0; ii < ni; ++ii) sum += fabsf(a[ii * ni + jj]);
+          norm1 = fmaxf(norm1, sum);
+        }
+        for (int o = 16; o > 0; o >>= 1) norm1 = fmaxf(norm1, __shfl_xor_sync(0xffffffffu, norm1, o));
+        __syncwarp();
+        if (ni <= 32 && gepp_warp<float>(a, ni, pvs, gpiv, lane)) {
+          const float kappa = norm1 * inv_norm1_f32(a, ni, pvs ? pvs : gpiv, lane);
+          tag64 = !(kappa <= condf);
+          if (!tag64) {
+            for (int e = lane; e < ni * ni; e += 32) {
+              if (gs32) dg32[dgoff[i] + e] = a[e];
+              dg[dgoff[i] + e] = (double)a[e];
+            }
+          }
+        }
+        __syncwarp();
+      }
+      if (tag64) {
+        double* a = gs64 ? reinterpret_cast<double*>(gb) : dg + dgoff[i];
+        for (int e = lane; e < ni * ni; e += 32) a[e] = (double)srcd[e];
+        __syncwarp();
+        ok = gepp_warp<double>(a, ni, pvs, gpiv, lane);
+        if (ok)
+          for (int e = lane; e < ni * ni; e += 32) {
+            if (gs64) dg[dgoff[i] + e] = a[e];
+            if (mixed) dg32[dgoff[i] + e] = (float)a[e];
+          }
+      }
+      __syncwarp();
+      if (!ok)
+        status_local = DEV_ESINGULAR;
+      else if (mixed && lane == 0)
+        ptag[i] = tag64 ? 1 : 0;
+    }
+    // U part: threshold on the blocks right of the diagonal (norm keys kept
+    // for lfil)
+    if (status_local == 0) {
       for (int q = lane; q < ns; q += 32) {
-        const int c = COL(q);
-        if (ST(q) == SL_LIVE && c > i) {
+        const int c = scol[q];
+        if (sstate[q] == SL_LIVE && c > i) {
           const int nc = A.rsz[c];
           bool drop;
-          long long key;
+          long long kq;
           if (sizeof(T) == sizeof(double)) {
-            const double f2 = fro2_batched(wv + OFF(q), ni * nc);
+            const double f2 = fro2_batched(wv + soff[q], ni * nc);
             drop = drop_rule(f2, ni, nc, t);
-            key = norm_key(f2);
+            kq = norm_key(f2);
           } else {
-            const float f2 = fro2_f32(wv + OFF(q), ni * nc);
+            const float f2 = fro2_f32(wv + soff[q], ni * nc);
             drop = drop_rule_f(f2, ni, nc, tf);
-            key = norm_key(f2);
+            kq = norm_key(f2);
           }
-          if (msh) mf2[q] = key; else sf2[q] = key;
-          if (drop) {
-            if (msh) mst[q] = SL_DEAD; else sstate[q] = SL_DEAD;
-          }
+          sf2[q] = kq;
+          if (drop) sstate[q] = SL_DEAD;
         }
       }
       __syncwarp();
-      // lfil: keep the lfil largest of the L part and of the U part (rank by
-      // (norm desc, column asc); ranks computed before any state changes)
-      if (lfil >= 0) {
-        unsigned cutmask[MAX_SLOTS / 1024] = {};  // bit tq: slot lane + 32 tq is cut
-        for (int tq = 0; tq * 32 < ns && tq < MAX_SLOTS / 32; ++tq) {
-          const int q = tq * 32 + lane;
-          if (q >= ns) continue;
-          const bool isL = IS_L(q), isU = IS_U(q);
-          if (!isL && !isU) continue;
-          const long long fq = F2(q);
-          const int cq = COL(q);
-          int rank = 0;
-          for (int r2 = 0; r2 < ns; ++r2) {
-            const bool same = isL ? IS_L(r2) : IS_U(r2);
-            if (same) {
-              const long long fr = F2(r2);
-              if (fr > fq || (fr == fq && COL(r2) < cq)) ++rank;
-            }
-          }
-          if (rank >= lfil) cutmask[tq >> 5] |= 1u << (tq & 31);
-        }
-        __syncwarp();
-        for (int tq = 0; tq < MAX_SLOTS / 32; ++tq)
-          if (cutmask[tq >> 5] & (1u << (tq & 31))) {
-            const int q = tq * 32 + lane;
-            if (msh) mst[q] = SL_DEAD; else sstate[q] = SL_DEAD;
-          }
-        __syncwarp();
-      }
+    }
+    // candidate lists of the kept L blocks and the surviving U blocks, the
+    // lfil cut of each, then each part sorted by column; in the stage buffers
+    // when they fit, else in the warp's global finish space
+    int nL = 0, nU = 0, n2L = 0, n2U = 0;
+    int* candL = nullptr;
+    int* candU = nullptr;
+    unsigned long long* srtL = nullptr;
+    unsigned long long* srtU = nullptr;
+    if (status_local == 0) {
+      int cl = 0, cu = 0;
       for (int q = lane; q < ns; q += 32) {
-        const int c = COL(q);
-        if (IS_L(q)) {
-          ++nl;
-          vl += (long long)ni * A.rsz[c];
-        } else if (IS_U(q)) {
-          ++nu;
-          vu += (long long)ni * A.rsz[c];
-        }
+        const int s = sstate[q];
+        cl += s == SL_LKEPT;
+        cu += s == SL_LIVE && scol[q] > i;
       }
-      nl = warp_sum_i(nl);
-      nu = warp_sum_i(nu);
+      cl = warp_sum_i(cl);
+      cu = warp_sum_i(cu);
+      int p2l = 1, p2u = 1;
+      while (p2l < cl) p2l <<= 1;
+      while (p2u < cu) p2u <<= 1;
+      const int64_t need = 4LL * (cl + cu) + 8LL * (p2l + p2u) + 16;
+      if (need <= 2LL * g.stage) {
+        candL = reinterpret_cast<int*>(stage0);
+        candU = candL + cl;
+        srtL = reinterpret_cast<unsigned long long*>(stage0 + ((4LL * (cl + cu) + 15) & ~15LL));
+        srtU = srtL + p2l;
+      } else {
+        candL = ws.fin + wid * 2 * ws.smax;
+        candU = candL + ws.smax;
+        srtL = ws.srt + wid * 4 * ws.smax;
+        srtU = srtL + 2 * ws.smax;
+      }
+      for (int base = 0; base < ns; base += 32) {
+        const int q = base + lane;
+        bool isL = false, isU = false;
+        if (q < ns) {
+          const int s = sstate[q];
+          isL = s == SL_LKEPT;
+          isU = s == SL_LIVE && scol[q] > i;
+        }
+        const unsigned bL = __ballot_sync(0xffffffffu, isL), bU = __ballot_sync(0xffffffffu, isU);
+        const unsigned lt = (1u << lane) - 1u;
+        if (isL) candL[nL + __popc(bL & lt)] = q;
+        if (isU) candU[nU + __popc(bU & lt)] = q;
+        nL += __popc(bL);
+        nU += __popc(bU);
+      }
+      __syncwarp();
+      // lfil: keep the lfil largest of the L part and of the U part
+      nL = lfil_cut(candL, nL, lfil, sf2, scol, sstate, M.hist, TS, lane);
+      nU = lfil_cut(candU, nU, lfil, sf2, scol, sstate, M.hist, TS, lane);
+      n2L = sort_by_column(candL, nL, scol, srtL, lane);
+      n2U = sort_by_column(candU, nU, scol, srtU, lane);
+    }
+    // sizes, then the pool space: the U record and the L blocks
+    long long vl = 0, vu = 0;
+    unsigned long long lb = 0, lvv = 0, roff16 = 0;
+    int64_t rbytes = 0;
+    int lu64r = 0;
+    if (status_local == 0) {
+      for (int p = lane; p < nL; p += 32) vl += (long long)ni * A.rsz[(int)(srtL[p] >> 32)];
+      for (int p = lane; p < nU; p += 32) vu += (long long)ni * A.rsz[(int)(srtU[p] >> 32)];
       vl = warp_sum_ll(vl);
       vu = warp_sum_ll(vu);
-      // U rows are reserved in whole 16-byte units so that every row starts
-      // 16-byte aligned (the readers stage them with 16-byte copies)
-      constexpr long long UQ = 16 / (long long)sizeof(T);
-      const long long vu_pad = (vu + UQ - 1) / UQ * UQ;
+      lu64r = (sizeof(T) == sizeof(double) || tag64) ? 1 : 0;
+      const RecLayout RL = rec_layout(nU, ni, lu64r, vu, TS);
+      rbytes = RL.bytes;
       if (lane == 0) {
-        lb = atomicAdd(P.ctr + 0, (unsigned long long)nl);
+        lb = atomicAdd(P.ctr + 0, (unsigned long long)nL);
         lvv = atomicAdd(P.ctr + 1, (unsigned long long)vl);
-        ub = atomicAdd(P.ctr + 2, (unsigned long long)nu);
-        uvv = atomicAdd(P.ctr + 3, (unsigned long long)vu_pad);
+        roff16 = atomicAdd(P.ctr + 2, (unsigned long long)(rbytes / 16));
       }
       lb = __shfl_sync(0xffffffffu, lb, 0);
       lvv = __shfl_sync(0xffffffffu, lvv, 0);
-      ub = __shfl_sync(0xffffffffu, ub, 0);
-      uvv = __shfl_sync(0xffffffffu, uvv, 0);
-      fits = (int64_t)(lb + nl) <= P.lbcap && (int64_t)(lvv + vl) <= P.lvcap && (int64_t)(ub + nu) <= P.ubcap &&
-             (int64_t)(uvv + vu_pad) <= P.uvcap;
+      roff16 = __shfl_sync(0xffffffffu, roff16, 0);
+      const bool fits = (int64_t)(lb + nL) <= P.lbcap && (int64_t)(lvv + vl) <= P.lvcap &&
+                        (int64_t)roff16 + rbytes / 16 <= P.ucap16 && rbytes / 16 <= kRecMaxUnits &&
+                        vu <= INT_MAX;
       if (!fits) status_local = DEV_OVERFLOW;
-      if (status_local == 0) {
-        // GEPP of the diagonal block, in shared memory when it fits.  FP64
-        // factor: FP64 in the oracle's operation order.  Mixed factor: FP32
-        // GEPP and 1-norm condition estimate (explicit inverse columns); a
-        // block above the threshold, larger than 32, or singular in FP32 is
-        // factored again in FP64 and tagged.
-        const T* srcd = wv + OFF(dslot);
-        // staging: the small-block buffer, else the U-row buffer (free now)
-        // of a shared working row or the value buffer of a global one
-        unsigned char* gb = nullptr;
-        int gcap = 0;
-        if (ni <= SMB) {
-          gb = W.lu, gcap = (int)sizeof(W.lu);
-        } else if (ni <= PVMAX) {
-          if (in_sh)
-            gb = W.ustage, gcap = USTAGE_BYTES;
-          else
-            gb = W.vals, gcap = WS_VBYTES;
-        }
-        const bool gs32 = gb && ni * ni * 4 <= gcap, gs64 = gb && ni * ni * 8 <= gcap;
-        int* pvs = gb ? W.pv : nullptr;
-        int32_t* gpiv = piv + A.roff[i];
-        bool ok = true, tag64 = true;
-        if (sizeof(T) == sizeof(float)) {
-          const bool gsh = gs32;
-          float* a = gsh ? reinterpret_cast<float*>(gb) : dg32 + dgoff[i];
-          for (int e = lane; e < ni * ni; e += 32) a[e] = (float)srcd[e];
-          __syncwarp();
-          float norm1 = 0.f;
-          for (int jj = lane; jj < ni; jj += 32) {
-            float sum = 0.f;
-            for (int ii = 0; ii < ni; ++ii) sum += fabsf(a[ii * ni + jj]);
-            norm1 = fmaxf(norm1, sum);
-          }
-          for (int o = 16; o > 0; o >>= 1) norm1 = fmaxf(norm1, __shfl_xor_sync(0xffffffffu, norm1, o));
-          __syncwarp();
-          if (ni <= 32 && gepp_warp<float>(a, ni, pvs, gpiv, lane)) {
-            const float kappa = norm1 * inv_norm1_f32(a, ni, pvs ? pvs : gpiv, lane);
-            tag64 = !(kappa <= condf);
-            if (!tag64) {
-              for (int e = lane; e < ni * ni; e += 32) {
-                if (gsh) dg32[dgoff[i] + e] = a[e];
-                dg[dgoff[i] + e] = (double)a[e];
-              }
-            }
-          }
-          __syncwarp();
-        }
-        if (tag64) {
-          const bool gsh = gs64;
-          double* a = gsh ? reinterpret_cast<double*>(gb) : dg + dgoff[i];
-          for (int e = lane; e < ni * ni; e += 32) a[e] = (double)srcd[e];
-          __syncwarp();
-          ok = gepp_warp<double>(a, ni, pvs, gpiv, lane);
-          if (ok)
-            for (int e = lane; e < ni * ni; e += 32) {
-              if (gsh) dg[dgoff[i] + e] = a[e];
-              if (mixed) dg32[dgoff[i] + e] = (float)a[e];
-            }
-        }
-        if (!ok)
-          status_local = DEV_ESINGULAR;
-        else if (mixed && lane == 0)
-          ptag[i] = tag64 ? 1 : 0;
-      }
     }
-    // Write the kept blocks of one part in column order: per chunk of 32
-    // slots the ranks come from the staged metadata, then the chunk's values
-    // are copied with lanes over the flattened elements, eight loads in
-    // flight per lane.
-    auto write_part = [&](bool isL, unsigned long long bstart, unsigned long long vstart, int32_t* pcol,
-                          int64_t* pvo, T* pval) {
-      for (int s0 = 0; s0 < ns; s0 += 32) {
-        const int q = s0 + lane;
-        int sz = 0;
-        int64_t src = 0, dstv = 0;
-        if (q < ns && (isL ? IS_L(q) : IS_U(q))) {
-          const int c = COL(q);
-          int rank = 0;
-          long long vo = 0;
-          for (int r2 = 0; r2 < ns; ++r2) {
-            const int cr = COL(r2);
-            if (cr < c && (isL ? IS_L(r2) : IS_U(r2))) {
-              ++rank;
-              vo += (long long)ni * A.rsz[cr];
-            }
-          }
+    // the U record: header, pivots, pivot LU, columns, value offsets, values
+    if (status_local == 0) {
+      const RecLayout RL = rec_layout(nU, ni, lu64r, vu, TS);
+      unsigned char* r = upool + (int64_t)roff16 * 16;
+      if (lane == 0) {
+        int* h = reinterpret_cast<int*>(r);
+        h[0] = nU;
+        h[1] = ni;
+        h[2] = lu64r;
+        h[3] = (int)vu;
+      }
+      const int32_t* gpiv = piv + A.roff[i];
+      for (int a = lane; a < ni; a += 32) reinterpret_cast<int*>(r + RL.piv)[a] = gpiv[a];
+      for (int e = lane; e < ni * ni; e += 32) {
+        if (lu64r)
+          reinterpret_cast<double*>(r + RL.lu)[e] = dg[dgoff[i] + e];
+        else
+          reinterpret_cast<float*>(r + RL.lu)[e] = dg32[dgoff[i] + e];
+      }
+      int* rcol = reinterpret_cast<int*>(r + RL.ucol);
+      int* rrel = reinterpret_cast<int*>(r + RL.urel);
+      T* rv = reinterpret_cast<T*>(r + RL.val);
+      int carry = 0;
+      for (int p0 = 0; p0 < nU; p0 += 32) {
+        const int p = p0 + lane;
+        int sz = 0, so = 0;
+        if (p < nU) {
+          const int c = (int)(srtU[p] >> 32), q = (int)(srtU[p] & 0xffffffffu);
           sz = ni * A.rsz[c];
-          src = OFF(q);
-          dstv = (int64_t)vstart + vo;
-          pcol[bstart + rank] = c;
-          pvo[bstart + rank] = dstv;
+          so = soff[q];
+          rcol[p] = c;
         }
         int incl = sz;
         for (int o = 1; o < 32; o <<= 1) {
           const int v = __shfl_up_sync(0xffffffffu, incl, o);
           if (lane >= o) incl += v;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        W.qpre[lane] = incl - sz;
-        W.qoff[lane] = (int)src;
-        W.wdst[lane] = dstv;
-        __syncwarp();
-        for (int e0 = lane; e0 < total; e0 += 32 * 8) {
-          T v[8];
-          int64_t d8[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int e = e0 + 32 * u;
-            d8[u] = -1;
-            if (e < total) {
-              int lo = 0, hi = 31;
-              while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (W.qpre[mid] <= e)
-                  lo = mid;
-                else
-                  hi = mid - 1;
-              }
-              // skip empty entries that share the same prefix
-              while (lo < 31 && W.qpre[lo + 1] <= e) ++lo;
-              const int local = e - W.qpre[lo];
-              v[u] = wv[W.qoff[lo] + local];
-              d8[u] = W.wdst[lo] + local;
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (d8[u] >= 0) pval[d8[u]] = v[u];
-        }
-        __syncwarp();
-      }
-    };
-    if (status_local == 0) {
-      write_part(false, ub, uvv, P.ucol, P.uvo, uval);
-      if (lane == 0) {
-        P.ustart[i] = (int64_t)ub;
-        P.ucnt[i] = nu;
-        P.uvstart[i] = (int64_t)uvv;
-        P.uvlen[i] = (int64_t)vu;
+        const int rel = carry + incl - sz;
+        if (p < nU) rrel[p] = rel;
+        copy_round<T>(M, sz, so, rel, wv, rv, lane);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
       }
     }
     if (status_local != 0 && lane == 0) {
       dev_fail(st, status_local);
       atomicExch(P.abort, 1);
       P.lcnt[i] = 0;
-      P.ucnt[i] = 0;
       P.lstart[i] = 0;
-      P.ustart[i] = 0;
-      P.uvstart[i] = 0;
-      P.uvlen[i] = 0;
     }
     if (lane == 0) {  // what the row asked for, to size a retry
-      atomicMax(P.ctr + 5, W.nvals);
-      atomicMax(P.ctr + 6, (unsigned long long)W.nslots);
+      atomicMax(P.ctr + 5, M.nvals);
+      atomicMax(P.ctr + 6, (unsigned long long)M.nslots);
     }
-    // publish the row (its U part and pivot block): every lane's writes are
-    // made visible device-wide before lane 0 raises the flag
+    // publish the row: every lane's writes are made visible device-wide (and
+    // to the bulk copies of the readers) before lane 0 sets the word
+    fence_proxy_async_all();
     __threadfence();
     __syncwarp();
-    if (lane == 0) atomicExch(&P.done[i], status_local == 0 ? 1 : 2);
-    // the L part is read by no other row: written after publishing
+    if (lane == 0)
+      atomicExch(P.done + i, status_local == 0 ? ((unsigned long long)roff16 << 24) | (unsigned long long)(rbytes / 16)
+                                               : kRowFailed);
+    // the L part is read by no other row: written after publishing, in
+    // column order
     if (status_local == 0) {
-      write_part(true, lb, lvv, P.lcol, P.lvo, lval);
+      long long carry = 0;
+      for (int p0 = 0; p0 < nL; p0 += 32) {
+        const int p = p0 + lane;
+        int sz = 0, so = 0;
+        if (p < nL) {
+          const int c = (int)(srtL[p] >> 32), q = (int)(srtL[p] & 0xffffffffu);
+          sz = ni * A.rsz[c];
+          so = soff[q];
+          P.lcol[lb + p] = c;
+        }
+        int incl = sz;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const long long dof = (long long)lvv + carry + incl - sz;
+        if (p < nL) P.lvo[lb + p] = dof;
+        copy_round<T>(M, sz, so, dof, wv, lval, lane);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
       if (lane == 0) {
         P.lstart[i] = (int64_t)lb;
-        P.lcnt[i] = nl;
+        P.lcnt[i] = nL;
       }
     }
+    (void)n2L;
+    (void)n2U;
     // clear the hash positions this row used
     if (in_sh) {
-      for (int q = lane; q < WS_HASH; q += 32) W.keys[q] = -1;
+      for (int q = lane; q < g.hash; q += 32) sh_keys[q] = -1;
     } else {
       for (int q = lane; q < ns; q += 32)
         if (hpos[q] >= 0) keys[hpos[q]] = -1;
     }
     __syncwarp();
   }
+  drain();
 }
 
-// Gather the pooled rows into VBCSR (warp per row).
+// Gather the pooled L rows into VBCSR (warp per row).
 template <typename T>
 __global__ void k_pool_to_vb(int64_t nbr, const int64_t* __restrict__ start, const int32_t* __restrict__ pcol,
                              const int64_t* __restrict__ pvo, const T* __restrict__ pval,
@@ -1139,6 +1412,35 @@ __global__ void k_pool_to_vb(int64_t nbr, const int64_t* __restrict__ start, con
   }
 }
 
+// U rows from the published records: counts (pass 0), columns (pass 1, after
+// the row pointers), values (pass 2, after the value offsets).  A record's
+// values are its row's blocks in column order, the VBCSR layout of the row.
+template <typename T>
+__global__ void k_rec_to_vb(int64_t nbr, int pass, const unsigned long long* __restrict__ done,
+                            const unsigned char* __restrict__ upool, int32_t* __restrict__ cnt,
+                            const int64_t* __restrict__ bptr, const int64_t* __restrict__ voff,
+                            int32_t* __restrict__ bcol, T* __restrict__ val) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t i = blockIdx.x * wpb + (threadIdx.x >> 5); i < nbr; i += (int64_t)gridDim.x * wpb) {
+    const unsigned char* r = upool + (int64_t)(done[i] >> 24) * 16;
+    const int* h = reinterpret_cast<const int*>(r);
+    const int ucnt = h[0];
+    if (pass == 0) {
+      if (lane == 0) cnt[i] = ucnt;
+      continue;
+    }
+    const RecLayout RL = rec_layout(ucnt, h[1], h[2], h[3], (int)sizeof(T));
+    if (pass == 1) {
+      for (int q = lane; q < ucnt; q += 32) bcol[bptr[i] + q] = reinterpret_cast<const int*>(r + RL.ucol)[q];
+      continue;
+    }
+    const T* src = reinterpret_cast<const T*>(r + RL.val);
+    T* dst = val + voff[bptr[i]];
+    for (int e = lane; e < h[3]; e += 32) dst[e] = src[e];
+  }
+}
+
 __global__ void k_sq_sizes(int64_t n, const int32_t* __restrict__ sz, int64_t* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (int64_t)sz[i] * sz[i];
@@ -1156,7 +1458,67 @@ __global__ void k_iota(int64_t n, int64_t* __restrict__ bptr, int32_t* __restric
   }
 }
 
+// Row statistics of the last-level matrix for the choice of the workspace:
+// [0] block rows with more than 24 blocks, [1] largest row in blocks.
+__global__ void k_row_stats(int64_t nbr, const int64_t* __restrict__ bptr, unsigned long long* __restrict__ out) {
+  unsigned long long big = 0, mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbr; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long nb = (unsigned long long)(bptr[i + 1] - bptr[i]);
+    big += nb > 24;
+    mx = nb > mx ? nb : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    big += __shfl_xor_sync(0xffffffffu, big, o);
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, big);
+    atomicMax(out + 1, mx);
+  }
+}
+
 }  // namespace
+
+// Shared workspace of one warp: slots, value bytes, stage-buffer bytes and
+// pending-column capacity, every part 16-byte aligned.
+static IlutGeom make_geom(int slots, int vbytes, int stage, int lcap) {
+  IlutGeom G{};
+  G.slots = slots;
+  G.hash = 1;
+  while (G.hash < 2 * slots) G.hash <<= 1;
+  G.vbytes = vbytes;
+  G.stage = stage;
+  G.lcap = lcap;
+  auto up = [](int v, int a) { return (v + a - 1) / a * a; };
+  int o = 0;
+  G.o_misc = o;
+  o = up(o + (int)sizeof(IlutMisc), 128);
+  G.o_stage = o;
+  o += 2 * stage;
+  G.o_vals = o;
+  o = up(o + vbytes, 16);
+  G.o_keys = o;
+  o = up(o + 4 * G.hash, 16);
+  G.o_hpos = o;
+  o = up(o + 4 * slots, 16);
+  G.o_scol = o;
+  o = up(o + 4 * slots, 16);
+  G.o_soff = o;
+  o = up(o + 4 * slots, 16);
+  G.o_sst = o;
+  o = up(o + 4 * slots, 16);
+  G.o_sf2 = o;
+  o = up(o + 8 * slots, 16);
+  G.o_lc = o;
+  o = up(o + 4 * lcap, 16);
+  G.o_ls = o;
+  o = up(o + 4 * lcap, 128);
+  G.bytes = o;
+  return G;
+}
+
+
 
 template <typename T>
 void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, uint64_t wait_limit, cudaStream_t s,
@@ -1202,42 +1564,64 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
 
   int dev = 0;
   VB_CUDA(cudaGetDevice(&dev));
-  int nsm = 0;
+  int nsm = 0, smem_sm = 0, smem_block = 0;
   VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  // L and U each hold about half of the last-level matrix on the configured
-  // workloads; the pools start at its full size and grow on overflow (retry)
+  VB_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  VB_CUDA(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // Shared workspace per warp, from the rows of the matrix: rows of a few
+  // large blocks (a dozen blocks, fill of a few dozen) keep 16 warps per SM
+  // with small workspaces; when many rows hold dozens of small blocks (and
+  // fill to hundreds) the workspaces grow and fewer warps share an SM, so
+  // that the working rows stay on chip.
+  DBuf<unsigned long long> rstat(2, s);
+  rstat.zero();
+  launch(k_row_stats, grid_for(p, 256), 256, 0, s, p, A.bptr.p, rstat.p);
+  VB_LAUNCH_CHECK();
+  const std::vector<unsigned long long> rs = d2h_vec(rstat.p, 2, s);
+  const bool wide = rs[0] * 4 > (unsigned long long)p;
+  const IlutGeom G = wide ? make_geom(512, sizeof(T) == sizeof(double) ? 16384 : 8192, 2048, 512)
+                          : make_geom(64, 4096, 2048, 128);
+  const int reserve = 1024;  // shared memory the system keeps per block
+  int wpb = std::min(8, smem_block / G.bytes);
+  if (wpb < 1) fail(VB_EINTERNAL, "last-level ILUT: shared workspace exceeds a block");
+  int bps = std::max(1, smem_sm / (wpb * G.bytes + reserve));
+  while (wpb * bps > 16 && bps > 1) --bps;
+  const size_t smem = (size_t)wpb * G.bytes;
+
+  // L pool: the L blocks; U pool: one record per row.  L and U each hold
+  // about half of the last-level matrix on the configured workloads; the
+  // pools start at its full size and grow on overflow (retry)
   int64_t lbcap = std::max<int64_t>(A.nnzb, 1024), lvcap = std::max<int64_t>(A.nval, 1 << 16);
-  int64_t ubcap = lbcap, uvcap = lvcap + 4 * p;  // U rows are padded to 16 bytes
+  int64_t ucap16 = (A.nval * (int64_t)sizeof(T) + X.Dg.nval * 8 + 8 * A.nnzb + 64 * p) / 16 + 4096;
   int smax = 1024;
   int64_t vmax = 32768;
-  const int blocks_per_sm = 2;  // two blocks of IW warps share the shared memory of an SM
   for (int attempt = 0; attempt < 6; ++attempt) {
-    const int64_t nblocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * blocks_per_sm, (p + IW - 1) / IW));
-    const int64_t nwarps = nblocks * IW;
+    const int64_t nblocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * bps, (p + wpb - 1) / wpb));
+    const int64_t nwarps = nblocks * wpb;
     int ht = 1;
     while (ht < 2 * smax) ht <<= 1;
     DBuf<int> keys(nwarps * ht, s), hpos(nwarps * smax, s), scol(nwarps * smax, s), sstate(nwarps * smax, s);
-    DBuf<int> soff(nwarps * smax, s);
+    DBuf<int> soff(nwarps * smax, s), fin(nwarps * 2 * smax, s);
     DBuf<long long> sf2(nwarps * smax, s);
+    DBuf<unsigned long long> srt(nwarps * 4 * smax, s);
     DBuf<T> wvals(nwarps * vmax, s);
-    Workspace ws{keys.p, hpos.p, scol.p, soff.p, sstate.p, sf2.p, ht, smax, vmax};
-    DBuf<int32_t> lcol(lbcap, s), ucol(ubcap, s), lcnt(p, s), ucnt(p, s), done(p, s);
-    DBuf<int64_t> lvo(lbcap, s), uvo(ubcap, s), lstart(p, s), ustart(p, s), uvstart(p, s), uvlen(p, s);
-    DBuf<T> lval(lvcap, s), uval(uvcap, s);
+    Workspace ws{keys.p, hpos.p, scol.p, soff.p, sstate.p, sf2.p, fin.p, srt.p, ht, smax, vmax};
+    DBuf<int32_t> lcol(lbcap, s), lcnt(p, s);
+    DBuf<int64_t> lvo(lbcap, s), lstart(p, s);
+    DBuf<unsigned long long> done(p, s);
+    DBuf<T> lval(lvcap, s);
+    DBuf<unsigned char> upool(ucap16 * 16, s);
     DBuf<unsigned long long> ctr(8, s);
     DBuf<int> abort(1, s);
     ctr.zero();
     done.zero();
     abort.zero();
     X.piv.zero();
-    Pools P{lcol.p, lvo.p,  ucol.p, uvo.p,  lstart.p, lcnt.p,  ustart.p,  ucnt.p,   ctr.p,
-            lbcap,  lvcap,  ubcap,  uvcap,  done.p,   abort.p, uvstart.p, uvlen.p, order};
-    VB_CUDA(cudaFuncSetAttribute(k_ilut<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ilut_smem()));
-    launch(k_ilut<T>, (unsigned)nblocks, IW * 32, ilut_smem(), s, A.view(), ws, wvals.p, P, lval.p, uval.p,
-           X.Dg.voff.p,
-                                                     X.Dg.val.p, mixed ? X.Dg32.val.p : nullptr, X.piv.p,
-                                                     mixed ? X.ptag.p : nullptr, mixed ? 1 : 0, cond_thr, t, lfil,
-                                                     (unsigned long long)wait_limit, dst);
+    Pools P{lcol.p, lvo.p, lstart.p, lcnt.p, done.p, ctr.p, lbcap, lvcap, ucap16, abort.p, order};
+    VB_CUDA(cudaFuncSetAttribute(k_ilut<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    launch(k_ilut<T>, (unsigned)nblocks, wpb * 32, smem, s, A.view(), G, ws, wvals.p, P, lval.p, upool.p,
+           X.Dg.voff.p, X.Dg.val.p, mixed ? X.Dg32.val.p : nullptr, X.piv.p, mixed ? X.ptag.p : nullptr,
+           mixed ? 1 : 0, cond_thr, t, lfil, (unsigned long long)wait_limit, dst);
     VB_LAUNCH_CHECK();
     const int st = d2h(dst, s);
     if (st == DEV_OVERFLOW) {
@@ -1245,8 +1629,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
       std::vector<unsigned long long> c = d2h_vec(ctr.p, 8, s);
       lbcap = std::max<int64_t>(2 * lbcap, (int64_t)c[0] + 1024);
       lvcap = std::max<int64_t>(2 * lvcap, (int64_t)c[1] + 4096);
-      ubcap = std::max<int64_t>(2 * ubcap, (int64_t)c[2] + 1024);
-      uvcap = std::max<int64_t>(2 * uvcap, (int64_t)c[3] + 4096);
+      ucap16 = std::max<int64_t>(2 * ucap16, (int64_t)c[2] + 4096);
       while ((int64_t)c[5] > vmax) vmax *= 2;
       if ((int64_t)c[6] > smax) {
         while (smax < (int)c[6] && smax < MAX_SLOTS) smax *= 2;
@@ -1255,34 +1638,52 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
       continue;
     }
     check_status(dst, s, "vbarms_factor: last-level block ILUT");
-    // assemble L and U
-    for (int which = 0; which < 2; ++which) {
-      VBDev<T>& M = which == 0 ? X.L : X.U;
-      DBuf<int32_t>& cnt = which == 0 ? lcnt : ucnt;
-      DBuf<int64_t>& start = which == 0 ? lstart : ustart;
-      DBuf<int32_t>& pcol = which == 0 ? lcol : ucol;
-      DBuf<int64_t>& pvo = which == 0 ? lvo : uvo;
-      DBuf<T>& pval = which == 0 ? lval : uval;
+    // assemble L from its pool
+    {
+      VBDev<T>& M = X.L;
       M.bptr.alloc(p + 1, s);
       DBuf<int64_t> c64(p, s);
-      launch(k_count_to_i64, grid_for(p, 256), 256, 0, s, p, cnt.p, c64.p);
+      launch(k_count_to_i64, grid_for(p, 256), 256, 0, s, p, lcnt.p, c64.p);
       VB_LAUNCH_CHECK();
       scan_i64(c64.p, M.bptr.p, p, s);
       M.nnzb = d2h(M.bptr.p + p, s);
       M.bcol.alloc(M.nnzb, s);
       // bcol first (needed by the offsets), then offsets, then values
-      launch(k_pool_to_vb<T>, grid_for(p, 8), 256, 0, s, p, start.p, pcol.p, pvo.p, pval.p, M.bptr.p, nullptr,
-                                                       M.bcol.p, nullptr);
+      launch(k_pool_to_vb<T>, grid_for(p, 8), 256, 0, s, p, lstart.p, lcol.p, lvo.p, lval.p, M.bptr.p, nullptr,
+             M.bcol.p, nullptr);
       VB_LAUNCH_CHECK();
       finish_offsets(M, s);
-      launch(k_pool_to_vb<T>, grid_for(p, 8), 256, 0, s, p, start.p, pcol.p, pvo.p, pval.p, M.bptr.p, M.voff.p,
-                                                       M.bcol.p, M.val.p);
+      launch(k_pool_to_vb<T>, grid_for(p, 8), 256, 0, s, p, lstart.p, lcol.p, lvo.p, lval.p, M.bptr.p, M.voff.p,
+             M.bcol.p, M.val.p);
+      VB_LAUNCH_CHECK();
+    }
+    // assemble U from the records
+    {
+      VBDev<T>& M = X.U;
+      M.bptr.alloc(p + 1, s);
+      DBuf<int32_t> ucnt(p, s);
+      DBuf<int64_t> c64(p, s);
+      launch(k_rec_to_vb<T>, grid_for(p, 8), 256, 0, s, p, 0, done.p, upool.p, ucnt.p, nullptr, nullptr, nullptr,
+             nullptr);
+      launch(k_count_to_i64, grid_for(p, 256), 256, 0, s, p, ucnt.p, c64.p);
+      VB_LAUNCH_CHECK();
+      scan_i64(c64.p, M.bptr.p, p, s);
+      M.nnzb = d2h(M.bptr.p + p, s);
+      M.bcol.alloc(M.nnzb, s);
+      launch(k_rec_to_vb<T>, grid_for(p, 8), 256, 0, s, p, 1, done.p, upool.p, nullptr, M.bptr.p, nullptr, M.bcol.p,
+             nullptr);
+      VB_LAUNCH_CHECK();
+      finish_offsets(M, s);
+      launch(k_rec_to_vb<T>, grid_for(p, 8), 256, 0, s, p, 2, done.p, upool.p, nullptr, M.bptr.p, M.voff.p, M.bcol.p,
+             M.val.p);
       VB_LAUNCH_CHECK();
     }
     return;
   }
   fail(VB_ENOMEM, "vbarms_factor: last-level ILUT workspace could not be sized");
 }
+
+
 
 namespace {
 __global__ void k_dom_start(int64_t p, int ndom, const int32_t* __restrict__ dom, int64_t* __restrict__ start) {
