@@ -53,6 +53,7 @@ enum : int { SL_LIVE = 0, SL_LKEPT = 1, SL_DEAD = 2 };
 //   TL lu[nk * nk]        the factored pivot block, row-major
 //   int32 ucol[ucnt]      U block columns, ascending
 //   int32 urel[ucnt]      each U block's first value within val
+//   int32 unj[ucnt]       each U block's column count
 //   T val[nval]           the U blocks, row-major, in column order
 // every part starting on a 16-byte boundary.  done[k] = (offset << 24) |
 // length, both in 16-byte units, once the record is complete; kRowFailed when
@@ -63,7 +64,7 @@ constexpr int64_t kRecMaxUnits = (1LL << 24) - 1;
 __host__ __device__ __forceinline__ int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }
 
 struct RecLayout {
-  int64_t piv, lu, ucol, urel, val, bytes;
+  int64_t piv, lu, ucol, urel, unj, val, bytes;
 };
 
 __host__ __device__ __forceinline__ RecLayout rec_layout(int ucnt, int nk, int lu64, int64_t nval, int tsize) {
@@ -72,7 +73,8 @@ __host__ __device__ __forceinline__ RecLayout rec_layout(int ucnt, int nk, int l
   L.lu = L.piv + pad16(4LL * nk);
   L.ucol = L.lu + pad16((int64_t)nk * nk * (lu64 ? 8 : tsize));
   L.urel = L.ucol + pad16(4LL * ucnt);
-  L.val = L.urel + pad16(4LL * ucnt);
+  L.unj = L.urel + pad16(4LL * ucnt);
+  L.val = L.unj + pad16(4LL * ucnt);
   L.bytes = L.val + pad16(nval * tsize);
   return L;
 }
@@ -101,6 +103,7 @@ struct Workspace {
   int* soff;       // [smax]
   int* sstate;     // [smax]
   long long* sf2;  // [smax] norm key of each slot
+  int* sncl;       // [smax] column count of each slot's block
   int* fin;        // [2 smax] candidate lists of the finish
   unsigned long long* srt;  // [4 smax] kept lists being sorted
   int ht, smax;
@@ -111,7 +114,7 @@ struct Workspace {
 // region; every part 16-byte aligned).
 struct IlutGeom {
   int slots, hash, vbytes, stage, lcap;
-  int o_misc, o_stage, o_vals, o_keys, o_hpos, o_scol, o_soff, o_sst, o_sf2, o_lc, o_ls;
+  int o_misc, o_stage, o_vals, o_keys, o_hpos, o_scol, o_soff, o_sst, o_sf2, o_sncl, o_lc, o_ls;
   int bytes;
 };
 
@@ -220,8 +223,8 @@ __device__ __forceinline__ int ws_lookup(const int* keys, const int* scol, uint3
 
 // Claim a new slot of sz values for column col; returns the slot or -1.
 __device__ __forceinline__ int ws_new_slot(int smax, int64_t vmax, int* keys, int* hpos, int* scol, int* soff,
-                                           int* sstate, int* nslots, unsigned long long* nvals, uint32_t hmask,
-                                           int col, int sz) {
+                                           int* sstate, int* sncl, int* nslots, unsigned long long* nvals,
+                                           uint32_t hmask, int col, int ncl, int sz) {
   const int slot = atomicAdd(nslots, 1);
   const long long off = (long long)atomicAdd(nvals, (unsigned long long)sz);
   if (slot >= smax) return -1;
@@ -230,6 +233,7 @@ __device__ __forceinline__ int ws_new_slot(int smax, int64_t vmax, int* keys, in
   scol[slot] = col;
   soff[slot] = (int)off;
   sstate[slot] = SL_LIVE;
+  sncl[slot] = ncl;
   hpos[slot] = ws_place(keys, hmask, slot, col);
   return hpos[slot] < 0 ? -1 : slot;
 }
@@ -528,9 +532,16 @@ __device__ int lfil_cut(int* cand, int n, int lfil, const long long* sf2, const 
     const int shift = 8 * d;
     for (int b = lane; b < 256; b += 32) hist[b] = 0;
     __syncwarp();
-    for (int c = lane; c < n; c += 32) {
-      const unsigned long long key = (unsigned long long)sf2[cand[c]];
-      if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255], 1);
+    for (int base = 0; base < n; base += 32) {
+      const int c = base + lane;
+      int bin = -1;
+      if (c < n) {
+        const unsigned long long key = (unsigned long long)sf2[cand[c]];
+        if ((key & pmask) == prefix) bin = (int)((key >> shift) & 255);
+      }
+      // lanes with the same bin add once (keys of one row crowd a few bins)
+      const unsigned peers = __match_any_sync(0xffffffffu, bin);
+      if (bin >= 0 && (__ffs(peers) - 1) == lane) atomicAdd(&hist[bin], __popc(peers));
     }
     __syncwarp();
     // lane l holds bins 255 - 8 l - u, u = 0..7 (the highest bins first)
@@ -569,31 +580,32 @@ __device__ int lfil_cut(int* cand, int n, int lfil, const long long* sf2, const 
     __syncwarp();
   }
   // keys above prefix are kept; of the keys equal to it, the `want` with the
-  // lowest columns
+  // lowest columns.  Every cut slot is marked first (the tie ranks read the
+  // whole list), then the list is compacted.
+  for (int c = lane; c < n; c += 32) {
+    const int q = cand[c];
+    const unsigned long long key = (unsigned long long)sf2[q];
+    bool keep = key > prefix;
+    if (key == prefix) {
+      const int col = scol[q];
+      int rank = 0;
+      for (int c2 = 0; c2 < n; ++c2) {
+        const int q2 = cand[c2];
+        if ((unsigned long long)sf2[q2] == prefix && scol[q2] < col) ++rank;
+      }
+      keep = rank < want;
+    }
+    if (!keep) sstate[q] = SL_DEAD;
+  }
+  __syncwarp();
   int kept = 0;
   for (int base = 0; base < n; base += 32) {
     const int c = base + lane;
-    int q = -1;
-    bool keep = false;
-    if (c < n) {
-      q = cand[c];
-      const unsigned long long key = (unsigned long long)sf2[q];
-      if (key > prefix) {
-        keep = true;
-      } else if (key == prefix) {
-        const int col = scol[q];
-        int rank = 0;
-        for (int c2 = 0; c2 < n; ++c2) {
-          const int q2 = cand[c2];
-          if ((unsigned long long)sf2[q2] == prefix && scol[q2] < col) ++rank;
-        }
-        keep = rank < want;
-      }
-    }
+    const int q = c < n ? cand[c] : -1;
+    const bool keep = q >= 0 && sstate[q] != SL_DEAD;
     __syncwarp();
     const unsigned bk = __ballot_sync(0xffffffffu, keep);
     if (keep) cand[kept + __popc(bk & ((1u << lane) - 1u))] = q;
-    else if (q >= 0) sstate[q] = SL_DEAD;
     kept += __popc(bk);
     __syncwarp();
   }
@@ -678,6 +690,7 @@ __global__ void __launch_bounds__(256, 2)
   int* const sh_soff = reinterpret_cast<int*>(wb + g.o_soff);
   int* const sh_sst = reinterpret_cast<int*>(wb + g.o_sst);
   long long* const sh_sf2 = reinterpret_cast<long long*>(wb + g.o_sf2);
+  int* const sh_sncl = reinterpret_cast<int*>(wb + g.o_sncl);
   int* const lc = reinterpret_cast<int*>(wb + g.o_lc);  // pending L columns (INT_MAX when processed)
   int* const ls = reinterpret_cast<int*>(wb + g.o_ls);  // their slots
   const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -738,6 +751,7 @@ __global__ void __launch_bounds__(256, 2)
     int* soff;
     int* sstate;
     long long* sf2;
+    int* sncl;
     T* wv;
     int smax_c;
     int64_t vmax_c;
@@ -745,11 +759,13 @@ __global__ void __launch_bounds__(256, 2)
     for (;;) {
       if (in_sh) {
         keys = sh_keys, hpos = sh_hpos, scol = sh_scol, soff = sh_soff, sstate = sh_sst, sf2 = sh_sf2;
+        sncl = sh_sncl;
         wv = sh_vals;
         smax_c = g.slots, vmax_c = VSH, hmask = (uint32_t)g.hash - 1;
       } else {
         keys = gkeys, hpos = ws.hpos + wid * ws.smax, scol = ws.scol + wid * ws.smax;
         soff = ws.soff + wid * ws.smax, sstate = ws.sstate + wid * ws.smax, sf2 = ws.sf2 + wid * ws.smax;
+        sncl = ws.sncl + wid * ws.smax;
         wv = wvals_all + wid * ws.vmax;
         smax_c = ws.smax, vmax_c = ws.vmax, hmask = (uint32_t)ws.ht - 1;
       }
@@ -776,6 +792,7 @@ __global__ void __launch_bounds__(256, 2)
           scol[slot] = J;
           soff[slot] = (int)(A.voff[b] - v0);
           sstate[slot] = SL_LIVE;
+          sncl[slot] = A.rsz[J];
           hpos[slot] = ws_place(keys, hmask, slot, J);  // the table holds 2 smax positions
           if (J < i) {
             const int q = atomicAdd(&M.nl, 1);
@@ -843,6 +860,11 @@ __global__ void __launch_bounds__(256, 2)
         int bi = btag0 == (int)k ? 0 : (btag1 == (int)k ? 1 : -1);
         const unsigned char* rec = nullptr;
         int64_t rlen = 0;
+        // the word of the next pending column is loaded now and looked at
+        // after the multiplier, so that its latency hides behind this step
+        const bool want_pf = knext != INT_MAX && btag0 != knext && btag1 != knext;
+        unsigned long long w2 = 0;
+        if (want_pf && lane == 0) w2 = ld_relaxed_u64(P.done + knext);
         if (bi < 0) {
           unsigned long long word = 0;
           if (lane == 0) word = wait_word(P.done + k, P.abort, wait_limit, st);
@@ -887,34 +909,6 @@ __global__ void __launch_bounds__(256, 2)
             rec = src;
           }
         }
-        // the next pending column's record, fetched ahead while this step
-        // computes, when its row is already published, no buffer holds it
-        // yet and a buffer is free (the current step's buffer holds k)
-        if (knext != INT_MAX && btag0 != knext && btag1 != knext) {
-          const int ob = btag0 < 0 ? 0 : (btag1 < 0 ? 1 : -1);
-          int go = 0;
-          unsigned long long w2 = 0;
-          if (ob >= 0 && lane == 0) {
-            w2 = ld_relaxed_u64(P.done + knext);
-            if (w2 != 0 && w2 != kRowFailed && (int64_t)(w2 & 0xFFFFFFull) * 16 <= g.stage) {
-              asm volatile("fence.acq_rel.gpu;" ::: "memory");
-              fence_proxy_async_all();
-              bulk_load(ob ? stage1 : stage0, upool + (int64_t)(w2 >> 24) * 16, (unsigned)((w2 & 0xFFFFFFull) * 16),
-                        &M.mbar[ob]);
-              go = 1;
-            }
-          }
-          go = __shfl_sync(0xffffffffu, go, 0);
-          if (go) {
-            if (ob) {
-              btag1 = knext;
-              bpend1 = true;
-            } else {
-              btag0 = knext;
-              bpend0 = true;
-            }
-          }
-        }
         if (bi >= 0) {
           bool ok = true;
           if (bi == 0 && bpend0) {
@@ -950,6 +944,7 @@ __global__ void __launch_bounds__(256, 2)
         const int* rpiv = reinterpret_cast<const int*>(rec + RL.piv);
         const int* rcol = reinterpret_cast<const int*>(rec + RL.ucol);
         const int* rrel = reinterpret_cast<const int*>(rec + RL.urel);
+        const int* rnj = reinterpret_cast<const int*>(rec + RL.unj);
         const T* rval = reinterpret_cast<const T*>(rec + RL.val);
         T* m = wv + soff[sk];
         // the multiplier m = a_ik (P^T L U)_k^{-1}, in place, one lane per row
@@ -985,6 +980,31 @@ __global__ void __launch_bounds__(256, 2)
           dropped = drop_rule_f(sf, ni, nk, tf);
           key = norm_key(sf);
         }
+        // the next pending column's record, fetched ahead while the update
+        // computes, when its row was already published at the start of the
+        // step, no buffer holds it yet and a buffer is free (the current
+        // step's buffer holds k)
+        if (want_pf) {
+          const int ob = btag0 < 0 ? 0 : (btag1 < 0 ? 1 : -1);
+          int go = 0;
+          if (ob >= 0 && lane == 0 && w2 != 0 && w2 != kRowFailed && (int64_t)(w2 & 0xFFFFFFull) * 16 <= g.stage) {
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            fence_proxy_async_all();
+            bulk_load(ob ? stage1 : stage0, upool + (int64_t)(w2 >> 24) * 16, (unsigned)((w2 & 0xFFFFFFull) * 16),
+                      &M.mbar[ob]);
+            go = 1;
+          }
+          go = __shfl_sync(0xffffffffu, go, 0);
+          if (go) {
+            if (ob) {
+              btag1 = knext;
+              bpend1 = true;
+            } else {
+              btag0 = knext;
+              bpend0 = true;
+            }
+          }
+        }
         if (dropped) {
           if (lane == 0) sstate[sk] = SL_DEAD;
           __syncwarp();
@@ -1004,12 +1024,13 @@ __global__ void __launch_bounds__(256, 2)
           const int q = q0 + lane;
           int32_t j = -1;
           int slot = -1;
-          int uo = 0;
+          int uo = 0, njq = 0;
           bool missing = false;
           if (q < ucnt) {
             j = staged ? rcol[q] : __ldcg(rcol + q);
             uo = staged ? rrel[q] : __ldcg(rrel + q);
-            if (j <= k || j >= A.nbr || uo < 0 || (int64_t)uo + (int64_t)nk * A.rsz[j] > uval_n) {
+            njq = staged ? rnj[q] : __ldcg(rnj + q);
+            if (j <= k || j >= A.nbr || uo < 0 || njq <= 0 || (int64_t)uo + (int64_t)nk * njq > uval_n) {
               *vflag = 4;  // a published U block lies right of k inside its record
               j = -1;
             } else {
@@ -1019,8 +1040,9 @@ __global__ void __launch_bounds__(256, 2)
           }
           __syncwarp();
           if (missing) {
-            const int sz = ni * A.rsz[j];
-            slot = ws_new_slot(smax_c, vmax_c, keys, hpos, scol, soff, sstate, &M.nslots, &M.nvals, hmask, j, sz);
+            const int sz = ni * njq;
+            slot = ws_new_slot(smax_c, vmax_c, keys, hpos, scol, soff, sstate, sncl, &M.nslots, &M.nvals, hmask, j,
+                               njq, sz);
             if (slot < 0) {
               *vflag = 1;
             } else {
@@ -1045,7 +1067,7 @@ __global__ void __launch_bounds__(256, 2)
             status_local = DEV_INTERNAL;
             break;
           }
-          const int nj = j >= 0 ? A.rsz[j] : 0;
+          const int nj = j >= 0 ? njq : 0;
           const int sz = ni * nj;
           int incl = sz;
           for (int o = 1; o < 32; o <<= 1) {
@@ -1118,6 +1140,31 @@ __global__ void __launch_bounds__(256, 2)
     }
     drain();  // every record fetched ahead has been used, unless the row failed
     const int ns = min(*vns, smax_c);
+    // A row that ends in the global workspace has its slot metadata copied
+    // to the shared working-row region (unused by such a row) when it fits,
+    // so that the scans of the finish read on-chip data; its values stay in
+    // the global workspace.
+    bool meta_sh = false;
+    if (!in_sh && status_local == 0) {
+      const int region = g.o_lc - g.o_vals;  // vals, hash and slot arrays of the shared workspace
+      if (ns * 24 <= region) {
+        meta_sh = true;
+        long long* mf2 = reinterpret_cast<long long*>(wb + g.o_vals);
+        int* mcol = reinterpret_cast<int*>(mf2 + ns);
+        int* mst = mcol + ns;
+        int* mncl = mst + ns;
+        int* moff = mncl + ns;
+        for (int q = lane; q < ns; q += 32) {
+          mf2[q] = sf2[q];
+          mcol[q] = scol[q];
+          mst[q] = sstate[q];
+          mncl[q] = sncl[q];
+          moff[q] = soff[q];
+        }
+        __syncwarp();
+        sf2 = mf2, scol = mcol, sstate = mst, sncl = mncl, soff = moff;
+      }
+    }
     // ---- finish the row.
     int dslot = -1;
     if (status_local == 0) {
@@ -1188,7 +1235,7 @@ __global__ void __launch_bounds__(256, 2)
       for (int q = lane; q < ns; q += 32) {
         const int c = scol[q];
         if (sstate[q] == SL_LIVE && c > i) {
-          const int nc = A.rsz[c];
+          const int nc = sncl[q];
           bool drop;
           long long kq;
           if (sizeof(T) == sizeof(double)) {
@@ -1266,8 +1313,8 @@ __global__ void __launch_bounds__(256, 2)
     int64_t rbytes = 0;
     int lu64r = 0;
     if (status_local == 0) {
-      for (int p = lane; p < nL; p += 32) vl += (long long)ni * A.rsz[(int)(srtL[p] >> 32)];
-      for (int p = lane; p < nU; p += 32) vu += (long long)ni * A.rsz[(int)(srtU[p] >> 32)];
+      for (int p = lane; p < nL; p += 32) vl += (long long)ni * sncl[(int)(srtL[p] & 0xffffffffu)];
+      for (int p = lane; p < nU; p += 32) vu += (long long)ni * sncl[(int)(srtU[p] & 0xffffffffu)];
       vl = warp_sum_ll(vl);
       vu = warp_sum_ll(vu);
       lu64r = (sizeof(T) == sizeof(double) || tag64) ? 1 : 0;
@@ -1307,6 +1354,7 @@ __global__ void __launch_bounds__(256, 2)
       }
       int* rcol = reinterpret_cast<int*>(r + RL.ucol);
       int* rrel = reinterpret_cast<int*>(r + RL.urel);
+      int* rnjw = reinterpret_cast<int*>(r + RL.unj);
       T* rv = reinterpret_cast<T*>(r + RL.val);
       int carry = 0;
       for (int p0 = 0; p0 < nU; p0 += 32) {
@@ -1314,9 +1362,11 @@ __global__ void __launch_bounds__(256, 2)
         int sz = 0, so = 0;
         if (p < nU) {
           const int c = (int)(srtU[p] >> 32), q = (int)(srtU[p] & 0xffffffffu);
-          sz = ni * A.rsz[c];
+          const int nc = sncl[q];
+          sz = ni * nc;
           so = soff[q];
           rcol[p] = c;
+          rnjw[p] = nc;
         }
         int incl = sz;
         for (int o = 1; o < 32; o <<= 1) {
@@ -1356,7 +1406,7 @@ __global__ void __launch_bounds__(256, 2)
         int sz = 0, so = 0;
         if (p < nL) {
           const int c = (int)(srtL[p] >> 32), q = (int)(srtL[p] & 0xffffffffu);
-          sz = ni * A.rsz[c];
+          sz = ni * sncl[q];
           so = soff[q];
           P.lcol[lb + p] = c;
         }
@@ -1377,10 +1427,12 @@ __global__ void __launch_bounds__(256, 2)
     }
     (void)n2L;
     (void)n2U;
-    // clear the hash positions this row used
-    if (in_sh) {
+    // clear the hash positions this row used (and the shared hash when the
+    // finish staged metadata over it)
+    if (in_sh || meta_sh) {
       for (int q = lane; q < g.hash; q += 32) sh_keys[q] = -1;
-    } else {
+    }
+    if (!in_sh) {
       for (int q = lane; q < ns; q += 32)
         if (hpos[q] >= 0) keys[hpos[q]] = -1;
     }
@@ -1510,6 +1562,8 @@ static IlutGeom make_geom(int slots, int vbytes, int stage, int lcap) {
   o = up(o + 4 * slots, 16);
   G.o_sf2 = o;
   o = up(o + 8 * slots, 16);
+  G.o_sncl = o;
+  o = up(o + 4 * slots, 16);
   G.o_lc = o;
   o = up(o + 4 * lcap, 16);
   G.o_ls = o;
@@ -1568,19 +1622,22 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   VB_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
   VB_CUDA(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // Shared workspace per warp, from the rows of the matrix: rows of a few
-  // large blocks (a dozen blocks, fill of a few dozen) keep 16 warps per SM
-  // with small workspaces; when many rows hold dozens of small blocks (and
-  // fill to hundreds) the workspaces grow and fewer warps share an SM, so
-  // that the working rows stay on chip.
+  // Shared workspace per warp, from the rows of the matrix (rows of a dozen
+  // large blocks, or rows of dozens of small blocks whose fill reaches
+  // hundreds).
   DBuf<unsigned long long> rstat(2, s);
   rstat.zero();
   launch(k_row_stats, grid_for(p, 256), 256, 0, s, p, A.bptr.p, rstat.p);
   VB_LAUNCH_CHECK();
   const std::vector<unsigned long long> rs = d2h_vec(rstat.p, 2, s);
   const bool wide = rs[0] * 4 > (unsigned long long)p;
-  const IlutGeom G = wide ? make_geom(512, sizeof(T) == sizeof(double) ? 16384 : 8192, 2048, 512)
-                          : make_geom(64, 4096, 2048, 128);
+  // Measured on the configured workloads (one GB300): small shared
+  // workspaces and 16 warps per SM are fastest, also for rows whose fill
+  // outgrows them (they continue in the global workspace and the L1 cache
+  // keeps what the shared memory leaves free), except for FP64 rows of many
+  // small blocks, which keep 128 slots and 8 KB of values.
+  const IlutGeom G = (wide && sizeof(T) == sizeof(double)) ? make_geom(128, 8192, 2048, 256)
+                                                           : make_geom(64, 2048, 2048, wide ? 256 : 128);
   const int reserve = 1024;  // shared memory the system keeps per block
   int wpb = std::min(8, smem_block / G.bytes);
   if (wpb < 1) fail(VB_EINTERNAL, "last-level ILUT: shared workspace exceeds a block");
@@ -1601,11 +1658,11 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
     int ht = 1;
     while (ht < 2 * smax) ht <<= 1;
     DBuf<int> keys(nwarps * ht, s), hpos(nwarps * smax, s), scol(nwarps * smax, s), sstate(nwarps * smax, s);
-    DBuf<int> soff(nwarps * smax, s), fin(nwarps * 2 * smax, s);
+    DBuf<int> soff(nwarps * smax, s), sncl(nwarps * smax, s), fin(nwarps * 2 * smax, s);
     DBuf<long long> sf2(nwarps * smax, s);
     DBuf<unsigned long long> srt(nwarps * 4 * smax, s);
     DBuf<T> wvals(nwarps * vmax, s);
-    Workspace ws{keys.p, hpos.p, scol.p, soff.p, sstate.p, sf2.p, fin.p, srt.p, ht, smax, vmax};
+    Workspace ws{keys.p, hpos.p, scol.p, soff.p, sstate.p, sf2.p, sncl.p, fin.p, srt.p, ht, smax, vmax};
     DBuf<int32_t> lcol(lbcap, s), lcnt(p, s);
     DBuf<int64_t> lvo(lbcap, s), lstart(p, s);
     DBuf<unsigned long long> done(p, s);
