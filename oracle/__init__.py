@@ -64,6 +64,7 @@ def lib():
                 "or_gepp": (i32, [vp, i32, vp]),
                 "or_dropped": (i32, [vp, i32, i32, d]),
                 "or_factor": (vp, [vp, i32, d, i32, d, i32]),
+                "or_factor_fixed": (vp, [vp, i32, d, i32, d, i32, vp]),
                 "or_prec_free": (None, [vp]),
                 "or_prec_levels": (i32, [vp]),
                 "or_prec_fill": (d, [vp]),
@@ -80,6 +81,18 @@ def lib():
                 "or_dd_local_prec": (vp, [vp, i32]),
                 "or_dd_apply": (None, [vp, vp, vp]),
                 "or_dd_fgmres": (i32, [vp, vp, vp, vp, d, i32, i32, P(i32), P(d)]),
+                "or_dds_build": (vp, [vp, i32, i32, i32, d, i32, d, i32]),
+                "or_dds_free": (None, [vp]),
+                "or_dds_iface": (i64, [vp, vp, vp]),
+                "or_dds_rows": (i64, [vp, i32, vp, P(i64)]),
+                "or_dds_local": (vp, [vp, i32]),
+                "or_dds_local_prec": (vp, [vp, i32]),
+                "or_dds_coupling": (vp, [vp]),
+                "or_dds_ng": (i64, [vp]),
+                "or_dds_sinv": (None, [vp, vp, vp]),
+                "or_dds_apply": (None, [vp, vp, vp]),
+                "or_dds_fgmres": (i32, [vp, vp, vp, vp, d, i32, i32, P(i32), P(d)]),
+                "or_prec_last_fixed": (i64, [vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -271,11 +284,20 @@ class Prec:
     """Multilevel factorization (Steps 2-4 repeated, Eq. 7-8, last-level ILUT)."""
 
     def __init__(self, A: VBMat, nlev: int, droptol: float, lfil: int, ddtol: float = 0.0,
-                 schur_drop_all: bool = False):
+                 schur_drop_all: bool = False, fixed=None):
+        """fixed: optional flags per block row; flagged rows never enter an
+        independent set (Section 5, Schur-complement preconditioner)."""
         self._A = _VBHandle(A)
         self.n = int(A.rsz.sum())
         L = lib()
-        self.h = L.or_factor(self._A.h, int(nlev), float(droptol), int(lfil), float(ddtol), int(bool(schur_drop_all)))
+        if fixed is None:
+            self.h = L.or_factor(self._A.h, int(nlev), float(droptol), int(lfil), float(ddtol),
+                                 int(bool(schur_drop_all)))
+        else:
+            self._fixed = np.ascontiguousarray(fixed, np.int32)
+            assert len(self._fixed) == A.nbr
+            self.h = L.or_factor_fixed(self._A.h, int(nlev), float(droptol), int(lfil), float(ddtol),
+                                       int(bool(schur_drop_all)), _p(self._fixed))
         if not self.h:
             raise OracleError(L.or_last_status(), "factor")
         self.levels = L.or_prec_levels(self.h)
@@ -306,6 +328,14 @@ class Prec:
             L.or_prec_vec(self.h, lev, IVEC[which], None, _p(out))
         if n < 0:
             raise KeyError(which)
+        return out
+
+    def last_fixed(self) -> np.ndarray:
+        """Rows of the last level kept out of every independent set (empty:
+        the factorization has none)."""
+        L = lib()
+        out = np.zeros(L.or_prec_last_fixed(self.h, None), np.int32)
+        L.or_prec_last_fixed(self.h, _p(out))
         return out
 
     @property
@@ -396,14 +426,78 @@ class DD:
         return x
 
 
+class DDSchur:
+    """Section 5 Schur-complement global preconditioner (eq. gschur and
+    eq. loc_var_schur) with VBARMS local factorizations whose interface rows
+    are kept to the last level."""
+
+    def __init__(self, A: VBMat, nparts: int, msteps: int, nlev: int, droptol: float, lfil: int,
+                 ddtol: float = 0.0, schur_drop_all: bool = False):
+        self._A = _VBHandle(A)
+        self.n = int(A.rsz.sum())
+        self.nparts = int(nparts)
+        L = lib()
+        self.h = L.or_dds_build(self._A.h, int(nparts), int(msteps), int(nlev), float(droptol), int(lfil),
+                                float(ddtol), int(bool(schur_drop_all)))
+        if not self.h:
+            raise OracleError(L.or_last_status(), "dds_build")
+        self.ng = int(L.or_dds_ng(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_dds_free(self.h)
+            self.h = None
+
+    def part(self):
+        """(subdomain, interface flag) of every block row of A."""
+        L = lib()
+        p = L.or_dds_iface(self.h, None, None)
+        part, iface = np.zeros(p, np.int32), np.zeros(p, np.int32)
+        L.or_dds_iface(self.h, _p(part), _p(iface))
+        return part, iface
+
+    def rows(self, i: int):
+        """Subdomain i's block rows of A (interior, then interface) and the
+        interior count."""
+        L = lib()
+        ni = C.c_int64()
+        out = np.zeros(L.or_dds_rows(self.h, i, None, C.byref(ni)), np.int32)
+        L.or_dds_rows(self.h, i, _p(out), C.byref(ni))
+        return out, int(ni.value)
+
+    def local(self, i: int) -> VBMat:
+        return _export(lib().or_dds_local(self.h, i))
+
+    def local_prec(self, i: int) -> Prec:
+        m = self.local(i)
+        return _LocalPrec(lib().or_dds_local_prec(self.h, i), int(m.rsz.sum()), self)
+
+    def coupling(self) -> VBMat:
+        """The E_ij blocks on the global interface numbering."""
+        return _export(lib().or_dds_coupling(self.h))
+
+    def sinv(self, v: np.ndarray) -> np.ndarray:
+        v = np.ascontiguousarray(v, np.float64)
+        out = np.zeros(self.ng)
+        lib().or_dds_sinv(self.h, _p(v), _p(out))
+        return out
+
+    def apply(self, b: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.zeros(self.n)
+        lib().or_dds_apply(self.h, _p(b), _p(x))
+        return x
+
+
 def fgmres(A: VBMat, prec, b, x0=None, rtol=1e-8, restart=50, maxit=1000):
     """Right-preconditioned FGMRES(m) on the block-permuted system; prec is a
-    Prec, a DD or None."""
+    Prec, a DD, a DDSchur or None."""
     h = _VBHandle(A)
     b = np.ascontiguousarray(b, np.float64)
     x = np.zeros_like(b) if x0 is None else np.ascontiguousarray(x0, np.float64).copy()
     it, rr = C.c_int(), C.c_double()
-    f = lib().or_dd_fgmres if isinstance(prec, DD) else lib().or_fgmres
+    f = (lib().or_dd_fgmres if isinstance(prec, DD) else
+         lib().or_dds_fgmres if isinstance(prec, DDSchur) else lib().or_fgmres)
     st = f(h.h, prec.h if prec is not None else None, _p(b), _p(x), float(rtol),
            int(restart), int(maxit), C.byref(it), C.byref(rr))
     return x, it.value, rr.value, st

@@ -11,7 +11,7 @@
 // (build with -ffp-contract=off), evaluated in the order written here.
 //
 // Readings of points the paper leaves open (R1-R9; T1-T3 at compress_two_pass and G1-G5
-// at graph_compress; D1-D3 for Section 5):
+// at graph_compress; D1-D7 for Section 5):
 //  R1  similarity of rows i,j (Section 2.1): cos = |P_i n P_j| / sqrt(|P_i||P_j|)
 //      on the stored pattern of the rows; j joins i's group iff cos >= tau,
 //      tested exactly as (double)(c*c) >= (tau*tau) * (double)(|P_i||P_j|).
@@ -39,6 +39,26 @@
 //  D3  block Jacobi (delta = 0) and additive Schwarz add R_i^T A_i^{-1} R_i
 //      over the subdomains in order; the restricted variant keeps from
 //      subdomain i only the rows of W_i^0.
+//  D4  Schur-complement preconditioner (Section 5, eq. paral): on the D1
+//      partition (no overlap), block row I is an interface row iff a stored
+//      block of A couples it, as row or as column, to a block row of another
+//      subdomain; A_i keeps the blocks of A with row and column in subdomain
+//      i, interior rows first, then interface rows (each ascending), i.e.
+//      [[B_i, F_i], [E_i, C_i]].
+//  D5  A_i is factored by VBARMS with the interface rows kept out of every
+//      independent set, so they reach the last level, after the remaining
+//      interior rows; the trailing interface rows of its block ILUT are
+//      L_S U_S, the by-product approximation of S_i = C_i - E_i B_i^{-1} F_i.
+//  D6  one application to r = (f_i, g_i): z = the interface parts of the
+//      local solves of r_i (= S_i^{-1} g'_i); y from msteps steps of GMRES
+//      (y_0 = 0, MGS, Givens, early stop on a zero Arnoldi norm) on
+//      (I + S^{-1} E) y = z: eq. gschur preconditioned by blockdiag(S_i),
+//      E the couplings E_ij; S_i^{-1} v = the interface part of the local
+//      solve of (0, v).
+//  D7  eq. loc_var_schur: u_i = the interior part of the local solve of r_i
+//      whose last-level backward sweep takes the interface unknowns from y_i
+//      (divided by the column scalings of each level on the way down)
+//      instead of solving for them; the result is (u_i, y_i).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -584,7 +604,9 @@ void scale(VB& A, std::vector<double>& r, std::vector<double>& c) {
 // Step 3 (R5): weighted greedy block independent set on the quotient graph of
 // A + A^T (Section 3, edge set E_B), self loops removed.  Returns pI (D
 // supernodes ascending, then C supernodes ascending) and the D count.
-void is_order(const VB& A, double ddtol, std::vector<int32_t>& pI, int64_t& nD, std::vector<double>& w) {
+// fixed (optional): rows that never enter the set (D5).
+void is_order(const VB& A, double ddtol, std::vector<int32_t>& pI, int64_t& nD, std::vector<double>& w,
+              const std::vector<char>* fixed = nullptr) {
   const int64_t p = A.nbr;
   w.assign(p, 0.0);
   for (int64_t Y = 0; Y < p; ++Y) {
@@ -614,6 +636,7 @@ void is_order(const VB& A, double ddtol, std::vector<int32_t>& pI, int64_t& nD, 
   for (int32_t v : order) {
     if (marked[v]) continue;
     if (w[v] < ddtol) continue;
+    if (fixed && (*fixed)[v]) continue;
     inD[v] = 1;
     marked[v] = 1;
     for (int32_t u : adj[v]) marked[u] = 1;
@@ -648,6 +671,7 @@ struct Last {
 struct Prec {
   std::vector<Level> lev;
   Last last;
+  std::vector<char> last_fixed;  // D5: the fixed rows at the last level (empty: none)
   int64_t n = 0;
   double fill = 0;  // stored scalars of all factors
 };
@@ -829,22 +853,33 @@ int ilut_last(Last& X, double t, int lfil) {
 
 // drop_all: the threshold is applied to the Schur complement at every
 // reduction (the ARMS habit) instead of only at the last one (Section 3).
-int factor(const VB& A0, int nlev, double t, int lfil, double ddtol, bool drop_all, Prec& P) {
+// fixed (optional, one flag per block row of A0): rows kept out of every
+// independent set (D5); they follow the C rows from level to level.
+int factor(const VB& A0, int nlev, double t, int lfil, double ddtol, bool drop_all, Prec& P,
+           const std::vector<char>* fixed = nullptr) {
   if (A0.nbr != A0.nbc || nlev < 0 || !(t >= 0.0)) return EINVAL;
   P.n = A0.roff[A0.nbr];
   VB cur = A0;
+  std::vector<char> fx;
+  if (fixed) fx = *fixed;
   for (int l = 0; l < nlev && cur.nbr > 0; ++l) {
     Level L;
     L.A = cur;
     scale(L.A, L.r, L.c);
-    is_order(L.A, ddtol, L.pI, L.nD, L.w);
+    is_order(L.A, ddtol, L.pI, L.nD, L.w, fixed ? &fx : nullptr);
     if (L.nD == 0) break;  // nothing to eliminate: cur becomes the last level
     const bool last_red = (l == nlev - 1) || drop_all;
     int st = factor_level(L, last_red, t, lfil);
     if (st != OK) return st;
+    if (fixed) {
+      std::vector<char> nx(L.nC);
+      for (int64_t k = 0; k < L.nC; ++k) nx[k] = fx[L.pI[L.nD + k]];
+      fx.swap(nx);
+    }
     cur = L.S;
     P.lev.push_back(std::move(L));
   }
+  if (fixed) P.last_fixed = fx;
   P.last.A = std::move(cur);
   scale(P.last.A, P.last.r, P.last.c);
   int st = ilut_last(P.last, t, lfil);
@@ -858,7 +893,11 @@ int factor(const VB& A0, int nlev, double t, int lfil, double ddtol, bool drop_a
 
 // ---------------------------------------------------------------------------
 // Solve phase, Alg. 2 (VBARMS_Solve), recursively over the levels.
-void solve_last(const Last& X, const double* g, double* z) {
+// fixv (optional, D7): the values of the rows flagged in fixed, in this
+// level's scaled variables before the column scaling; those rows are not
+// solved for in the backward sweep.
+void solve_last(const Last& X, const double* g, double* z, const double* fixv = nullptr,
+                const std::vector<char>* fixed = nullptr) {
   const VB& A = X.A;
   const int64_t p = A.nbr, n = A.roff[p];
   std::vector<double> y(n);
@@ -881,6 +920,10 @@ void solve_last(const Last& X, const double* g, double* z) {
   std::vector<double> x(n);
   for (int64_t i = p - 1; i >= 0; --i) {
     const int ni = A.rsz[i];
+    if (fixv && (*fixed)[i]) {
+      for (int a = 0; a < ni; ++a) x[A.roff[i] + a] = fixv[A.roff[i] + a] / X.c[A.roff[i] + a];
+      continue;
+    }
     std::vector<double> s(y.begin() + A.roff[i], y.begin() + A.roff[i] + ni);
     for (int64_t b = X.U.bptr[i]; b < X.U.bptr[i + 1]; ++b) {
       const int32_t j = X.U.bcol[b];
@@ -899,9 +942,10 @@ void solve_last(const Last& X, const double* g, double* z) {
   for (int64_t i = 0; i < n; ++i) z[i] = X.c[i] * x[i];
 }
 
-void solve_level(const Prec& P, size_t l, const double* b, double* x) {
+// fixv (optional, D7): values of the fixed rows in this level's variables.
+void solve_level(const Prec& P, size_t l, const double* b, double* x, const double* fixv = nullptr) {
   if (l == P.lev.size()) {
-    solve_last(P.last, b, x);
+    solve_last(P.last, b, x, fixv, &P.last_fixed);
     return;
   }
   const Level& L = P.lev[l];
@@ -938,8 +982,18 @@ void solve_level(const Prec& P, size_t l, const double* b, double* x) {
       }
     }
   }
+  // the fixed values in the next level's variables: x = c * z on the C rows
+  std::vector<double> fnext;
+  if (fixv) {
+    fnext.assign(n - nf, 0.0);
+    for (int64_t k = L.nD; k < p; ++k) {
+      const int32_t Y = L.pI[k];
+      for (int a = 0; a < A.rsz[Y]; ++a)
+        fnext[newoff[k] - nf + a] = fixv[A.roff[Y] + a] / L.c[A.roff[Y] + a];
+    }
+  }
   std::vector<double> z(n - nf);
-  solve_level(P, l + 1, g.data(), z.data());
+  solve_level(P, l + 1, g.data(), z.data(), fixv ? fnext.data() : nullptr);
   // y = U^{-1} (u - W z)
   for (int64_t y = 0; y < L.nD; ++y) {
     const int m = L.W.rsz[y];
@@ -1073,6 +1127,215 @@ void dd_apply(const DD& D, const double* x, double* y) {
       if (D.restricted && D.part[Wi[k]] != i) continue;
       for (int a = 0; a < Ai.rsz[k]; ++a) y[D.roff[Wi[k]] + a] = y[D.roff[Wi[k]] + a] + zi[Ai.roff[k] + a];
     }
+  }
+}
+
+// Section 5, Schur-complement global preconditioner (D4-D7), all subdomains
+// in one address space.
+struct DDS {
+  int nparts = 0, msteps = 0;
+  int64_t n = 0, ng = 0;
+  std::vector<int64_t> roff;            // scalar offsets of A's block rows
+  std::vector<int32_t> part;            // D1
+  std::vector<char> iface;              // D4, per block row of A
+  std::vector<std::vector<int32_t>> W;  // subdomain rows: interior, then interface
+  std::vector<int64_t> nint;            // interior block rows per subdomain
+  std::vector<int64_t> gofs;            // start of each subdomain's interface in the global interface vector
+  std::vector<VB> Aloc;                 // A_i (D4)
+  std::vector<Prec> loc;                // VBARMS of A_i with fixed interface (D5)
+  VB E;                                 // E_ij on the global interface numbering
+};
+
+int dds_build(const VB& A, int nparts, int msteps, int nlev, double t, int lfil, double ddtol, bool drop_all,
+              DDS& D) {
+  if (A.nbr != A.nbc || nparts < 1 || msteps < 1) return EINVAL;
+  const int64_t p = A.nbr, n = A.roff[p];
+  D.nparts = nparts;
+  D.msteps = msteps;
+  D.n = n;
+  D.roff = A.roff;
+  D.part.assign(p, 0);
+  for (int64_t I = 0; I < p; ++I) D.part[I] = (int32_t)(((int64_t)nparts * A.roff[I]) / n);
+  // D4: interface rows
+  D.iface.assign(p, 0);
+  for (int64_t I = 0; I < p; ++I)
+    for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b) {
+      const int32_t J = A.bcol[b];
+      if (D.part[J] != D.part[I]) {
+        D.iface[I] = 1;
+        D.iface[J] = 1;
+      }
+    }
+  D.W.assign(nparts, {});
+  D.nint.assign(nparts, 0);
+  D.Aloc.assign(nparts, VB());
+  D.loc.assign(nparts, Prec());
+  std::vector<int32_t> local(p, -1);
+  for (int i = 0; i < nparts; ++i) {
+    std::vector<int32_t>& Wi = D.W[i];
+    for (int64_t I = 0; I < p; ++I)
+      if (D.part[I] == i && !D.iface[I]) Wi.push_back((int32_t)I);
+    D.nint[i] = (int64_t)Wi.size();
+    for (int64_t I = 0; I < p; ++I)
+      if (D.part[I] == i && D.iface[I]) Wi.push_back((int32_t)I);
+    for (size_t k = 0; k < Wi.size(); ++k) local[Wi[k]] = (int32_t)k;
+  }
+  for (int i = 0; i < nparts; ++i) {
+    const std::vector<int32_t>& Wi = D.W[i];
+    if (Wi.empty()) continue;
+    std::vector<int32_t> sz;
+    for (int32_t I : Wi) sz.push_back(A.rsz[I]);
+    VB& Ai = D.Aloc[i];
+    Ai.init(sz, sz);
+    for (int32_t I : Wi) {
+      std::vector<std::pair<int32_t, int64_t>> blks;  // (local column, block of A)
+      for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b)
+        if (D.part[A.bcol[b]] == i) blks.push_back({local[A.bcol[b]], b});
+      std::sort(blks.begin(), blks.end());
+      for (auto& cb : blks) Ai.push(cb.first, A.blk(cb.second));
+      Ai.end_row();
+    }
+    std::vector<char> fixed(Wi.size(), 0);
+    for (size_t k = (size_t)D.nint[i]; k < Wi.size(); ++k) fixed[k] = 1;
+    const int st = factor(Ai, nlev, t, lfil, ddtol, drop_all, D.loc[i], &fixed);
+    if (st != OK) return st;
+  }
+  // the global interface vector: every subdomain's interface rows in turn
+  std::vector<int32_t> gpos(p, -1), gsz;
+  D.gofs.assign(nparts + 1, 0);
+  int64_t o = 0;
+  for (int i = 0; i < nparts; ++i) {
+    D.gofs[i] = o;
+    for (size_t k = (size_t)D.nint[i]; k < D.W[i].size(); ++k) {
+      gpos[D.W[i][k]] = (int32_t)gsz.size();
+      gsz.push_back(A.rsz[D.W[i][k]]);
+      o += A.rsz[D.W[i][k]];
+    }
+  }
+  D.gofs[nparts] = o;
+  D.ng = o;
+  // E: the blocks of A between interface rows of different subdomains
+  D.E.init(gsz, gsz);
+  for (int i = 0; i < nparts; ++i)
+    for (size_t k = (size_t)D.nint[i]; k < D.W[i].size(); ++k) {
+      const int32_t I = D.W[i][k];
+      std::vector<std::pair<int32_t, int64_t>> blks;
+      for (int64_t b = A.bptr[I]; b < A.bptr[I + 1]; ++b)
+        if (D.part[A.bcol[b]] != i) blks.push_back({gpos[A.bcol[b]], b});
+      std::sort(blks.begin(), blks.end());
+      for (auto& cb : blks) D.E.push(cb.first, A.blk(cb.second));
+      D.E.end_row();
+    }
+  return OK;
+}
+
+// Local solve of subdomain i: r in A's numbering (or, when rloc, already in
+// the subdomain's), result in the subdomain's numbering.
+void dds_local_solve(const DDS& D, int i, const double* r, bool rloc, std::vector<double>& out,
+                     const double* fixv = nullptr) {
+  const VB& Ai = D.Aloc[i];
+  const int64_t ni = Ai.roff[Ai.nbr];
+  std::vector<double> ri(ni);
+  if (rloc) {
+    for (int64_t q = 0; q < ni; ++q) ri[q] = r[q];
+  } else {
+    for (size_t k = 0; k < D.W[i].size(); ++k)
+      for (int a = 0; a < Ai.rsz[k]; ++a) ri[Ai.roff[k] + a] = r[D.roff[D.W[i][k]] + a];
+  }
+  out.assign(ni, 0.0);
+  solve_level(D.loc[i], 0, ri.data(), out.data(), fixv);
+}
+
+// out = blockdiag(S_i)^{-1} v on the global interface vector (D6).
+void dds_sinv(const DDS& D, const double* v, double* out) {
+  for (int i = 0; i < D.nparts; ++i) {
+    const VB& Ai = D.Aloc[i];
+    if (D.W[i].empty()) continue;
+    const int64_t ni = Ai.roff[Ai.nbr], i0 = Ai.roff[D.nint[i]];
+    std::vector<double> ri(ni, 0.0), zi;
+    for (int64_t q = i0; q < ni; ++q) ri[q] = v[D.gofs[i] + q - i0];
+    dds_local_solve(D, i, ri.data(), true, zi);
+    for (int64_t q = i0; q < ni; ++q) out[D.gofs[i] + q - i0] = zi[q];
+  }
+}
+
+// D6: msteps steps of GMRES with y_0 = 0 on op(y) = z.
+void gmres_steps(const std::function<void(const double*, double*)>& op, const std::vector<double>& z, int m,
+                 std::vector<double>& y) {
+  const size_t n = z.size();
+  y.assign(n, 0.0);
+  const double beta = std::sqrt(dot(z, z));
+  if (beta == 0.0) return;
+  std::vector<std::vector<double>> V(m + 1, std::vector<double>(n));
+  std::vector<double> w(n), H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1, 0.0), yv(m);
+  for (size_t q = 0; q < n; ++q) V[0][q] = z[q] / beta;
+  gv[0] = beta;
+  int j = 0;
+  for (; j < m; ++j) {
+    op(V[j].data(), w.data());
+    for (int i = 0; i <= j; ++i) {
+      const double h = dot(w, V[i]);
+      H[(size_t)i * m + j] = h;
+      for (size_t q = 0; q < n; ++q) w[q] = w[q] - h * V[i][q];
+    }
+    const double hn = std::sqrt(dot(w, w));
+    H[(size_t)(j + 1) * m + j] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+      H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+      H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+    }
+    const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+    const double d = std::sqrt(a * a + c * c);
+    cs[j] = d > 0.0 ? a / d : 1.0;
+    sn[j] = d > 0.0 ? c / d : 0.0;
+    H[(size_t)j * m + j] = d;
+    H[(size_t)(j + 1) * m + j] = 0.0;
+    gv[j + 1] = -sn[j] * gv[j];
+    gv[j] = cs[j] * gv[j];
+    if (hn == 0.0) {
+      ++j;
+      break;
+    }
+    for (size_t q = 0; q < n; ++q) V[j + 1][q] = w[q] / hn;
+  }
+  for (int i = j - 1; i >= 0; --i) {
+    double sacc = gv[i];
+    for (int k = i + 1; k < j; ++k) sacc = sacc - H[(size_t)i * m + k] * yv[k];
+    yv[i] = H[(size_t)i * m + i] != 0.0 ? sacc / H[(size_t)i * m + i] : 0.0;
+  }
+  for (int i = 0; i < j; ++i)
+    for (size_t q = 0; q < n; ++q) y[q] = y[q] + yv[i] * V[i][q];
+}
+
+// One application y = M^{-1} x (D6, D7), both in A's numbering.
+void dds_apply(const DDS& D, const double* x, double* yout) {
+  std::vector<double> z(D.ng), yg;
+  std::vector<double> zi;
+  for (int i = 0; i < D.nparts; ++i) {  // z_i = S_i^{-1} g'_i
+    if (D.W[i].empty()) continue;
+    dds_local_solve(D, i, x, false, zi);
+    const VB& Ai = D.Aloc[i];
+    const int64_t ni = Ai.roff[Ai.nbr], i0 = Ai.roff[D.nint[i]];
+    for (int64_t q = i0; q < ni; ++q) z[D.gofs[i] + q - i0] = zi[q];
+  }
+  auto op = [&D](const double* v, double* out) {  // v + S^{-1} E v
+    std::vector<double> w(D.ng), t(D.ng);
+    spmv(D.E, v, w.data());
+    dds_sinv(D, w.data(), t.data());
+    for (int64_t q = 0; q < D.ng; ++q) out[q] = v[q] + t[q];
+  };
+  gmres_steps(op, z, D.msteps, yg);
+  for (int i = 0; i < D.nparts; ++i) {  // u_i = B_i^{-1} (f_i - F_i y_i)
+    if (D.W[i].empty()) continue;
+    const VB& Ai = D.Aloc[i];
+    const int64_t ni = Ai.roff[Ai.nbr], i0 = Ai.roff[D.nint[i]];
+    std::vector<double> fv(ni, 0.0), ui;
+    for (int64_t q = i0; q < ni; ++q) fv[q] = yg[D.gofs[i] + q - i0];
+    dds_local_solve(D, i, x, false, ui, fv.data());
+    for (size_t k = 0; k < D.W[i].size(); ++k)
+      for (int a = 0; a < Ai.rsz[k]; ++a)
+        yout[D.roff[D.W[i][k]] + a] = (int64_t)k < D.nint[i] ? ui[Ai.roff[k] + a] : fv[Ai.roff[k] + a];
   }
 }
 
@@ -1263,6 +1526,21 @@ void* or_factor(const void* A, int nlev, double droptol, int lfil, double ddtol,
   }
   return P;
 }
+// The same with fixed rows (D5): fixed[nbr] flags, or NULL.
+void* or_factor_fixed(const void* A, int nlev, double droptol, int lfil, double ddtol, int drop_all,
+                      const int32_t* fixed) {
+  const VB& M = *(const VB*)A;
+  std::vector<char> fx;
+  if (fixed)
+    for (int64_t I = 0; I < M.nbr; ++I) fx.push_back(fixed[I] != 0);
+  auto* P = new Prec();
+  g_last_status = factor(M, nlev, droptol, lfil, ddtol, drop_all != 0, *P, fixed ? &fx : nullptr);
+  if (g_last_status != OK) {
+    delete P;
+    return nullptr;
+  }
+  return P;
+}
 void or_prec_free(void* h) { delete (Prec*)h; }
 int or_prec_levels(void* h) { return (int)((Prec*)h)->lev.size(); }
 double or_prec_fill(void* h) { return ((Prec*)h)->fill; }
@@ -1358,6 +1636,50 @@ int or_dd_fgmres(const void* A, void* h, const double* b, double* x, double rtol
   const DD* D = (const DD*)h;
   PrecFn M = [D](const double* v, double* z) { dd_apply(*D, v, z); };
   return fgmres(*(const VB*)A, M, b, x, rtol, m, maxit, iters, relres);
+}
+
+
+void* or_dds_build(const void* A, int nparts, int msteps, int nlev, double t, int lfil, double ddtol, int drop_all) {
+  auto* D = new DDS();
+  g_last_status = dds_build(*(const VB*)A, nparts, msteps, nlev, t, lfil, ddtol, drop_all != 0, *D);
+  if (g_last_status != OK) {
+    delete D;
+    return nullptr;
+  }
+  return D;
+}
+void or_dds_free(void* h) { delete (DDS*)h; }
+int64_t or_dds_iface(void* h, int32_t* part, int32_t* iface) {
+  const DDS* D = (const DDS*)h;
+  for (size_t I = 0; I < D->part.size(); ++I) {
+    if (part) part[I] = D->part[I];
+    if (iface) iface[I] = D->iface[I];
+  }
+  return (int64_t)D->part.size();
+}
+int64_t or_dds_rows(void* h, int i, int32_t* rows, int64_t* nint) {
+  const DDS* D = (const DDS*)h;
+  if (rows) std::copy(D->W[i].begin(), D->W[i].end(), rows);
+  if (nint) *nint = D->nint[i];
+  return (int64_t)D->W[i].size();
+}
+const void* or_dds_local(void* h, int i) { return &((DDS*)h)->Aloc[i]; }
+void* or_dds_local_prec(void* h, int i) { return &((DDS*)h)->loc[i]; }
+const void* or_dds_coupling(void* h) { return &((DDS*)h)->E; }
+int64_t or_dds_ng(void* h) { return ((DDS*)h)->ng; }
+void or_dds_sinv(void* h, const double* v, double* out) { dds_sinv(*(const DDS*)h, v, out); }
+void or_dds_apply(void* h, const double* x, double* y) { dds_apply(*(const DDS*)h, x, y); }
+int or_dds_fgmres(const void* A, void* h, const double* b, double* x, double rtol, int m, int maxit, int* iters,
+                  double* relres) {
+  const DDS* D = (const DDS*)h;
+  PrecFn M = [D](const double* v, double* z) { dds_apply(*D, v, z); };
+  return fgmres(*(const VB*)A, M, b, x, rtol, m, maxit, iters, relres);
+}
+int64_t or_prec_last_fixed(void* h, int32_t* out) {
+  const Prec* P = (const Prec*)h;
+  if (out)
+    for (size_t k = 0; k < P->last_fixed.size(); ++k) out[k] = P->last_fixed[k];
+  return (int64_t)P->last_fixed.size();
 }
 
 }  // extern "C"
