@@ -47,10 +47,14 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator factor")
+    p.add_argument("--lean", action="store_true",
+                   help="release each level's intermediate factors once consumed (vbarms_opts.keep_factors = 0)")
     p.add_argument("--dd", type=int, default=0,
                    help="domain decomposition (Section 5) with this many subdomains; 0 = one global VBARMS")
     p.add_argument("--overlap", type=int, default=1, help="subdomain overlap levels with --dd (0 = block Jacobi)")
     p.add_argument("--additive", action="store_true", help="with --dd: additive instead of restricted Schwarz")
+    p.add_argument("--schur", type=int, default=0,
+                   help="with --dd: the Schur-complement global preconditioner with this many inner GMRES steps")
     return p.parse_args()
 
 
@@ -169,14 +173,29 @@ def workload(name, scale, seed):
 
 
 def dd_config(args):
-    """(nparts, overlap, restricted) of a Section 5 run, or None."""
-    return (args.dd, args.overlap, not args.additive) if getattr(args, "dd", 0) else None
+    """(nparts, overlap, restricted, inner steps) of a Section 5 run, or None;
+    inner steps > 0 selects the Schur-complement preconditioner (no overlap)."""
+    if not getattr(args, "dd", 0):
+        return None
+    ms = getattr(args, "schur", 0)
+    return (args.dd, 0, True, ms) if ms else (args.dd, args.overlap, not args.additive, 0)
 
 
 def dd_name(dd):
     if dd is None:
         return "vbarms"
+    if dd[3]:
+        return "schur"
     return "bj" if dd[1] == 0 else ("ras" if dd[2] else "asm")
+
+
+def dd_keys(dd):
+    """The config keys of a Section 5 run."""
+    if dd is None:
+        return {}
+    k = {"precond": dd_name(dd), "nparts": dd[0]}
+    k.update({"inner_steps": dd[3]} if dd[3] else {"overlap": dd[1]})
+    return k
 
 
 def cpu_model() -> str:
@@ -225,6 +244,8 @@ def oracle_setup_seconds(m, w, restart=50, dd=None, keep=False):
     t1 = time.perf_counter()
     if dd is None:
         P = oracle.Prec(c.A, w["nlev"], w["droptol"], w["lfil"])
+    elif dd[3]:
+        P = oracle.DDSchur(c.A, dd[0], dd[3], w["nlev"], w["droptol"], w["lfil"])
     else:
         P = oracle.DD(c.A, dd[0], dd[1], dd[2], w["nlev"], w["droptol"], w["lfil"])
     t2 = time.perf_counter()
@@ -281,7 +302,7 @@ def run_reference(args):
         "config": {"workload": args.workload, "nodes": m.meta.get("nodes"), "n": m.n, "nnz": m.nnz,
                    "ell": full["ell"], "tau": full["tau"], "nlev": full["nlev"], "droptol": full["droptol"],
                    "lfil": full["lfil"], "scale": args.scale,
-                   **({"precond": dd_name(dd), "nparts": dd[0], "overlap": dd[1]} if dd else {})},
+                   **dd_keys(dd)},
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"the whole {args.workload} matrix (n = {m.n}), one run of the oracle's "
                                    f"compress + factor, pinned to one core",
@@ -453,10 +474,16 @@ def main():
     torch.cuda.synchronize()
     dd = dd_config(args)
 
+    kf = not args.lean
+
     def factor(A, precision):
         if dd is None:
-            return V.vbarms_factor(A, w["nlev"], w["droptol"], w["lfil"], precision=precision)
-        return V.vbarms_dd_factor(A, dd[0], dd[1], dd[2], w["nlev"], w["droptol"], w["lfil"], precision=precision)
+            return V.vbarms_factor(A, w["nlev"], w["droptol"], w["lfil"], precision=precision, keep_factors=kf)
+        if dd[3]:
+            return V.vbarms_dd_schur_factor(A, dd[0], dd[3], w["nlev"], w["droptol"], w["lfil"], precision=precision,
+                                            keep_factors=kf)
+        return V.vbarms_dd_factor(A, dd[0], dd[1], dd[2], w["nlev"], w["droptol"], w["lfil"], precision=precision,
+                                  keep_factors=kf)
 
     def step(precision, solve=True, keep=False):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -473,21 +500,26 @@ def main():
         torch.cuda.synchronize()
         r = dict(compress_s=e[0].elapsed_time(e[1]) / 1e3, factor_s=e[1].elapsed_time(e[2]) / 1e3,
                  solve_s=e[2].elapsed_time(e[3]) / 1e3, its=its, relres=rr, stats=P.stats(),
-                 kstats=P.kernel_stats(0), av_bd=A.query()["av_bd"], av_bs=A.query()["av_bs"])
+                 kstats=P.kernel_stats(0), av_bd=A.query()["av_bd"], av_bs=A.query()["av_bs"],
+                 ilut=P.ilut_geometry())
         if keep:  # the factorization is kept for the error report (after timing)
             r.update(P=P, A=A, x=xd.clone())
         del P, A
         return r
 
-    for _ in range(args.warmup):
-        step(prec)
+    # the first factorization of the process times the ILUT's candidate
+    # workspace shapes (reported below); the later ones reuse the choice
+    warm = [step(prec) for _ in range(args.warmup)]
     barrier(dist)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
     l0 = V.launch_count()
     t0 = time.perf_counter()
-    res = [step(prec, keep=(k == args.steps - 1)) for k in range(args.steps)]
+    # the last step's factorization is kept (after its timing) only when the
+    # error report against the oracle will use it
+    want_report = not args.no_cpu_baseline and dd is None and prec == "fp32" and rank == 0 and kf
+    res = [step(prec, keep=(want_report and k == args.steps - 1)) for k in range(args.steps)]
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     launches = V.launch_count() - l0
@@ -517,10 +549,14 @@ def main():
     # FP32 vs FP64: the plain FP64 GPU factor on the same GB300
     fp64 = None
     if not args.no_fp64 and prec == "fp32":
-        r64 = step("fp64")
-        fp64 = {"setup_s": r64["compress_s"] + r64["factor_s"], "factor_s": r64["factor_s"],
-                "fgmres_its": r64["its"], "relres": r64["relres"], "phase_s": r64["stats"]["phase_s"],
-                "schur_numeric": r64["kstats"]}
+        try:
+            r64 = step("fp64")
+            fp64 = {"setup_s": r64["compress_s"] + r64["factor_s"], "factor_s": r64["factor_s"],
+                    "fgmres_its": r64["its"], "relres": r64["relres"], "phase_s": r64["stats"]["phase_s"],
+                    "mem_ratio": r64["stats"]["mem_ratio"], "schur_numeric": r64["kstats"]}
+        except V.VbarmsError as e:  # e.g. the FP64 factor does not fit in device memory
+            fp64 = {"error": str(e)}
+            torch.cuda.synchronize()
 
     # end to end through the C ABI with host buffers (pinned), copies timed:
     # compress from the host CSR (copied inside the call), factor, upload b,
@@ -583,7 +619,7 @@ def main():
                        "nnz": m.nnz, "tau": w["tau"], "nlev": w["nlev"], "droptol": w["droptol"],
                        "lfil": w["lfil"], "factor_precision": prec, "fgmres": "FGMRES(50) rtol 1e-8",
                        "parallelism": "replicas" if ws > 1 else "single",
-                       **({"precond": dd_name(dd), "nparts": dd[0], "overlap": dd[1]} if dd else {}),
+                       **dd_keys(dd),
                        "l2": "inputs larger than L2 (CSR %.2f GB)" % ((m.nnz * 12 + m.n * 8) / 1e9)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
@@ -593,7 +629,9 @@ def main():
                        "relres": last["relres"], "levels": last["stats"]["levels"],
                        "mem_ratio": last["stats"]["mem_ratio"], "phase_s": last["stats"]["phase_s"],
                        "av_bd": last["av_bd"], "av_bs": last["av_bs"], "wall_timed_s": wall,
-                       "fp64_factor": fp64, "error_vs_fp64_oracle": errors},
+                       "fp64_factor": fp64, "error_vs_fp64_oracle": errors,
+                       "ilut_geometry": {"first_factorization": (warm or res)[0]["ilut"],
+                                         "timed_steps": last["ilut"]}},
         }
         print(json.dumps(out), flush=True)
     if dist is not None:

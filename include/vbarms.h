@@ -79,6 +79,12 @@ typedef struct {
                              complement at every reduction (the ARMS habit);
                              0 (default): only at the last one, as Section 3
                              prescribes                                      */
+  int keep_factors;       /* 1 (default): keep every level's scaled matrix,
+                             F, E, C and S for vbarms_prec_export; 0: release
+                             them as soon as the factorization has consumed
+                             them (the solve never reads them), which lowers
+                             the factorization's device memory by about half;
+                             exporting a released factor is then VB_EINVAL  */
 } vbarms_opts;
 
 /* Fill *opt with the defaults above. */
@@ -101,6 +107,36 @@ void vbarms_opts_default(vbarms_opts* opt);
 vb_status vbarms_compress(int64_t n, const int64_t* rowptr, const int32_t* colind,
                           const double* val, int on_device, double tau, void* stream,
                           vbarms_vbsr* out);
+
+/* The two-pass variant of Section 2.1: rows with identical stored patterns
+ * form a group when there are two or more of them (and the pattern is not
+ * empty), groups in ascending order of their smallest row; then every other
+ * row joins the first group whose pattern P_g passes the angle test
+ * |P_j n P_g| / sqrt(|P_j| |P_g|) >= tau (evaluated as in vbarms_compress),
+ * else it stays a block of its own.  Blocks are ordered by their smallest
+ * row, rows ascending.  Arguments, ownership, layout and errors as in
+ * vbarms_compress.                                                          */
+vb_status vbarms_compress_two_pass(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                                   const double* val, int on_device, double tau, void* stream,
+                                   vbarms_vbsr* out);
+
+/* Graph-based compression (Section 2.2, Alg. 1) with minimum block density
+ * mu >= 0: vertices with identical closed neighbourhoods adj(i) in the
+ * graph of A + A^T form the initial supernodes (Alg. 1's checksum scan);
+ * then, in ascending order of their smallest vertex, each supernode X tries
+ * the supernodes owning a vertex of adj(X), in ascending order of their
+ * smallest vertex, and absorbs Z when the merged supernode S = X u Z has
+ * density N/T >= mu, with T = 2 |adj(S)| |S| - |S|^2 and
+ * N = 2 sum_{v in S} |adj(v)| - sum_{v in S} |adj(v) n S| (the T and N of
+ * Section 2.2).  Blocks are ordered by their smallest vertex, vertices
+ * ascending.  Arguments, ownership and the result's layout are those of
+ * vbarms_compress (which this call replaces for the grouping only).
+ * Errors: VB_EINVAL for mu < 0 or a malformed CSR; VB_ENOMEM when a
+ * supernode's candidate set exceeds 1024 supernodes or the adjacency pool
+ * of the merge pass runs out.                                              */
+vb_status vbarms_compress_graph(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                                const double* val, int on_device, double mu, void* stream,
+                                vbarms_vbsr* out);
 
 /* Build a VBCSR handle directly from host block arrays (square partition,
  * P_B = identity).  bsz int32[nblk]; bptr int64[nblk+1]; bcol int32[nnzb]
@@ -187,6 +223,46 @@ vb_status vbarms_dd_factor(vbarms_vbsr A, int nparts, int overlap, int restricte
 vb_status vbarms_dd_layout(vbarms_prec M, int* nparts, int* overlap, int* restricted, int64_t* union_blocks,
                            int32_t* part, int64_t* dstart, int32_t* rows);
 
+/* The Schur-complement global preconditioner of Section 5 (eq. paral,
+ * eq. gschur, eq. loc_var_schur), all subdomains on one GPU.  Subdomains as
+ * in vbarms_dd_factor with overlap 0.  A block row of subdomain i is an
+ * interface row when a stored block of A couples it, as row or as column, to
+ * another subdomain; the others are interior.  A_i lists its interior rows,
+ * then its interface rows (each ascending): [[B_i, F_i], [E_i, C_i]].  Every
+ * A_i is factored by VBARMS with (nlev, droptol, lfil, opt), all as one
+ * block-diagonal union, with the interface rows kept out of every
+ * independent set; they reach the last level, whose trailing block ILUT
+ * factors are the LU of the approximate local Schur complement
+ * S_i = C_i - E_i B_i^{-1} F_i.  One application to r = (f_i, g_i):
+ *   z = S_i^{-1} g'_i           (interface part of the local solve of r_i)
+ *   y = msteps steps of GMRES (y_0 = 0, modified Gram-Schmidt, Givens
+ *       rotations, early stop on a zero Arnoldi norm) on (I + S^{-1} E) y = z,
+ *       E the couplings E_ij between interface rows of different subdomains:
+ *       the global system eq. gschur preconditioned by blockdiag(S_i)
+ *   u_i = B_i^{-1} (f_i - F_i y_i)  (the local solve of r_i whose last-level
+ *       backward sweep keeps the interface unknowns at y_i)
+ * and returns (u_i, y_i).  The inner steps read their Hessenberg columns on
+ * the host, so an application synchronizes the stream msteps + 1 times.  The
+ * handle works with vbarms_apply, vbarms_apply_static (one application's
+ * scratch: five vectors of n, msteps + 5 interface vectors and the union
+ * solve's own), fgmres_solve and vbarms_prec_stats; vbarms_prec_export /
+ * _vector / _kernel_stats describe the union's factorization.  A: handle of
+ * vbarms_compress or vbarms_vbsr_from_blocks (input, not consumed).
+ * Errors: VB_EINVAL (nparts outside [1, 4096], msteps outside [1, 1000],
+ * nlev < 0, droptol < 0), then as vbarms_factor.                            */
+vb_status vbarms_dd_schur_factor(vbarms_vbsr A, int nparts, int msteps, int nlev, double droptol, int lfil,
+                                 const vbarms_opts* opt, vbarms_prec* out);
+
+/* Layout of a vbarms_dd_schur_factor handle: nparts, msteps, the interface
+ * size (scalars and block rows); part[nblk(A)] and iface[nblk(A)] = the
+ * subdomain and the interface flag of every block row of A; rows[nblk(A)] =
+ * the block row of A behind each union block row (each subdomain's interior
+ * rows, then its interface rows); nint[nparts] = the interior block rows of
+ * each subdomain.  Any pointer may be NULL.  VB_EINVAL for a handle of
+ * another kind.                                                              */
+vb_status vbarms_dd_schur_layout(vbarms_prec M, int* nparts, int* msteps, int64_t* ng, int64_t* ngb, int32_t* part,
+                                 int32_t* iface, int32_t* rows, int64_t* nint);
+
 /* y = M^{-1} x (Alg. 2).  x, y: device double[n], original numbering, must
  * not alias.  Runs on the stream of the matrix the handle was built from.   */
 vb_status vbarms_apply(vbarms_prec M, const double* x, double* y);
@@ -269,6 +345,18 @@ vb_status vbarms_prec_vector(vbarms_prec M, int lev, int which, double* d, int32
  * 2 n_r n_Y n_s over the block triples.  Any pointer may be NULL.           */
 vb_status vbarms_prec_kernel_stats(vbarms_prec M, int kernel, int* launches, double* ms, double* bytes,
                                    double* flops);
+
+/* The per-warp workspace the last-level ILUT of M ran with ("tile shape"
+ * of its kernel): slots (blocks of a working row held in shared memory),
+ * value_bytes (their values), warps_per_sm; source = 0 default (last level
+ * under 16384 block rows), 1 chosen by timing the candidate shapes on a
+ * prefix of this factorization's own rows (tune_s seconds of timing), 2
+ * taken from an earlier timing of a matrix of the same device, precision and
+ * class of row sizes in this process.  A prefix of the ILUT's row order is
+ * factored exactly on its own, so the timing needs no other data.  Any
+ * pointer may be NULL.                                                      */
+vb_status vbarms_prec_ilut_geometry(vbarms_prec M, int* slots, int* value_bytes, int* warps_per_sm, int* source,
+                                    double* tune_s);
 
 /* Number of kernels this library has launched since it was loaded (all
  * threads, all handles); read it before and after a call to count the

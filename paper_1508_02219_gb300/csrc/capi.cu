@@ -68,9 +68,12 @@ struct PhaseTimer {
 // dom (device, may be NULL): for a matrix made of ndom independent diagonal
 // blocks, the block of each block row (nondecreasing); it follows the rows
 // through the levels so that the last-level ILUT can interleave the blocks.
+// fixed (device, may be NULL): one flag per block row; flagged rows never
+// enter an independent set, so they reach the last level (Section 5, the
+// interface rows of the Schur-complement preconditioner).
 template <typename T>
-std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts& o, const int32_t* dom = nullptr,
-                                      int ndom = 0) {
+std::unique_ptr<PrecDev<T>> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts& o, const int32_t* dom = nullptr,
+                                        int ndom = 0, const int32_t* fixed = nullptr) {
   auto P = std::make_unique<PrecDev<T>>();
   cudaStream_t s = Ah.s;
   P->s = s;
@@ -98,6 +101,12 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
     dcur.alloc(Ah.C.A.nbr, s);
     VB_CUDA(cudaMemcpyAsync(dcur.p, dom, Ah.C.A.nbr * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   }
+  DBuf<int32_t> fcur;
+  if (fixed) {
+    fcur.alloc(std::max<int64_t>(Ah.C.A.nbr, 1), s);
+    if (Ah.C.A.nbr)
+      VB_CUDA(cudaMemcpyAsync(fcur.p, fixed, Ah.C.A.nbr * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  }
   for (int l = 0; l < o.nlev; ++l) {
     const int64_t p = cur_is64 ? cur64->nbr : curT.nbr;
     if (p == 0) break;
@@ -108,7 +117,7 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
       copy_vb<double, double>(*cur64, L.A64, s);
       scale_level_t<double>(L.A64, L.r, L.c, s);
       tm.mark(PH_SCALE);
-      nD = is_order<double>(L.A64, o.ddtol, L.w, L.pI, newpos, s);
+      nD = is_order<double>(L.A64, o.ddtol, L.w, L.pI, newpos, s, fixed ? fcur.p : nullptr);
       tm.mark(PH_ORDER);
       if (nD == 0) break;
       gather_parts<double, T>(L.A64, L.pI, newpos, nD, L, s, dst);
@@ -116,7 +125,7 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
       copy_vb<T, T>(curT, L.AT, s);
       scale_level_t<T>(L.AT, L.r, L.c, s);
       tm.mark(PH_SCALE);
-      nD = is_order<T>(L.AT, o.ddtol, L.w, L.pI, newpos, s);
+      nD = is_order<T>(L.AT, o.ddtol, L.w, L.pI, newpos, s, fixed ? fcur.p : nullptr);
       tm.mark(PH_ORDER);
       if (nD == 0) break;
       gather_parts<T, T>(L.AT, L.pI, newpos, nD, L, s, dst);
@@ -126,6 +135,11 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
       DBuf<int32_t> dn(std::max<int64_t>(p - nD, 1), s);
       take_i32(dcur.p, L.pI.p + nD, p - nD, dn.p, s);
       dcur = std::move(dn);
+    }
+    if (fixed) {
+      DBuf<int32_t> fn(std::max<int64_t>(p - nD, 1), s);
+      take_i32(fcur.p, L.pI.p + nD, p - nD, fn.p, s);
+      fcur = std::move(fn);
     }
     pivot_lu(L.D, L.piv, L.ptag, L.D32, mixed, o.fp64_pivot_cond, s, dst);
     tm.mark(PH_PIVOT);
@@ -146,7 +160,17 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
     else
       build_level_maps<T>(L, L.AT.rsz.p, L.AT.roff.p, L.AT.nbr, M, s);
     // the next level starts from S; F, E, C are no longer needed by the solve
-    copy_vb<T, T>(L.S, curT, s);
+    if (o.keep_factors) {
+      copy_vb<T, T>(L.S, curT, s);
+    } else {
+      // released once consumed: the scaled level matrix, F, E, C; S moves on
+      curT = std::move(L.S);
+      L.A64 = VBDev<double>();
+      L.AT = VBDev<T>();
+      L.F = VBDev<T>();
+      L.E = VBDev<T>();
+      L.C = VBDev<T>();
+    }
     cur_is64 = false;
     P->maps.push_back(std::move(M));
     P->lev.push_back(std::move(L));
@@ -162,6 +186,7 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
   DBuf<int32_t> tickets;
   if (track) ticket_order(dcur.p, X.A.nbr, ndom, tickets, s);
   ilut_last<T>(X, o.droptol, o.lfil, mixed, o.fp64_pivot_cond, o.wait_limit, s, dst, tickets.p);
+  if (fixed) X.fixed = std::move(fcur);
   tm.mark(PH_ILUT);
   level_orders<T>(X, o.wait_limit, dst, s);
   fill += (double)(X.Dg.nval + X.L.nval + X.U.nval);
@@ -177,28 +202,12 @@ std::unique_ptr<PrecBase> factor_impl(const vbarms_vbsr_st& Ah, const FactorOpts
   return P;
 }
 
-}  // namespace
-
-void vb::set_last_error(const std::string& msg) { g_err = msg; }
-
-// ============================================================================
-extern "C" {
-
-void vbarms_opts_default(vbarms_opts* opt) {
-  if (!opt) return;
-  opt->precision = VB_FP64;
-  opt->fp64_pivot_cond = 1e4;
-  opt->ddtol = 0.0;
-  opt->wait_limit = 0;
-  opt->schur_drop_all = 0;
-}
-
-const char* vbarms_last_error(void) { return g_err.c_str(); }
-
-vb_status vbarms_compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, int on_device,
-                          double tau, void* stream, vbarms_vbsr* out) {
-  if (!out) return set_err(VB_EINVAL, "out is NULL");
-  if (n < 0 || !(tau > 0.0 && tau <= 1.0)) return set_err(VB_EINVAL, "n < 0 or tau outside (0, 1]");
+// Step 1 with either grouping: angle-based (compress_device) or graph-based
+// (graph_compress_device); host arrays are copied to the device first.
+template <typename F>
+vb_status compress_entry(const char* who, int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                         int on_device, void* stream, vbarms_vbsr* out, F&& group) {
+  if (!out) return set_err(VB_EINVAL, std::string(who) + ": out is NULL");
   if (n > 0 && !rowptr) return set_err(VB_EINVAL, "rowptr is NULL");
   if (n > 0 && !on_device && rowptr[n] > 0 && (!colind || !val)) return set_err(VB_EINVAL, "colind/val NULL");
   if (n > 0 && on_device && (!colind || !val)) return set_err(VB_EINVAL, "colind/val NULL");
@@ -235,12 +244,55 @@ vb_status vbarms_compress(int64_t n, const int64_t* rowptr, const int32_t* colin
       rp.zero();
       d_rowptr = rp.p;
     }
-    compress_device(n, d_rowptr, d_colind, d_val, tau, s, h->status.p, h->C);
+    group(n, d_rowptr, d_colind, d_val, s, h->status.p, h->C);
     VB_CUDA(cudaStreamSynchronize(s));
   });
   if (st != VB_OK) return st;
   *out = h.release();
   return VB_OK;
+}
+
+}  // namespace
+
+void vb::set_last_error(const std::string& msg) { g_err = msg; }
+
+// ============================================================================
+extern "C" {
+
+void vbarms_opts_default(vbarms_opts* opt) {
+  if (!opt) return;
+  opt->precision = VB_FP64;
+  opt->fp64_pivot_cond = 1e4;
+  opt->ddtol = 0.0;
+  opt->wait_limit = 0;
+  opt->schur_drop_all = 0;
+  opt->keep_factors = 1;
+}
+
+const char* vbarms_last_error(void) { return g_err.c_str(); }
+
+vb_status vbarms_compress(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, int on_device,
+                          double tau, void* stream, vbarms_vbsr* out) {
+  if (n < 0 || !(tau > 0.0 && tau <= 1.0)) return set_err(VB_EINVAL, "n < 0 or tau outside (0, 1]");
+  return compress_entry("vbarms_compress", n, rowptr, colind, val, on_device, stream, out,
+                        [&](int64_t nn, const int64_t* r, const int32_t* c, const double* v, cudaStream_t s, int* dst,
+                            Compressed& C) { compress_device(nn, r, c, v, tau, s, dst, C); });
+}
+
+vb_status vbarms_compress_two_pass(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                                   int on_device, double tau, void* stream, vbarms_vbsr* out) {
+  if (n < 0 || !(tau > 0.0 && tau <= 1.0)) return set_err(VB_EINVAL, "n < 0 or tau outside (0, 1]");
+  return compress_entry("vbarms_compress_two_pass", n, rowptr, colind, val, on_device, stream, out,
+                        [&](int64_t nn, const int64_t* r, const int32_t* c, const double* v, cudaStream_t s, int* dst,
+                            Compressed& C) { two_pass_compress_device(nn, r, c, v, tau, s, dst, C); });
+}
+
+vb_status vbarms_compress_graph(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                                int on_device, double mu, void* stream, vbarms_vbsr* out) {
+  if (n < 0 || !(mu >= 0.0)) return set_err(VB_EINVAL, "n < 0 or mu < 0");
+  return compress_entry("vbarms_compress_graph", n, rowptr, colind, val, on_device, stream, out,
+                        [&](int64_t nn, const int64_t* r, const int32_t* c, const double* v, cudaStream_t s, int* dst,
+                            Compressed& C) { graph_compress_device(nn, r, c, v, mu, s, dst, C); });
 }
 
 vb_status vbarms_vbsr_from_blocks(int64_t nblk, const int32_t* bsz, const int64_t* bptr, const int32_t* bcol,
@@ -330,7 +382,8 @@ vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil, const
   if (!opt) opt = &d;
   if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
   FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
-               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
+               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0,
+               opt->keep_factors != 0};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
     DeviceScope ds(A->dev);
@@ -386,7 +439,8 @@ vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev,
       DBuf<int32_t> dom;
       union_part_ids(parts, s, dom);
       FactorOpts o{nlev[m0], droptol[m0], lfil[m0], opt->precision, opt->fp64_pivot_cond, opt->ddtol,
-                   opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
+                   opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0,
+               opt->keep_factors != 0};
       std::shared_ptr<PrecBase> P;
       if (o.precision == VB_FP64)
         P = factor_impl<double>(U, o, dom.p, (int)parts.size());
@@ -419,7 +473,8 @@ vb_status vbarms_dd_factor(vbarms_vbsr A, int nparts, int overlap, int restricte
   if (!opt) opt = &d;
   if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
   FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
-               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0};
+               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0,
+               opt->keep_factors != 0};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
     DeviceScope ds(A->dev);
@@ -457,6 +512,80 @@ vb_status vbarms_dd_factor(vbarms_vbsr A, int nparts, int overlap, int restricte
   }
   *out = h.release();
   return VB_OK;
+}
+
+vb_status vbarms_dd_schur_factor(vbarms_vbsr A, int nparts, int msteps, int nlev, double droptol, int lfil,
+                                 const vbarms_opts* opt, vbarms_prec* out) {
+  if (!A || !out) return set_err(VB_EINVAL, "NULL handle");
+  if (nlev < 0 || !(droptol >= 0.0)) return set_err(VB_EINVAL, "nlev < 0 or droptol < 0");
+  if (nparts < 1 || nparts > kDDMaxParts) return set_err(VB_EINVAL, "nparts must lie in [1, 4096]");
+  if (msteps < 1 || msteps > 1000) return set_err(VB_EINVAL, "msteps must lie in [1, 1000]");
+  vbarms_opts d;
+  vbarms_opts_default(&d);
+  if (!opt) opt = &d;
+  if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
+  FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
+               opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0,
+               opt->keep_factors != 0};
+  auto h = std::make_unique<vbarms_prec_st>();
+  vb_status st = guarded([&] {
+    DeviceScope ds(A->dev);
+    cudaStream_t s = A->s;
+    auto D = std::make_unique<PrecDDS>();
+    D->s = s;
+    D->dev = A->dev;
+    D->n = A->C.n;
+    D->precision = o.precision;
+    D->wait_limit = o.wait_limit;
+    D->perm.alloc(std::max<int64_t>(A->C.n, 1), s);
+    if (A->C.n)
+      VB_CUDA(cudaMemcpyAsync(D->perm.p, A->C.perm.p, A->C.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    D->status.alloc(1, s);
+    D->status.zero();
+    // the union of the A_i, interface rows last in each, factored once with
+    // the interface rows fixed; its rows carry their subdomain so that the
+    // last-level ILUT interleaves the subdomains
+    vbarms_vbsr_st U;
+    U.s = s;
+    U.dev = A->dev;
+    dds_build(A->C, nparts, msteps, s, D->L, U.C);
+    if (o.precision == VB_FP64)
+      D->inner = factor_impl<double>(U, o, D->L.ud.p, nparts, D->L.ufix.p);
+    else
+      D->inner = factor_impl<float>(U, o, D->L.ud.p, nparts, D->L.ufix.p);
+    for (int i = 0; i < PH_COUNT; ++i) D->phase_s[i] = D->inner->phase_s[i];
+    D->mem_ratio = D->inner->mem_ratio;
+    D->krec = std::move(D->inner->krec);
+    D->inner->krec.clear();
+    h->impl = std::move(D);
+  });
+  if (st != VB_OK) {
+    cudaStreamSynchronize(A->s);
+    return st;
+  }
+  *out = h.release();
+  return VB_OK;
+}
+
+vb_status vbarms_dd_schur_layout(vbarms_prec M, int* nparts, int* msteps, int64_t* ng, int64_t* ngb, int32_t* part,
+                                 int32_t* iface, int32_t* rows, int64_t* nint) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  auto* D = dynamic_cast<PrecDDS*>(M->impl.get());
+  if (!D) return set_err(VB_EINVAL, "not a Schur-complement preconditioner");
+  return guarded([&] {
+    DeviceScope ds(D->dev);
+    const DDSLayout& L = D->L;
+    if (nparts) *nparts = L.nparts;
+    if (msteps) *msteps = L.msteps;
+    if (ng) *ng = L.ng;
+    if (ngb) *ngb = L.ngb;
+    if (part && L.p) VB_CUDA(cudaMemcpyAsync(part, L.part.p, L.p * sizeof(int32_t), cudaMemcpyDeviceToHost, D->s));
+    if (iface && L.p)
+      VB_CUDA(cudaMemcpyAsync(iface, L.iface.p, L.p * sizeof(int32_t), cudaMemcpyDeviceToHost, D->s));
+    if (rows && L.p) VB_CUDA(cudaMemcpyAsync(rows, L.ug.p, L.p * sizeof(int32_t), cudaMemcpyDeviceToHost, D->s));
+    if (nint) VB_CUDA(cudaMemcpyAsync(nint, L.nint.p, L.nparts * sizeof(int64_t), cudaMemcpyDeviceToHost, D->s));
+    VB_CUDA(cudaStreamSynchronize(D->s));
+  });
 }
 
 vb_status vbarms_dd_layout(vbarms_prec M, int* nparts, int* overlap, int* restricted, int64_t* union_blocks,
@@ -671,6 +800,18 @@ vb_status vbarms_prec_stats(vbarms_prec M, int* levels_used, double* mem_ratio, 
 uint64_t vbarms_launch_count(void) { return g_launch_count.load(); }
 
 uint64_t vbarms_alloc_count(void) { return g_alloc_count.load(); }
+
+vb_status vbarms_prec_ilut_geometry(vbarms_prec M, int* slots, int* value_bytes, int* warps_per_sm, int* source,
+                                    double* tune_s) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  const IlutInfo I = M->impl->ilut_info();
+  if (slots) *slots = I.slots;
+  if (value_bytes) *value_bytes = I.vbytes;
+  if (warps_per_sm) *warps_per_sm = I.warps_per_sm;
+  if (source) *source = I.source;
+  if (tune_s) *tune_s = I.tune_s;
+  return VB_OK;
+}
 
 vb_status vbarms_prec_kernel_stats(vbarms_prec M, int kernel, int* launches, double* ms, double* bytes,
                                    double* flops) {

@@ -224,6 +224,11 @@ inline unsigned grid_for(int64_t work, int per_block, int64_t cap = 152LL * 64) 
 void scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
 
+// Stable ascending sort of keys[0, n) on their low key_bits bits (8 bits a
+// pass), moving vals (may be NULL) alongside.  The buffers are swapped with
+// scratch ones: keys and *vals hold the result.
+void radix_sort_u64(DBuf<unsigned long long>& keys, DBuf<int32_t>* vals, int64_t n, int key_bits, cudaStream_t s);
+
 // --------------------------------------------------------------------------
 // Integer hash-set helpers (open addressing, linear probing, key -1 = empty).
 __device__ __forceinline__ uint32_t hmix(uint32_t x) {

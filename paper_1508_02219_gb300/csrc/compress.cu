@@ -430,6 +430,13 @@ __global__ void k_scatter_values(int64_t n, const int64_t* __restrict__ rowptr, 
 
 }  // namespace
 
+void validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colind, int32_t* len, cudaStream_t s, int* dst) {
+  if (n) {
+    launch(k_validate, grid_for(n, 256), 256, 0, s, n, rowptr, colind, len, dst);
+    VB_LAUNCH_CHECK();
+  }
+}
+
 void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau,
                      cudaStream_t s, int* dst, Compressed& out) {
   out.n = n;
@@ -555,8 +562,17 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   isleader.release();
   lead_scan.release();
   simbuf.release();
+  heavy.release();
+  assemble_vbcsr(n, rowptr, colind, val, p, bsz, boff, blk.p, offin.p, s, dst, out);
+}
 
-  // A4: VBCSR of P_B A P_B^T
+// A4: VBCSR of P_B A P_B^T from a grouping of the rows (out.perm already set).
+void assemble_vbcsr(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, int64_t p,
+                    DBuf<int32_t>& bsz, DBuf<int64_t>& boff, const int32_t* blkp, const int32_t* offinp,
+                    cudaStream_t s, int* dst, Compressed& out) {
+  const int64_t nnz = out.nnz;
+  DBuf<int32_t> heavy(std::max<int64_t>(n, 1), s);
+  DBuf<int> nheavy(1, s);
   VBDev<double>& A = out.A;
   A.nbr = A.nbc = p;
   A.same_partition = true;
@@ -570,7 +586,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   nheavy.zero();
   if (p) {
     launch(k_block_pattern<false, 0>, grid_for(p, CW, 152LL * 24), CW * 32, smem_pat, s, 
-        p, nullptr, A.roff.p, out.perm.p, rowptr, colind, blk.p, nullptr, 0, bcnt.p, nullptr, nullptr, heavy.p,
+        p, nullptr, A.roff.p, out.perm.p, rowptr, colind, blkp, nullptr, 0, bcnt.p, nullptr, nullptr, heavy.p,
         nheavy.p, dst);
     VB_LAUNCH_CHECK();
   }
@@ -588,7 +604,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
     hblocks = (warps + CW - 1) / CW;
     gtabb.alloc((size_t)hblocks * CW * gcapb, s);
     launch(k_block_pattern<true, 0>, (unsigned)hblocks, CW * 32, 0, s, nhb, heavy.p, A.roff.p, out.perm.p, rowptr,
-                                                                  colind, blk.p, gtabb.p, gcapb, bcnt.p, nullptr,
+                                                                  colind, blkp, gtabb.p, gcapb, bcnt.p, nullptr,
                                                                   nullptr, nullptr, nullptr, dst);
     VB_LAUNCH_CHECK();
   }
@@ -602,13 +618,13 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
     dummy.zero();
     DBuf<int32_t> hv2(std::max<int>(nhb, 1), s);
     launch(k_block_pattern<false, 1>, grid_for(p, CW, 152LL * 24), CW * 32, smem_pat, s, 
-        p, nullptr, A.roff.p, out.perm.p, rowptr, colind, blk.p, nullptr, 0, nullptr, A.bptr.p, A.bcol.p, hv2.p,
+        p, nullptr, A.roff.p, out.perm.p, rowptr, colind, blkp, nullptr, 0, nullptr, A.bptr.p, A.bcol.p, hv2.p,
         dummy.p, dst);
     VB_LAUNCH_CHECK();
   }
   if (nhb > 0) {
     launch(k_block_pattern<true, 1>, (unsigned)hblocks, CW * 32, 0, s, nhb, heavy.p, A.roff.p, out.perm.p, rowptr,
-                                                                  colind, blk.p, gtabb.p, gcapb, nullptr, A.bptr.p,
+                                                                  colind, blkp, gtabb.p, gcapb, nullptr, A.bptr.p,
                                                                   A.bcol.p, nullptr, nullptr, dst);
     VB_LAUNCH_CHECK();
   }
@@ -616,7 +632,7 @@ void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, co
   finish_offsets(A, s);
   A.val.zero();
   if (n) {
-    launch(k_scatter_values, grid_for(n, 8), 256, 0, s, n, rowptr, colind, val, blk.p, offin.p, A.rsz.p, A.bptr.p,
+    launch(k_scatter_values, grid_for(n, 8), 256, 0, s, n, rowptr, colind, val, blkp, offinp, A.rsz.p, A.bptr.p,
                                                      A.bcol.p, A.voff.p, A.val.p, dst);
     VB_LAUNCH_CHECK();
   }

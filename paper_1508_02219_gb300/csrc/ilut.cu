@@ -33,7 +33,10 @@
 // pool or the global workspace sets an overflow code and the host repeats the
 // kernel with larger buffers.
 #include <algorithm>
+#include <chrono>
 #include <climits>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "internal.h"
@@ -93,6 +96,10 @@ struct Pools {
   // ticket -> row (nullptr: ticket t is row t); every row's dependencies
   // must come earlier in it
   const int32_t* order;
+  // tickets handed out (the rows of the first nticket tickets: every prefix
+  // of the ticket order holds its rows' dependencies, so it is factored
+  // exactly on its own)
+  int64_t nticket;
 };
 
 // Global fallback workspace, per warp.
@@ -117,6 +124,12 @@ struct IlutGeom {
   int o_misc, o_stage, o_vals, o_keys, o_hpos, o_scol, o_soff, o_sst, o_sf2, o_sncl, o_lc, o_ls;
   int bytes;
 };
+
+// Geometries chosen by timing, per device, precision and class of row sizes
+// (the process keeps them), and the smallest matrix that is timed.
+std::mutex g_geom_mu;
+std::map<long long, struct IlutGeom> g_geom;
+constexpr int64_t kTuneMinRows = 16384;
 
 constexpr int PVMAX = 64;
 struct IlutMisc {
@@ -731,7 +744,10 @@ __global__ void __launch_bounds__(256, 2)
     long long row = 0;
     if (lane == 0) {
       row = (long long)atomicAdd(P.ctr + 4, 1ULL);
-      if (P.order && row < A.nbr) row = P.order[row];
+      if (row >= P.nticket)
+        row = A.nbr;
+      else if (P.order)
+        row = P.order[row];
     }
     row = __shfl_sync(0xffffffffu, row, 0);
     if (row >= A.nbr) break;
@@ -1577,6 +1593,7 @@ static IlutGeom make_geom(int slots, int vbytes, int stage, int lcap) {
 template <typename T>
 void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, uint64_t wait_limit, cudaStream_t s,
                int* dst, const int32_t* order) {
+  IlutInfo* info = &X.info;
   const VBDev<T>& A = X.A;
   const int64_t p = A.nbr;
   const int64_t n = p ? d2h(A.roff.p + p, s) : 0;
@@ -1622,29 +1639,38 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   VB_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
   VB_CUDA(cudaDeviceGetAttribute(&smem_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // Shared workspace per warp, from the rows of the matrix (rows of a dozen
-  // large blocks, or rows of dozens of small blocks whose fill reaches
-  // hundreds).
+  // Shared workspace per warp ("tile shape" of the kernel): chosen by timing
+  // the candidates below on a prefix of this matrix's own tickets (every
+  // prefix of the ticket order is factored exactly on its own), the fastest
+  // kept per device, precision and class of row sizes for the rest of the
+  // process; small matrices take the measured default.  The candidates span
+  // what the configured workloads were measured to prefer: 64 to 256 slots,
+  // 2 to 8 KB of values, 16 down to 5 warps per SM.
   DBuf<unsigned long long> rstat(2, s);
   rstat.zero();
   launch(k_row_stats, grid_for(p, 256), 256, 0, s, p, A.bptr.p, rstat.p);
   VB_LAUNCH_CHECK();
   const std::vector<unsigned long long> rs = d2h_vec(rstat.p, 2, s);
   const bool wide = rs[0] * 4 > (unsigned long long)p;
-  // Measured on the configured workloads (one GB300): small shared
-  // workspaces and 16 warps per SM are fastest, also for rows whose fill
-  // outgrows them (they continue in the global workspace and the L1 cache
-  // keeps what the shared memory leaves free), except for FP64 rows of many
-  // small blocks, which keep 128 slots and 8 KB of values.
-  const IlutGeom G = (wide && sizeof(T) == sizeof(double)) ? make_geom(128, 8192, 2048, 256)
-                                                           : make_geom(64, 2048, 2048, wide ? 256 : 128);
+  const bool f64 = sizeof(T) == sizeof(double);
+  std::vector<IlutGeom> cands;
+  cands.push_back((wide && f64) ? make_geom(128, 8192, 2048, 256) : make_geom(64, 2048, 2048, wide ? 256 : 128));
+  cands.push_back(make_geom(64, 4096, 2048, 128));
+  cands.push_back(make_geom(128, f64 ? 8192 : 4096, 2048, 256));
+  cands.push_back(make_geom(256, f64 ? 8192 : 4096, 2048, 256));
   const int reserve = 1024;  // shared memory the system keeps per block
-  int wpb = std::min(8, smem_block / G.bytes);
-  if (wpb < 1) fail(VB_EINTERNAL, "last-level ILUT: shared workspace exceeds a block");
-  int bps = std::max(1, smem_sm / (wpb * G.bytes + reserve));
-  while (wpb * bps > 16 && bps > 1) --bps;
-  const size_t smem = (size_t)wpb * G.bytes;
-
+  // warps per block and blocks per SM of a geometry: the most warps per SM
+  // (at most 16)
+  auto shape = [&](const IlutGeom& G, int& wpb, int& bps) {
+    wpb = 0, bps = 0;
+    for (int w = 8; w >= 1; --w) {
+      if (w * G.bytes > smem_block) continue;
+      int b = smem_sm / (w * G.bytes + reserve);
+      while (w * b > 16) --b;
+      if (b >= 1 && w * b > wpb * bps) wpb = w, bps = b;
+    }
+    return wpb >= 1;
+  };
   // L pool: the L blocks; U pool: one record per row.  L and U each hold
   // about half of the last-level matrix on the configured workloads; the
   // pools start at its full size and grow on overflow (retry)
@@ -1652,8 +1678,21 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   int64_t ucap16 = (A.nval * (int64_t)sizeof(T) + X.Dg.nval * 8 + 8 * A.nnzb + 64 * p) / 16 + 4096;
   int smax = 1024;
   int64_t vmax = 32768;
-  for (int attempt = 0; attempt < 6; ++attempt) {
-    const int64_t nblocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * bps, (p + wpb - 1) / wpb));
+  // buffers of one launch
+  struct Run {
+    DBuf<int32_t> lcol, lcnt;
+    DBuf<int64_t> lvo, lstart;
+    DBuf<unsigned long long> done, ctr;
+    DBuf<T> lval;
+    DBuf<unsigned char> upool;
+  };
+  // one launch of the kernel over the first nticket tickets with geometry G;
+  // returns the device status (the time of the launch in *ms when asked)
+  auto run = [&](const IlutGeom& G, int64_t nticket, Run& R, float* ms) -> int {
+    int wpb = 0, bps = 0;
+    if (!shape(G, wpb, bps)) fail(VB_EINTERNAL, "last-level ILUT: shared workspace exceeds a block");
+    const size_t smem = (size_t)wpb * G.bytes;
+    const int64_t nblocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * bps, (nticket + wpb - 1) / wpb));
     const int64_t nwarps = nblocks * wpb;
     int ht = 1;
     while (ht < 2 * smax) ht <<= 1;
@@ -1663,24 +1702,97 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
     DBuf<unsigned long long> srt(nwarps * 4 * smax, s);
     DBuf<T> wvals(nwarps * vmax, s);
     Workspace ws{keys.p, hpos.p, scol.p, soff.p, sstate.p, sf2.p, sncl.p, fin.p, srt.p, ht, smax, vmax};
-    DBuf<int32_t> lcol(lbcap, s), lcnt(p, s);
-    DBuf<int64_t> lvo(lbcap, s), lstart(p, s);
-    DBuf<unsigned long long> done(p, s);
-    DBuf<T> lval(lvcap, s);
-    DBuf<unsigned char> upool(ucap16 * 16, s);
-    DBuf<unsigned long long> ctr(8, s);
+    R.lcol.alloc(lbcap, s);
+    R.lcnt.alloc(p, s);
+    R.lvo.alloc(lbcap, s);
+    R.lstart.alloc(p, s);
+    R.done.alloc(p, s);
+    R.lval.alloc(lvcap, s);
+    R.upool.alloc(ucap16 * 16, s);
+    R.ctr.alloc(8, s);
     DBuf<int> abort(1, s);
-    ctr.zero();
-    done.zero();
+    R.ctr.zero();
+    R.done.zero();
     abort.zero();
     X.piv.zero();
-    Pools P{lcol.p, lvo.p, lstart.p, lcnt.p, done.p, ctr.p, lbcap, lvcap, ucap16, abort.p, order};
+    Pools P{R.lcol.p, R.lvo.p, R.lstart.p, R.lcnt.p, R.done.p, R.ctr.p, lbcap, lvcap, ucap16, abort.p, order,
+            nticket};
     VB_CUDA(cudaFuncSetAttribute(k_ilut<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    launch(k_ilut<T>, (unsigned)nblocks, wpb * 32, smem, s, A.view(), G, ws, wvals.p, P, lval.p, upool.p,
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) {
+      VB_CUDA(cudaEventCreate(&e0));
+      VB_CUDA(cudaEventCreate(&e1));
+      VB_CUDA(cudaEventRecord(e0, s));
+    }
+    launch(k_ilut<T>, (unsigned)nblocks, wpb * 32, smem, s, A.view(), G, ws, wvals.p, P, R.lval.p, R.upool.p,
            X.Dg.voff.p, X.Dg.val.p, mixed ? X.Dg32.val.p : nullptr, X.piv.p, mixed ? X.ptag.p : nullptr,
            mixed ? 1 : 0, cond_thr, t, lfil, (unsigned long long)wait_limit, dst);
     VB_LAUNCH_CHECK();
-    const int st = d2h(dst, s);
+    if (ms) {
+      VB_CUDA(cudaEventRecord(e1, s));
+      VB_CUDA(cudaEventSynchronize(e1));
+      VB_CUDA(cudaEventElapsedTime(ms, e0, e1));
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+    if (info) {
+      info->warps_per_sm = wpb * bps;
+    }
+    return d2h(dst, s);
+  };
+  // the geometry: cached, tuned on a prefix, or the default
+  IlutGeom G = cands[0];
+  {
+    int m1 = 0, m2 = 0;
+    const double mb = (double)A.nnzb / (double)p, mv = (double)A.nval / (double)p;
+    while ((1 << m1) < mb) ++m1;
+    while ((1 << m2) < mv) ++m2;
+    const long long key = ((long long)dev << 40) | ((long long)sizeof(T) << 32) | ((long long)wide << 24) |
+                          ((long long)m1 << 8) | (long long)m2;
+    std::lock_guard<std::mutex> lk(g_geom_mu);
+    auto it = g_geom.find(key);
+    if (it != g_geom.end()) {
+      G = it->second;
+      if (info) info->source = 2;
+    } else if (p >= kTuneMinRows) {
+      const int64_t m = std::min<int64_t>(std::max<int64_t>(p / 16, 4096), 65536);
+      const auto t0 = std::chrono::steady_clock::now();
+      float best = 0.f;
+      int bi = -1;
+      for (size_t c = 0; c < cands.size(); ++c) {
+        Run R;
+        float ms = 0.f;
+        const int st = run(cands[c], m, R, &ms);
+        if (st != DEV_OK) {
+          VB_CUDA(cudaMemsetAsync(dst, 0, sizeof(int), s));
+          if (st == DEV_ETIMEOUT || st == DEV_INTERNAL) check_status(dst, s, "last-level ILUT tuning");
+          continue;
+        }
+        if (bi < 0 || ms < best) best = ms, bi = (int)c;
+      }
+      if (bi >= 0) G = cands[bi];
+      g_geom[key] = G;
+      if (info) {
+        info->source = 1;
+        info->tune_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      }
+    }
+  }
+  if (info) {
+    info->slots = G.slots;
+    info->vbytes = G.vbytes;
+  }
+  for (int attempt = 0; attempt < 6; ++attempt) {
+    Run R;
+    const int st = run(G, p, R, nullptr);
+    auto& lcol = R.lcol;
+    auto& lcnt = R.lcnt;
+    auto& lvo = R.lvo;
+    auto& lstart = R.lstart;
+    auto& done = R.done;
+    auto& lval = R.lval;
+    auto& upool = R.upool;
+    auto& ctr = R.ctr;
     if (st == DEV_OVERFLOW) {
       VB_CUDA(cudaMemsetAsync(dst, 0, sizeof(int), s));
       std::vector<unsigned long long> c = d2h_vec(ctr.p, 8, s);

@@ -16,6 +16,40 @@ struct Compressed {
 void compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double tau,
                      cudaStream_t s, int* dstatus, Compressed& out);
 
+// A1: CSR validation (columns in range, ascending, unique; rowptr monotone)
+// into the status word; len[i] = row lengths.
+void validate_csr(int64_t n, const int64_t* rowptr, const int32_t* colind, int32_t* len, cudaStream_t s, int* dst);
+
+// A4: the VBCSR matrix P_B A P_B^T of a grouping of the rows into p blocks:
+// bsz/boff block sizes and offsets, blk[r] the block of row r, offin[r] its
+// place in the block, out.perm and out.nnz already set.
+void assemble_vbcsr(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, int64_t p,
+                    DBuf<int32_t>& bsz, DBuf<int64_t>& boff, const int32_t* blk, const int32_t* offin,
+                    cudaStream_t s, int* dstatus, Compressed& out);
+
+// leader[v] = the smallest u whose CSR list (ptr, col; sorted lists) equals
+// v's: classes of identical lists, by a hash, a sort and exact comparisons.
+void list_classes(int64_t n, const int64_t* ptr, const int32_t* col, int32_t* leader, cudaStream_t s);
+
+// VBCSR of the grouping whose every row r belongs to the group of lead[r],
+// the group's smallest row (lead[lead[r]] = lead[r]); blocks in ascending
+// order of their smallest row, rows ascending.
+void assemble_from_leaders(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                           const int32_t* lead, cudaStream_t s, int* dst, Compressed& out);
+
+// Two-pass checksum and angle compression (Section 2.1, readings T1-T3):
+// classes of identical nonempty row patterns with two or more rows form the
+// groups (ordered by smallest row); every other row joins the first group
+// whose pattern passes the angle test cos >= tau, else stays alone.
+void two_pass_compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                              double tau, cudaStream_t s, int* dst, Compressed& out);
+
+// Graph-based compression (Section 2.2, Alg. 1) with minimum block density
+// mu: exact classes of identical closed neighbourhoods of A + A^T, then the
+// merge pass; the same VBCSR assembly as compress_device.
+void graph_compress_device(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val, double mu,
+                           cudaStream_t s, int* dstatus, Compressed& out);
+
 // The block-diagonal union of several compressed matrices, for batched
 // factorization: parts keep their order, their block and scalar rows are
 // numbered consecutively.
@@ -38,6 +72,15 @@ struct LevelDev {
   VBDev<T> F, E, C, W, G, S;
 };
 
+// How the last-level ILUT ran: its per-warp shared workspace (slots, value
+// bytes), warps per SM, and whether the geometry was the default (0), timed
+// on a prefix of this matrix (1, tune_s seconds) or taken from an earlier
+// timing of a matrix of the same class (2).
+struct IlutInfo {
+  int slots = 0, vbytes = 0, warps_per_sm = 0, source = 0;
+  double tune_s = 0;
+};
+
 template <typename T>
 struct LastDev {
   VBDev<T> A;  // scaled last-level matrix
@@ -50,6 +93,10 @@ struct LastDev {
   // (backward) sweep: the triangular solves take rows in this order
   DBuf<int32_t> lorder, uorder;
   int64_t ldepth = 0, udepth = 0;
+  IlutInfo info;
+  // rows kept out of every independent set (the interface rows of the
+  // Schur-complement preconditioner), one flag per row; empty when none
+  DBuf<int32_t> fixed;
 };
 
 // Level orders of the last level's triangular sweeps (L forward: row i
@@ -67,6 +114,7 @@ struct FactorOpts {
   double ddtol;
   uint64_t wait_limit;
   bool schur_drop_all;
+  bool keep_factors;
 };
 
 // Step 2: two-sided max-abs scaling in place (FP64 values).

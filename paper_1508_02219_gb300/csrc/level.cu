@@ -232,10 +232,13 @@ __device__ __forceinline__ bool better(const double* w, int64_t u, int64_t v) {
 }
 
 // state: 0 undecided, 1 in D, 2 out (in the current MIS round), 3 out.
+// fixed (may be NULL): rows that never enter the set (interface rows of the
+// Section 5 Schur-complement preconditioner); they are out from the start.
 __global__ void k_is_init(int64_t p, const int64_t* __restrict__ bptr, const int32_t* __restrict__ bcol,
                           const int64_t* __restrict__ tptr, const int32_t* __restrict__ trow,
-                          const double* __restrict__ w, double ddtol, int32_t* __restrict__ pending,
-                          int32_t* __restrict__ state, unsigned long long* remaining) {
+                          const double* __restrict__ w, double ddtol, const int32_t* __restrict__ fixed,
+                          int32_t* __restrict__ pending, int32_t* __restrict__ state,
+                          unsigned long long* remaining) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p; v += (int64_t)gridDim.x * blockDim.x) {
     int cnt = 0;
     for (int64_t b = bptr[v]; b < bptr[v + 1]; ++b) {
@@ -247,7 +250,7 @@ __global__ void k_is_init(int64_t p, const int64_t* __restrict__ bptr, const int
       if (u != v && better(w, u, v)) ++cnt;
     }
     pending[v] = cnt;
-    if (w[v] < ddtol) {  // too weakly dominant: never a pivot (forced into C)
+    if (w[v] < ddtol || (fixed && fixed[v])) {  // too weakly dominant or fixed: never a pivot (forced into C)
       state[v] = 2;
       atomicAdd(remaining, (unsigned long long)-1LL);
     } else {
@@ -1105,7 +1108,7 @@ void scale_level(VBDev<double>& A, DBuf<double>& r, DBuf<double>& c, cudaStream_
 
 template <typename TA>
 int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t>& pI, DBuf<int32_t>& newpos,
-                 cudaStream_t s) {
+                 cudaStream_t s, const int32_t* fixed) {
   const int64_t p = A.nbr;
   w.alloc(p, s);
   pI.alloc(p, s);
@@ -1129,7 +1132,8 @@ int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t
     unsigned long long pp = (unsigned long long)p;
     h2d(remaining.p, &pp, 1, s);
   }
-  launch(k_is_init, g, 256, 0, s, p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, ddtol, pending.p, state.p, remaining.p);
+  launch(k_is_init, g, 256, 0, s, p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, ddtol, fixed, pending.p, state.p,
+         remaining.p);
   VB_LAUNCH_CHECK();
   for (int64_t round = 0;; ++round) {
     launch(k_is_round_b, g, 256, 0, s, p, A.bptr.p, A.bcol.p, tptr.p, trow.p, w.p, pending.p, state.p);
@@ -1152,9 +1156,9 @@ int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t
   return nD;
 }
 template int64_t is_order<double>(const VBDev<double>&, double, DBuf<double>&, DBuf<int32_t>&, DBuf<int32_t>&,
-                                  cudaStream_t);
+                                  cudaStream_t, const int32_t*);
 template int64_t is_order<float>(const VBDev<float>&, double, DBuf<double>&, DBuf<int32_t>&, DBuf<int32_t>&,
-                                 cudaStream_t);
+                                 cudaStream_t, const int32_t*);
 
 template <typename TA, typename T>
 void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_t>& newpos, int64_t nD,

@@ -6,10 +6,11 @@
 
 namespace vb {
 
-// Step 3: weights, independent set, P_I.  Returns nD.
+// Step 3: weights, independent set, P_I.  Returns nD.  fixed (device, may
+// be NULL): rows kept out of the set.
 template <typename TA>
 int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t>& pI, DBuf<int32_t>& newpos,
-                 cudaStream_t s);
+                 cudaStream_t s, const int32_t* fixed = nullptr);
 
 // Eq. 4: the D (FP64 pivot blocks), F, E, C parts of P_I A P_I^T.
 template <typename TA, typename T>

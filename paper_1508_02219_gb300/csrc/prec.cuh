@@ -47,8 +47,19 @@ struct PrecBase {
   // (256-byte aligned, scratch_bytes() long): allocates nothing.
   virtual void apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm) = 0;
   virtual void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) = 0;
+  // How the last-level ILUT ran.
+  virtual IlutInfo ilut_info() const = 0;
   // The device status word the solve kernels report to.
   virtual int* status_dev() { return status.p; }
+  // Factorizations with fixed rows (the Schur-complement preconditioner's
+  // local solver): the solve with the fixed rows' unknowns given, in the
+  // factorization's own numbering, with its own buffers or with scratch.
+  virtual void apply_fixed(const double*, double*, const double*) {
+    fail(VB_EINTERNAL, "this factorization has no fixed rows");
+  }
+  virtual void solve_scratch(const double*, double*, unsigned char*, int, const double*) {
+    fail(VB_EINTERNAL, "this factorization has no scratch solve");
+  }
 };
 
 template <typename T>
@@ -64,14 +75,22 @@ struct PrecDev : PrecBase {
   DBuf<int32_t> flags;
   DBuf<unsigned long long> tick;
   DBuf<int> abort_flag;
+  DBuf<double> fwork;  // fixed values on the levels (apply_fixed)
   void prepare_apply();
   int levels() const override { return (int)lev.size(); }
   void apply_perm(const double* x, double* y) override;
+  // The same with the fixed rows' unknowns given (fixv, this numbering):
+  // the last level's backward sweep keeps them instead of solving for them.
+  void apply_fixed(const double* x, double* y, const double* fixv) override;
   size_t scratch_bytes() const override;
   void apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm) override;
+  // Alg. 2 in this numbering (x, y not permuted) with scratch_bytes() of
+  // scratch; fixv as in apply_fixed (may be NULL).
+  void solve_scratch(const double* x, double* y, unsigned char* scratch, int nsm, const double* fixv) override;
   void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval, int32_t* rsz,
                   int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) override;
   void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) override;
+  IlutInfo ilut_info() const override { return last.info; }
 };
 
 // Section 5 global preconditioners (dd.cu): the subdomains of A, their
@@ -123,6 +142,48 @@ struct PrecDD : PrecBase {
   void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) override {
     inner->export_vec(lev, which, d, iv, len);
   }
+  IlutInfo ilut_info() const override { return inner->ilut_info(); }
+  int* status_dev() override { return inner->status_dev(); }
+};
+
+// Section 5 Schur-complement global preconditioner (ddschur.cu): the
+// interior/interface split of the subdomains, their union (each subdomain's
+// interior rows, then its interface rows) and the interface couplings E_ij.
+struct DDSLayout {
+  int nparts = 0, msteps = 0;
+  int64_t n = 0, p = 0;      // scalar and block rows of A (and of the union)
+  int64_t ng = 0, ngb = 0;   // interface scalars and interface block rows
+  DBuf<int32_t> part, iface; // per block row of A: subdomain, interface flag
+  DBuf<int32_t> ug, ud, ufix;// per union block row: block row of A, subdomain, interface flag
+  DBuf<int64_t> dstart;      // first union block row of each subdomain (nparts + 1)
+  DBuf<int64_t> nint;        // interior block rows of each subdomain
+  DBuf<int32_t> gidx;        // union scalar row -> scalar row of A
+  DBuf<int32_t> gpos;        // interface scalar -> union scalar row
+  VBDev<double> E;           // E_ij on the interface numbering (interface rows ascending)
+  DBuf<int64_t> Erb;         // scalar row of E -> its block row
+};
+
+void dds_build(const Compressed& A, int nparts, int msteps, cudaStream_t s, DDSLayout& L, Compressed& U);
+
+// One application: local solves, msteps of GMRES on the global interface
+// system preconditioned by the local Schur complements, recovery of the
+// interior unknowns.
+struct PrecDDS : PrecBase {
+  std::unique_ptr<PrecBase> inner;  // the union's factorization, interface rows fixed
+  DDSLayout L;
+  DBuf<unsigned char> work;         // apply_perm's scratch (allocated on first use)
+  int levels() const override { return inner->levels(); }
+  void apply_perm(const double* x, double* y) override;
+  size_t scratch_bytes() const override;
+  void apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm) override;
+  void export_mat(int lev, int which, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval, int32_t* rsz,
+                  int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) override {
+    inner->export_mat(lev, which, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+  }
+  void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) override {
+    inner->export_vec(lev, which, d, iv, len);
+  }
+  IlutInfo ilut_info() const override { return inner->ilut_info(); }
   int* status_dev() override { return inner->status_dev(); }
 };
 

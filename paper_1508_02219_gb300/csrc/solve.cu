@@ -193,6 +193,7 @@ constexpr size_t tri_smem() {
 // of a row sits in an earlier level and so holds an earlier ticket.
 //   forward  (BWD = false): y_i <- y_i - sum_{k<i} L_ik y_k        (in place)
 //   backward (BWD = true):  x_i <- D_i^{-1} (y_i - sum_{j>i} U_ij x_j)
+//                           (rows flagged in fixed keep the x_i in out)
 // Rows of up to TRI_MR scalars: the row's block values (static) are staged in
 // shared memory before any wait; every lane then owns some blocks of the row,
 // waits for its own dependency, loads that dependency's values in one batch
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(SW * 32)
           const float* __restrict__ lu32, const int32_t* __restrict__ ptag, const int32_t* __restrict__ piv,
           const double* __restrict__ rhs, double* __restrict__ out, const int32_t* __restrict__ order,
           int32_t* __restrict__ done, unsigned long long* ticket, int* abort, unsigned long long wait_limit,
-          int* st) {
+          int* st, const int32_t* __restrict__ fixed) {
   extern __shared__ __align__(16) unsigned char tri_sm[];
   T* stage = (T*)tri_sm + (size_t)(threadIdx.x >> 5) * TRI_STAGE;
   double* sv = (double*)(tri_sm + (size_t)SW * TRI_STAGE * sizeof(T)) + (size_t)(threadIdx.x >> 5) * 32 * TRI_R;
@@ -216,6 +217,10 @@ __global__ void __launch_bounds__(SW * 32)
     t0 = __shfl_sync(0xffffffffu, t0, 0);
     if (t0 >= M.nbr) break;
     const int64_t i = order[t0];
+    if (BWD && fixed && fixed[i]) {  // the caller gave this row's unknowns (already in out)
+      if (lane == 0) atomicExch(&done[i], 1);
+      continue;
+    }
     const int ni = M.rsz[i];
     const int64_t r0 = M.roff[i];
     bool failed = false;
@@ -513,83 +518,170 @@ void PrecDev<T>::prepare_apply() {
   prepared = true;
 }
 
-// Alg. 2 over all levels; enqueues work only (no synchronization).
-template <typename T>
-void PrecDev<T>::apply_perm(const double* x, double* y) {
-  prepare_apply();
-  const int nl = (int)lev.size();
-  const bool mixed = sizeof(T) != sizeof(double);
-  double* wp = work.p;
-  const double* in = x;
-  double* out = y;
-  std::vector<double*> bh(nl), xh(nl);
-  for (int l = 0; l < nl; ++l) {
-    bh[l] = wp;
-    wp += maps[l].n;
-    xh[l] = wp;
-    wp += maps[l].n;
+namespace {
+constexpr int kMaxLev = 64;  // fixed host arrays: the scratch path allocates nothing
+
+// Device buffers of one application of Alg. 2.
+struct SolveBufs {
+  double* bh[kMaxLev];          // per level: P_I S_1 b, then y = U^{-1}(u - W z)
+  double* xh[kMaxLev];          // per level: [y; z] before S_2 P_I^T
+  const int64_t* grow[kMaxLev]; // scalar row -> block row of G
+  const int64_t* wrow[kMaxLev]; // scalar row -> block row of W
+  double* fv[kMaxLev + 1];      // fixed values per level (fv[0]: the caller's)
+  double* yy;                   // last level: S_1 g, then L^{-1} S_1 g
+  double* xx;                   // last level: U^{-1} L^{-1} S_1 g
+  int32_t* flags;               // 2 p_last completion flags
+  unsigned long long* tick;     // 2 tickets
+  int* abort;
+  int nsm;
+};
+
+// fv_next[q] = fv[sp[nf + q]] / c[sp[nf + q]]: the fixed values of the C rows
+// in the next level's variables (the backward sweep forms x = c * z there).
+__global__ void k_fix_down(int64_t n, const int32_t* __restrict__ sp, const double* __restrict__ c,
+                           const double* __restrict__ fv, double* __restrict__ fnext) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t o = sp[q];
+    fnext[q] = __ddiv_rn(fv[o], c[o]);
   }
+}
+
+// Last level: the fixed rows' unknowns before the column scaling.
+__global__ void k_fix_last(int64_t p, const int64_t* __restrict__ roff, const int32_t* __restrict__ fixed,
+                           const double* __restrict__ fv, const double* __restrict__ c, double* __restrict__ xx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!fixed[i]) continue;
+    for (int64_t q = roff[i]; q < roff[i + 1]; ++q) xx[q] = __ddiv_rn(fv[q], c[q]);
+  }
+}
+
+// Alg. 2 over all levels, in the factorization's own numbering; enqueues
+// work only.  fixv (may be NULL; factorizations with fixed rows only): the
+// values the last level's backward sweep takes for its fixed rows instead of
+// solving for them (Section 5, the recovery u_i = B_i^{-1}(f_i - F_i y_i)).
+template <typename T>
+void solve_core(const PrecDev<T>& P, const double* in, double* out, const SolveBufs& B, const double* fixv) {
+  cudaStream_t s = P.s;
+  const int nl = (int)P.lev.size();
+  const bool mixed = sizeof(T) != sizeof(double);
+  const auto& last = P.last;
   // forward sweep down the levels: u = L^{-1} P f, g' = g - G u
   for (int l = 0; l < nl; ++l) {
-    const LevelDev<T>& L = lev[l];
-    const LevelMaps& M = maps[l];
-    const double* b = l == 0 ? in : bh[l - 1] + maps[l - 1].nf;
-    if (M.n) launch(k_gather_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.r.p, b, bh[l]);
+    const LevelDev<T>& L = P.lev[l];
+    const LevelMaps& M = P.maps[l];
+    const double* b = l == 0 ? in : B.bh[l - 1] + P.maps[l - 1].nf;
+    if (M.n) launch(k_gather_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.r.p, b, B.bh[l]);
     if (L.nD)
       launch(k_pivot_fwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
-             mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, bh[l]);
+             mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, B.bh[l]);
     const int64_t ng = M.n - M.nf;
     if (ng && L.G.nnzb)
-      launch(k_bsr_sub<T>, grid_for(ng, 128), 128, 0, s, L.G.view(), M.grow.p, ng, bh[l], bh[l] + M.nf);
+      launch(k_bsr_sub<T>, grid_for(ng, 128), 128, 0, s, L.G.view(), B.grow[l], ng, B.bh[l], B.bh[l] + M.nf);
+    if (fixv && ng)
+      launch(k_fix_down, grid_for(ng, 256), 256, 0, s, ng, M.sperm.p + M.nf, L.c.p, l == 0 ? fixv : B.fv[l],
+             B.fv[l + 1]);
     VB_LAUNCH_CHECK();
   }
   // last level: z = S2 (L U)^{-1} S1 g
   {
-    const double* g = nl == 0 ? in : bh[nl - 1] + maps[nl - 1].nf;
-    double* z = nl == 0 ? out : xh[nl - 1] + maps[nl - 1].nf;
-    if (nlast) {
-      double* yy = wp;
-      double* xx = wp + nlast;
-      launch(k_mul, grid_for(nlast, 256), 256, 0, s, nlast, last.r.p, g, yy);
+    const int64_t nl_last = nl == 0 ? P.n : P.maps[nl - 1].n - P.maps[nl - 1].nf;
+    const double* g = nl == 0 ? in : B.bh[nl - 1] + P.maps[nl - 1].nf;
+    double* z = nl == 0 ? out : B.xh[nl - 1] + P.maps[nl - 1].nf;
+    if (nl_last) {
+      launch(k_mul, grid_for(nl_last, 256), 256, 0, s, nl_last, last.r.p, g, B.yy);
       const int64_t p = last.A.nbr;
-      VB_CUDA(cudaMemsetAsync(flags.p, 0, 2 * p * sizeof(int32_t), s));
-      VB_CUDA(cudaMemsetAsync(tick.p, 0, 2 * sizeof(unsigned long long), s));
-      VB_CUDA(cudaMemsetAsync(abort_flag.p, 0, sizeof(int), s));
-      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 2, (p + SW - 1) / SW));
+      const int32_t* fixed = fixv ? last.fixed.p : nullptr;
+      if (fixed)
+        launch(k_fix_last, grid_for(p, 256), 256, 0, s, p, last.A.roff.p, fixed, nl == 0 ? fixv : B.fv[nl],
+               last.c.p, B.xx);
+      // the buffers keep the previous call's contents: clear what starts at 0
+      VB_CUDA(cudaMemsetAsync(B.flags, 0, 2 * p * sizeof(int32_t), s));
+      VB_CUDA(cudaMemsetAsync(B.tick, 0, 2 * sizeof(unsigned long long), s));
+      VB_CUDA(cudaMemsetAsync(B.abort, 0, sizeof(int), s));
+      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)B.nsm * 2, (p + SW - 1) / SW));
       launch(k_tri<T, false>, nb, SW * 32, tri_smem<T>(), s, last.L.view(), nullptr, nullptr, nullptr, nullptr,
-             nullptr, yy, yy, last.lorder.p, flags.p, tick.p, abort_flag.p, (unsigned long long)wait_limit,
-             status.p);
+             nullptr, B.yy, B.yy, last.lorder.p, B.flags, B.tick, B.abort, (unsigned long long)P.wait_limit,
+             P.status.p, nullptr);
       launch(k_tri<T, true>, nb, SW * 32, tri_smem<T>(), s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
-             mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx, last.uorder.p, flags.p + p,
-             tick.p + 1, abort_flag.p, (unsigned long long)wait_limit, status.p);
-      launch(k_mul, grid_for(nlast, 256), 256, 0, s, nlast, last.c.p, xx, z);
+             mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, B.yy, B.xx, last.uorder.p, B.flags + p,
+             B.tick + 1, B.abort, (unsigned long long)P.wait_limit, P.status.p, fixed);
+      launch(k_mul, grid_for(nl_last, 256), 256, 0, s, nl_last, last.c.p, B.xx, z);
       VB_LAUNCH_CHECK();
     }
   }
   // backward sweep up the levels: y = U^{-1} (u - W z), x = S2 P_I^T [y; z]
   for (int l = nl - 1; l >= 0; --l) {
-    const LevelDev<T>& L = lev[l];
-    const LevelMaps& M = maps[l];
-    double* xo = l == 0 ? out : xh[l - 1] + maps[l - 1].nf;
+    const LevelDev<T>& L = P.lev[l];
+    const LevelMaps& M = P.maps[l];
+    double* xo = l == 0 ? out : B.xh[l - 1] + P.maps[l - 1].nf;
     if (M.nf && L.W.nnzb)
-      launch(k_bsr_sub<T>, grid_for(M.nf, 128), 128, 0, s, L.W.view(), M.wrow.p, M.nf, xh[l] + M.nf, bh[l]);
+      launch(k_bsr_sub<T>, grid_for(M.nf, 128), 128, 0, s, L.W.view(), B.wrow[l], M.nf, B.xh[l] + M.nf, B.bh[l]);
     if (L.nD)
       launch(k_pivot_bwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
-             mixed ? L.D32.val.p : nullptr, L.ptag.p, bh[l], xh[l]);
-    if (M.n) launch(k_scatter_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.c.p, xh[l], xo);
+             mixed ? L.D32.val.p : nullptr, L.ptag.p, B.bh[l], B.xh[l]);
+    if (M.n) launch(k_scatter_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.c.p, B.xh[l], xo);
     VB_LAUNCH_CHECK();
   }
+}
+
+// Doubles of fixed-value work: the C rows of every level.
+template <typename T>
+int64_t fixed_work(const PrecDev<T>& P) {
+  if (!P.last.fixed.p) return 0;
+  int64_t t = 0;
+  for (const auto& M : P.maps) t += M.n - M.nf;
+  return t;
+}
+}  // namespace
+
+template <typename T>
+void PrecDev<T>::apply_perm(const double* x, double* y) {
+  apply_fixed(x, y, nullptr);
+}
+
+template <typename T>
+void PrecDev<T>::apply_fixed(const double* x, double* y, const double* fixv) {
+  prepare_apply();
+  const int nl = (int)lev.size();
+  if (nl > kMaxLev) fail(VB_EINVAL, "more than 64 levels");
+  if (fixv && !last.fixed.p) fail(VB_EINVAL, "the factorization has no fixed rows");
+  SolveBufs B{};
+  double* wp = work.p;
+  for (int l = 0; l < nl; ++l) {
+    B.bh[l] = wp;
+    wp += maps[l].n;
+    B.xh[l] = wp;
+    wp += maps[l].n;
+    B.grow[l] = maps[l].grow.p;
+    B.wrow[l] = maps[l].wrow.p;
+  }
+  B.yy = wp;
+  B.xx = wp + nlast;
+  if (fixv) {
+    const int64_t nf = fixed_work(*this);
+    if ((int64_t)fwork.n < nf) fwork.alloc(std::max<int64_t>(nf, 1), s);
+    double* fp = fwork.p;
+    for (int l = 0; l < nl; ++l) {
+      B.fv[l + 1] = fp;
+      fp += maps[l].n - maps[l].nf;
+    }
+  }
+  B.flags = flags.p;
+  B.tick = tick.p;
+  B.abort = abort_flag.p;
+  B.nsm = nsm;
+  solve_core(*this, x, y, B, fixv);
 }
 
 // ---- the same solve with caller-provided scratch (no allocation) ----------
 // Layout of the scratch, each piece 256-byte aligned: the permuted x and y
 // (n doubles each), the per-level work vectors (2 n_l doubles each), the
 // last-level vectors (2 n_last doubles), the row->block maps of G and W
-// (n_l int64 per level), the last-level flags (2 p_last int32), two tickets
-// and the abort word.
+// (n_l int64 per level), the last-level flags (2 p_last int32), two tickets,
+// the abort word, and (factorizations with fixed rows) the fixed-value work.
 namespace {
 struct ScratchPlan {
-  size_t xp, yp, work, maps, flags, tick, abort, total;
+  size_t xp, yp, work, maps, flags, tick, abort, fwork, total;
 };
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -619,6 +711,8 @@ ScratchPlan plan_scratch(const PrecDev<T>& P) {
   o = align256(o + 2 * 8);
   sp.abort = o;
   o = align256(o + 4);
+  sp.fwork = o;
+  o = align256(o + (size_t)fixed_work(P) * 8);
   sp.total = o;
   return sp;
 }
@@ -631,89 +725,53 @@ size_t PrecDev<T>::scratch_bytes() const {
 
 template <typename T>
 void PrecDev<T>::apply_with_scratch(const double* x, double* y, unsigned char* scratch, int nsm_dev) {
-  tri_attributes<T>();
   const ScratchPlan sp = plan_scratch(*this);
   double* xp = (double*)(scratch + sp.xp);
   double* yp = (double*)(scratch + sp.yp);
+  gather_dev(xp, x, perm.p, n, s);
+  solve_scratch(xp, yp, scratch, nsm_dev, nullptr);
+  scatter_dev(y, yp, perm.p, n, s);
+}
+
+template <typename T>
+void PrecDev<T>::solve_scratch(const double* x, double* y, unsigned char* scratch, int nsm_dev, const double* fixv) {
+  tri_attributes<T>();
+  const ScratchPlan sp = plan_scratch(*this);
+  const int nl = (int)lev.size();
+  if (nl > kMaxLev) fail(VB_EINVAL, "more than 64 levels");
+  if (fixv && !last.fixed.p) fail(VB_EINVAL, "the factorization has no fixed rows");
   double* wp = (double*)(scratch + sp.work);
   int64_t* mp = (int64_t*)(scratch + sp.maps);
-  int32_t* fl = (int32_t*)(scratch + sp.flags);
-  unsigned long long* tk = (unsigned long long*)(scratch + sp.tick);
-  int* ab = (int*)(scratch + sp.abort);
-  const int nl = (int)lev.size();
-  const bool mixed = sizeof(T) != sizeof(double);
-  constexpr int kMaxLev = 64;  // fixed host arrays: this path allocates nothing
-  if (nl > kMaxLev) fail(VB_EINVAL, "more than 64 levels");
-  gather_dev(xp, x, perm.p, n, s);
-  double* bh[kMaxLev];
-  double* xh[kMaxLev];
-  int64_t* gmap[kMaxLev];
-  int64_t* wmap[kMaxLev];
+  double* fp = (double*)(scratch + sp.fwork);
+  SolveBufs B{};
   for (int l = 0; l < nl; ++l) {
-    bh[l] = wp;
+    B.bh[l] = wp;
     wp += maps[l].n;
-    xh[l] = wp;
+    B.xh[l] = wp;
     wp += maps[l].n;
-    gmap[l] = mp;
-    wmap[l] = mp + (maps[l].n - maps[l].nf);
+    int64_t* gm = mp;
+    int64_t* wm = mp + (maps[l].n - maps[l].nf);
     mp += maps[l].n;
     const LevelDev<T>& L = lev[l];
     if (maps[l].n - maps[l].nf > 0 && L.G.nbr)
-      launch(k_rowblk, grid_for(L.G.nbr, 8), 256, 0, s, L.G.nbr, L.G.roff.p, gmap[l]);
-    if (maps[l].nf > 0 && L.W.nbr) launch(k_rowblk, grid_for(L.W.nbr, 8), 256, 0, s, L.W.nbr, L.W.roff.p, wmap[l]);
+      launch(k_rowblk, grid_for(L.G.nbr, 8), 256, 0, s, L.G.nbr, L.G.roff.p, gm);
+    if (maps[l].nf > 0 && L.W.nbr) launch(k_rowblk, grid_for(L.W.nbr, 8), 256, 0, s, L.W.nbr, L.W.roff.p, wm);
     VB_LAUNCH_CHECK();
-  }
-  const double* in = xp;
-  double* out = yp;
-  for (int l = 0; l < nl; ++l) {
-    const LevelDev<T>& L = lev[l];
-    const LevelMaps& M = maps[l];
-    const double* b = l == 0 ? in : bh[l - 1] + maps[l - 1].nf;
-    if (M.n) launch(k_gather_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.r.p, b, bh[l]);
-    if (L.nD)
-      launch(k_pivot_fwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
-             mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, bh[l]);
-    const int64_t ng = M.n - M.nf;
-    if (ng && L.G.nnzb)
-      launch(k_bsr_sub<T>, grid_for(ng, 128), 128, 0, s, L.G.view(), gmap[l], ng, bh[l], bh[l] + M.nf);
-    VB_LAUNCH_CHECK();
-  }
-  {
-    const int64_t nl_last = maps.empty() ? n : maps.back().n - maps.back().nf;
-    const double* g = nl == 0 ? in : bh[nl - 1] + maps[nl - 1].nf;
-    double* z = nl == 0 ? out : xh[nl - 1] + maps[nl - 1].nf;
-    if (nl_last) {
-      double* yy = wp;
-      double* xx = wp + nl_last;
-      launch(k_mul, grid_for(nl_last, 256), 256, 0, s, nl_last, last.r.p, g, yy);
-      const int64_t p = last.A.nbr;
-      // the scratch keeps the previous call's contents: clear what starts at 0
-      VB_CUDA(cudaMemsetAsync(fl, 0, 2 * p * sizeof(int32_t), s));
-      VB_CUDA(cudaMemsetAsync(tk, 0, 2 * sizeof(unsigned long long), s));
-      VB_CUDA(cudaMemsetAsync(ab, 0, sizeof(int), s));
-      const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm_dev * 2, (p + SW - 1) / SW));
-      launch(k_tri<T, false>, nb, SW * 32, tri_smem<T>(), s, last.L.view(), nullptr, nullptr, nullptr, nullptr,
-             nullptr, yy, yy, last.lorder.p, fl, tk, ab, (unsigned long long)wait_limit, status.p);
-      launch(k_tri<T, true>, nb, SW * 32, tri_smem<T>(), s, last.U.view(), last.Dg.voff.p, last.Dg.val.p,
-             mixed ? last.Dg32.val.p : nullptr, last.ptag.p, last.piv.p, yy, xx, last.uorder.p, fl + p, tk + 1,
-             ab, (unsigned long long)wait_limit, status.p);
-      launch(k_mul, grid_for(nl_last, 256), 256, 0, s, nl_last, last.c.p, xx, z);
-      VB_LAUNCH_CHECK();
+    B.grow[l] = gm;
+    B.wrow[l] = wm;
+    if (fixv) {
+      B.fv[l + 1] = fp;
+      fp += maps[l].n - maps[l].nf;
     }
   }
-  for (int l = nl - 1; l >= 0; --l) {
-    const LevelDev<T>& L = lev[l];
-    const LevelMaps& M = maps[l];
-    double* xo = l == 0 ? out : xh[l - 1] + maps[l - 1].nf;
-    if (M.nf && L.W.nnzb)
-      launch(k_bsr_sub<T>, grid_for(M.nf, 128), 128, 0, s, L.W.view(), wmap[l], M.nf, xh[l] + M.nf, bh[l]);
-    if (L.nD)
-      launch(k_pivot_bwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
-             mixed ? L.D32.val.p : nullptr, L.ptag.p, bh[l], xh[l]);
-    if (M.n) launch(k_scatter_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.c.p, xh[l], xo);
-    VB_LAUNCH_CHECK();
-  }
-  scatter_dev(y, yp, perm.p, n, s);
+  const int64_t nl_last = maps.empty() ? n : maps.back().n - maps.back().nf;
+  B.yy = wp;
+  B.xx = wp + nl_last;
+  B.flags = (int32_t*)(scratch + sp.flags);
+  B.tick = (unsigned long long*)(scratch + sp.tick);
+  B.abort = (int*)(scratch + sp.abort);
+  B.nsm = nsm_dev;
+  solve_core(*this, x, y, B, fixv);
 }
 
 template <typename T>

@@ -130,4 +130,71 @@ void set_partition(DBuf<int32_t>& sz, DBuf<int64_t>& off, const int32_t* src, in
   scan_i32_to_i64(sz.p, off.p, nb, s);
 }
 
+
+// --------------------------------------------------------------------------
+// Stable least-significant-digit radix sort of 64-bit keys, 8 bits a pass:
+// per tile of RS_T keys a digit histogram, one scan over (digit, tile), then
+// every key goes to its digit's range after the keys of earlier tiles and of
+// earlier warps and lanes of its own tile.
+namespace {
+constexpr int RS64_T = 256;
+
+__global__ void __launch_bounds__(RS64_T) k_rs64_hist(int64_t n, const unsigned long long* __restrict__ key, int shift,
+                                                      int64_t ntile, int32_t* __restrict__ hist) {
+  __shared__ int h[256];
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)RS64_T + threadIdx.x;
+  if (e < n) atomicAdd(&h[(key[e] >> shift) & 255], 1);
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * ntile + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(RS64_T) k_rs64_scatter(int64_t n, const unsigned long long* __restrict__ key,
+                                                         const int32_t* __restrict__ val, int shift, int64_t ntile,
+                                                         const int64_t* __restrict__ base,
+                                                         unsigned long long* __restrict__ okey,
+                                                         int32_t* __restrict__ oval) {
+  __shared__ int cnt[RS64_T / 32][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int x = threadIdx.x; x < (RS64_T / 32) * 256; x += blockDim.x) (&cnt[0][0])[x] = 0;
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)RS64_T + threadIdx.x;
+  const bool has = e < n;
+  const unsigned long long k = has ? key[e] : 0ull;
+  const int d = has ? (int)((k >> shift) & 255) : 256;
+  const unsigned peers = __match_any_sync(0xffffffffu, d);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  if (has && rank == 0) cnt[warp][d] = __popc(peers);
+  __syncthreads();
+  if (has) {
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += cnt[w][d];
+    const int64_t pos = base[(int64_t)d * ntile + blockIdx.x] + off + rank;
+    okey[pos] = k;
+    if (val) oval[pos] = val[e];
+  }
+}
+}  // namespace
+
+void radix_sort_u64(DBuf<unsigned long long>& keys, DBuf<int32_t>* vals, int64_t n, int key_bits, cudaStream_t s) {
+  if (n <= 1) return;
+  const int64_t ntile = (n + RS64_T - 1) / RS64_T;
+  DBuf<int32_t> hist(256 * ntile, s);
+  DBuf<int64_t> base(256 * ntile + 1, s);
+  DBuf<unsigned long long> k2(n, s);
+  DBuf<int32_t> v2;
+  if (vals) v2.alloc(n, s);
+  for (int shift = 0; shift < key_bits; shift += 8) {
+    launch(k_rs64_hist, (unsigned)ntile, RS64_T, 0, s, n, keys.p, shift, ntile, hist.p);
+    VB_LAUNCH_CHECK();
+    scan_i32_to_i64(hist.p, base.p, 256 * ntile, s);
+    launch(k_rs64_scatter, (unsigned)ntile, RS64_T, 0, s, n, keys.p, vals ? vals->p : nullptr, shift, ntile, base.p,
+           k2.p, vals ? v2.p : nullptr);
+    VB_LAUNCH_CHECK();
+    std::swap(keys, k2);
+    if (vals) std::swap(*vals, v2);
+  }
+}
+
 }  // namespace vb

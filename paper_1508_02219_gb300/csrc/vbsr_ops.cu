@@ -157,6 +157,7 @@ void copy_vb(const VBDev<TS>& src, VBDev<TD>& dst, cudaStream_t s) {
 template <typename T>
 void export_vb(const VBDev<T>& M, cudaStream_t s, int64_t* nbr, int64_t* nbc, int64_t* nnzb, int64_t* nval,
                int32_t* rsz, int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) {
+  if (!M.bptr.p) fail(VB_EINVAL, "this factor was released after use (vbarms_opts.keep_factors = 0)");
   if (nbr) *nbr = M.nbr;
   if (nbc) *nbc = M.nbc;
   if (nnzb) *nnzb = M.nnzb;

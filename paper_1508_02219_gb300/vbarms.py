@@ -39,7 +39,7 @@ class VbarmsError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("fp64_pivot_cond", C.c_double), ("ddtol", C.c_double),
-                ("wait_limit", C.c_uint64), ("schur_drop_all", C.c_int)]
+                ("wait_limit", C.c_uint64), ("schur_drop_all", C.c_int), ("keep_factors", C.c_int)]
 
 
 def library_path() -> str:
@@ -61,6 +61,8 @@ def lib():
                 "vbarms_opts_default": (None, [P(Opts)]),
                 "vbarms_last_error": (C.c_char_p, []),
                 "vbarms_compress": (i32, [i64, vp, vp, vp, i32, d, vp, P(vp)]),
+                "vbarms_compress_graph": (i32, [i64, vp, vp, vp, i32, d, vp, P(vp)]),
+                "vbarms_compress_two_pass": (i32, [i64, vp, vp, vp, i32, d, vp, P(vp)]),
                 "vbarms_vbsr_from_blocks": (i32, [i64, vp, vp, vp, vp, vp, vp, P(vp)]),
                 "vbarms_vbsr_query": (i32, [vp, P(i64), P(i64), P(i64), P(i64), P(d), P(d)]),
                 "vbarms_vbsr_export": (i32, [vp, vp, vp, vp, vp, vp, vp]),
@@ -70,6 +72,8 @@ def lib():
                 "vbarms_apply_batched": (i32, [i32, vp, vp, vp]),
                 "vbarms_dd_factor": (i32, [vp, i32, i32, i32, i32, d, i32, P(Opts), P(vp)]),
                 "vbarms_dd_layout": (i32, [vp, P(i32), P(i32), P(i32), P(i64), vp, vp, vp]),
+                "vbarms_dd_schur_factor": (i32, [vp, i32, i32, i32, d, i32, P(Opts), P(vp)]),
+                "vbarms_dd_schur_layout": (i32, [vp, P(i32), P(i32), P(i64), P(i64), vp, vp, vp, vp]),
                 "fgmres_solve": (i32, [vp, vp, vp, vp, d, i32, i32, P(i32), P(d)]),
                 "vbarms_prec_stats": (i32, [vp, P(i32), P(d), vp]),
                 "vbarms_prec_export": (i32, [vp, i32, i32, P(i64), P(i64), P(i64), P(i64), vp, vp, vp, vp, vp,
@@ -81,6 +85,7 @@ def lib():
                 "vbarms_apply_static_max_bytes": (C.c_uint64, []),
                 "vbarms_apply_static_need": (i32, [vp, P(C.c_uint64)]),
                 "vbarms_alloc_count": (C.c_uint64, []),
+                "vbarms_prec_ilut_geometry": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(d)]),
                 "vbarms_vbsr_destroy": (None, [vp]),
                 "vbarms_prec_destroy": (None, [vp]),
             }
@@ -163,6 +168,40 @@ def vbarms_compress(n, rowptr, colind, val, tau, stream=None) -> VBSR:
     return VBSR(h.value)
 
 
+def vbarms_compress_graph(n, rowptr, colind, val, mu, stream=None) -> VBSR:
+    """Graph-based compression (Section 2.2, Alg. 1) with minimum block
+    density mu.  Host numpy arrays or device torch tensors."""
+    h = C.c_void_p()
+    if isinstance(rowptr, np.ndarray):
+        rp = np.ascontiguousarray(rowptr, np.int64)
+        ci = np.ascontiguousarray(colind, np.int32)
+        vv = np.ascontiguousarray(val, np.float64)
+        st = lib().vbarms_compress_graph(int(n), _hp(rp), _hp(ci), _hp(vv), 0, float(mu), _stream(stream),
+                                         C.byref(h))
+    else:
+        st = lib().vbarms_compress_graph(int(n), _dp(rowptr), _dp(colind), _dp(val), 1, float(mu),
+                                         _stream(stream), C.byref(h))
+    _check(st)
+    return VBSR(h.value)
+
+
+def vbarms_compress_two_pass(n, rowptr, colind, val, tau, stream=None) -> VBSR:
+    """The two-pass checksum and angle variant of Section 2.1.  Host numpy
+    arrays or device torch tensors."""
+    h = C.c_void_p()
+    if isinstance(rowptr, np.ndarray):
+        rp = np.ascontiguousarray(rowptr, np.int64)
+        ci = np.ascontiguousarray(colind, np.int32)
+        vv = np.ascontiguousarray(val, np.float64)
+        st = lib().vbarms_compress_two_pass(int(n), _hp(rp), _hp(ci), _hp(vv), 0, float(tau), _stream(stream),
+                                            C.byref(h))
+    else:
+        st = lib().vbarms_compress_two_pass(int(n), _dp(rowptr), _dp(colind), _dp(val), 1, float(tau),
+                                            _stream(stream), C.byref(h))
+    _check(st)
+    return VBSR(h.value)
+
+
 def vbarms_vbsr_from_blocks(bsz, bptr, bcol, voff, val, stream=None) -> VBSR:
     bsz = np.ascontiguousarray(bsz, np.int32)
     bptr = np.ascontiguousarray(bptr, np.int64)
@@ -203,6 +242,15 @@ class Prec:
     def levels(self) -> int:
         return self.stats()["levels"]
 
+    def ilut_geometry(self) -> dict:
+        """The per-warp workspace of the last-level ILUT and how it was chosen."""
+        sl, vb_, wps, src = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        ts = C.c_double()
+        _check(lib().vbarms_prec_ilut_geometry(self.h, C.byref(sl), C.byref(vb_), C.byref(wps), C.byref(src),
+                                               C.byref(ts)))
+        return dict(slots=sl.value, value_bytes=vb_.value, warps_per_sm=wps.value,
+                    source=["default", "timed", "cached"][src.value], tune_s=ts.value)
+
     def shape(self, lev: int, which: str) -> dict:
         """Sizes of one exported factor (nbr, nbc, nnzb, nval) without its arrays."""
         nbr, nbc, nnzb, nval = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
@@ -238,7 +286,8 @@ class Prec:
         return out
 
 
-def make_opts(precision="fp64", fp64_pivot_cond=1e4, ddtol=0.0, wait_limit=0, schur_drop_all=False) -> Opts:
+def make_opts(precision="fp64", fp64_pivot_cond=1e4, ddtol=0.0, wait_limit=0, schur_drop_all=False,
+              keep_factors=True) -> Opts:
     o = Opts()
     lib().vbarms_opts_default(C.byref(o))
     o.precision = VB_FP64 if precision in ("fp64", VB_FP64) else VB_FP32_MIXED
@@ -246,6 +295,7 @@ def make_opts(precision="fp64", fp64_pivot_cond=1e4, ddtol=0.0, wait_limit=0, sc
     o.ddtol = float(ddtol)
     o.wait_limit = int(wait_limit)
     o.schur_drop_all = int(bool(schur_drop_all))
+    o.keep_factors = int(bool(keep_factors))
     return o
 
 
@@ -295,6 +345,33 @@ def dd_layout(M: Prec):
     rows = np.zeros(max(nu.value, 1), np.int32)
     _check(L.vbarms_dd_layout(M.h, None, None, None, None, _hp(part), _hp(dstart), _hp(rows)))
     return part[:M.A.query()["nblk"]], dstart, rows[:nu.value]
+
+
+def vbarms_dd_schur_factor(A: VBSR, nparts: int, msteps: int, nlev: int, droptol: float, lfil: int,
+                           precision="fp64", **kw) -> Prec:
+    """Section 5 Schur-complement global preconditioner: VBARMS local
+    factorizations with the interface rows kept to the last level, msteps of
+    GMRES on the global interface system per application."""
+    o = make_opts(precision, **kw)
+    h = C.c_void_p()
+    _check(lib().vbarms_dd_schur_factor(A.h, int(nparts), int(msteps), int(nlev), float(droptol), int(lfil),
+                                        C.byref(o), C.byref(h)))
+    return Prec(h.value, A)
+
+
+def dd_schur_layout(M: Prec) -> dict:
+    """Subdomain and interface flag per block row of A, the union's rows (each
+    subdomain's interior rows, then its interface rows), interior counts."""
+    L = lib()
+    npart, ms, ng, ngb = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+    _check(L.vbarms_dd_schur_layout(M.h, C.byref(npart), C.byref(ms), C.byref(ng), C.byref(ngb), None, None, None,
+                                    None))
+    p = M.A.query()["nblk"]
+    part, iface, rows = (np.zeros(max(p, 1), np.int32) for _ in range(3))
+    nint = np.zeros(max(npart.value, 1), np.int64)
+    _check(L.vbarms_dd_schur_layout(M.h, None, None, None, None, _hp(part), _hp(iface), _hp(rows), _hp(nint)))
+    return dict(nparts=npart.value, msteps=ms.value, ng=ng.value, ngb=ngb.value, part=part[:p], iface=iface[:p],
+                rows=rows[:p], nint=nint[:npart.value])
 
 
 def vbarms_apply_batched(Ms, xs, ys):

@@ -44,6 +44,8 @@ def test_invalid_arguments_rejected_on_host():
     assert L.vbarms_factor(None, 2, 1e-3, -1, C.byref(o), C.byref(h)) == vbarms.VB_EINVAL
     assert L.vbarms_dd_factor(None, 4, 1, 1, 2, 1e-3, -1, C.byref(o), C.byref(h)) == vbarms.VB_EINVAL
     assert L.vbarms_dd_layout(None, None, None, None, None, None, None, None) == vbarms.VB_EINVAL
+    assert L.vbarms_dd_schur_factor(None, 4, 5, 2, 1e-3, -1, C.byref(o), C.byref(h)) == vbarms.VB_EINVAL
+    assert L.vbarms_dd_schur_layout(None, None, None, None, None, None, None, None, None) == vbarms.VB_EINVAL
     assert L.vbarms_apply(None, None, None) == vbarms.VB_EINVAL
     assert L.vbarms_factor_batched(-1, None, None, None, None, C.byref(o), None) == vbarms.VB_EINVAL
     assert L.fgmres_solve(None, None, None, None, 1e-8, 50, 1000, None, None) == vbarms.VB_EINVAL

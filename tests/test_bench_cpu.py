@@ -23,7 +23,8 @@ def _run(*args):
 
 @pytest.mark.parametrize("extra,precond", [([], None), (["--dd", "4", "--overlap", "1"], "ras"),
                                            (["--dd", "4", "--overlap", "0"], "bj"),
-                                           (["--dd", "4", "--overlap", "1", "--additive"], "asm")])
+                                           (["--dd", "4", "--overlap", "1", "--additive"], "asm"),
+                                           (["--dd", "4", "--schur", "3"], "schur")])
 def test_reference_arm_line(extra, precond):
     d = _run("--workload", "geo60k_l6", "--scale", "0.007", "--steps", "3", "--warmup", "2", *extra)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
@@ -38,3 +39,5 @@ def test_reference_arm_line(extra, precond):
     assert d["config"].get("precond") == precond
     if precond:
         assert d["config"]["nparts"] == 4
+    if precond == "schur":
+        assert d["config"]["inner_steps"] == 3 and "overlap" not in d["config"]

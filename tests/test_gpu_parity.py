@@ -179,3 +179,50 @@ def test_singular_pivot_reported():
     with pytest.raises(V.VbarmsError) as e:
         V.vbarms_factor(A, 1, 0.0, -1)
     assert e.value.status == V.VB_ESINGULAR
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_lean_factorization_applies_like_the_kept_one(precision):
+    """keep_factors = 0 releases every level's scaled matrix, F, E, C and S
+    once consumed; the factors the solve reads are unchanged, so the
+    application is bit-identical, and exporting a released factor fails."""
+    V = vb()
+    m = synth.geometric(2500, 6, seed=7)
+    A = gpu_compress(m, 0.8)
+    P = V.vbarms_factor(A, 3, 1e-4, -1, precision=precision)
+    Q = V.vbarms_factor(A, 3, 1e-4, -1, precision=precision, keep_factors=False)
+    x = torch.from_numpy(np.random.default_rng(9).standard_normal(m.n)).cuda()
+    y1 = torch.zeros_like(x)
+    y2 = torch.zeros_like(x)
+    V.vbarms_apply(P, x, y1)
+    V.vbarms_apply(Q, x, y2)
+    assert torch.equal(y1, y2)
+    for lev, name in [(0, "W"), (0, "G"), (0, "D"), (Q.levels, "L"), (Q.levels, "U")]:
+        assert np.array_equal(P.export(lev, name)["val"], Q.export(lev, name)["val"]), (lev, name)
+    for name in ("A", "F", "E", "C", "S"):
+        with pytest.raises(V.VbarmsError) as e:
+            Q.export(0, name)
+        assert e.value.status == V.VB_EINVAL
+
+
+def test_ilut_geometry_is_timed_then_reused_and_results_do_not_depend_on_it():
+    """The last-level ILUT's per-warp workspace is chosen by timing the
+    candidate shapes on a prefix of the matrix's own rows (large last levels
+    only), then reused for matrices of the same class; the factors do not
+    depend on it (every element sees the oracle's operation order)."""
+    V = vb()
+    m = synth.geometric(24000, 4, seed=3)
+    A = gpu_compress(m, 0.8)
+    P1 = V.vbarms_factor(A, 1, 1e-3, 20)
+    g1 = P1.ilut_geometry()
+    P2 = V.vbarms_factor(A, 1, 1e-3, 20)
+    g2 = P2.ilut_geometry()
+    assert P1.shape(P1.levels, "A")["nbr"] >= 16384
+    assert g1["source"] in ("timed", "cached") and g2["source"] == "cached"
+    assert (g1["slots"], g1["value_bytes"]) == (g2["slots"], g2["value_bytes"]) and g2["warps_per_sm"] >= 1
+    for name in ("L", "U", "D"):
+        assert np.array_equal(P1.export(P1.levels, name)["val"], P2.export(P2.levels, name)["val"]), name
+    b = torch.from_numpy(synth.ones_rhs(m)).cuda()
+    x = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+    its, rr, st = V.fgmres_solve(A, P1, b, x, rtol=1e-8)
+    assert st == V.VB_OK
