@@ -65,6 +65,8 @@ def lib():
                 "or_dropped": (i32, [vp, i32, i32, d]),
                 "or_factor": (vp, [vp, i32, d, i32, d, i32]),
                 "or_factor_fixed": (vp, [vp, i32, d, i32, d, i32, vp]),
+                "or_factor_groups": (vp, [vp, i32, d, i32, d, i32, i32, i32]),
+                "or_prec_gptr": (i64, [vp, i32, vp]),
                 "or_prec_free": (None, [vp]),
                 "or_prec_levels": (i32, [vp]),
                 "or_prec_fill": (d, [vp]),
@@ -275,7 +277,7 @@ def spmv(m: VBMat, x: np.ndarray) -> np.ndarray:
     return y
 
 
-MAT = dict(A=0, D=1, F=2, E=3, C=4, W=5, G=6, S=7, L=8, U=9)
+MAT = dict(A=0, D=1, F=2, E=3, C=4, W=5, G=6, S=7, L=8, U=9, Lg=10, Ug=11)
 DVEC = dict(r=0, c=1, w=2)
 IVEC = dict(pI=3, piv=4)
 
@@ -284,13 +286,19 @@ class Prec:
     """Multilevel factorization (Steps 2-4 repeated, Eq. 7-8, last-level ILUT)."""
 
     def __init__(self, A: VBMat, nlev: int, droptol: float, lfil: int, ddtol: float = 0.0,
-                 schur_drop_all: bool = False, fixed=None):
+                 schur_drop_all: bool = False, fixed=None, gs: int = 1, grouped: bool = False):
         """fixed: optional flags per block row; flagged rows never enter an
-        independent set (Section 5, Schur-complement preconditioner)."""
+        independent set (Section 5, Schur-complement preconditioner).  gs:
+        supernodes per independent group (grouped: the grouped code even for
+        gs = 1)."""
         self._A = _VBHandle(A)
         self.n = int(A.rsz.sum())
         L = lib()
-        if fixed is None:
+        if gs > 1 or grouped:
+            assert fixed is None
+            self.h = L.or_factor_groups(self._A.h, int(nlev), float(droptol), int(lfil), float(ddtol),
+                                        int(bool(schur_drop_all)), int(gs), int(bool(grouped)))
+        elif fixed is None:
             self.h = L.or_factor(self._A.h, int(nlev), float(droptol), int(lfil), float(ddtol),
                                  int(bool(schur_drop_all)))
         else:
@@ -328,6 +336,13 @@ class Prec:
             L.or_prec_vec(self.h, lev, IVEC[which], None, _p(out))
         if n < 0:
             raise KeyError(which)
+        return out
+
+    def gptr(self, lev: int) -> np.ndarray:
+        """Group boundaries over the D rows of a grouped level."""
+        L = lib()
+        out = np.zeros(L.or_prec_gptr(self.h, lev, None), np.int64)
+        L.or_prec_gptr(self.h, lev, _p(out))
         return out
 
     def last_fixed(self) -> np.ndarray:

@@ -39,6 +39,27 @@
 //  D3  block Jacobi (delta = 0) and additive Schwarz add R_i^T A_i^{-1} R_i
 //      over the subdomains in order; the restricted variant keeps from
 //      subdomain i only the rows of W_i^0.
+//  A1  groups of Step 3 (gs > 1; the diagonal blocks D_i of D block sparse):
+//      supernodes visited as in R5; an unmarked eligible one seeds a group,
+//      which grows breadth first (members in the order they joined, each
+//      member's neighbours in ascending order) by unmarked eligible
+//      supernodes until it holds gs of them; then the group's members and
+//      all their neighbours are marked.  P_I lists the groups by their
+//      smallest member, members ascending, then C ascending.  gs = 1 is R5.
+//  A2  the partial factorization with groups splits each pivot the way the
+//      single-supernode levels do: sweep 1 over the rows y of [D, F] in
+//      order eliminates w_k for the group columns k < y (ascending, fill
+//      included) with m = w_k U_k^{-1} (drop test R6), w_j -= m ubar_kj for
+//      the blocks j > k of row k (group part and W part); lfil trims the
+//      multipliers after use (L); the updated diagonal block is GEPP
+//      factored (P_y^T L_y U_y), and the rest of the row becomes
+//      ubar_yj = L_y^{-1} P_y w_j (drop test; lfil separately on the group
+//      part and on W).  Sweep 2 over the rows of [E, C] eliminates the E
+//      part the same way (G candidates; fill only inside a group), keeps
+//      the lfil largest as G and forms S = C - G W as for gs = 1.
+//  A3  the level solve: u_y = L_y^{-1} P_y (f_y - sum_k m_yk u_k) in order;
+//      backward x_y = U_y^{-1} (u_y - W_y z - sum_{j>y} ubar_yj x_j) in
+//      reverse order (W terms first, then the group terms ascending).
 //  D4  Schur-complement preconditioner (Section 5, eq. paral): on the D1
 //      partition (no overlap), block row I is an interface row iff a stored
 //      block of A couples it, as row or as column, to a block row of another
@@ -649,6 +670,68 @@ void is_order(const VB& A, double ddtol, std::vector<int32_t>& pI, int64_t& nD, 
     if (!inD[Y]) pI.push_back((int32_t)Y);
 }
 
+// Step 3 with groups (A1): up to gs supernodes per independent group.  gptr
+// returns the group boundaries over the D positions of pI.
+void is_order_groups(const VB& A, double ddtol, int gs, std::vector<int32_t>& pI, int64_t& nD,
+                     std::vector<double>& w, std::vector<int64_t>& gptr, const std::vector<char>* fixed) {
+  const int64_t p = A.nbr;
+  std::vector<int32_t> pI1;
+  int64_t nD1 = 0;
+  is_order(A, ddtol, pI1, nD1, w, fixed);  // the weights (R5)
+  std::vector<std::vector<int32_t>> adj(p);
+  for (int64_t Y = 0; Y < p; ++Y)
+    for (int64_t b = A.bptr[Y]; b < A.bptr[Y + 1]; ++b) {
+      const int32_t Z = A.bcol[b];
+      if (Z == Y) continue;
+      adj[Y].push_back(Z);
+      adj[Z].push_back((int32_t)Y);
+    }
+  for (auto& a : adj) {
+    std::sort(a.begin(), a.end());
+    a.erase(std::unique(a.begin(), a.end()), a.end());
+  }
+  std::vector<int32_t> order(p);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    if (w[a] != w[b]) return w[a] > w[b];
+    return a < b;
+  });
+  auto eligible = [&](int32_t v) { return !(w[v] < ddtol) && !(fixed && (*fixed)[v]); };
+  std::vector<char> marked(p, 0);
+  std::vector<std::vector<int32_t>> groups;
+  for (int32_t v : order) {
+    if (marked[v] || !eligible(v)) continue;
+    std::vector<int32_t> grp{v};
+    marked[v] = 1;
+    for (size_t head = 0; head < grp.size() && (int)grp.size() < gs; ++head)
+      for (int32_t z : adj[grp[head]]) {
+        if ((int)grp.size() >= gs) break;
+        if (marked[z] || !eligible(z)) continue;
+        grp.push_back(z);
+        marked[z] = 1;
+      }
+    for (int32_t u : grp)
+      for (int32_t z : adj[u]) marked[z] = 1;
+    std::sort(grp.begin(), grp.end());
+    groups.push_back(std::move(grp));
+  }
+  std::sort(groups.begin(), groups.end(),
+            [](const std::vector<int32_t>& a, const std::vector<int32_t>& b) { return a[0] < b[0]; });
+  std::vector<char> inD(p, 0);
+  pI.clear();
+  gptr.assign(1, 0);
+  for (auto& g : groups) {
+    for (int32_t v : g) {
+      pI.push_back(v);
+      inD[v] = 1;
+    }
+    gptr.push_back((int64_t)pI.size());
+  }
+  nD = (int64_t)pI.size();
+  for (int64_t Y = 0; Y < p; ++Y)
+    if (!inD[Y]) pI.push_back((int32_t)Y);
+}
+
 // ---------------------------------------------------------------------------
 struct Level {
   VB A;  // input of the level after Step 2 scaling
@@ -658,6 +741,9 @@ struct Level {
   VB D;  // pivot blocks (block diagonal), LU in place
   std::vector<int32_t> piv;
   VB F, E, C, W, G, S;
+  bool grouped = false;       // A2: D block sparse within groups
+  std::vector<int64_t> gptr;  // group boundaries over the D rows
+  VB Lg, Ug;                  // group multipliers (below) and group part of Ubar (above the diagonal)
 };
 
 struct Last {
@@ -790,6 +876,178 @@ int factor_level(Level& L, bool last_reduction, double t, int lfil) {
   return OK;
 }
 
+// Steps 3-4 with groups (A2): D block sparse inside groups, the two sweeps
+// of Section 3.1 with block IKJ elimination inside each group.
+int factor_level_groups(Level& L, bool last_reduction, double t, int lfil) {
+  const VB& A = L.A;
+  const int64_t p = A.nbr;
+  L.grouped = true;
+  std::vector<int32_t> newpos(p);
+  for (int64_t k = 0; k < p; ++k) newpos[L.pI[k]] = (int32_t)k;
+  L.nC = p - L.nD;
+  std::vector<int32_t> szD(L.nD), szC(L.nC);
+  for (int64_t k = 0; k < p; ++k) (k < L.nD ? szD[k] : szC[k - L.nD]) = A.rsz[L.pI[k]];
+  L.D.init(szD, szD);
+  L.F.init(szD, szC);
+  L.E.init(szC, szD);
+  L.C.init(szC, szC);
+  for (int64_t k = 0; k < p; ++k) {
+    const int32_t Y = L.pI[k];
+    const bool rowD = k < L.nD;
+    // columns in the new order (a group's members are ascending and
+    // contiguous, so D columns stay sorted; C columns are ascending)
+    std::vector<std::pair<int32_t, int64_t>> cols;
+    for (int64_t b = A.bptr[Y]; b < A.bptr[Y + 1]; ++b) cols.push_back({newpos[A.bcol[b]], b});
+    std::sort(cols.begin(), cols.end());
+    for (auto& cb : cols) {
+      const int32_t nz = cb.first;
+      const bool colD = nz < L.nD;
+      if (rowD)
+        (colD ? L.D : L.F).push(colD ? nz : (int32_t)(nz - L.nD), A.blk(cb.second));
+      else
+        (colD ? L.E : L.C).push(colD ? nz : (int32_t)(nz - L.nD), A.blk(cb.second));
+    }
+    if (rowD) {
+      L.D.end_row();
+      L.F.end_row();
+    } else {
+      L.E.end_row();
+      L.C.end_row();
+    }
+  }
+  // pivot block of each D row after its elimination, GEPP LU in place
+  VB Dp;
+  Dp.init(szD, szD);
+  L.piv.assign(L.D.roff[L.nD], 0);
+  L.Lg.init(szD, szD);
+  L.Ug.init(szD, szD);
+  L.W.init(szD, szC);
+  // sweep 1 over the rows of [D, F]; keys: D columns, then nD + F column
+  for (int64_t y = 0; y < L.nD; ++y) {
+    const int ny = szD[y];
+    auto csize = [&](int64_t key) { return key < L.nD ? szD[key] : szC[key - L.nD]; };
+    std::map<int64_t, std::vector<double>> w;
+    for (int64_t b = L.D.bptr[y]; b < L.D.bptr[y + 1]; ++b)
+      w[L.D.bcol[b]].assign(L.D.blk(b), L.D.blk(b) + (int64_t)ny * szD[L.D.bcol[b]]);
+    for (int64_t b = L.F.bptr[y]; b < L.F.bptr[y + 1]; ++b)
+      w[L.nD + L.F.bcol[b]].assign(L.F.blk(b), L.F.blk(b) + (int64_t)ny * szC[L.F.bcol[b]]);
+    std::vector<int32_t> lcols;
+    std::vector<double> lf2;
+    std::vector<std::vector<double>> lblocks;
+    auto it = w.begin();
+    while (it != w.end() && it->first < y) {
+      const int32_t k = (int32_t)it->first;
+      const int nk = szD[k];
+      std::vector<double> m = std::move(it->second);
+      w.erase(it);
+      apply_Uinv_right(Dp.blk(Dp.bptr[k]), nk, m.data(), ny);
+      if (!dropped(m.data(), ny, nk, t)) {
+        for (int64_t b = L.Ug.bptr[k]; b < L.Ug.bptr[k + 1]; ++b) {
+          const int32_t j = L.Ug.bcol[b];
+          std::vector<double>& blk = w[j];
+          if (blk.empty()) blk.assign((size_t)ny * szD[j], 0.0);
+          sub_prod(blk.data(), m.data(), L.Ug.blk(b), ny, nk, szD[j]);
+        }
+        for (int64_t b = L.W.bptr[k]; b < L.W.bptr[k + 1]; ++b) {
+          const int32_t c = L.W.bcol[b];
+          std::vector<double>& blk = w[L.nD + c];
+          if (blk.empty()) blk.assign((size_t)ny * szC[c], 0.0);
+          sub_prod(blk.data(), m.data(), L.W.blk(b), ny, nk, szC[c]);
+        }
+        lcols.push_back(k);
+        lf2.push_back(fro2(m.data(), (int64_t)ny * nk));
+        lblocks.push_back(std::move(m));
+      }
+      it = w.upper_bound(k);
+    }
+    for (int k : select_lfil(lcols, lf2, lfil)) L.Lg.push(lcols[k], lblocks[k].data());
+    L.Lg.end_row();
+    auto d = w.find(y);
+    if (d == w.end()) return ESINGULAR;  // zero pivot block
+    std::vector<double> dg = d->second;
+    int32_t* pv = L.piv.data() + L.D.roff[y];
+    if (gepp(dg.data(), ny, pv) != OK) return ESINGULAR;
+    Dp.push((int32_t)y, dg.data());
+    Dp.end_row();
+    std::vector<int32_t> ucols, fcols;
+    std::vector<double> uf2, ff2;
+    std::vector<std::vector<double>> ublocks, fblocks;
+    for (auto& kv : w) {
+      if (kv.first <= y) continue;
+      const int ns = csize(kv.first);
+      std::vector<double> x = kv.second;
+      apply_LinvP(dg.data(), pv, ny, x.data(), ns);
+      if (dropped(x.data(), ny, ns, t)) continue;
+      if (kv.first < L.nD) {
+        ucols.push_back((int32_t)kv.first);
+        uf2.push_back(fro2(x.data(), (int64_t)ny * ns));
+        ublocks.push_back(std::move(x));
+      } else {
+        fcols.push_back((int32_t)(kv.first - L.nD));
+        ff2.push_back(fro2(x.data(), (int64_t)ny * ns));
+        fblocks.push_back(std::move(x));
+      }
+    }
+    for (int k : select_lfil(ucols, uf2, lfil)) L.Ug.push(ucols[k], ublocks[k].data());
+    L.Ug.end_row();
+    for (int k : select_lfil(fcols, ff2, lfil)) L.W.push(fcols[k], fblocks[k].data());
+    L.W.end_row();
+  }
+  L.D = std::move(Dp);
+  // sweep 2 over the rows of [E, C]: G = E Ubar^{-1} and S = C - G W
+  L.G.init(szC, szD);
+  L.S.init(szC, szC);
+  for (int64_t r = 0; r < L.nC; ++r) {
+    const int nr = szC[r];
+    std::map<int32_t, std::vector<double>> e;
+    for (int64_t b = L.E.bptr[r]; b < L.E.bptr[r + 1]; ++b)
+      e[L.E.bcol[b]].assign(L.E.blk(b), L.E.blk(b) + (int64_t)nr * szD[L.E.bcol[b]]);
+    std::vector<int32_t> cols;
+    std::vector<double> f2;
+    std::vector<std::vector<double>> blocks;
+    while (!e.empty()) {
+      auto it = e.begin();
+      const int32_t k = it->first;
+      const int nk = szD[k];
+      std::vector<double> m = std::move(it->second);
+      e.erase(it);
+      apply_Uinv_right(L.D.blk(L.D.bptr[k]), nk, m.data(), nr);
+      if (dropped(m.data(), nr, nk, t)) continue;
+      for (int64_t b = L.Ug.bptr[k]; b < L.Ug.bptr[k + 1]; ++b) {
+        const int32_t j = L.Ug.bcol[b];
+        std::vector<double>& blk = e[j];
+        if (blk.empty()) blk.assign((size_t)nr * szD[j], 0.0);
+        sub_prod(blk.data(), m.data(), L.Ug.blk(b), nr, nk, szD[j]);
+      }
+      cols.push_back(k);
+      f2.push_back(fro2(m.data(), (int64_t)nr * nk));
+      blocks.push_back(std::move(m));
+    }
+    std::vector<int> keep = select_lfil(cols, f2, lfil);
+    for (int k : keep) L.G.push(cols[k], blocks[k].data());
+    L.G.end_row();
+    std::map<int32_t, std::vector<double>> acc;
+    for (int64_t b = L.C.bptr[r]; b < L.C.bptr[r + 1]; ++b)
+      acc[L.C.bcol[b]].assign(L.C.blk(b), L.C.blk(b) + (int64_t)nr * szC[L.C.bcol[b]]);
+    for (int k : keep) {
+      const int32_t y = cols[k];
+      const int m = szD[y];
+      for (int64_t b = L.W.bptr[y]; b < L.W.bptr[y + 1]; ++b) {
+        const int32_t sc = L.W.bcol[b];
+        std::vector<double>& blk = acc[sc];
+        if (blk.empty()) blk.assign((size_t)nr * szC[sc], 0.0);
+        sub_prod(blk.data(), blocks[k].data(), L.W.blk(b), nr, m, szC[sc]);
+      }
+    }
+    for (auto& kv : acc) {
+      if (last_reduction && kv.first != r && dropped(kv.second.data(), nr, szC[kv.first], t)) continue;
+      L.S.push(kv.first, kv.second.data());
+    }
+    L.S.end_row();
+  }
+  return OK;
+}
+
 // Last level (R8): block ILUT in natural order, the block IKJ form of Alg. 3
 // with the dropping of Section 3.
 int ilut_last(Last& X, double t, int lfil) {
@@ -855,8 +1113,12 @@ int ilut_last(Last& X, double t, int lfil) {
 // reduction (the ARMS habit) instead of only at the last one (Section 3).
 // fixed (optional, one flag per block row of A0): rows kept out of every
 // independent set (D5); they follow the C rows from level to level.
+// gs: supernodes per independent group (A1; 1 = one supernode per group);
+// grouped selects the grouped factorization (A2) even for gs = 1.
 int factor(const VB& A0, int nlev, double t, int lfil, double ddtol, bool drop_all, Prec& P,
-           const std::vector<char>* fixed = nullptr) {
+           const std::vector<char>* fixed = nullptr, int gs = 1, bool grouped = false) {
+  if (gs < 1) return EINVAL;
+  grouped = grouped || gs > 1;
   if (A0.nbr != A0.nbc || nlev < 0 || !(t >= 0.0)) return EINVAL;
   P.n = A0.roff[A0.nbr];
   VB cur = A0;
@@ -866,10 +1128,13 @@ int factor(const VB& A0, int nlev, double t, int lfil, double ddtol, bool drop_a
     Level L;
     L.A = cur;
     scale(L.A, L.r, L.c);
-    is_order(L.A, ddtol, L.pI, L.nD, L.w, fixed ? &fx : nullptr);
+    if (grouped)
+      is_order_groups(L.A, ddtol, gs, L.pI, L.nD, L.w, L.gptr, fixed ? &fx : nullptr);
+    else
+      is_order(L.A, ddtol, L.pI, L.nD, L.w, fixed ? &fx : nullptr);
     if (L.nD == 0) break;  // nothing to eliminate: cur becomes the last level
     const bool last_red = (l == nlev - 1) || drop_all;
-    int st = factor_level(L, last_red, t, lfil);
+    int st = grouped ? factor_level_groups(L, last_red, t, lfil) : factor_level(L, last_red, t, lfil);
     if (st != OK) return st;
     if (fixed) {
       std::vector<char> nx(L.nC);
@@ -963,10 +1228,24 @@ void solve_level(const Prec& P, size_t l, const double* b, double* x, const doub
   }
   newoff[p] = o;
   const int64_t nf = newoff[L.nD];
-  // u = L^{-1} P f (Alg. 2: solve L y = f)
+  // u = L^{-1} P f (Alg. 2: solve L y = f; with groups, A3)
   std::vector<double> u(bh.begin(), bh.begin() + nf);
-  for (int64_t y = 0; y < L.nD; ++y)
+  for (int64_t y = 0; y < L.nD; ++y) {
+    if (L.grouped) {
+      const int ny = L.D.rsz[y];
+      for (int64_t bb = L.Lg.bptr[y]; bb < L.Lg.bptr[y + 1]; ++bb) {
+        const int32_t k = L.Lg.bcol[bb];
+        const int nk = L.Lg.csz[k];
+        const double* mm = L.Lg.blk(bb);
+        for (int a = 0; a < ny; ++a) {
+          double v = u[L.D.roff[y] + a];
+          for (int q = 0; q < nk; ++q) v = v - mm[a * nk + q] * u[L.D.roff[k] + q];
+          u[L.D.roff[y] + a] = v;
+        }
+      }
+    }
     apply_LinvP(L.D.blk(L.D.bptr[y]), L.piv.data() + L.D.roff[y], L.D.rsz[y], u.data() + L.D.roff[y], 1);
+  }
   // g' = g - E U^{-1} u = g - G u
   std::vector<double> g(bh.begin() + nf, bh.end());
   for (int64_t r = 0; r < L.nC; ++r) {
@@ -994,8 +1273,10 @@ void solve_level(const Prec& P, size_t l, const double* b, double* x, const doub
   }
   std::vector<double> z(n - nf);
   solve_level(P, l + 1, g.data(), z.data(), fixv ? fnext.data() : nullptr);
-  // y = U^{-1} (u - W z)
-  for (int64_t y = 0; y < L.nD; ++y) {
+  // y = U^{-1} (u - W z); with groups in reverse order, the group part of
+  // Ubar after W (A3)
+  for (int64_t yy = 0; yy < L.nD; ++yy) {
+    const int64_t y = L.grouped ? L.nD - 1 - yy : yy;
     const int m = L.W.rsz[y];
     for (int64_t bb = L.W.bptr[y]; bb < L.W.bptr[y + 1]; ++bb) {
       const int32_t s = L.W.bcol[bb];
@@ -1007,6 +1288,17 @@ void solve_level(const Prec& P, size_t l, const double* b, double* x, const doub
         u[L.W.roff[y] + a] = v;
       }
     }
+    if (L.grouped)
+      for (int64_t bb = L.Ug.bptr[y]; bb < L.Ug.bptr[y + 1]; ++bb) {
+        const int32_t j = L.Ug.bcol[bb];
+        const int nj = L.Ug.csz[j];
+        const double* um = L.Ug.blk(bb);
+        for (int a = 0; a < m; ++a) {
+          double v = u[L.D.roff[y] + a];
+          for (int q = 0; q < nj; ++q) v = v - um[a * nj + q] * u[L.D.roff[j] + q];
+          u[L.D.roff[y] + a] = v;
+        }
+      }
     apply_Uinv_left(L.D.blk(L.D.bptr[y]), m, u.data() + L.D.roff[y], 1);
   }
   // x = S_2 P_I^T [y; z]
@@ -1526,6 +1818,23 @@ void* or_factor(const void* A, int nlev, double droptol, int lfil, double ddtol,
   }
   return P;
 }
+// With groups of up to gs supernodes (A1, A2); grouped != 0 takes the grouped
+// code even for gs = 1.
+void* or_factor_groups(const void* A, int nlev, double droptol, int lfil, double ddtol, int drop_all, int gs,
+                       int grouped) {
+  auto* P = new Prec();
+  g_last_status = factor(*(const VB*)A, nlev, droptol, lfil, ddtol, drop_all != 0, *P, nullptr, gs, grouped != 0);
+  if (g_last_status != OK) {
+    delete P;
+    return nullptr;
+  }
+  return P;
+}
+int64_t or_prec_gptr(void* h, int l, int64_t* out) {
+  const Level& L = ((Prec*)h)->lev[l];
+  if (out) std::copy(L.gptr.begin(), L.gptr.end(), out);
+  return (int64_t)L.gptr.size();
+}
 // The same with fixed rows (D5): fixed[nbr] flags, or NULL.
 void* or_factor_fixed(const void* A, int nlev, double droptol, int lfil, double ddtol, int drop_all,
                       const int32_t* fixed) {
@@ -1545,7 +1854,8 @@ void or_prec_free(void* h) { delete (Prec*)h; }
 int or_prec_levels(void* h) { return (int)((Prec*)h)->lev.size(); }
 double or_prec_fill(void* h) { return ((Prec*)h)->fill; }
 int64_t or_prec_nd(void* h, int l) { return ((Prec*)h)->lev[l].nD; }
-// which: 0 scaled A, 1 D (pivot LU), 2 F, 3 E, 4 C, 5 W, 6 G, 7 S;
+// which: 0 scaled A, 1 D (pivot LU), 2 F, 3 E, 4 C, 5 W, 6 G, 7 S, 10 group
+// multipliers, 11 group part of Ubar (grouped levels);
 // for l == levels (last level): 0 scaled A, 1 pivot LU, 8 L, 9 U.
 const void* or_prec_mat(void* h, int l, int which) {
   Prec* P = (Prec*)h;
@@ -1568,6 +1878,8 @@ const void* or_prec_mat(void* h, int l, int which) {
     case 5: return &L.W;
     case 6: return &L.G;
     case 7: return &L.S;
+    case 10: return L.grouped ? &L.Lg : nullptr;
+    case 11: return L.grouped ? &L.Ug : nullptr;
   }
   return nullptr;
 }
