@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator factor")
+    p.add_argument("--group-size", type=int, default=1,
+                   help="Step 3 groups of up to this many supernodes (block-sparse D_i); 1 = one per group")
     p.add_argument("--lean", action="store_true",
                    help="release each level's intermediate factors once consumed (vbarms_opts.keep_factors = 0)")
     p.add_argument("--dd", type=int, default=0,
@@ -236,14 +238,14 @@ class OneCore:
             os.sched_setaffinity(0, self.prev)
 
 
-def oracle_setup_seconds(m, w, restart=50, dd=None, keep=False):
+def oracle_setup_seconds(m, w, restart=50, dd=None, keep=False, gs=1):
     """The CPU oracle (single-threaded) on matrix m: setup seconds and FGMRES."""
     import oracle
     t0 = time.perf_counter()
     c = oracle.compress(m.n, m.rowptr, m.colind, m.val, w["tau"])
     t1 = time.perf_counter()
     if dd is None:
-        P = oracle.Prec(c.A, w["nlev"], w["droptol"], w["lfil"])
+        P = oracle.Prec(c.A, w["nlev"], w["droptol"], w["lfil"], gs=gs)
     elif dd[3]:
         P = oracle.DDSchur(c.A, dd[0], dd[3], w["nlev"], w["droptol"], w["lfil"])
     else:
@@ -293,7 +295,7 @@ def run_reference(args):
     m = synth.make_workload(args.workload, seed=args.seed, scale=args.scale)
     dd = dd_config(args)
     with OneCore() as oc:
-        r = oracle_setup_seconds(m, full, dd=dd)
+        r = oracle_setup_seconds(m, full, dd=dd, gs=getattr(args, "group_size", 1))
     v = r["compress_s"] + r["factor_s"]
     out = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": 1,
@@ -302,7 +304,7 @@ def run_reference(args):
         "config": {"workload": args.workload, "nodes": m.meta.get("nodes"), "n": m.n, "nnz": m.nnz,
                    "ell": full["ell"], "tau": full["tau"], "nlev": full["nlev"], "droptol": full["droptol"],
                    "lfil": full["lfil"], "scale": args.scale,
-                   **dd_keys(dd)},
+                   **dd_keys(dd), **({"group_size": args.group_size} if getattr(args, "group_size", 1) > 1 else {})},
         "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": f"the whole {args.workload} matrix (n = {m.n}), one run of the oracle's "
                                    f"compress + factor, pinned to one core",
@@ -478,12 +480,13 @@ def main():
 
     def factor(A, precision):
         if dd is None:
-            return V.vbarms_factor(A, w["nlev"], w["droptol"], w["lfil"], precision=precision, keep_factors=kf)
+            return V.vbarms_factor(A, w["nlev"], w["droptol"], w["lfil"], precision=precision, keep_factors=kf,
+                                   group_size=args.group_size)
         if dd[3]:
             return V.vbarms_dd_schur_factor(A, dd[0], dd[3], w["nlev"], w["droptol"], w["lfil"], precision=precision,
-                                            keep_factors=kf)
+                                            keep_factors=kf, group_size=args.group_size)
         return V.vbarms_dd_factor(A, dd[0], dd[1], dd[2], w["nlev"], w["droptol"], w["lfil"], precision=precision,
-                                  keep_factors=kf)
+                                  keep_factors=kf, group_size=args.group_size)
 
     def step(precision, solve=True, keep=False):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -600,7 +603,7 @@ def main():
     errors = None
     if rank == 0 and not args.no_cpu_baseline:
         with OneCore():
-            r = oracle_setup_seconds(m, w, dd=dd, keep=True)
+            r = oracle_setup_seconds(m, w, dd=dd, keep=True, gs=args.group_size)
         cpu = {"value": r["compress_s"] + r["factor_s"], "unit": "s", "cores": 1, "kind": "oracle",
                "sample": f"the whole {args.workload} matrix (n = {m.n}), one run of the oracle's compress + factor "
                          f"(FP64, single thread, pinned to one core); its FGMRES took {r['solve_s']:.1f} s and "
@@ -619,7 +622,7 @@ def main():
                        "nnz": m.nnz, "tau": w["tau"], "nlev": w["nlev"], "droptol": w["droptol"],
                        "lfil": w["lfil"], "factor_precision": prec, "fgmres": "FGMRES(50) rtol 1e-8",
                        "parallelism": "replicas" if ws > 1 else "single",
-                       **dd_keys(dd),
+                       **dd_keys(dd), **({"group_size": args.group_size} if getattr(args, "group_size", 1) > 1 else {}),
                        "l2": "inputs larger than L2 (CSR %.2f GB)" % ((m.nnz * 12 + m.n * 8) / 1e9)},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,

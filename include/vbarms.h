@@ -85,6 +85,14 @@ typedef struct {
                              them (the solve never reads them), which lowers
                              the factorization's device memory by about half;
                              exporting a released factor is then VB_EINVAL  */
+  int group_size;         /* Step 3: supernodes per independent group, 1 to
+                             64 (default 1: one supernode per group).  With
+                             more, each group grows breadth first from its
+                             seed (visited by weight) up to group_size
+                             supernodes, its neighbours going to C, so the
+                             diagonal blocks D_i of D are block sparse; each
+                             group is eliminated inside (Section 3.1's two
+                             sweeps).  The greedy is sequential (one warp)  */
 } vbarms_opts;
 
 /* Fill *opt with the defaults above. */
@@ -322,7 +330,9 @@ vb_status fgmres_solve(vbarms_vbsr A, vbarms_prec M, const double* b, double* x,
 vb_status vbarms_prec_stats(vbarms_prec M, int* levels_used, double* mem_ratio, double* phase_s);
 
 /* Export one factor of level lev (0 <= lev < levels: which = 0 scaled level
- * matrix, 1 pivot LU blocks, 2 F, 3 E, 4 C, 5 W, 6 G, 7 S; lev == levels:
+ * matrix, 1 pivot LU blocks, 2 F, 3 E, 4 C, 5 W, 6 G, 7 S, and on a level
+ * factored with group_size > 1: 10 the group multipliers (below the
+ * diagonal of Ltilde), 11 the group part of Ubar; lev == levels:
  * which = 0 scaled last-level matrix, 1 pivot LU blocks, 8 L_S, 9 U_S) as
  * host VBCSR arrays with values converted to double.  Call once with the
  * array pointers NULL to get the sizes.                                     */
@@ -332,9 +342,11 @@ vb_status vbarms_prec_export(vbarms_prec M, int lev, int which, int64_t* nbr, in
 
 /* Export a per-level vector: which = 0 row scaling r, 1 column scaling c,
  * 2 Step 3 weights w (doubles, into d); 3 the ordering P_I (D supernodes
- * ascending then C supernodes ascending), 4 GEPP pivots, 5 pivot precision
- * tags (1 = FP64 kept) (int32, into iv).  *len receives the length; pass
- * NULL arrays to query it.                                                  */
+ * ascending then C supernodes ascending; with groups, the groups by their
+ * smallest member, members ascending), 4 GEPP pivots, 5 pivot precision
+ * tags (1 = FP64 kept), 6 the group boundaries over the D rows of a level
+ * factored with group_size > 1 (int32, into iv).  *len receives the length;
+ * pass NULL arrays to query it.                                             */
 vb_status vbarms_prec_vector(vbarms_prec M, int lev, int which, double* d, int32_t* iv, int64_t* len);
 
 /* Measured launches of one kernel of a factorization, timed with CUDA events

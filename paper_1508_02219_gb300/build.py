@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libvbarms.so")
 SOURCES = ["util.cu", "vbsr_ops.cu", "compress.cu", "level.cu", "ilut.cu", "solve.cu", "capi.cu",
-           "apply_static.cu", "batch.cu", "dd.cu", "ddschur.cu", "graph.cu", "twopass.cu"]
+           "apply_static.cu", "batch.cu", "dd.cu", "ddschur.cu", "graph.cu", "groups.cu", "twopass.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",

@@ -112,23 +112,38 @@ std::unique_ptr<PrecDev<T>> factor_impl(const vbarms_vbsr_st& Ah, const FactorOp
     if (p == 0) break;
     LevelDev<T> L;
     DBuf<int32_t> newpos;
-    int64_t nD = 0;
+    DBuf<int64_t> gptr;
+    int64_t nD = 0, ngroups = 0;
     if (cur_is64) {
       copy_vb<double, double>(*cur64, L.A64, s);
       scale_level_t<double>(L.A64, L.r, L.c, s);
       tm.mark(PH_SCALE);
-      nD = is_order<double>(L.A64, o.ddtol, L.w, L.pI, newpos, s, fixed ? fcur.p : nullptr);
+      if (o.group_size > 1)
+        nD = group_order<double>(L.A64, o.ddtol, o.group_size, fixed ? fcur.p : nullptr, L.w, L.pI, newpos, gptr,
+                                 ngroups, s);
+      else
+        nD = is_order<double>(L.A64, o.ddtol, L.w, L.pI, newpos, s, fixed ? fcur.p : nullptr);
       tm.mark(PH_ORDER);
       if (nD == 0) break;
-      gather_parts<double, T>(L.A64, L.pI, newpos, nD, L, s, dst);
+      if (o.group_size > 1)
+        grouped_level<double, T>(L.A64, L.pI, newpos, nD, gptr, ngroups, o.droptol, o.lfil, L, s, dst);
+      else
+        gather_parts<double, T>(L.A64, L.pI, newpos, nD, L, s, dst);
     } else {
       copy_vb<T, T>(curT, L.AT, s);
       scale_level_t<T>(L.AT, L.r, L.c, s);
       tm.mark(PH_SCALE);
-      nD = is_order<T>(L.AT, o.ddtol, L.w, L.pI, newpos, s, fixed ? fcur.p : nullptr);
+      if (o.group_size > 1)
+        nD = group_order<T>(L.AT, o.ddtol, o.group_size, fixed ? fcur.p : nullptr, L.w, L.pI, newpos, gptr, ngroups,
+                            s);
+      else
+        nD = is_order<T>(L.AT, o.ddtol, L.w, L.pI, newpos, s, fixed ? fcur.p : nullptr);
       tm.mark(PH_ORDER);
       if (nD == 0) break;
-      gather_parts<T, T>(L.AT, L.pI, newpos, nD, L, s, dst);
+      if (o.group_size > 1)
+        grouped_level<T, T>(L.AT, L.pI, newpos, nD, gptr, ngroups, o.droptol, o.lfil, L, s, dst);
+      else
+        gather_parts<T, T>(L.AT, L.pI, newpos, nD, L, s, dst);
     }
     tm.mark(PH_GATHER);
     if (track) {  // the next level's rows are the C rows, in P_I order
@@ -141,19 +156,21 @@ std::unique_ptr<PrecDev<T>> factor_impl(const vbarms_vbsr_st& Ah, const FactorOp
       take_i32(fcur.p, L.pI.p + nD, p - nD, fn.p, s);
       fcur = std::move(fn);
     }
-    pivot_lu(L.D, L.piv, L.ptag, L.D32, mixed, o.fp64_pivot_cond, s, dst);
-    tm.mark(PH_PIVOT);
-    w_or_g<T>(L.F, 0, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.W, s);
-    tm.mark(PH_W);
-    w_or_g<T>(L.E, 1, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.G, s);
-    tm.mark(PH_G);
+    if (!L.grouped) {  // grouped levels made D, W and G in their two sweeps
+      pivot_lu(L.D, L.piv, L.ptag, L.D32, mixed, o.fp64_pivot_cond, s, dst);
+      tm.mark(PH_PIVOT);
+      w_or_g<T>(L.F, 0, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.W, s);
+      tm.mark(PH_W);
+      w_or_g<T>(L.E, 1, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.G, s);
+      tm.mark(PH_G);
+    }
     KernelRec rec;
     rec.kernel = 0;
     rec.level = l;
     schur<T>(L.C, L.G, L.W, l == o.nlev - 1 || o.schur_drop_all, o.droptol, L.S, s, dst, &rec);
     P->krec.push_back(rec);
     tm.mark(PH_SCHUR);
-    fill += (double)(L.D.nval + L.W.nval + L.G.nval);
+    fill += (double)(L.D.nval + L.W.nval + L.G.nval + L.Lg.nval + L.Ug.nval);
     LevelMaps M;
     if (cur_is64)
       build_level_maps<T>(L, L.A64.rsz.p, L.A64.roff.p, L.A64.nbr, M, s);
@@ -267,6 +284,7 @@ void vbarms_opts_default(vbarms_opts* opt) {
   opt->wait_limit = 0;
   opt->schur_drop_all = 0;
   opt->keep_factors = 1;
+  opt->group_size = 1;
 }
 
 const char* vbarms_last_error(void) { return g_err.c_str(); }
@@ -381,9 +399,10 @@ vb_status vbarms_factor(vbarms_vbsr A, int nlev, double droptol, int lfil, const
   vbarms_opts_default(&d);
   if (!opt) opt = &d;
   if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
+  if (opt->group_size < 1 || opt->group_size > 64) return set_err(VB_EINVAL, "group_size must lie in [1, 64]");
   FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
                opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0,
-               opt->keep_factors != 0};
+               opt->keep_factors != 0, opt->group_size};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
     DeviceScope ds(A->dev);
@@ -413,6 +432,7 @@ vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev,
   vbarms_opts_default(&d);
   if (!opt) opt = &d;
   if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
+  if (opt->group_size < 1 || opt->group_size > 64) return set_err(VB_EINVAL, "group_size must lie in [1, 64]");
   std::vector<std::unique_ptr<vbarms_prec_st>> res(nmat);
   vb_status st = guarded([&] {
     // matrices with the same (nlev, droptol, lfil) form one batch: one
@@ -440,7 +460,7 @@ vb_status vbarms_factor_batched(int nmat, const vbarms_vbsr* A, const int* nlev,
       union_part_ids(parts, s, dom);
       FactorOpts o{nlev[m0], droptol[m0], lfil[m0], opt->precision, opt->fp64_pivot_cond, opt->ddtol,
                    opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0,
-               opt->keep_factors != 0};
+               opt->keep_factors != 0, opt->group_size};
       std::shared_ptr<PrecBase> P;
       if (o.precision == VB_FP64)
         P = factor_impl<double>(U, o, dom.p, (int)parts.size());
@@ -472,9 +492,10 @@ vb_status vbarms_dd_factor(vbarms_vbsr A, int nparts, int overlap, int restricte
   vbarms_opts_default(&d);
   if (!opt) opt = &d;
   if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
+  if (opt->group_size < 1 || opt->group_size > 64) return set_err(VB_EINVAL, "group_size must lie in [1, 64]");
   FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
                opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0,
-               opt->keep_factors != 0};
+               opt->keep_factors != 0, opt->group_size};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
     DeviceScope ds(A->dev);
@@ -524,9 +545,10 @@ vb_status vbarms_dd_schur_factor(vbarms_vbsr A, int nparts, int msteps, int nlev
   vbarms_opts_default(&d);
   if (!opt) opt = &d;
   if (opt->precision != VB_FP64 && opt->precision != VB_FP32_MIXED) return set_err(VB_EINVAL, "precision");
+  if (opt->group_size < 1 || opt->group_size > 64) return set_err(VB_EINVAL, "group_size must lie in [1, 64]");
   FactorOpts o{nlev, droptol, lfil, opt->precision, opt->fp64_pivot_cond, opt->ddtol,
                opt->wait_limit ? opt->wait_limit : (uint64_t)kDefaultWaitNs, opt->schur_drop_all != 0,
-               opt->keep_factors != 0};
+               opt->keep_factors != 0, opt->group_size};
   auto h = std::make_unique<vbarms_prec_st>();
   vb_status st = guarded([&] {
     DeviceScope ds(A->dev);

@@ -129,7 +129,7 @@ struct IlutGeom {
 // (the process keeps them), and the smallest matrix that is timed.
 std::mutex g_geom_mu;
 std::map<long long, struct IlutGeom> g_geom;
-constexpr int64_t kTuneMinRows = 16384;
+constexpr int64_t kTuneMinRows = 65536;
 
 constexpr int PVMAX = 64;
 struct IlutMisc {
@@ -1644,8 +1644,10 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   // prefix of the ticket order is factored exactly on its own), the fastest
   // kept per device, precision and class of row sizes for the rest of the
   // process; small matrices take the measured default.  The candidates span
-  // what the configured workloads were measured to prefer: 64 to 256 slots,
-  // 2 to 8 KB of values, 16 down to 5 warps per SM.
+  // what the configured workloads were measured to prefer: 64 or 128 slots,
+  // 2 to 8 KB of values, 16 down to 6 warps per SM.  The prefix is 1/64 of
+  // the tickets (2 048 to 16 384), so the three timings add at most about
+  // 5 % to the first factorization of a class.
   DBuf<unsigned long long> rstat(2, s);
   rstat.zero();
   launch(k_row_stats, grid_for(p, 256), 256, 0, s, p, A.bptr.p, rstat.p);
@@ -1657,7 +1659,6 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   cands.push_back((wide && f64) ? make_geom(128, 8192, 2048, 256) : make_geom(64, 2048, 2048, wide ? 256 : 128));
   cands.push_back(make_geom(64, 4096, 2048, 128));
   cands.push_back(make_geom(128, f64 ? 8192 : 4096, 2048, 256));
-  cands.push_back(make_geom(256, f64 ? 8192 : 4096, 2048, 256));
   const int reserve = 1024;  // shared memory the system keeps per block
   // warps per block and blocks per SM of a geometry: the most warps per SM
   // (at most 16)
@@ -1755,7 +1756,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
       G = it->second;
       if (info) info->source = 2;
     } else if (p >= kTuneMinRows) {
-      const int64_t m = std::min<int64_t>(std::max<int64_t>(p / 16, 4096), 65536);
+      const int64_t m = std::min<int64_t>(std::max<int64_t>(p / 64, 2048), 16384);
       const auto t0 = std::chrono::steady_clock::now();
       float best = 0.f;
       int bi = -1;

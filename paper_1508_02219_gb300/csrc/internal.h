@@ -70,6 +70,11 @@ struct LevelDev {
   DBuf<int32_t> piv;      // GEPP interchanges, per scalar row of D
   DBuf<int32_t> ptag;     // 1 = pivot block kept in FP64 (mixed precision)
   VBDev<T> F, E, C, W, G, S;
+  // groups of more than one supernode (Step 3 with block-sparse D_i)
+  bool grouped = false;
+  int64_t ngroups = 0;
+  DBuf<int64_t> gptr;     // group boundaries over the D rows
+  VBDev<T> Lg, Ug;        // group multipliers (below), group part of Ubar (above)
 };
 
 // How the last-level ILUT ran: its per-warp shared workspace (slots, value
@@ -115,6 +120,7 @@ struct FactorOpts {
   uint64_t wait_limit;
   bool schur_drop_all;
   bool keep_factors;
+  int group_size;  // supernodes per independent group (Step 3)
 };
 
 // Step 2: two-sided max-abs scaling in place (FP64 values).

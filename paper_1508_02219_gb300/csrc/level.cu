@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "blockops.cuh"
 #include "level.cuh"
 #include "vbsr_ops.cuh"
 
@@ -33,16 +34,6 @@ constexpr int LW = 8;           // warps per block
 constexpr int PAT_CAP = 1024;   // per-warp shared hash capacity
 constexpr int PAT_LIMIT = 640;
 
-template <typename T>
-__device__ __forceinline__ T msub(T acc, T a, T b);
-template <>
-__device__ __forceinline__ double msub<double>(double acc, double a, double b) {
-  return __dsub_rn(acc, __dmul_rn(a, b));
-}
-template <>
-__device__ __forceinline__ float msub<float>(float acc, float a, float b) {
-  return __fmaf_rn(-a, b, acc);
-}
 
 // ---- A5: Step 2 scaling ----------------------------------------------------
 // |x| maxima: exact in any precision and any order.  FP64 values are
@@ -502,49 +493,6 @@ __global__ void k_gepp(int64_t nD, const int32_t* __restrict__ sz, const int64_t
 // Each lane owns one block of its warp's block row.  X is computed in place
 // in a copy of F (resp. E).  The FP32 path uses the FP32 LU unless the pivot
 // block is tagged FP64, then it promotes the block to FP64.
-template <typename T, typename TL>
-__device__ void linvp_block(const TL* lu, const int32_t* pv, int m, T* x, int n) {
-  for (int k = 0; k < m; ++k)
-    if (pv[k] != k)
-      for (int j = 0; j < n; ++j) {
-        const T t = x[k * n + j];
-        x[k * n + j] = x[pv[k] * n + j];
-        x[pv[k] * n + j] = t;
-      }
-  for (int i = 1; i < m; ++i)
-    for (int k = 0; k < i; ++k) {
-      const TL l = lu[i * m + k];
-      for (int j = 0; j < n; ++j) x[i * n + j] = (T)msub<TL>((TL)x[i * n + j], l, (TL)x[k * n + j]);
-    }
-}
-
-template <typename T, typename TL>
-__device__ void uinv_right_block(const TL* lu, int m, T* x, int r) {
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j < m; ++j) {
-      TL s = (TL)x[i * m + j];
-      for (int k = 0; k < j; ++k) s = msub<TL>(s, (TL)x[i * m + k], lu[k * m + j]);
-      x[i * m + j] = (T)(s / lu[j * m + j]);
-    }
-}
-
-__device__ __forceinline__ double fro2_d(const double* v, int n) {
-  double s = 0.0;
-  for (int e = 0; e < n; ++e) s = __dadd_rn(s, __dmul_rn(v[e], v[e]));
-  return s;
-}
-// FP32 blocks (the FP32 levels of the mixed factor): the sum of squares in
-// FP32, returned as a double
-__device__ __forceinline__ double fro2_d(const float* v, int n) {
-  float s = 0.f;
-  for (int e = 0; e < n; ++e) s = __fmaf_rn(v[e], v[e], s);
-  return (double)s;
-}
-
-__device__ __forceinline__ bool drop_rule(double f2, int m, int n, double t) {
-  const double thr = __dmul_rn(__dmul_rn(t, (double)m), (double)n);
-  return f2 < __dmul_rn(thr, thr);
-}
 
 // WHICH = 0: W rows (D nodes) from F; WHICH = 1: G rows (C nodes) from E.
 template <typename T, int WHICH>
@@ -1155,6 +1103,17 @@ int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t
   VB_LAUNCH_CHECK();
   return nD;
 }
+template <typename TA>
+void level_weights(const VBDev<TA>& A, DBuf<double>& w, cudaStream_t s) {
+  const int64_t p = A.nbr;
+  w.alloc(std::max<int64_t>(p, 1), s);
+  if (!p) return;
+  launch(k_weights<TA>, grid_for(p, LW), LW * 32, 0, s, A.view(), w.p);
+  VB_LAUNCH_CHECK();
+}
+template void level_weights<double>(const VBDev<double>&, DBuf<double>&, cudaStream_t);
+template void level_weights<float>(const VBDev<float>&, DBuf<double>&, cudaStream_t);
+
 template int64_t is_order<double>(const VBDev<double>&, double, DBuf<double>&, DBuf<int32_t>&, DBuf<int32_t>&,
                                   cudaStream_t, const int32_t*);
 template int64_t is_order<float>(const VBDev<float>&, double, DBuf<double>&, DBuf<int32_t>&, DBuf<int32_t>&,

@@ -12,6 +12,35 @@ template <typename TA>
 int64_t is_order(const VBDev<TA>& A, double ddtol, DBuf<double>& w, DBuf<int32_t>& pI, DBuf<int32_t>& newpos,
                  cudaStream_t s, const int32_t* fixed = nullptr);
 
+// Step 3 weights w(Y) = ||A_YY||_F / sum_Z ||A_YZ||_F (R5).
+template <typename TA>
+void level_weights(const VBDev<TA>& A, DBuf<double>& w, cudaStream_t s);
+
+// Step 3 with groups of up to gs supernodes (the diagonal blocks D_i of D
+// block sparse): pI lists the groups by smallest member (members ascending),
+// then C ascending; gptr[ngroups + 1] bounds the groups over the D rows.
+// Returns nD.
+template <typename TA>
+int64_t group_order(const VBDev<TA>& A, double ddtol, int gs, const int32_t* fixed, DBuf<double>& w,
+                    DBuf<int32_t>& pI, DBuf<int32_t>& newpos, DBuf<int64_t>& gptr, int64_t& ngroups,
+                    cudaStream_t s);
+
+// Steps 3-4 of a grouped level (Section 3.1's two sweeps inside each group):
+// D (pivot LU after the group elimination), piv, the group multipliers Lg,
+// the group part Ug of Ubar, W = Ltilde^{-1} F and G = E Ubar^{-1}; F, E, C
+// gathered.  S follows from schur() as for ungrouped levels.
+template <typename TA, typename T>
+void grouped_level(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_t>& newpos, int64_t nD,
+                   const DBuf<int64_t>& gptr, int64_t ngroups, double t, int lfil, LevelDev<T>& L, cudaStream_t s,
+                   int* dst);
+
+// The level solve of a grouped level: forward u = Ltilde^{-1} P f in place
+// in bh (its D part), backward xh = Ubar^{-1} bh (bh already holds u - W z).
+template <typename T>
+void grouped_forward(const LevelDev<T>& L, double* bh, cudaStream_t s);
+template <typename T>
+void grouped_backward(const LevelDev<T>& L, const double* bh, double* xh, cudaStream_t s);
+
 // Eq. 4: the D (FP64 pivot blocks), F, E, C parts of P_I A P_I^T.
 template <typename TA, typename T>
 void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_t>& newpos, int64_t nD,

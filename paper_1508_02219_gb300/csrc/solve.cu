@@ -571,7 +571,9 @@ void solve_core(const PrecDev<T>& P, const double* in, double* out, const SolveB
     const LevelMaps& M = P.maps[l];
     const double* b = l == 0 ? in : B.bh[l - 1] + P.maps[l - 1].nf;
     if (M.n) launch(k_gather_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.r.p, b, B.bh[l]);
-    if (L.nD)
+    if (L.grouped)
+      grouped_forward<T>(L, B.bh[l], s);
+    else if (L.nD)
       launch(k_pivot_fwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
              mixed ? L.D32.val.p : nullptr, L.ptag.p, L.piv.p, B.bh[l]);
     const int64_t ng = M.n - M.nf;
@@ -616,7 +618,9 @@ void solve_core(const PrecDev<T>& P, const double* in, double* out, const SolveB
     double* xo = l == 0 ? out : B.xh[l - 1] + P.maps[l - 1].nf;
     if (M.nf && L.W.nnzb)
       launch(k_bsr_sub<T>, grid_for(M.nf, 128), 128, 0, s, L.W.view(), B.wrow[l], M.nf, B.xh[l] + M.nf, B.bh[l]);
-    if (L.nD)
+    if (L.grouped)
+      grouped_backward<T>(L, B.bh[l], B.xh[l], s);
+    else if (L.nD)
       launch(k_pivot_bwd, grid_for(L.nD, 128), 128, 0, s, L.nD, L.D.rsz.p, L.D.roff.p, L.D.voff.p, L.D.val.p,
              mixed ? L.D32.val.p : nullptr, L.ptag.p, B.bh[l], B.xh[l]);
     if (M.n) launch(k_scatter_scale, grid_for(M.n, 256), 256, 0, s, M.n, M.sperm.p, L.c.p, B.xh[l], xo);
@@ -800,6 +804,12 @@ void PrecDev<T>::export_mat(int l, int which, int64_t* nbr, int64_t* nbc, int64_
     case 5: return export_vb(L.W, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
     case 6: return export_vb(L.G, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
     case 7: return export_vb(L.S, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 10:
+      if (!L.grouped) fail(VB_EINVAL, "not a grouped level");
+      return export_vb(L.Lg, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
+    case 11:
+      if (!L.grouped) fail(VB_EINVAL, "not a grouped level");
+      return export_vb(L.Ug, s, nbr, nbc, nnzb, nval, rsz, csz, bptr, bcol, voff, val);
   }
   fail(VB_EINVAL, "matrix selector out of range");
 }
@@ -823,6 +833,14 @@ void PrecDev<T>::export_vec(int l, int which, double* d, int32_t* iv, int64_t* l
     if (which == 3) ivb = &L.pI;
     if (which == 4) ivb = &L.piv;
     if (which == 5) ivb = &L.ptag;
+    if (which == 6) {  // group boundaries of a grouped level (ngroups + 1)
+      if (!L.grouped) fail(VB_EINVAL, "not a grouped level");
+      const std::vector<int64_t> g = d2h_vec(L.gptr.p, L.ngroups + 1, s);
+      if (len) *len = (int64_t)g.size();
+      if (iv)
+        for (size_t k = 0; k < g.size(); ++k) iv[k] = (int32_t)g[k];
+      return;
+    }
   }
   if (!dv && !ivb) fail(VB_EINVAL, "vector selector out of range");
   const int64_t n = dv ? (int64_t)dv->n : (int64_t)ivb->n;

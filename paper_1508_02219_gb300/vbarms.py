@@ -25,9 +25,9 @@ VB_OK, VB_EINVAL, VB_ENOMEM, VB_ECUDA, VB_ESINGULAR, VB_ETIMEOUT, VB_ENOCONV, VB
 VB_FP64, VB_FP32_MIXED = 0, 1
 STATUS_NAMES = {0: "VB_OK", 1: "VB_EINVAL", 2: "VB_ENOMEM", 3: "VB_ECUDA", 4: "VB_ESINGULAR",
                 5: "VB_ETIMEOUT", 6: "VB_ENOCONV", 7: "VB_EINTERNAL"}
-MAT = dict(A=0, D=1, F=2, E=3, C=4, W=5, G=6, S=7, L=8, U=9)
+MAT = dict(A=0, D=1, F=2, E=3, C=4, W=5, G=6, S=7, L=8, U=9, Lg=10, Ug=11)
 VEC_D = dict(r=0, c=1, w=2)
-VEC_I = dict(pI=3, piv=4, ptag=5)
+VEC_I = dict(pI=3, piv=4, ptag=5, gptr=6)
 PHASES = ["scale", "ordering", "gather", "pivot_lu", "W", "G", "schur", "last_ilut"]
 
 
@@ -39,7 +39,8 @@ class VbarmsError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("fp64_pivot_cond", C.c_double), ("ddtol", C.c_double),
-                ("wait_limit", C.c_uint64), ("schur_drop_all", C.c_int), ("keep_factors", C.c_int)]
+                ("wait_limit", C.c_uint64), ("schur_drop_all", C.c_int), ("keep_factors", C.c_int),
+                ("group_size", C.c_int)]
 
 
 def library_path() -> str:
@@ -287,7 +288,7 @@ class Prec:
 
 
 def make_opts(precision="fp64", fp64_pivot_cond=1e4, ddtol=0.0, wait_limit=0, schur_drop_all=False,
-              keep_factors=True) -> Opts:
+              keep_factors=True, group_size=1) -> Opts:
     o = Opts()
     lib().vbarms_opts_default(C.byref(o))
     o.precision = VB_FP64 if precision in ("fp64", VB_FP64) else VB_FP32_MIXED
@@ -296,6 +297,7 @@ def make_opts(precision="fp64", fp64_pivot_cond=1e4, ddtol=0.0, wait_limit=0, sc
     o.wait_limit = int(wait_limit)
     o.schur_drop_all = int(bool(schur_drop_all))
     o.keep_factors = int(bool(keep_factors))
+    o.group_size = int(group_size)
     return o
 
 
