@@ -504,7 +504,7 @@ def main():
         r = dict(compress_s=e[0].elapsed_time(e[1]) / 1e3, factor_s=e[1].elapsed_time(e[2]) / 1e3,
                  solve_s=e[2].elapsed_time(e[3]) / 1e3, its=its, relres=rr, stats=P.stats(),
                  kstats=P.kernel_stats(0), av_bd=A.query()["av_bd"], av_bs=A.query()["av_bs"],
-                 ilut=P.ilut_geometry())
+                 ilut=P.ilut_geometry(), chain=P.ilut_chain())
         if keep:  # the factorization is kept for the error report (after timing)
             r.update(P=P, A=A, x=xd.clone())
         del P, A
@@ -548,6 +548,16 @@ def main():
             "algorithmic_bytes_per_launch": kb / max(1, kl), "avg_launch_ms": kms / max(1, kl),
             "flops_per_launch": kfl / max(1, kl),
             "achieved_tflops": kfl / (kms / 1e3) / 1e12 if kms > 0 else 0.0}
+    # the step's dominant kernel, the last-level ILUT, is bound by its chain of
+    # dependent rows, not by a bandwidth: its longest chain of waits and the
+    # time per link of that chain
+    chain = res[-1]["chain"]
+    ilut_s = statistics.mean(r["stats"]["phase_s"]["last_ilut"] for r in res)
+    roof["ilut"] = {"bound": "latency (dependency chain)", "kernel": "k_ilut", "ms": ilut_s * 1e3,
+                    "chain_links": chain, "us_per_link": ilut_s * 1e6 / chain if chain else None,
+                    "note": "rows on the longest chain of waits (every pending L column, dropped multipliers "
+                            "included); the kernel time is this chain times the latency from a dependency's "
+                            "publication to the row's own"}
 
     # FP32 vs FP64: the plain FP64 GPU factor on the same GB300
     fp64 = None

@@ -370,6 +370,26 @@ vb_status vbarms_prec_kernel_stats(vbarms_prec M, int kernel, int* launches, dou
 vb_status vbarms_prec_ilut_geometry(vbarms_prec M, int* slots, int* value_bytes, int* warps_per_sm, int* source,
                                     double* tune_s);
 
+/* Length (in rows) of the longest chain of waits in M's last-level block
+ * ILUT: every row waits for each pending L column of its working row,
+ * dropped multipliers included, so this chain, times the latency from a
+ * dependency's publication to the row's own, bounds the kernel's time from
+ * below whatever the number of warps.  The kept L pattern's depth is shorter
+ * (a dropped multiplier leaves no block).                                   */
+vb_status vbarms_prec_ilut_chain(vbarms_prec M, int64_t* links);
+
+/* How the pivot phase (GEPP of every pivot block) of reduction level lev ran:
+ * it is one persistent launch over the pivot blocks flattened into block-size
+ * classes (<= 4, <= 8, <= 16, <= 32, more); counts[5] receives the blocks per
+ * class, modes[5] the mode each class ran in (0: one thread per block, 1: one
+ * warp per block; both give the same factors bit for bit), source = 0
+ * defaults, 1 a class was timed in both modes on a copy of this level's own
+ * blocks (classes of at least 1024 blocks), 2 modes taken from an earlier
+ * timing in this process on the same device and precision.  Levels factored
+ * with group_size > 1 run their pivots inside the group sweeps (all zero).
+ * Any pointer may be NULL; VB_EINVAL for lev outside [0, levels).           */
+vb_status vbarms_prec_pivot_tiles(vbarms_prec M, int lev, int* counts, int* modes, int* source);
+
 /* Number of kernels this library has launched since it was loaded (all
  * threads, all handles); read it before and after a call to count the
  * launches of that call.                                                   */

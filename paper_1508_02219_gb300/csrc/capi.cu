@@ -157,7 +157,7 @@ std::unique_ptr<PrecDev<T>> factor_impl(const vbarms_vbsr_st& Ah, const FactorOp
       fcur = std::move(fn);
     }
     if (!L.grouped) {  // grouped levels made D, W and G in their two sweeps
-      pivot_lu(L.D, L.piv, L.ptag, L.D32, mixed, o.fp64_pivot_cond, s, dst);
+      pivot_lu(L.D, L.piv, L.ptag, L.D32, mixed, o.fp64_pivot_cond, s, dst, &L.tiles);
       tm.mark(PH_PIVOT);
       w_or_g<T>(L.F, 0, L.D, L.D32, L.piv, L.ptag, mixed, o.droptol, o.lfil, L.W, s);
       tm.mark(PH_W);
@@ -822,6 +822,24 @@ vb_status vbarms_prec_stats(vbarms_prec M, int* levels_used, double* mem_ratio, 
 uint64_t vbarms_launch_count(void) { return g_launch_count.load(); }
 
 uint64_t vbarms_alloc_count(void) { return g_alloc_count.load(); }
+
+vb_status vbarms_prec_ilut_chain(vbarms_prec M, int64_t* links) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  if (links) *links = M->impl->ilut_info().chain;
+  return VB_OK;
+}
+
+vb_status vbarms_prec_pivot_tiles(vbarms_prec M, int lev, int* counts, int* modes, int* source) {
+  if (!M) return set_err(VB_EINVAL, "NULL handle");
+  return guarded([&] {
+    const PivotTiles T = M->impl->pivot_tiles(lev);
+    for (int c = 0; c < 5; ++c) {
+      if (counts) counts[c] = T.count[c];
+      if (modes) modes[c] = T.mode[c];
+    }
+    if (source) *source = T.source;
+  });
+}
 
 vb_status vbarms_prec_ilut_geometry(vbarms_prec M, int* slots, int* value_bytes, int* warps_per_sm, int* source,
                                     double* tune_s) {

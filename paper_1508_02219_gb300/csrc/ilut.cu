@@ -100,6 +100,10 @@ struct Pools {
   // of the ticket order holds its rows' dependencies, so it is factored
   // exactly on its own)
   int64_t nticket;
+  // per row (may be NULL): 1 + the largest depth among the rows it waited
+  // on (every pending L column, the dropped multipliers' included), i.e. the
+  // length of the longest chain of waits ending at the row
+  int32_t* depth;
 };
 
 // Global fallback workspace, per warp.
@@ -752,6 +756,7 @@ __global__ void __launch_bounds__(256, 2)
     row = __shfl_sync(0xffffffffu, row, 0);
     if (row >= A.nbr) break;
     const int64_t i = row;
+    int maxdep = 0;  // lane 0: the deepest row waited on
     const int ni = A.rsz[i];
     const int64_t b0 = A.bptr[i], b1 = A.bptr[i + 1];
     const int64_t v0 = A.voff[b0], nv = A.voff[b1] - v0;
@@ -944,6 +949,7 @@ __global__ void __launch_bounds__(256, 2)
           rec = bi ? stage1 : stage0;
         }
         const bool staged = bi >= 0;
+        if (P.depth && lane == 0) maxdep = max(maxdep, ld_relaxed_gpu(P.depth + k));
         // header: U blocks, pivot size, pivot precision, U values
         int hv = 0;
         if (lane < 4) hv = staged ? reinterpret_cast<const int*>(rec)[lane] : __ldcg(reinterpret_cast<const int*>(rec) + lane);
@@ -1405,6 +1411,7 @@ __global__ void __launch_bounds__(256, 2)
       atomicMax(P.ctr + 5, M.nvals);
       atomicMax(P.ctr + 6, (unsigned long long)M.nslots);
     }
+    if (P.depth && lane == 0) P.depth[i] = maxdep + 1;
     // publish the row: every lane's writes are made visible device-wide (and
     // to the bulk copies of the readers) before lane 0 sets the word
     fence_proxy_async_all();
@@ -1590,6 +1597,18 @@ static IlutGeom make_geom(int slots, int vbytes, int stage, int lcap) {
 
 
 
+namespace {
+// m = the largest a[i]
+__global__ void k_max_i32(int64_t n, const int32_t* __restrict__ a, unsigned long long* __restrict__ m) {
+  unsigned long long v = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v = max(v, (unsigned long long)a[i]);
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v) atomicMax(m, v);
+}
+
+}  // namespace
+
 template <typename T>
 void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, uint64_t wait_limit, cudaStream_t s,
                int* dst, const int32_t* order) {
@@ -1681,7 +1700,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   int64_t vmax = 32768;
   // buffers of one launch
   struct Run {
-    DBuf<int32_t> lcol, lcnt;
+    DBuf<int32_t> lcol, lcnt, depth;
     DBuf<int64_t> lvo, lstart;
     DBuf<unsigned long long> done, ctr;
     DBuf<T> lval;
@@ -1689,7 +1708,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   };
   // one launch of the kernel over the first nticket tickets with geometry G;
   // returns the device status (the time of the launch in *ms when asked)
-  auto run = [&](const IlutGeom& G, int64_t nticket, Run& R, float* ms) -> int {
+  auto run = [&](const IlutGeom& G, int64_t nticket, Run& R, float* ms, bool track = false) -> int {
     int wpb = 0, bps = 0;
     if (!shape(G, wpb, bps)) fail(VB_EINTERNAL, "last-level ILUT: shared workspace exceeds a block");
     const size_t smem = (size_t)wpb * G.bytes;
@@ -1711,13 +1730,17 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
     R.lval.alloc(lvcap, s);
     R.upool.alloc(ucap16 * 16, s);
     R.ctr.alloc(8, s);
+    if (track) {
+      R.depth.alloc(p, s);
+      R.depth.zero();
+    }
     DBuf<int> abort(1, s);
     R.ctr.zero();
     R.done.zero();
     abort.zero();
     X.piv.zero();
     Pools P{R.lcol.p, R.lvo.p, R.lstart.p, R.lcnt.p, R.done.p, R.ctr.p, lbcap, lvcap, ucap16, abort.p, order,
-            nticket};
+            nticket, R.depth.p};
     VB_CUDA(cudaFuncSetAttribute(k_ilut<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ms) {
@@ -1785,7 +1808,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   }
   for (int attempt = 0; attempt < 6; ++attempt) {
     Run R;
-    const int st = run(G, p, R, nullptr);
+    const int st = run(G, p, R, nullptr, true);
     auto& lcol = R.lcol;
     auto& lcnt = R.lcnt;
     auto& lvo = R.lvo;
@@ -1808,6 +1831,13 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
       continue;
     }
     check_status(dst, s, "vbarms_factor: last-level block ILUT");
+    if (info) {  // the longest chain of waits
+      DBuf<unsigned long long> mx(1, s);
+      mx.zero();
+      launch(k_max_i32, grid_for(p, 256), 256, 0, s, p, R.depth.p, mx.p);
+      VB_LAUNCH_CHECK();
+      info->chain = (long long)d2h(mx.p, s);
+    }
     // assemble L from its pool
     {
       VBDev<T>& M = X.L;

@@ -57,6 +57,16 @@ void compressed_union(const std::vector<const Compressed*>& parts, cudaStream_t 
 // dom[k] = the part that block row k of the union comes from.
 void union_part_ids(const std::vector<const Compressed*>& parts, cudaStream_t s, DBuf<int32_t>& dom);
 
+// How a level's pivot phase ran: pivot blocks per size class (<= 4, <= 8,
+// <= 16, <= 32, more), the mode of each class (0: a thread per block, 1: a
+// warp per block) and how the modes were chosen (0 default, 1 timed on this
+// level's blocks, 2 taken from an earlier timing in this process).
+struct PivotTiles {
+  int count[5] = {0, 0, 0, 0, 0};
+  int mode[5] = {0, 0, 1, 1, 1};
+  int source = 0;
+};
+
 // One reduction level (Steps 2-4) on the device.
 template <typename T>
 struct LevelDev {
@@ -75,6 +85,7 @@ struct LevelDev {
   int64_t ngroups = 0;
   DBuf<int64_t> gptr;     // group boundaries over the D rows
   VBDev<T> Lg, Ug;        // group multipliers (below), group part of Ubar (above)
+  PivotTiles tiles;       // how the pivot phase ran
 };
 
 // How the last-level ILUT ran: its per-warp shared workspace (slots, value
@@ -83,6 +94,7 @@ struct LevelDev {
 // timing of a matrix of the same class (2).
 struct IlutInfo {
   int slots = 0, vbytes = 0, warps_per_sm = 0, source = 0;
+  long long chain = 0;  // rows on the longest chain of waits of the final run
   double tune_s = 0;
 };
 

@@ -21,6 +21,8 @@
 // results match the CPU oracle bit for bit.  FP32 kernels use fused
 // multiply-adds.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "internal.h"
 #include "blockops.cuh"
@@ -408,83 +410,220 @@ __global__ void k_copy_blocks(int64_t nblocks, const int64_t* __restrict__ src, 
 // ---- A7: batched GEPP ------------------------------------------------------
 constexpr int KAPPA_MAX = 64;  // largest block given a condition estimate
 
-__global__ void k_gepp(int64_t nD, const int32_t* __restrict__ sz, const int64_t* __restrict__ roff,
-                       const int64_t* __restrict__ voff, double* __restrict__ val, int32_t* __restrict__ piv,
-                       int mixed, double cond_thr, int32_t* __restrict__ ptag, float* __restrict__ val32, int* st) {
-  for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < nD; y += (int64_t)gridDim.x * blockDim.x) {
-    const int m = sz[y];
-    double* a = val + voff[y];
-    int32_t* pv = piv + roff[y];
-    double norm1 = 0.0;
-    if (mixed) {
-      for (int j = 0; j < m; ++j) {
-        double s = 0.0;
-        for (int i = 0; i < m; ++i) s += fabs(a[i * m + j]);
-        norm1 = fmax(norm1, s);
+// One pivot block, one thread: GEPP, then (mixed factor) the 1-norm
+// condition estimate from the explicit inverse columns, the FP64 tag and the
+// FP32 copy.
+__device__ void gepp_item_thread(int64_t y, const int32_t* __restrict__ sz, const int64_t* __restrict__ roff,
+                                 const int64_t* __restrict__ voff, double* __restrict__ val,
+                                 int32_t* __restrict__ piv, int mixed, double cond_thr, int32_t* __restrict__ ptag,
+                                 float* __restrict__ val32, int* st) {
+  const int m = sz[y];
+  double* a = val + voff[y];
+  int32_t* pv = piv + roff[y];
+  double norm1 = 0.0;
+  if (mixed) {
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += fabs(a[i * m + j]);
+      norm1 = fmax(norm1, s);
+    }
+  }
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    double best = fabs(a[k * m + k]);
+    for (int i = k + 1; i < m; ++i) {
+      const double v = fabs(a[i * m + k]);
+      if (v > best) {
+        best = v;
+        p = i;
       }
     }
-    bool singular = false;
-    for (int k = 0; k < m; ++k) {
-      int p = k;
-      double best = fabs(a[k * m + k]);
-      for (int i = k + 1; i < m; ++i) {
-        const double v = fabs(a[i * m + k]);
-        if (v > best) {
-          best = v;
-          p = i;
-        }
-      }
-      if (best == 0.0) {
-        singular = true;
-        break;
-      }
-      pv[k] = p;
-      if (p != k)
-        for (int j = 0; j < m; ++j) {
-          const double t = a[k * m + j];
-          a[k * m + j] = a[p * m + j];
-          a[p * m + j] = t;
-        }
-      const double d = a[k * m + k];
-      for (int i = k + 1; i < m; ++i) {
-        const double l = __ddiv_rn(a[i * m + k], d);
-        a[i * m + k] = l;
-        for (int j = k + 1; j < m; ++j) a[i * m + j] = __dsub_rn(a[i * m + j], __dmul_rn(l, a[k * m + j]));
-      }
-    }
-    if (singular) {
+    if (best == 0.0) {
       dev_fail(st, DEV_ESINGULAR);
-      continue;
+      return;
     }
-    if (mixed) {
-      int tag = 1;
-      if (m <= KAPPA_MAX) {
-        // ||D^{-1}||_1 from the explicit inverse columns
-        double inv1 = 0.0;
-        double x[KAPPA_MAX];
-        for (int j = 0; j < m; ++j) {
-          for (int i = 0; i < m; ++i) x[i] = (i == j) ? 1.0 : 0.0;
-          for (int k = 0; k < m; ++k)
-            if (pv[k] != k) {
-              const double t = x[k];
-              x[k] = x[pv[k]];
-              x[pv[k]] = t;
-            }
-          for (int i = 1; i < m; ++i)
-            for (int k = 0; k < i; ++k) x[i] -= a[i * m + k] * x[k];
-          for (int i = m - 1; i >= 0; --i) {
-            double s = x[i];
-            for (int k = i + 1; k < m; ++k) s -= a[i * m + k] * x[k];
-            x[i] = s / a[i * m + i];
-          }
-          double cs = 0.0;
-          for (int i = 0; i < m; ++i) cs += fabs(x[i]);
-          inv1 = fmax(inv1, cs);
-        }
-        tag = (norm1 * inv1 > cond_thr) ? 1 : 0;
+    pv[k] = p;
+    if (p != k)
+      for (int j = 0; j < m; ++j) {
+        const double t = a[k * m + j];
+        a[k * m + j] = a[p * m + j];
+        a[p * m + j] = t;
       }
-      ptag[y] = tag;
-      for (int e = 0; e < m * m; ++e) val32[voff[y] + e] = (float)a[e];
+    const double d = a[k * m + k];
+    for (int i = k + 1; i < m; ++i) {
+      const double l = __ddiv_rn(a[i * m + k], d);
+      a[i * m + k] = l;
+      for (int j = k + 1; j < m; ++j) a[i * m + j] = __dsub_rn(a[i * m + j], __dmul_rn(l, a[k * m + j]));
+    }
+  }
+  if (mixed) {
+    int tag = 1;
+    if (m <= KAPPA_MAX) {
+      // ||D^{-1}||_1 from the explicit inverse columns
+      double inv1 = 0.0;
+      double x[KAPPA_MAX];
+      for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < m; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+        for (int k = 0; k < m; ++k)
+          if (pv[k] != k) {
+            const double t = x[k];
+            x[k] = x[pv[k]];
+            x[pv[k]] = t;
+          }
+        for (int i = 1; i < m; ++i)
+          for (int k = 0; k < i; ++k) x[i] -= a[i * m + k] * x[k];
+        for (int i = m - 1; i >= 0; --i) {
+          double s = x[i];
+          for (int k = i + 1; k < m; ++k) s -= a[i * m + k] * x[k];
+          x[i] = s / a[i * m + i];
+        }
+        double cs = 0.0;
+        for (int i = 0; i < m; ++i) cs += fabs(x[i]);
+        inv1 = fmax(inv1, cs);
+      }
+      tag = (norm1 * inv1 > cond_thr) ? 1 : 0;
+    }
+    ptag[y] = tag;
+    for (int e = 0; e < m * m; ++e) val32[voff[y] + e] = (float)a[e];
+  }
+}
+
+// The same for one block with the 32 lanes of a warp: pivot search by a warp
+// reduction (largest magnitude, lowest row on ties), multipliers and the
+// trailing update over lanes, column sums and inverse columns over lanes;
+// every element receives the sequential algorithm's operations in its order,
+// so the result equals gepp_item_thread's bit for bit.
+__device__ void gepp_item_warp(int64_t y, int lane, const int32_t* __restrict__ sz,
+                               const int64_t* __restrict__ roff, const int64_t* __restrict__ voff,
+                               double* __restrict__ val, int32_t* __restrict__ piv, int mixed, double cond_thr,
+                               int32_t* __restrict__ ptag, float* __restrict__ val32, int* st) {
+  const int m = sz[y];
+  double* a = val + voff[y];
+  int32_t* pv = piv + roff[y];
+  double norm1 = 0.0;
+  if (mixed) {
+    for (int j = lane; j < m; j += 32) {
+      double s = 0.0;
+      for (int i = 0; i < m; ++i) s += fabs(a[i * m + j]);
+      norm1 = fmax(norm1, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) norm1 = fmax(norm1, __shfl_xor_sync(0xffffffffu, norm1, o));
+  }
+  for (int k = 0; k < m; ++k) {
+    double best = -1.0;
+    int p = 0x7fffffff;
+    for (int i = k + lane; i < m; i += 32) {
+      const double v = fabs(a[i * m + k]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int op = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ob > best || (ob == best && op < p)) {
+        best = ob;
+        p = op;
+      }
+    }
+    if (best == 0.0) {
+      if (lane == 0) dev_fail(st, DEV_ESINGULAR);
+      return;
+    }
+    if (lane == 0) pv[k] = p;
+    if (p != k)
+      for (int j = lane; j < m; j += 32) {
+        const double t = a[k * m + j];
+        a[k * m + j] = a[p * m + j];
+        a[p * m + j] = t;
+      }
+    __syncwarp();
+    const double d = a[k * m + k];
+    const int w = m - k - 1;
+    for (int r = lane; r < w; r += 32) a[(k + 1 + r) * m + k] = __ddiv_rn(a[(k + 1 + r) * m + k], d);
+    __syncwarp();
+    for (int e = lane; e < w * w; e += 32) {
+      const int r = e / w, c = e - r * w;
+      const int i = k + 1 + r, j = k + 1 + c;
+      a[i * m + j] = __dsub_rn(a[i * m + j], __dmul_rn(a[i * m + k], a[k * m + j]));
+    }
+    __syncwarp();
+  }
+  if (mixed) {
+    int tag = 1;
+    if (m <= KAPPA_MAX) {
+      double inv1 = 0.0;
+      for (int j = lane; j < m; j += 32) {
+        double x[KAPPA_MAX];
+        for (int i = 0; i < m; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+        for (int k = 0; k < m; ++k)
+          if (pv[k] != k) {
+            const double t = x[k];
+            x[k] = x[pv[k]];
+            x[pv[k]] = t;
+          }
+        for (int i = 1; i < m; ++i)
+          for (int k = 0; k < i; ++k) x[i] -= a[i * m + k] * x[k];
+        for (int i = m - 1; i >= 0; --i) {
+          double s = x[i];
+          for (int k = i + 1; k < m; ++k) s -= a[i * m + k] * x[k];
+          x[i] = s / a[i * m + i];
+        }
+        double cs = 0.0;
+        for (int i = 0; i < m; ++i) cs += fabs(x[i]);
+        inv1 = fmax(inv1, cs);
+      }
+      for (int o = 16; o > 0; o >>= 1) inv1 = fmax(inv1, __shfl_xor_sync(0xffffffffu, inv1, o));
+      tag = (norm1 * inv1 > cond_thr) ? 1 : 0;
+    }
+    if (lane == 0) ptag[y] = tag;
+    for (int e = lane; e < m * m; e += 32) val32[voff[y] + e] = (float)a[e];
+  }
+}
+
+// Block-size classes of the queued pivot phase.
+constexpr int PQ_NCLASS = 5;
+__device__ __forceinline__ int pq_class(int m) { return m <= 4 ? 0 : m <= 8 ? 1 : m <= 16 ? 2 : m <= 32 ? 3 : 4; }
+
+__global__ void k_pq_keys(int64_t nD, const int32_t* __restrict__ sz, unsigned long long* __restrict__ key,
+                          int* __restrict__ cnt) {
+  for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < nD; y += (int64_t)gridDim.x * blockDim.x) {
+    const int c = pq_class(sz[y]);
+    key[y] = ((unsigned long long)c << 32) | (unsigned long long)y;
+    atomicAdd(&cnt[c], 1);
+  }
+}
+
+// The pivot phase as one persistent launch over the flattened pivot blocks,
+// class by class (items[cstart[c] .. cstart[c+1]) in ascending block order):
+// mode[c] = 0 gives each thread an item (a warp claims 32 at a time), 1 gives
+// each warp an item.
+__global__ void __launch_bounds__(128)
+    k_gepp_q(const unsigned long long* __restrict__ items, const int64_t* __restrict__ cstart,
+             const int32_t* __restrict__ mode, unsigned long long* __restrict__ ctr, int only,
+             const int32_t* __restrict__ sz, const int64_t* __restrict__ roff, const int64_t* __restrict__ voff,
+             double* __restrict__ val, int32_t* __restrict__ piv, int mixed, double cond_thr,
+             int32_t* __restrict__ ptag, float* __restrict__ val32, int* st) {
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < PQ_NCLASS; ++c) {
+    const int64_t c0 = cstart[c], c1 = cstart[c + 1];
+    if (c0 == c1 || (only >= 0 && c != only)) continue;
+    const int md = mode[c];
+    for (;;) {
+      long long base = 0;
+      if (lane == 0) base = (long long)atomicAdd(&ctr[c], md == 0 ? 32ULL : 1ULL);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (c0 + base >= c1) break;
+      if (md == 0) {
+        const int64_t q = c0 + base + lane;
+        if (q < c1)
+          gepp_item_thread((int64_t)(items[q] & 0xffffffffull), sz, roff, voff, val, piv, mixed, cond_thr, ptag,
+                           val32, st);
+      } else {
+        gepp_item_warp((int64_t)(items[c0 + base] & 0xffffffffull), lane, sz, roff, voff, val, piv, mixed,
+                       cond_thr, ptag, val32, st);
+      }
     }
   }
 }
@@ -1179,8 +1318,19 @@ void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_
   check_status(dst, s, "vbarms_factor: gather");
 }
 
+namespace {
+std::mutex g_pq_mu;
+std::map<long long, int> g_pq_mode;  // (device, class, mixed) -> the faster mode
+constexpr int64_t kPqTuneMin = 1024;  // items of a class before its modes are timed
+}  // namespace
+
+// A7 as one persistent launch over block-size-class queues (A14): the pivot
+// blocks are flattened into classes by size (<= 4, <= 8, <= 16, <= 32, more),
+// each class run one item per thread or one per warp.  The mode of a class is
+// timed on a copy of this level's own blocks of that class the first time the
+// process meets it on a device (results do not depend on it), and reused.
 void pivot_lu(VBDev<double>& D, DBuf<int32_t>& piv, DBuf<int32_t>& ptag, VBDev<float>& D32, bool mixed,
-              double cond_thr, cudaStream_t s, int* dst) {
+              double cond_thr, cudaStream_t s, int* dst, PivotTiles* info) {
   const int64_t nD = D.nbr;
   const int64_t nsc = nD ? d2h(D.roff.p + nD, s) : 0;
   piv.alloc(nsc, s);
@@ -1188,12 +1338,85 @@ void pivot_lu(VBDev<double>& D, DBuf<int32_t>& piv, DBuf<int32_t>& ptag, VBDev<f
   if (mixed) {
     copy_vb<float, double>(D, D32, s);
   }
-  if (nD) {
-    launch(k_gepp, grid_for(nD, 128), 128, 0, s, nD, D.rsz.p, D.roff.p, D.voff.p, D.val.p, piv.p, mixed ? 1 : 0,
-                                             cond_thr, ptag.p, mixed ? D32.val.p : nullptr, dst);
-    VB_LAUNCH_CHECK();
+  if (!nD) return;
+  DBuf<unsigned long long> items(nD, s);
+  DBuf<int> cnt(PQ_NCLASS, s);
+  cnt.zero();
+  launch(k_pq_keys, grid_for(nD, 256), 256, 0, s, nD, D.rsz.p, items.p, cnt.p);
+  VB_LAUNCH_CHECK();
+  radix_sort_u64(items, nullptr, nD, 35, s);
+  const std::vector<int> hc = d2h_vec(cnt.p, PQ_NCLASS, s);
+  std::vector<int64_t> hs(PQ_NCLASS + 1, 0);
+  for (int c = 0; c < PQ_NCLASS; ++c) hs[c + 1] = hs[c] + hc[c];
+  DBuf<int64_t> cstart(PQ_NCLASS + 1, s);
+  h2d(cstart.p, hs.data(), PQ_NCLASS + 1, s);
+  int dev = 0, nsm = 0;
+  VB_CUDA(cudaGetDevice(&dev));
+  VB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * 8, (nD + 127) / 128));
+  int32_t mode[PQ_NCLASS];
+  int source = 0;
+  DBuf<int32_t> dmode(PQ_NCLASS, s);
+  DBuf<unsigned long long> ctr(PQ_NCLASS, s);
+  {
+    std::lock_guard<std::mutex> lk(g_pq_mu);
+    DBuf<double> sv;
+    DBuf<int32_t> sp, st2;
+    DBuf<float> s32;
+    for (int c = 0; c < PQ_NCLASS; ++c) {
+      mode[c] = c >= 2 ? 1 : 0;  // default: a thread per block up to 8, a warp above
+      const long long key = ((long long)dev << 8) | ((long long)c << 1) | (mixed ? 1 : 0);
+      auto it = g_pq_mode.find(key);
+      if (it != g_pq_mode.end()) {
+        mode[c] = it->second;
+        source = std::max(source, 2);
+        continue;
+      }
+      if (hc[c] < kPqTuneMin) continue;
+      if (!sv.p) {
+        sv.alloc(std::max<int64_t>(D.nval, 1), s);
+        sp.alloc(std::max<int64_t>(nsc, 1), s);
+        st2.alloc(nD, s);
+        if (mixed) s32.alloc(std::max<int64_t>(D.nval, 1), s);
+      }
+      float ms[2] = {0.f, 0.f};
+      cudaEvent_t e0, e1;
+      VB_CUDA(cudaEventCreate(&e0));
+      VB_CUDA(cudaEventCreate(&e1));
+      for (int md = 0; md < 2; ++md) {
+        VB_CUDA(cudaMemcpyAsync(sv.p, D.val.p, D.nval * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        int32_t hm[PQ_NCLASS];
+        for (int q = 0; q < PQ_NCLASS; ++q) hm[q] = md;
+        h2d(dmode.p, hm, PQ_NCLASS, s);
+        ctr.zero();
+        VB_CUDA(cudaEventRecord(e0, s));
+        launch(k_gepp_q, grid, 128, 0, s, items.p, cstart.p, dmode.p, ctr.p, c, D.rsz.p, D.roff.p, D.voff.p, sv.p,
+               sp.p, mixed ? 1 : 0, cond_thr, st2.p, mixed ? s32.p : nullptr, dst);
+        VB_CUDA(cudaEventRecord(e1, s));
+        VB_LAUNCH_CHECK();
+        VB_CUDA(cudaEventSynchronize(e1));
+        VB_CUDA(cudaEventElapsedTime(&ms[md], e0, e1));
+      }
+      VB_CUDA(cudaEventDestroy(e0));
+      VB_CUDA(cudaEventDestroy(e1));
+      mode[c] = ms[1] < ms[0] ? 1 : 0;
+      g_pq_mode[key] = mode[c];
+      source = std::max(source, 1);
+    }
   }
+  h2d(dmode.p, mode, PQ_NCLASS, s);
+  ctr.zero();
+  launch(k_gepp_q, grid, 128, 0, s, items.p, cstart.p, dmode.p, ctr.p, -1, D.rsz.p, D.roff.p, D.voff.p, D.val.p,
+         piv.p, mixed ? 1 : 0, cond_thr, ptag.p, mixed ? D32.val.p : nullptr, dst);
+  VB_LAUNCH_CHECK();
   check_status(dst, s, "vbarms_factor: pivot LU");
+  if (info) {
+    for (int c = 0; c < PQ_NCLASS; ++c) {
+      info->count[c] = hc[c];
+      info->mode[c] = mode[c];
+    }
+    info->source = source;
+  }
 }
 
 template <typename T>

@@ -46,9 +46,11 @@ template <typename TA, typename T>
 void gather_parts(const VBDev<TA>& A, const DBuf<int32_t>& pI, const DBuf<int32_t>& newpos, int64_t nD,
                   LevelDev<T>& L, cudaStream_t s, int* dst);
 
-// Batched GEPP of the pivot blocks (in place), with the mixed-precision tag.
+// Batched GEPP of the pivot blocks (in place), with the mixed-precision tag:
+// one persistent launch over block-size-class queues; info (may be NULL)
+// receives the classes' sizes and modes.
 void pivot_lu(VBDev<double>& D, DBuf<int32_t>& piv, DBuf<int32_t>& ptag, VBDev<float>& D32, bool mixed,
-              double cond_thr, cudaStream_t s, int* dst);
+              double cond_thr, cudaStream_t s, int* dst, PivotTiles* info = nullptr);
 
 // which = 0: W = L^{-1} P F from F;  which = 1: G = E U^{-1} from E.
 template <typename T>

@@ -49,6 +49,8 @@ struct PrecBase {
   virtual void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) = 0;
   // How the last-level ILUT ran.
   virtual IlutInfo ilut_info() const = 0;
+  // How level lev's pivot phase ran (size classes and their modes).
+  virtual PivotTiles pivot_tiles(int lev) const = 0;
   // The device status word the solve kernels report to.
   virtual int* status_dev() { return status.p; }
   // Factorizations with fixed rows (the Schur-complement preconditioner's
@@ -91,6 +93,10 @@ struct PrecDev : PrecBase {
                   int32_t* csz, int64_t* bptr, int32_t* bcol, int64_t* voff, double* val) override;
   void export_vec(int lev, int which, double* d, int32_t* iv, int64_t* len) override;
   IlutInfo ilut_info() const override { return last.info; }
+  PivotTiles pivot_tiles(int l) const override {
+    if (l < 0 || l >= (int)lev.size()) fail(VB_EINVAL, "level out of range");
+    return lev[l].tiles;
+  }
 };
 
 // Section 5 global preconditioners (dd.cu): the subdomains of A, their
@@ -143,6 +149,7 @@ struct PrecDD : PrecBase {
     inner->export_vec(lev, which, d, iv, len);
   }
   IlutInfo ilut_info() const override { return inner->ilut_info(); }
+  PivotTiles pivot_tiles(int l) const override { return inner->pivot_tiles(l); }
   int* status_dev() override { return inner->status_dev(); }
 };
 
@@ -184,6 +191,7 @@ struct PrecDDS : PrecBase {
     inner->export_vec(lev, which, d, iv, len);
   }
   IlutInfo ilut_info() const override { return inner->ilut_info(); }
+  PivotTiles pivot_tiles(int l) const override { return inner->pivot_tiles(l); }
   int* status_dev() override { return inner->status_dev(); }
 };
 

@@ -87,6 +87,8 @@ def lib():
                 "vbarms_apply_static_need": (i32, [vp, P(C.c_uint64)]),
                 "vbarms_alloc_count": (C.c_uint64, []),
                 "vbarms_prec_ilut_geometry": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(d)]),
+                "vbarms_prec_pivot_tiles": (i32, [vp, i32, vp, vp, P(i32)]),
+                "vbarms_prec_ilut_chain": (i32, [vp, P(i64)]),
                 "vbarms_vbsr_destroy": (None, [vp]),
                 "vbarms_prec_destroy": (None, [vp]),
             }
@@ -242,6 +244,22 @@ class Prec:
     @property
     def levels(self) -> int:
         return self.stats()["levels"]
+
+    def ilut_chain(self) -> int:
+        """Rows on the longest chain of waits of the last-level ILUT."""
+        n = C.c_int64()
+        _check(lib().vbarms_prec_ilut_chain(self.h, C.byref(n)))
+        return n.value
+
+    def pivot_tiles(self, lev: int) -> dict:
+        """Blocks per size class of level lev's pivot phase and the mode each
+        class ran in (thread or warp per block), and how the modes were chosen."""
+        cnt = np.zeros(5, np.int32)
+        md = np.zeros(5, np.int32)
+        src = C.c_int()
+        _check(lib().vbarms_prec_pivot_tiles(self.h, int(lev), _hp(cnt), _hp(md), C.byref(src)))
+        return dict(counts=cnt.tolist(), modes=[["thread", "warp"][m] for m in md],
+                    source=["default", "timed", "cached"][src.value])
 
     def ilut_geometry(self) -> dict:
         """The per-warp workspace of the last-level ILUT and how it was chosen."""

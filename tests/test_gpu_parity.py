@@ -226,3 +226,42 @@ def test_ilut_geometry_is_timed_then_reused_and_results_do_not_depend_on_it():
     x = torch.zeros(m.n, dtype=torch.float64, device="cuda")
     its, rr, st = V.fgmres_solve(A, P1, b, x, rtol=1e-8)
     assert st == V.VB_OK
+
+
+def test_pivot_phase_size_classes_are_reported_and_factors_unchanged():
+    """The pivot phase runs over block-size-class queues: the class counts add
+    up to the pivot blocks of the level, every class names its mode, a class
+    of 1024 blocks or more is timed once and then taken from the cache, and
+    the factors of the timed and the cached run are identical."""
+    V = vb()
+    m = synth.geometric(60000, 4, seed=11)
+    A = gpu_compress(m, 0.8)
+    P1 = V.vbarms_factor(A, 2, 1e-3, 20)
+    P2 = V.vbarms_factor(A, 2, 1e-3, 20)
+    for lev in range(P1.levels):
+        t1, t2 = P1.pivot_tiles(lev), P2.pivot_tiles(lev)
+        assert sum(t1["counts"]) == P1.shape(lev, "D")["nbr"]
+        assert all(md in ("thread", "warp") for md in t1["modes"])
+        assert t1["modes"] == t2["modes"] and t2["source"] in ("default", "cached")
+        assert np.array_equal(P1.export(lev, "D")["val"], P2.export(lev, "D")["val"])
+        assert np.array_equal(P1.vector(lev, "piv"), P2.vector(lev, "piv"))
+    assert P1.pivot_tiles(0)["source"] in ("timed", "cached")
+    with pytest.raises(V.VbarmsError):
+        P1.pivot_tiles(P1.levels)
+
+
+def test_ilut_wait_chain_bounds_the_kept_l_depth():
+    """The ILUT reports its longest chain of waits: every kept L block is a
+    wait, so the chain is at least the depth of the kept L pattern (longest
+    path computed here on the host), and at most the last level's rows."""
+    V = vb()
+    m = synth.geometric(8000, 4, seed=12)
+    A = gpu_compress(m, 0.8)
+    P = V.vbarms_factor(A, 2, 1e-3, 20)
+    L = P.export(P.levels, "L")
+    depth = np.zeros(len(L["bptr"]) - 1, np.int64)
+    for i in range(len(depth)):
+        cols = L["bcol"][L["bptr"][i]:L["bptr"][i + 1]]
+        depth[i] = 1 + (depth[cols].max() if len(cols) else 0)
+    chain = P.ilut_chain()
+    assert depth.max() <= chain <= len(depth), (depth.max(), chain, len(depth))
