@@ -220,8 +220,8 @@ def cpu_model() -> str:
 
 class OneCore:
     """Pin the calling thread to one host core for the oracle (the oracle is
-    single-threaded; pinning keeps it on one core as the survey's taskset
-    -c 0 would), restoring the previous affinity afterwards."""
+    single-threaded; pinning keeps it on one core, as `taskset -c 0` would),
+    restoring the previous affinity afterwards."""
 
     def __enter__(self):
         self.prev = None

@@ -162,6 +162,113 @@ __global__ void __launch_bounds__(32) k_gr_greedy(int64_t p, const int32_t* __re
   if (lane == 0) *ngroups = G;
 }
 
+// The same greedy with the marks and the eligibility flags as bit masks in
+// shared memory (level matrices of up to GR_SHMAX supernodes): mark tests
+// cost a shared load, and the members' neighbours are marked in one pass
+// over their flattened adjacency.  Same result as k_gr_greedy.
+constexpr int64_t GR_SHMAX = 880000;  // supernodes whose two masks fit in 220 KB
+
+__global__ void k_gr_elig(int64_t p, const double* __restrict__ w, double ddtol, const int32_t* __restrict__ fixed,
+                          uint32_t* __restrict__ elig) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p; v += (int64_t)gridDim.x * blockDim.x) {
+    if (!(w[v] < ddtol) && !(fixed && fixed[v])) atomicOr(&elig[v >> 5], 1u << (v & 31));
+  }
+}
+
+__global__ void __launch_bounds__(32) k_gr_greedy_sh(int64_t p, const int32_t* __restrict__ order,
+                                                     const int64_t* __restrict__ aptr,
+                                                     const int32_t* __restrict__ acol,
+                                                     const uint32_t* __restrict__ elig_g, int gs,
+                                                     int32_t* __restrict__ gid, int* __restrict__ ngroups) {
+  extern __shared__ uint32_t gr_sh[];
+  __shared__ int32_t grp[GR_GSMAX];
+  __shared__ int64_t nb0[GR_GSMAX];
+  __shared__ int32_t nbc[GR_GSMAX + 1];
+  const int lane = threadIdx.x & 31;
+  const int64_t nwd = (p + 31) >> 5;
+  uint32_t* mark = gr_sh;
+  uint32_t* elig = gr_sh + nwd;
+  for (int64_t q = lane; q < nwd; q += 32) {
+    mark[q] = 0u;
+    elig[q] = elig_g[q];
+  }
+  __syncwarp();
+  auto marked = [&](int v) { return (mark[v >> 5] >> (v & 31)) & 1u; };
+  auto eligible = [&](int v) { return (elig[v >> 5] >> (v & 31)) & 1u; };
+  auto setmark = [&](int v) { atomicOr(&mark[v >> 5], 1u << (v & 31)); };
+  int G = 0;
+  for (int64_t base = 0; base < p; base += 32) {
+    const int64_t i = base + lane;
+    const int v = i < p ? order[i] : -1;
+    const bool el = v >= 0 && eligible(v);
+    unsigned pend = __ballot_sync(0xffffffffu, el);
+    while (pend) {
+      const bool ok = ((pend >> lane) & 1u) && !marked(v);
+      const unsigned cand = __ballot_sync(0xffffffffu, ok);
+      if (!cand) break;
+      const int src = __ffs(cand) - 1;
+      const int seed = __shfl_sync(0xffffffffu, v, src);
+      pend &= ~((2u << src) - 1u);
+      if (lane == 0) {
+        grp[0] = seed;
+        setmark(seed);
+        gid[seed] = G;
+      }
+      __syncwarp();
+      int n = 1;
+      for (int head = 0; head < n && n < gs; ++head) {
+        const int u = grp[head];
+        const int64_t a1 = aptr[u + 1];
+        for (int64_t a0 = aptr[u]; a0 < a1 && n < gs; a0 += 32) {
+          const int64_t a = a0 + lane;
+          int z = -1;
+          bool take = false;
+          if (a < a1) {
+            z = acol[a];
+            take = !marked(z) && eligible(z);
+          }
+          const unsigned tm = __ballot_sync(0xffffffffu, take);
+          const int rank = __popc(tm & ((1u << lane) - 1u));
+          const int room = gs - n;
+          if (take && rank < room) {
+            grp[n + rank] = z;
+            setmark(z);
+            gid[z] = G;
+          }
+          n += min(__popc(tm), room);
+          __syncwarp();
+        }
+      }
+      // every member's neighbours, in one pass over the flattened lists
+      for (int k = lane; k < n; k += 32) {
+        const int u = grp[k];
+        nb0[k] = aptr[u];
+        nbc[k] = (int32_t)(aptr[u + 1] - aptr[u]);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        int acc = 0;
+        for (int k = 0; k < n; ++k) {
+          const int c = nbc[k];
+          nbc[k] = acc;
+          acc += c;
+        }
+        nbc[n] = acc;
+      }
+      __syncwarp();
+      const int tot = nbc[n];
+      int k = 0;
+      for (int e = lane; e < tot; e += 32) {
+        while (nbc[k + 1] <= e) ++k;
+        setmark(acol[nb0[k] + (e - nbc[k])]);
+      }
+      __syncwarp();
+      ++G;
+    }
+  }
+  if (lane == 0) *ngroups = G;
+}
+
 // ---- group ranks and the ordering ------------------------------------------
 __global__ void k_gr_gmin(int64_t p, const int32_t* __restrict__ gid, int32_t* __restrict__ gmin,
                           int32_t* __restrict__ gcnt) {
@@ -1010,11 +1117,22 @@ int64_t group_order(const VBDev<TA>& A, double ddtol, int gs, const int32_t* fix
     radix_sort_u64(wk, &order, p, 64, s);
   }
   // the greedy
-  DBuf<int32_t> mark(p, s), gid(p, s);
+  DBuf<int32_t> gid(p, s);
   DBuf<int> ng_dev(1, s);
-  mark.zero();
   launch(k_gr_fill, grid_for(p, 256), 256, 0, s, p, -1, gid.p);
-  launch(k_gr_greedy, 1, 32, 0, s, p, order.p, aptr.p, acol.p, w.p, ddtol, fixed, gs, mark.p, gid.p, ng_dev.p);
+  if (p <= GR_SHMAX) {
+    const int64_t nwd = (p + 31) >> 5;
+    DBuf<uint32_t> elig(nwd, s);
+    elig.zero();
+    launch(k_gr_elig, grid_for(p, 256), 256, 0, s, p, w.p, ddtol, fixed, elig.p);
+    const size_t smem = (size_t)2 * nwd * sizeof(uint32_t);
+    VB_CUDA(cudaFuncSetAttribute(k_gr_greedy_sh, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    launch(k_gr_greedy_sh, 1, 32, smem, s, p, order.p, aptr.p, acol.p, elig.p, gs, gid.p, ng_dev.p);
+  } else {
+    DBuf<int32_t> mark(p, s);
+    mark.zero();
+    launch(k_gr_greedy, 1, 32, 0, s, p, order.p, aptr.p, acol.p, w.p, ddtol, fixed, gs, mark.p, gid.p, ng_dev.p);
+  }
   VB_LAUNCH_CHECK();
   const int64_t ng = d2h(ng_dev.p, s);
   ngroups = ng;
