@@ -11,7 +11,7 @@
 // (build with -ffp-contract=off), evaluated in the order written here.
 //
 // Readings of points the paper leaves open (R1-R9; T1-T3 at compress_two_pass and G1-G5
-// at graph_compress; D1-D7 for Section 5):
+// at graph_compress; A1-A3 for groups of several supernodes in Step 3; D1-D7 for Section 5):
 //  R1  similarity of rows i,j (Section 2.1): cos = |P_i n P_j| / sqrt(|P_i||P_j|)
 //      on the stored pattern of the rows; j joins i's group iff cos >= tau,
 //      tested exactly as (double)(c*c) >= (tau*tau) * (double)(|P_i||P_j|).
