@@ -94,4 +94,51 @@ __device__ __forceinline__ bool gepp_block(double* a, int m, int32_t* pv) {
   return true;
 }
 
+// The same with the 32 lanes of a warp: the pivot by a warp reduction
+// (largest magnitude, lowest row on ties), the multipliers and the trailing
+// update over lanes; every element receives gepp_block's operations in its
+// order, so the factors are the same bit for bit.  All lanes return the
+// same value.
+__device__ __forceinline__ bool gepp_block_warp(double* a, int m, int32_t* pv, int lane) {
+  for (int k = 0; k < m; ++k) {
+    double best = -1.0;
+    int p = 0x7fffffff;
+    for (int i = k + lane; i < m; i += 32) {
+      const double v = fabs(a[i * m + k]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int op = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ob > best || (ob == best && op < p)) {
+        best = ob;
+        p = op;
+      }
+    }
+    if (best == 0.0) return false;
+    if (lane == 0) pv[k] = p;
+    if (p != k)
+      for (int j = lane; j < m; j += 32) {
+        const double t = a[k * m + j];
+        a[k * m + j] = a[p * m + j];
+        a[p * m + j] = t;
+      }
+    __syncwarp();
+    const double d = a[k * m + k];
+    const int w = m - k - 1;
+    for (int r = lane; r < w; r += 32) a[(k + 1 + r) * m + k] = __ddiv_rn(a[(k + 1 + r) * m + k], d);
+    __syncwarp();
+    for (int e = lane; e < w * w; e += 32) {
+      const int r = e / w, c = e - r * w;
+      const int i = k + 1 + r, j = k + 1 + c;
+      a[i * m + j] = __dsub_rn(a[i * m + j], __dmul_rn(a[i * m + k], a[k * m + j]));
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
 }  // namespace vb

@@ -489,16 +489,18 @@ __device__ __forceinline__ void gr_linvp(const double* lu, const int32_t* pv, in
 }
 
 // Keep at most lfil of n candidates (largest f2, lower column on ties); the
-// kept ones flagged in keep[].  One lane.
-__device__ void gr_lfil(int n, const int32_t* col, const double* f2, int8_t* keep, int lfil) {
-  for (int i = 0; i < n; ++i) keep[i] = 1;
-  if (lfil < 0 || n <= lfil) return;
-  for (int i = 0; i < n; ++i) {
+// kept ones flagged in keep[].  The warp's lanes rank one candidate each.
+__device__ void gr_lfil(int n, const int32_t* col, const double* f2, int8_t* keep, int lfil, int lane) {
+  __syncwarp();
+  const bool all = lfil < 0 || n <= lfil;
+  for (int i = lane; i < n; i += 32) {
     int better = 0;
-    for (int j = 0; j < n; ++j)
-      if (f2[j] > f2[i] || (f2[j] == f2[i] && col[j] < col[i])) ++better;
-    keep[i] = better < lfil ? 1 : 0;
+    if (!all)
+      for (int j = 0; j < n; ++j)
+        if (f2[j] > f2[i] || (f2[j] == f2[i] && col[j] < col[i])) ++better;
+    keep[i] = all || better < lfil ? 1 : 0;
   }
+  __syncwarp();
 }
 
 // ---- F-column union of every group -----------------------------------------
@@ -726,8 +728,8 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
         __syncwarp();
       }
       // lfil on the multipliers, then the kept ones in ascending column order
-      if (lane == 0) {
-        gr_lfil(nl, cc, f2, keep, lfil);
+      gr_lfil(nl, cc, f2, keep, lfil, lane);
+      {
         int64_t vo = oL.vslot[y];
         int c = 0;
         for (int q = 0; q < nl; ++q) {
@@ -735,12 +737,12 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
           const int kk = cc[q] - (int)y0;
           const int nk = Dm.rsz[cc[q]];
           const double* m = wD + (int64_t)ny * doff[kk];
-          for (int e = 0; e < ny * nk; ++e) Lv[vo + e] = (T)m[e];
-          oL.col[oL.slot[y] + c] = cc[q];
+          for (int e = lane; e < ny * nk; e += 32) Lv[vo + e] = (T)m[e];
+          if (lane == 0) oL.col[oL.slot[y] + c] = cc[q];
           vo += (int64_t)ny * nk;
           ++c;
         }
-        oL.cnt[y] = c;
+        if (lane == 0) oL.cnt[y] = c;
       }
       __syncwarp();
       // the pivot block
@@ -752,9 +754,7 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
       int32_t* pv = piv + Dm.roff[y];
       for (int e = lane; e < ny * ny; e += 32) lu[e] = wD[(int64_t)ny * doff[yy] + e];
       __syncwarp();
-      int ok = 1;
-      if (lane == 0) ok = gepp_block(lu, ny, pv) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
+      const bool ok = gepp_block_warp(lu, ny, pv, lane);
       if (!ok) {
         if (lane == 0) dev_fail(st, DEV_ESINGULAR);
         break;
@@ -780,8 +780,8 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
         }
         __syncwarp();
       }
-      if (lane == 0) {
-        gr_lfil(nc, cc, f2, keep, lfil);
+      gr_lfil(nc, cc, f2, keep, lfil, lane);
+      {
         int64_t vo = oU.vslot[y];
         int c = 0;
         for (int q = 0; q < nc; ++q) {
@@ -789,12 +789,12 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
           const int jj = cc[q] - (int)y0;
           const int nj = Dm.rsz[cc[q]];
           const double* x = wD + (int64_t)ny * doff[jj];
-          for (int e = 0; e < ny * nj; ++e) Uv[vo + e] = (T)x[e];
-          oU.col[oU.slot[y] + c] = cc[q];
+          for (int e = lane; e < ny * nj; e += 32) Uv[vo + e] = (T)x[e];
+          if (lane == 0) oU.col[oU.slot[y] + c] = cc[q];
           vo += (int64_t)ny * nj;
           ++c;
         }
-        oU.cnt[y] = c;
+        if (lane == 0) oU.cnt[y] = c;
       }
       __syncwarp();
       // W part
@@ -817,9 +817,9 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
         }
         __syncwarp();
       }
-      if (lane == 0) {
-        // lfil compares columns: the union is sorted, so u orders like the column
-        gr_lfil(nc, cc, f2, keep, lfil);
+      // lfil compares columns: the union is sorted, so u orders like the column
+      gr_lfil(nc, cc, f2, keep, lfil, lane);
+      {
         int64_t vo = oW.vslot[y];
         int c = 0;
         for (int q = 0; q < nc; ++q) {
@@ -827,12 +827,12 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
           const int u = cc[q];
           const int ns = Csz[ucol[u]];
           const double* x = wF + (int64_t)ny * uoff[u];
-          for (int e = 0; e < ny * ns; ++e) Wv[vo + e] = (T)x[e];
-          oW.col[oW.slot[y] + c] = ucol[u];
+          for (int e = lane; e < ny * ns; e += 32) Wv[vo + e] = (T)x[e];
+          if (lane == 0) oW.col[oW.slot[y] + c] = ucol[u];
           vo += (int64_t)ny * ns;
           ++c;
         }
-        oW.cnt[y] = c;
+        if (lane == 0) oW.cnt[y] = c;
       }
       __syncwarp();
     }
@@ -939,9 +939,9 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
       ++nc;
       __syncwarp();
     }
-    if (lane == 0) {
-      // lfil compares columns: workspace positions order like the columns
-      gr_lfil(nc, cc, f2, keep, lfil);
+    // lfil compares columns: workspace positions order like the columns
+    gr_lfil(nc, cc, f2, keep, lfil, lane);
+    {
       int64_t vo = oG.vslot[r];
       int c = 0;
       for (int q = 0; q < nc; ++q) {
@@ -949,12 +949,12 @@ __global__ void __launch_bounds__(GR_WARPS * 32)
         const int i = cc[q];
         const int nk = dsz[col[i]];
         const double* m = ws + (int64_t)nr * off[i];
-        for (int e = 0; e < nr * nk; ++e) Gv[vo + e] = (T)m[e];
-        oG.col[oG.slot[r] + c] = col[i];
+        for (int e = lane; e < nr * nk; e += 32) Gv[vo + e] = (T)m[e];
+        if (lane == 0) oG.col[oG.slot[r] + c] = col[i];
         vo += (int64_t)nr * nk;
         ++c;
       }
-      oG.cnt[r] = c;
+      if (lane == 0) oG.cnt[r] = c;
     }
     __syncwarp();
   }
