@@ -434,6 +434,179 @@ __device__ float inv_norm1_f32(const float* a, int n, const int* pv, int lane) {
   return cs;
 }
 
+// ---- pivot blocks of at most 8 rows (FP32), held in registers ---------------
+// The block size is a template argument, so every loop is unrolled and no
+// array is indexed at run time.  Each routine gives every element the
+// operations of its generic counterpart (ainv_right_row_sh, gepp_warp,
+// inv_norm1_f32) in the same order, so the results are identical bit for
+// bit; only the latency of the dependent chain changes.
+
+// x (one row of length N, shared or global memory) <- x (P^T L U)^{-1}.
+template <int N>
+__device__ __forceinline__ void ainv_right_row_n(const float* lu, const int* pv, float* x) {
+  float r[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) r[j] = x[j];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    float s = r[j];
+#pragma unroll
+    for (int q = 0; q < j; ++q) s = msub<float>(s, r[q], lu[q * N + j]);
+    r[j] = s / lu[j * N + j];
+  }
+#pragma unroll
+  for (int j = N - 1; j >= 0; --j) {
+    float s = r[j];
+#pragma unroll
+    for (int q = j + 1; q < N; ++q) s = msub<float>(s, r[q], lu[q * N + j]);
+    r[j] = s;
+  }
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    const int p = pv[k];
+#pragma unroll
+    for (int q = k + 1; q < N; ++q)
+      if (q == p) {
+        const float t = r[k];
+        r[k] = r[q];
+        r[q] = t;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) x[j] = r[j];
+}
+
+// GEPP of the N x N row-major block a (shared memory), row i in lane i's
+// registers: the pivot is the largest |a_ik| (lowest row on ties) found by a
+// warp max-reduction of the keys and a ballot; interchanges and the pivot
+// row travel by shuffles.  Pivot rows go to gpiv (and pvs when not null).
+template <int N>
+__device__ __forceinline__ bool gepp_n(float* a, int* pvs, int32_t* gpiv, int lane) {
+  float r[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) r[j] = lane < N ? a[lane * N + j] : 0.f;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const unsigned key = (lane >= k && lane < N) ? (unsigned)abs_key(r[k]) + 1u : 0u;
+    const unsigned mk = __reduce_max_sync(0xffffffffu, key);
+    if (mk <= 1u) {  // the pivot column is exactly zero
+      ok = false;
+      break;
+    }
+    const int p = __ffs(__ballot_sync(0xffffffffu, key == mk)) - 1;
+    if (lane == 0) {
+      gpiv[k] = p;
+      if (pvs) pvs[k] = p;
+    }
+    if (p != k) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const float vk = __shfl_sync(0xffffffffu, r[j], k);
+        const float vp = __shfl_sync(0xffffffffu, r[j], p);
+        if (lane == k) r[j] = vp;
+        if (lane == p) r[j] = vk;
+      }
+    }
+    float u[N];
+#pragma unroll
+    for (int j = k; j < N; ++j) u[j] = __shfl_sync(0xffffffffu, r[j], k);
+    if (lane > k && lane < N) {
+      const float l = div_rn<float>(r[k], u[k]);
+      r[k] = l;
+#pragma unroll
+      for (int j = k + 1; j < N; ++j) r[j] = msub<float>(r[j], l, u[j]);
+    }
+  }
+  if (lane < N) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) a[lane * N + j] = r[j];
+  }
+  __syncwarp();
+  return ok;
+}
+
+// ||B^{-1}||_1 of a GEPP-factored N x N block: lane c solves B x = e_c in
+// registers; the largest column sum, on every lane.
+template <int N>
+__device__ __forceinline__ float inv_norm1_n(const float* a, const int* pv, int lane) {
+  float cs = 0.f;
+  if (lane < N) {
+    float x[N];
+#pragma unroll
+    for (int ii = 0; ii < N; ++ii) x[ii] = ii == lane ? 1.f : 0.f;
+#pragma unroll
+    for (int kk = 0; kk < N; ++kk) {
+      const int pk = pv[kk];
+#pragma unroll
+      for (int q = kk + 1; q < N; ++q)
+        if (q == pk) {
+          const float t = x[kk];
+          x[kk] = x[q];
+          x[q] = t;
+        }
+    }
+#pragma unroll
+    for (int ii = 1; ii < N; ++ii) {
+      float sum = x[ii];
+#pragma unroll
+      for (int kk = 0; kk < ii; ++kk) sum = __fmaf_rn(-a[ii * N + kk], x[kk], sum);
+      x[ii] = sum;
+    }
+#pragma unroll
+    for (int ii = N - 1; ii >= 0; --ii) {
+      float sum = x[ii];
+#pragma unroll
+      for (int kk = ii + 1; kk < N; ++kk) sum = __fmaf_rn(-a[ii * N + kk], x[kk], sum);
+      x[ii] = __fdiv_rn(sum, a[ii * N + ii]);
+    }
+#pragma unroll
+    for (int ii = 0; ii < N; ++ii) cs += fabsf(x[ii]);
+  }
+  for (int o = 16; o > 0; o >>= 1) cs = fmaxf(cs, __shfl_xor_sync(0xffffffffu, cs, o));
+  return cs;
+}
+
+// Dispatch on the block size (false / a negative norm: larger than 8, the
+// caller takes the generic routine).
+__device__ __forceinline__ bool ainv_right_row_small(const float* lu, const int* pv, int m, float* x) {
+  switch (m) {
+    case 1: ainv_right_row_n<1>(lu, pv, x); return true;
+    case 2: ainv_right_row_n<2>(lu, pv, x); return true;
+    case 3: ainv_right_row_n<3>(lu, pv, x); return true;
+    case 4: ainv_right_row_n<4>(lu, pv, x); return true;
+    case 5: ainv_right_row_n<5>(lu, pv, x); return true;
+    case 6: ainv_right_row_n<6>(lu, pv, x); return true;
+    case 7: ainv_right_row_n<7>(lu, pv, x); return true;
+    case 8: ainv_right_row_n<8>(lu, pv, x); return true;
+    default: return false;
+  }
+}
+__device__ __forceinline__ bool gepp_small(float* a, int n, int* pvs, int32_t* gpiv, int lane) {
+  switch (n) {
+    case 1: return gepp_n<1>(a, pvs, gpiv, lane);
+    case 2: return gepp_n<2>(a, pvs, gpiv, lane);
+    case 3: return gepp_n<3>(a, pvs, gpiv, lane);
+    case 4: return gepp_n<4>(a, pvs, gpiv, lane);
+    case 5: return gepp_n<5>(a, pvs, gpiv, lane);
+    case 6: return gepp_n<6>(a, pvs, gpiv, lane);
+    case 7: return gepp_n<7>(a, pvs, gpiv, lane);
+    default: return gepp_n<8>(a, pvs, gpiv, lane);
+  }
+}
+__device__ __forceinline__ float inv_norm1_small(const float* a, int n, const int* pv, int lane) {
+  switch (n) {
+    case 1: return inv_norm1_n<1>(a, pv, lane);
+    case 2: return inv_norm1_n<2>(a, pv, lane);
+    case 3: return inv_norm1_n<3>(a, pv, lane);
+    case 4: return inv_norm1_n<4>(a, pv, lane);
+    case 5: return inv_norm1_n<5>(a, pv, lane);
+    case 6: return inv_norm1_n<6>(a, pv, lane);
+    case 7: return inv_norm1_n<7>(a, pv, lane);
+    default: return inv_norm1_n<8>(a, pv, lane);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies into shared memory, completing on an mbarrier.
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -974,8 +1147,13 @@ __global__ void __launch_bounds__(256, 2)
           if (staged) {
             if (lu64)
               ainv_right_row_sh<T, double, double>(reinterpret_cast<const double*>(rec + RL.lu), rpiv, nk, m + a * nk);
-            else
-              ainv_right_row_sh<T, float, T>(reinterpret_cast<const T*>(rec + RL.lu), rpiv, nk, m + a * nk);
+            else {
+              bool small = false;
+              if constexpr (std::is_same<T, float>::value)
+                small = ainv_right_row_small(reinterpret_cast<const float*>(rec + RL.lu), rpiv, nk, m + a * nk);
+              if (!small)
+                ainv_right_row_sh<T, float, T>(reinterpret_cast<const T*>(rec + RL.lu), rpiv, nk, m + a * nk);
+            }
           } else {
             if (lu64)
               ainv_right_row<T, double>(reinterpret_cast<const double*>(rec + RL.lu), rpiv, nk, m + a * nk);
@@ -1222,8 +1400,10 @@ __global__ void __launch_bounds__(256, 2)
         }
         for (int o = 16; o > 0; o >>= 1) norm1 = fmaxf(norm1, __shfl_xor_sync(0xffffffffu, norm1, o));
         __syncwarp();
-        if (ni <= 32 && gepp_warp<float>(a, ni, pvs, gpiv, lane)) {
-          const float kappa = norm1 * inv_norm1_f32(a, ni, pvs ? pvs : gpiv, lane);
+        const bool small = ni <= 8 && pvs;  // registers; M.pv holds the interchanges
+        if (small ? gepp_small(a, ni, pvs, gpiv, lane) : (ni <= 32 && gepp_warp<float>(a, ni, pvs, gpiv, lane))) {
+          const float kappa = norm1 * (small ? inv_norm1_small(a, ni, pvs, lane)
+                                             : inv_norm1_f32(a, ni, pvs ? pvs : gpiv, lane));
           tag64 = !(kappa <= condf);
           if (!tag64) {
             for (int e = lane; e < ni * ni; e += 32) {
