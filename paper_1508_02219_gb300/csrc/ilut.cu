@@ -146,6 +146,8 @@ struct IlutMisc {
   int qnj[32];
   int qpre[33];        // element prefix of a chunk's blocks
   int pv[PVMAX];       // GEPP interchanges of the row's own diagonal block
+  float lu32[64];      // the row's FP32 pivot LU (at most 8 x 8) for its record
+  float mbuf[64];      // a step's FP32 multiplier (at most 64 values) for its update
   int nl, nslots, flag, pad;
 };
 
@@ -298,10 +300,13 @@ __device__ __forceinline__ double fro2_batched(const T* __restrict__ v, int n) {
 template <typename T>
 __device__ __forceinline__ float fro2_f32(const T* __restrict__ v, int n) {
   float s = 0.f;
-#pragma unroll 4
-  for (int e = 0; e < n; ++e) {
-    const float x = (float)v[e];
-    s = __fmaf_rn(x, x, s);
+  for (int e0 = 0; e0 < n; e0 += 16) {  // sixteen loads in flight, summed in element order
+    float x[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = e0 + u < n ? (float)v[e0 + u] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (e0 + u < n) s = __fmaf_rn(x[u], x[u], s);
   }
   return s;
 }
@@ -443,7 +448,7 @@ __device__ float inv_norm1_f32(const float* a, int n, const int* pv, int lane) {
 
 // x (one row of length N, shared or global memory) <- x (P^T L U)^{-1}.
 template <int N>
-__device__ __forceinline__ void ainv_right_row_n(const float* lu, const int* pv, float* x) {
+__device__ __forceinline__ void ainv_right_row_n(const float* lu, const int* pv, float* x, float* x2) {
   float r[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) r[j] = x[j];
@@ -474,6 +479,10 @@ __device__ __forceinline__ void ainv_right_row_n(const float* lu, const int* pv,
   }
 #pragma unroll
   for (int j = 0; j < N; ++j) x[j] = r[j];
+  if (x2) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) x2[j] = r[j];
+  }
 }
 
 // GEPP of the N x N row-major block a (shared memory), row i in lane i's
@@ -569,16 +578,16 @@ __device__ __forceinline__ float inv_norm1_n(const float* a, const int* pv, int 
 
 // Dispatch on the block size (false / a negative norm: larger than 8, the
 // caller takes the generic routine).
-__device__ __forceinline__ bool ainv_right_row_small(const float* lu, const int* pv, int m, float* x) {
+__device__ __forceinline__ bool ainv_right_row_small(const float* lu, const int* pv, int m, float* x, float* x2) {
   switch (m) {
-    case 1: ainv_right_row_n<1>(lu, pv, x); return true;
-    case 2: ainv_right_row_n<2>(lu, pv, x); return true;
-    case 3: ainv_right_row_n<3>(lu, pv, x); return true;
-    case 4: ainv_right_row_n<4>(lu, pv, x); return true;
-    case 5: ainv_right_row_n<5>(lu, pv, x); return true;
-    case 6: ainv_right_row_n<6>(lu, pv, x); return true;
-    case 7: ainv_right_row_n<7>(lu, pv, x); return true;
-    case 8: ainv_right_row_n<8>(lu, pv, x); return true;
+    case 1: ainv_right_row_n<1>(lu, pv, x, x2); return true;
+    case 2: ainv_right_row_n<2>(lu, pv, x, x2); return true;
+    case 3: ainv_right_row_n<3>(lu, pv, x, x2); return true;
+    case 4: ainv_right_row_n<4>(lu, pv, x, x2); return true;
+    case 5: ainv_right_row_n<5>(lu, pv, x, x2); return true;
+    case 6: ainv_right_row_n<6>(lu, pv, x, x2); return true;
+    case 7: ainv_right_row_n<7>(lu, pv, x, x2); return true;
+    case 8: ainv_right_row_n<8>(lu, pv, x, x2); return true;
     default: return false;
   }
 }
@@ -807,6 +816,18 @@ __device__ int lfil_cut(int* cand, int n, int lfil, const long long* sf2, const 
 __device__ int sort_by_column(const int* cand, int k, const int* scol, unsigned long long* srt, int lane) {
   int n2 = 1;
   while (n2 < k) n2 <<= 1;
+  if (k <= 32) {  // the keys are distinct: each goes to its rank
+    const unsigned long long key =
+        lane < k ? ((unsigned long long)(unsigned)scol[cand[lane]] << 32) | (unsigned)cand[lane] : ~0ull;
+    int rank = 0;
+    for (int j = 0; j < k; ++j) rank += __shfl_sync(0xffffffffu, key, j) < key ? 1 : 0;
+    if (lane < k)
+      srt[rank] = key;
+    else if (lane < n2)
+      srt[lane] = ~0ull;
+    __syncwarp();
+    return n2;
+  }
   for (int p = lane; p < n2; p += 32)
     srt[p] = p < k ? ((unsigned long long)(unsigned)scol[cand[p]] << 32) | (unsigned)cand[p] : ~0ull;
   __syncwarp();
@@ -1142,7 +1163,14 @@ __global__ void __launch_bounds__(256, 2)
         const int* rnj = reinterpret_cast<const int*>(rec + RL.unj);
         const T* rval = reinterpret_cast<const T*>(rec + RL.val);
         T* m = wv + soff[sk];
-        // the multiplier m = a_ik (P^T L U)_k^{-1}, in place, one lane per row
+        // the multiplier m = a_ik (P^T L U)_k^{-1}, in place, one lane per row;
+        // an FP32 multiplier of at most 64 values is also kept in M.mbuf, where
+        // the drop test and the update read it
+        bool mb = false;
+        if constexpr (std::is_same<T, float>::value) mb = staged && !lu64 && nk <= 8 && ni * nk <= 64;
+        const T* msrc = m;
+        if constexpr (std::is_same<T, float>::value)
+          if (mb) msrc = M.mbuf;
         for (int a = lane; a < ni; a += 32) {
           if (staged) {
             if (lu64)
@@ -1150,7 +1178,8 @@ __global__ void __launch_bounds__(256, 2)
             else {
               bool small = false;
               if constexpr (std::is_same<T, float>::value)
-                small = ainv_right_row_small(reinterpret_cast<const float*>(rec + RL.lu), rpiv, nk, m + a * nk);
+                small = ainv_right_row_small(reinterpret_cast<const float*>(rec + RL.lu), rpiv, nk, m + a * nk,
+                                             mb ? M.mbuf + a * nk : nullptr);
               if (!small)
                 ainv_right_row_sh<T, float, T>(reinterpret_cast<const T*>(rec + RL.lu), rpiv, nk, m + a * nk);
             }
@@ -1173,7 +1202,7 @@ __global__ void __launch_bounds__(256, 2)
         } else {  // mixed factor: FP32 squares summed by a warp reduction
           float sf = 0.f;
           for (int e = lane; e < ni * nk; e += 32) {
-            const float x = (float)m[e];
+            const float x = (float)msrc[e];
             sf = __fmaf_rn(x, x, sf);
           }
           for (int o = 16; o > 0; o >>= 1) sf += __shfl_xor_sync(0xffffffffu, sf, o);
@@ -1316,9 +1345,9 @@ __global__ void __launch_bounds__(256, 2)
               const T* U = rval + uo4[u];
               T av = acc[u];
               if (staged) {
-                for (int r = 0; r < nk; ++r) av = msub<T>(av, m[a4[u] * nk + r], U[r * nj4[u] + jj4[u]]);
+                for (int r = 0; r < nk; ++r) av = msub<T>(av, msrc[a4[u] * nk + r], U[r * nj4[u] + jj4[u]]);
               } else {
-                for (int r = 0; r < nk; ++r) av = msub<T>(av, m[a4[u] * nk + r], __ldcg(U + r * nj4[u] + jj4[u]));
+                for (int r = 0; r < nk; ++r) av = msub<T>(av, msrc[a4[u] * nk + r], __ldcg(U + r * nj4[u] + jj4[u]));
               }
               *dst[u] = av;
             }
@@ -1379,6 +1408,7 @@ __global__ void __launch_bounds__(256, 2)
     // inverse columns); a block above the threshold, larger than 32, or
     // singular in FP32 is factored again in FP64 and tagged.
     bool tag64 = sizeof(T) == sizeof(double);
+    bool lu_sm = false;  // the FP32 pivot LU is in M.lu32
     if (status_local == 0) {
       const T* srcd = wv + soff[dslot];
       unsigned char* gb = stage0;
@@ -1406,9 +1436,11 @@ __global__ void __launch_bounds__(256, 2)
                                              : inv_norm1_f32(a, ni, pvs ? pvs : gpiv, lane));
           tag64 = !(kappa <= condf);
           if (!tag64) {
+            lu_sm = small;
             for (int e = lane; e < ni * ni; e += 32) {
               if (gs32) dg32[dgoff[i] + e] = a[e];
               dg[dgoff[i] + e] = (double)a[e];
+              if (small) M.lu32[e] = a[e];
             }
           }
         }
@@ -1547,12 +1579,12 @@ __global__ void __launch_bounds__(256, 2)
         h[3] = (int)vu;
       }
       const int32_t* gpiv = piv + A.roff[i];
-      for (int a = lane; a < ni; a += 32) reinterpret_cast<int*>(r + RL.piv)[a] = gpiv[a];
+      for (int a = lane; a < ni; a += 32) reinterpret_cast<int*>(r + RL.piv)[a] = ni <= PVMAX ? M.pv[a] : gpiv[a];
       for (int e = lane; e < ni * ni; e += 32) {
         if (lu64r)
           reinterpret_cast<double*>(r + RL.lu)[e] = dg[dgoff[i] + e];
         else
-          reinterpret_cast<float*>(r + RL.lu)[e] = dg32[dgoff[i] + e];
+          reinterpret_cast<float*>(r + RL.lu)[e] = lu_sm ? M.lu32[e] : dg32[dgoff[i] + e];
       }
       int* rcol = reinterpret_cast<int*>(r + RL.ucol);
       int* rrel = reinterpret_cast<int*>(r + RL.urel);
