@@ -11,8 +11,9 @@
 //
 // The warp keeps its working row in a private workspace (hash table column ->
 // slot, dense values): in shared memory when the row fits, else in global
-// memory (a shared row whose fill outgrows the buffer starts again in the
-// global one).  The size of the shared workspace is chosen at launch from the
+// memory (a shared row whose fill would outgrow the buffer moves, slots and
+// values as they are, to the global one before the blocks that overflow it are
+// created).  The size of the shared workspace is chosen by timing from the
 // last-level matrix (rows of a few large blocks, or rows of many small ones).
 // The warp eliminates its L part in ascending column order including fill.
 // For each column k it needs row k's factored pivot block and its U row:
@@ -1268,6 +1269,50 @@ __global__ void __launch_bounds__(256, 2)
             }
           }
           __syncwarp();
+          // A shared working row that this chunk's new blocks would overflow
+          // moves to the warp's global workspace first: slot numbers (so the
+          // pending L columns and the lookups above), value offsets and the
+          // multiplier's values stay as they are; the global hash is rebuilt.
+          // (When the global workspace is too small as well, the creation
+          // below fails and the row takes the overflow path.)
+          if (in_sh) {
+            const unsigned mm = __ballot_sync(0xffffffffu, missing);
+            if (mm) {
+              const int add_s = __popc(mm);
+              const int add_v = warp_sum_i(missing ? ni * njq : 0);
+              const int ns0 = *vns;
+              const long long nv0 = (long long)M.nvals;
+              if ((ns0 + add_s > smax_c || nv0 + add_v > vmax_c) && ns0 + add_s <= ws.smax &&
+                  nv0 + add_v <= ws.vmax) {
+                int* const gh = ws.hpos + wid * ws.smax;
+                int* const gc = ws.scol + wid * ws.smax;
+                int* const go = ws.soff + wid * ws.smax;
+                int* const gs = ws.sstate + wid * ws.smax;
+                long long* const gf = ws.sf2 + wid * ws.smax;
+                int* const gn = ws.sncl + wid * ws.smax;
+                T* const gv = wvals_all + wid * ws.vmax;
+                for (int q = lane; q < ns0; q += 32) {
+                  gc[q] = scol[q];
+                  go[q] = soff[q];
+                  gs[q] = sstate[q];
+                  gf[q] = sf2[q];
+                  gn[q] = sncl[q];
+                }
+                for (long long e = lane; e < nv0; e += 32) gv[e] = wv[e];
+                __syncwarp();
+                const uint32_t gmask = (uint32_t)ws.ht - 1;
+                for (int q = lane; q < ns0; q += 32) gh[q] = ws_place(gkeys, gmask, q, gc[q]);
+                for (int q = lane; q < g.hash; q += 32) sh_keys[q] = -1;
+                __syncwarp();
+                keys = gkeys, hpos = gh, scol = gc, soff = go, sstate = gs, sf2 = gf, sncl = gn;
+                wv = gv;
+                smax_c = ws.smax, vmax_c = ws.vmax, hmask = gmask;
+                in_sh = false;
+                m = wv + soff[sk];
+                if (!mb) msrc = m;
+              }
+            }
+          }
           if (missing) {
             const int sz = ni * njq;
             slot = ws_new_slot(smax_c, vmax_c, keys, hpos, scol, soff, sstate, sncl, &M.nslots, &M.nvals, hmask, j,
