@@ -1922,7 +1922,7 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   // process; small matrices take the measured default.  The candidates span
   // what the configured workloads were measured to prefer: 64 or 128 slots,
   // 2 to 8 KB of values, 16 down to 6 warps per SM.  The prefix is 1/64 of
-  // the tickets (2 048 to 16 384), so the three timings add at most about
+  // the tickets (2 048 to 16 384), so the two or three timings add at most about
   // 5 % to the first factorization of a class.
   DBuf<unsigned long long> rstat(2, s);
   rstat.zero();
@@ -1934,7 +1934,11 @@ void ilut_last(LastDev<T>& X, double t, int lfil, bool mixed, double cond_thr, u
   std::vector<IlutGeom> cands;
   cands.push_back((wide && f64) ? make_geom(128, 8192, 2048, 256) : make_geom(64, 2048, 2048, wide ? 256 : 128));
   cands.push_back(make_geom(64, 4096, 2048, 128));
-  cands.push_back(make_geom(128, f64 ? 8192 : 4096, 2048, 256));
+  // Fewer warps per SM means fewer rows in flight; a prefix under-weights
+  // that window, which a matrix of narrow rows depends on (on the 3M-unknown
+  // workload the prefix preferred 12 warps per SM, which ran the whole matrix
+  // 12 % slower than 16), so only wide rows also time the 128-slot shape.
+  if (wide) cands.push_back(make_geom(128, f64 ? 8192 : 4096, 2048, 256));
   const int reserve = 1024;  // shared memory the system keeps per block
   // warps per block and blocks per SM of a geometry: the most warps per SM
   // (at most 16)
