@@ -183,9 +183,19 @@ constexpr int TRI_MR = 16;      // block rows up to this size use the lane-per-b
 constexpr int TRI_STAGE = 1024;  // values of a row staged in shared memory per warp
 constexpr int TRI_XQ = 16;       // dependency values loaded in one batch
 
+constexpr int TRI_PIV = 72;  // per warp: an FP32 pivot LU of up to 8 x 8 and its 8 interchanges
+
 template <typename T>
 constexpr size_t tri_smem() {
-  return (size_t)SW * TRI_STAGE * sizeof(T) + (size_t)SW * 32 * TRI_R * sizeof(double);
+  return (size_t)SW * TRI_STAGE * sizeof(T) + (size_t)SW * 32 * TRI_R * sizeof(double) +
+         (size_t)SW * TRI_PIV * sizeof(float);
+}
+
+// The calling warp's pivot-block buffer in the sweep's shared memory.
+template <typename T>
+__device__ __forceinline__ float* tri_piv_buf(unsigned char* sm) {
+  return (float*)(sm + (size_t)SW * TRI_STAGE * sizeof(T) + (size_t)SW * 32 * TRI_R * sizeof(double)) +
+         (size_t)(threadIdx.x >> 5) * TRI_PIV;
 }
 
 // Sync-free block triangular sweep over the last-level factors, one warp per
@@ -224,6 +234,15 @@ __global__ void __launch_bounds__(SW * 32)
     const int ni = M.rsz[i];
     const int64_t r0 = M.roff[i];
     bool failed = false;
+    // backward sweep, FP32 pivot block of at most 8 rows: the pivot LU and its
+    // interchanges are static, so they come into shared memory before the
+    // waits below and the final solve reads them on chip
+    if (BWD && lu32 && ni <= 8 && !ptag[i]) {
+      float* slu = tri_piv_buf<T>(tri_sm);
+      const int64_t lo = dgoff[i];
+      for (int e = lane; e < ni * ni; e += 32) slu[e] = lu32[lo + e];
+      if (lane < ni) reinterpret_cast<int32_t*>(slu + 64)[lane] = piv[r0 + lane];
+    }
     if (ni <= TRI_MR) {
       const int64_t b0 = M.bptr[i], b1 = M.bptr[i + 1];
       const int64_t v0 = M.voff[b0];
@@ -306,7 +325,10 @@ __global__ void __launch_bounds__(SW * 32)
     __syncwarp();
     if (!failed) {
       if (BWD && lane == 0) {
-        if (lu32 && !ptag[i] && ni <= 32) {
+        if (lu32 && ni <= 8 && !ptag[i]) {  // the pivot block staged on chip before the waits
+          const float* slu = tri_piv_buf<T>(tri_sm);
+          pivot_solve_f32(slu, reinterpret_cast<const int32_t*>(slu + 64), ni, sv);
+        } else if (lu32 && !ptag[i] && ni <= 32) {
           pivot_solve_f32(lu32 + dgoff[i], piv + r0, ni, sv);
         } else if (lu32 && !ptag[i]) {
           pivot_forward<float>(lu32 + dgoff[i], piv + r0, ni, sv);
