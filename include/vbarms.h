@@ -296,8 +296,8 @@ vb_status vbarms_apply_batched(int nmat, const vbarms_prec* M, const double* con
  * double[n] on the handle's device, original numbering, no aliasing; the
  * call synchronizes the handle's stream before returning.  The first call on
  * a device does a set-up: it looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the same array and it keeps
+ * (cudaGetSymbolAddress) with that device current.  Every call shares the
+ * same array and it keeps
  * the previous call's contents (the call clears what must start at zero):
  * calls that overlap on the GPU -- from several host threads, or on several
  * streams -- race and must be serialized by the caller.  Handles of a
