@@ -556,8 +556,9 @@ def main():
     roof["ilut"] = {"bound": "latency (dependency chain)", "kernel": "k_ilut", "ms": ilut_s * 1e3,
                     "chain_links": chain, "us_per_link": ilut_s * 1e6 / chain if chain else None,
                     "note": "rows on the longest chain of waits (every pending L column, dropped multipliers "
-                            "included); the kernel time is this chain times the latency from a dependency's "
-                            "publication to the row's own"}
+                            "included) and the kernel time per row of that chain; the time-critical path is "
+                            "longer (rows also wait for a free warp, and chains join), so the latency of one "
+                            "link, from a dependency's publication to the row's own, is below this figure"}
 
     # FP32 vs FP64: the plain FP64 GPU factor on the same GB300
     fp64 = None
